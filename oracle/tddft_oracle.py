@@ -1,0 +1,449 @@
+"""FP64 CPU oracle for the TDA Liouville operator of hybrid LR-TDDFT.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the bench's
+CPU-baseline leg may import this module. It shares no code with the CUDA
+library and never imports it.
+
+What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
+
+* the Tamm-Dancoff eigen-operator L = D + K1e - K1d applied to a batch of
+  trial vectors A (Eq. 8), with D from Eq. 3 (H^KS contains the hybrid
+  exact exchange alpha*V_X of the exchange-operator equation in Sec. 3.1),
+  K1e from Eq. 4 and K1d from Eq. 6, and the projector P^c = 1 - sum |phi><phi|
+  stated after Eq. 7;
+* the spin-flip operator of Eq. 21 (D^SF, K1e^SF with the local f_xc^SF and no
+  Hartree part, K1d^SF over source-spin pairs; Sec. 2.3);
+* the bilinear form omega = <X|L X> (the excitation energy of Sec. 2.2) and
+  its gradient with respect to the occupied orbitals and the local potential
+  (the u_v ingredient of the Z-vector equation, Eq. 16, Supporting Information
+  Sec. S1), with X, eps, f_xc and the Coulomb kernels held fixed;
+* a dense matrix of L on tiny systems and a plain block-Davidson solver
+  (Sec. 4 names Davidson's method for diagonalising L).
+
+Discretisation (the paper works in plane waves at the Gamma point, Sec. 2):
+cubic cell of side a, Omega = a^3, grid N^3 (N_r points), r_j = a j / N,
+G_m = (2 pi / a) m, m_i in [-N/2, N/2). Wavefunction sphere
+S = {m : (1/2)|G_m|^2 < E_cut}, ordered by (|m|^2, m_x, m_y, m_z).
+phi(r_j) = Omega^{-1/2} sum_{G in S} c(G) exp(i G.r_j).
+Forward DFT F[f](m) = sum_j f(r_j) exp(-2 pi i m.j/N); inverse
+F^{-1}[g](j) = sum_m g(m) exp(+2 pi i m.j/N).  Real space -> plane waves:
+c(G) = Omega^{1/2} N_r^{-1} F[f](G), G in S (truncation).
+Periodic convolution with a kernel kappa(G):
+Conv_kappa[rho] = F^{-1}[kappa * N_r^{-1} F[rho]].
+Exchange kernel kappa_x(G) = 4 pi/|G|^2, kappa_x(0) = 2 pi R_c^2; Hartree kernel
+kappa_H(G) = 4 pi/|G|^2, kappa_H(0) = 0.  Integrals are grid sums with
+weight Omega / N_r.
+
+The DFTs are numpy/scipy FFTs, used as the library primitive for the plain
+DFT definition above (tests pin them against explicit DFT sums).
+
+Arrays: plane-wave coefficients [..., npw] complex128; real-space fields
+[..., N, N, N] indexed [j_z, j_y, j_x].
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import scipy.fft as sfft
+
+# Term bits of the operator (same meaning as the library's term mask).
+D_KIN = 1     # (1/2|G|^2 - eps_v) a_v                     (Eq. 3, kinetic part of H^KS)
+D_VLOC = 2    # V_loc(r) a_v(r)                            (Eq. 3, local part of H^KS)
+D_EXX = 4     # +alpha V_X a_v                             (Eq. 3 with the exchange operator of Sec. 3.1)
+K1E_H = 8     # phi_v Conv_H[Delta rho]                    (Eq. 4, Coulomb part of f_Hxc)
+K1E_XC = 16   # phi_v f_xc Delta rho                       (Eq. 4, local xc kernel)
+K1D = 32      # -alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]  (Eq. 6)
+PROJ = 64     # P^c = 1 - sum_u |phi_u><phi_u|             (after Eq. 7)
+ALL_TERMS = 127
+
+_WORKERS = int(os.environ.get("ORACLE_FFT_WORKERS", os.cpu_count() or 1))
+
+
+def fft_workers() -> int:
+    """Threads the oracle's FFT primitive uses."""
+    return _WORKERS
+
+
+# --------------------------------------------------------------------------
+# Grid, sphere, transforms
+# --------------------------------------------------------------------------
+
+def miller_sphere(n: int, a: float, ecut: float) -> np.ndarray:
+    """Miller indices [npw, 3] (m_x, m_y, m_z) of S = {m : (1/2)|G_m|^2 < ecut}.
+
+    |G|^2 is evaluated as tpiba2 * |m|^2 with tpiba2 = (2 pi / a)^2 in FP64.
+    Ordered by (|m|^2, m_x, m_y, m_z) ascending. Raises if S reaches the edge
+    of the grid (|m_i| >= N/2), where the sphere would not be symmetric.
+    """
+    h = n // 2
+    r = np.arange(-h, n - h)
+    mz, my, mx = np.meshgrid(r, r, r, indexing="ij")
+    m2 = mx * mx + my * my + mz * mz
+    tpiba = 2.0 * np.pi / a
+    tpiba2 = tpiba * tpiba
+    g2 = tpiba2 * m2.astype(np.float64)
+    sel = 0.5 * g2 < ecut
+    pts = np.stack([mx[sel], my[sel], mz[sel]], axis=1)
+    if np.any(np.abs(pts) >= h):
+        raise ValueError("wavefunction sphere does not fit inside the FFT grid")
+    order = np.lexsort((pts[:, 2], pts[:, 1], pts[:, 0], m2[sel]))
+    return pts[order].astype(np.int64)
+
+
+def grid_miller(n: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Miller components of every FFT-cube position, arrays [N, N, N] indexed [k_z, k_y, k_x]."""
+    k = np.arange(n)
+    m = np.where(k < n - n // 2, k, k - n)  # k -> m in [-N/2, N/2) for even N
+    mz, my, mx = np.meshgrid(m, m, m, indexing="ij")
+    return mx, my, mz
+
+
+class Grid:
+    """Cell, FFT grid and sphere of one system."""
+
+    def __init__(self, n: int, a: float, ecut: float):
+        self.n = n
+        self.a = float(a)
+        self.ecut = float(ecut)
+        self.omega = self.a ** 3
+        self.nr = n ** 3
+        self.miller = miller_sphere(n, a, ecut)
+        self.npw = self.miller.shape[0]
+        m = self.miller % n
+        self.idx = (m[:, 2], m[:, 1], m[:, 0])  # cube position [k_z, k_y, k_x] of each sphere point
+        tpiba = 2.0 * np.pi / self.a
+        self.g2_sphere = (tpiba * tpiba) * np.sum(self.miller.astype(np.float64) ** 2, axis=1)
+        mx, my, mz = grid_miller(n)
+        self.g2_cube = (tpiba * tpiba) * (mx * mx + my * my + mz * mz).astype(np.float64)
+
+    # -- DFT primitives (definitions in the module docstring) --
+    def fwd(self, f: np.ndarray) -> np.ndarray:
+        return sfft.fftn(f, axes=(-3, -2, -1), workers=_WORKERS)
+
+    def inv(self, g: np.ndarray) -> np.ndarray:
+        return sfft.ifftn(g, axes=(-3, -2, -1), workers=_WORKERS) * self.nr
+
+    def pw_to_real(self, c: np.ndarray) -> np.ndarray:
+        """phi(r_j) = Omega^{-1/2} sum_{G in S} c(G) exp(i G.r_j)."""
+        c = np.asarray(c)
+        cube = np.zeros(c.shape[:-1] + (self.n,) * 3, dtype=np.complex128)
+        cube[(Ellipsis,) + self.idx] = c
+        return self.inv(cube) / np.sqrt(self.omega)
+
+    def real_to_pw(self, f: np.ndarray) -> np.ndarray:
+        """c(G) = Omega^{1/2} N_r^{-1} F[f](G) for G in S."""
+        g = self.fwd(f)
+        return g[(Ellipsis,) + self.idx] * (np.sqrt(self.omega) / self.nr)
+
+    def coulomb(self, g0: float) -> np.ndarray:
+        """kappa(G) = 4 pi / |G|^2 on the FFT cube, kappa(0) = g0."""
+        g2 = self.g2_cube.copy()
+        g2[0, 0, 0] = 1.0
+        k = 4.0 * np.pi / g2
+        k[0, 0, 0] = g0
+        return k
+
+    def conv(self, rho: np.ndarray, kappa: np.ndarray) -> np.ndarray:
+        """Conv_kappa[rho] = F^{-1}[kappa N_r^{-1} F[rho]] (periodic convolution)."""
+        return self.inv(kappa * self.fwd(rho) / self.nr)
+
+    def inner(self, f: np.ndarray, g: np.ndarray) -> complex:
+        """Real-space integral of conj(f) g with weight Omega / N_r."""
+        return np.vdot(f, g) * (self.omega / self.nr)
+
+
+# --------------------------------------------------------------------------
+# The system and the operator
+# --------------------------------------------------------------------------
+
+class System:
+    """Inputs of one spin-conserving (SC) or spin-flip (SF, source up -> target down) system.
+
+    phi_src: orbitals phi_v of the source spin, [nocc_src, npw]; they form the
+             pair densities of K1e / K1d and index the trial orbitals a_v.
+    phi_tgt: occupied orbitals of the target spin, [nocc_tgt, npw]; they enter
+             the projector P^c and the exchange operator V_X inside D.
+             For SC the two are the same set.
+    eps_src: eps_v of the source spin (Eq. 3; D^SF uses eps_{v, source}).
+    vloc:    local potential of the target spin on the grid (or None = 0).
+    fxc:     local xc kernel f_xc(r) (SC) or f_xc^SF(r) (SF) (or None = 0).
+    """
+
+    def __init__(self, n, a, ecut, phi_src, eps_src, *, alpha=0.18, kx_g0=0.0,
+                 spin_flip=False, phi_tgt=None, vloc=None, fxc=None,
+                 kernel_x=None, kernel_h=None):
+        self.grid = Grid(n, a, ecut)
+        self.alpha = float(alpha)
+        self.spin_flip = bool(spin_flip)
+        self.phi_src = np.asarray(phi_src, dtype=np.complex128)
+        self.phi_tgt = self.phi_src if phi_tgt is None else np.asarray(phi_tgt, dtype=np.complex128)
+        if self.spin_flip and phi_tgt is None:
+            raise ValueError("spin-flip needs the target-spin orbitals")
+        self.eps_src = np.asarray(eps_src, dtype=np.float64)
+        self.vloc = None if vloc is None else np.asarray(vloc, dtype=np.float64)
+        self.fxc = None if fxc is None else np.asarray(fxc, dtype=np.float64)
+        self.kx = self.grid.coulomb(kx_g0) if kernel_x is None else np.asarray(kernel_x, dtype=np.float64)
+        self.kh = self.grid.coulomb(0.0) if kernel_h is None else np.asarray(kernel_h, dtype=np.float64)
+        if self.phi_src.shape[1] != self.grid.npw or self.phi_tgt.shape[1] != self.grid.npw:
+            raise ValueError("orbital arrays do not match the sphere size")
+        self._phi_src_r = None
+        self._phi_tgt_r = None
+
+    @property
+    def nocc_src(self):
+        return self.phi_src.shape[0]
+
+    @property
+    def nocc_tgt(self):
+        return self.phi_tgt.shape[0]
+
+    def phi_src_r(self):
+        if self._phi_src_r is None:
+            self._phi_src_r = self.grid.pw_to_real(self.phi_src)
+        return self._phi_src_r
+
+    def phi_tgt_r(self):
+        if not self.spin_flip and self.phi_tgt is self.phi_src:
+            return self.phi_src_r()
+        if self._phi_tgt_r is None:
+            self._phi_tgt_r = self.grid.pw_to_real(self.phi_tgt)
+        return self._phi_tgt_r
+
+    def project(self, Y: np.ndarray) -> np.ndarray:
+        """P^c Y = Y - Phi_tgt (Phi_tgt^dagger Y) on the last axis (plane waves)."""
+        P = self.phi_tgt
+        return Y - np.einsum("ug,...u->...g", P, np.einsum("ug,...g->...u", P.conj(), Y))
+
+    # -- pieces of the operator --
+    def delta_rho(self, a_r: np.ndarray) -> np.ndarray:
+        """Delta rho(r) = sum_v phi_v^*(r) a_v(r) (Eq. 2 diagonal; Sec. 2.3 for SF)."""
+        return np.einsum("vzyx,vzyx->zyx", self.phi_src_r().conj(), a_r)
+
+    def k1e_potential(self, drho: np.ndarray, terms: int) -> np.ndarray:
+        """W = Conv_H[Delta rho] + f_xc Delta rho (Eq. 4); SF: f_xc^SF Delta rho only (Sec. 2.3)."""
+        W = np.zeros_like(drho)
+        if (terms & K1E_H) and not self.spin_flip:
+            W += self.grid.conv(drho, self.kh)
+        if (terms & K1E_XC) and self.fxc is not None:
+            W += self.fxc * drho
+        return W
+
+    def unprojected_row(self, a_r, Xb, W, v, terms, tau_row=None) -> np.ndarray:
+        """The bracket of row v before P^c, in plane waves:
+        (1/2|G|^2 - eps_v) a_v + [V_loc a_v + alpha V_X a_v + phi_v W
+        - alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]] -> PW.
+        """
+        g = self.grid
+        out_r = np.zeros(a_r.shape[1:], dtype=np.complex128)
+        if (terms & D_VLOC) and self.vloc is not None:
+            out_r += self.vloc * a_r[v]
+        if terms & D_EXX:
+            # alpha V_X a_v = -alpha sum_w phi_w Conv_x[phi_w^* a_v]   (Sec. 3.1, exchange operator)
+            phit = self.phi_tgt_r()
+            for w in range(self.nocc_tgt):
+                out_r -= self.alpha * phit[w] * g.conv(phit[w].conj() * a_r[v], self.kx)
+        if terms & (K1E_H | K1E_XC):
+            out_r += self.phi_src_r()[v] * W
+        if terms & K1D:
+            phis = self.phi_src_r()
+            for vp in range(self.nocc_src):
+                tau = g.conv(phis[vp].conj() * phis[v], self.kx)  # tau_{v v'} (Sec. 3.2)
+                out_r -= self.alpha * a_r[vp] * tau
+        out = g.real_to_pw(out_r)
+        if terms & D_KIN:
+            out += (0.5 * g.g2_sphere - self.eps_src[v]) * Xb[v]
+        return out
+
+    def apply(self, X: np.ndarray, terms: int = ALL_TERMS, rows=None) -> np.ndarray:
+        """L X for X [nb, nocc_src, npw] (Eq. 8 / Eq. 21).
+
+        rows: optional list of (b, v) pairs; then only those rows are
+        computed and returned as [len(rows), npw] (K1e still uses all v).
+        """
+        X = np.asarray(X, dtype=np.complex128)
+        nb = X.shape[0]
+        want = [(b, v) for b in range(nb) for v in range(self.nocc_src)] if rows is None else list(rows)
+        by_b = {}
+        for i, (b, v) in enumerate(want):
+            by_b.setdefault(b, []).append((i, v))
+        out = np.zeros((len(want), self.grid.npw), dtype=np.complex128)
+        for b, items in by_b.items():
+            a_r = self.grid.pw_to_real(X[b])
+            W = self.k1e_potential(self.delta_rho(a_r), terms) if terms & (K1E_H | K1E_XC) else None
+            for i, v in items:
+                row = self.unprojected_row(a_r, X[b], W, v, terms)
+                out[i] = self.project(row) if terms & PROJ else row
+        if rows is None:
+            return out.reshape(nb, self.nocc_src, self.grid.npw)
+        return out
+
+    # -- bilinear form and gradient (spin-conserving) --
+    def omega(self, X: np.ndarray) -> np.ndarray:
+        """omega_b = <P^c X_b | M | P^c X_b>, M = the bracket of L without P^c.
+
+        For X orthogonal to the occupied orbitals this is <X_b | L X_b>
+        (Eq. 8); written this way it stays real when the orbitals move, which
+        is what the gradient and the finite-difference checks differentiate.
+        """
+        P = self.project(np.asarray(X, dtype=np.complex128))
+        Y = self.apply(P, ALL_TERMS & ~PROJ)
+        return np.einsum("bvg,bvg->b", P.conj(), Y).real
+
+    def omega_grad(self, X: np.ndarray, w: np.ndarray):
+        """omega_b and the gradients of sum_b w_b omega_b (spin-conserving only).
+
+        Returns (omega [nb], grad_phi [nocc, npw], grad_vloc [N,N,N]).
+        grad_phi is the Wirtinger derivative d/d c_u^*(G) with X, eps,
+        V_loc, f_xc and the kernels fixed and P^c taken on the given orbitals.
+        In real space (grid integrals, weight Omega/N_r) it is, per b:
+          -alpha sum_v p_v Conv_x[p_v^* phi_u]        (from alpha V_X in D)
+          + p_u conj(W)                                (from K1e, W as in Eq. 4)
+          -alpha sum_v phi_v Conv_x[p_v^* p_u]         (from K1d)
+        mapped to plane waves, plus the plane-wave terms of the projector
+          -sum_v [<x_v|phi_u> y_v + <y_v|phi_u> x_v],  y = M p, p = P^c x.
+        These are the counterparts of terms 2, 4, 7 and 5, 8 of u_v in the
+        Supporting Information (Sec. S1), without the terms that come from
+        H^KS, eps and V_xc depending on the ground-state density, which are
+        inputs here.  grad_vloc(r_j) = (Omega/N_r) sum_b w_b sum_v |p_{b,v}(r_j)|^2.
+        """
+        if self.spin_flip:
+            raise NotImplementedError("the spin-flip gradient is not part of this oracle")
+        g = self.grid
+        X = np.asarray(X, dtype=np.complex128)
+        w = np.asarray(w, dtype=np.float64)
+        nb = X.shape[0]
+        Pm = self.project(X)
+        Y = self.apply(Pm, ALL_TERMS & ~PROJ)
+        omega = np.einsum("bvg,bvg->b", Pm.conj(), Y).real
+        phi_r = self.phi_src_r()
+        nocc = self.nocc_src
+        grad_r = np.zeros((nocc,) + (g.n,) * 3, dtype=np.complex128)
+        grad_v = np.zeros((g.n,) * 3)
+        for b in range(nb):
+            if w[b] == 0.0:
+                continue
+            p_r = g.pw_to_real(Pm[b])
+            W = self.k1e_potential(self.delta_rho(p_r), ALL_TERMS)
+            for u in range(nocc):
+                acc = np.zeros((g.n,) * 3, dtype=np.complex128)
+                for v in range(nocc):
+                    acc -= self.alpha * p_r[v] * g.conv(p_r[v].conj() * phi_r[u], self.kx)
+                    acc -= self.alpha * phi_r[v] * g.conv(p_r[v].conj() * p_r[u], self.kx)
+                acc += p_r[u] * W.conj()
+                grad_r[u] += w[b] * acc
+            grad_v += w[b] * (g.omega / g.nr) * np.sum(np.abs(p_r) ** 2, axis=0)
+        grad = g.real_to_pw(grad_r)
+        phi = self.phi_src
+        for b in range(nb):
+            if w[b] == 0.0:
+                continue
+            xs = np.einsum("vg,ug->vu", X[b].conj(), phi)  # <x_v|phi_u>
+            ys = np.einsum("vg,ug->vu", Y[b].conj(), phi)  # <y_v|phi_u>
+            grad -= w[b] * (np.einsum("vu,vg->ug", xs, Y[b]) + np.einsum("vu,vg->ug", ys, X[b]))
+        return omega, grad, grad_v
+
+    # -- dense operator on tiny systems --
+    def complement_basis(self) -> np.ndarray:
+        """Orthonormal basis [npw, npw - nocc_tgt] of the plane-wave space orthogonal to phi_tgt."""
+        npw = self.grid.npw
+        q, _ = np.linalg.qr(np.concatenate([self.phi_tgt.T, np.eye(npw)], axis=1))
+        return q[:, self.nocc_tgt:npw]
+
+    def dense_matrix(self, terms: int = ALL_TERMS) -> tuple[np.ndarray, np.ndarray]:
+        """Matrix of L on the unoccupied space: H[(v,k),(v',k')] = <q_k e_v | L | q_k' e_v'>.
+
+        Returns (H, Qc) with Qc the complement basis. Only for tiny systems.
+        """
+        Qc = self.complement_basis()
+        nc = Qc.shape[1]
+        nocc = self.nocc_src
+        dim = nocc * nc
+        H = np.zeros((dim, dim), dtype=np.complex128)
+        cols = []
+        for vp in range(nocc):
+            for k in range(nc):
+                x = np.zeros((nocc, self.grid.npw), dtype=np.complex128)
+                x[vp] = Qc[:, k]
+                cols.append(x)
+        for j0 in range(0, dim, 64):
+            batch = np.stack(cols[j0:j0 + 64])
+            LX = self.apply(batch, terms)
+            coeff = np.einsum("gk,bvg->bvk", Qc.conj(), LX)
+            H[:, j0:j0 + batch.shape[0]] = coeff.reshape(batch.shape[0], dim).T
+        return H, Qc
+
+
+# --------------------------------------------------------------------------
+# Davidson (the paper only names the method; this follows Davidson's block scheme)
+# --------------------------------------------------------------------------
+
+def davidson(sys: System, X0: np.ndarray, nroots: int, tol: float = 1e-8, max_iter: int = 60,
+             max_basis: int | None = None):
+    """Lowest eigenpairs of L by block Davidson in FP64.
+
+    Basis vectors live in the unoccupied space (P^c applied twice), are
+    orthonormalised by two passes of Gram-Schmidt, and the correction for
+    root i is r_i / (1/2|G|^2 - eps_v - theta_i) with the denominator's
+    modulus clamped to >= 0.1 Ha. The Rayleigh-Ritz step diagonalises
+    V^dagger L V with numpy's Hermitian eigensolver. Restart keeps the
+    current Ritz vectors once the basis would exceed max_basis.
+    Returns (theta [nroots], vectors [nroots, nocc, npw], iterations).
+    """
+    g = sys.grid
+    nocc = sys.nocc_src
+    max_basis = max_basis or 8 * nroots
+    shape = (nocc, g.npw)
+
+    def orth_add(V, cands):
+        for c in cands:
+            c = sys.project(sys.project(c))
+            for _ in range(2):
+                for v in V:
+                    c = c - np.vdot(v, c) * v
+            nrm = np.sqrt(np.vdot(c, c).real)
+            if nrm > 1e-10:
+                V.append(c / nrm)
+        return V
+
+    V = orth_add([], [x.reshape(shape) for x in X0])
+    if len(V) < nroots:
+        raise ValueError("the initial guess spans fewer vectors than the requested roots")
+    LV = [sys.apply(v[None])[0] for v in V]
+    denom_base = 0.5 * g.g2_sphere[None, :] - sys.eps_src[:, None]
+    theta = None
+    for it in range(1, max_iter + 1):
+        m = len(V)
+        Vm = np.stack(V).reshape(m, -1)
+        LVm = np.stack(LV).reshape(m, -1)
+        Hs = Vm.conj() @ LVm.T
+        Hs = 0.5 * (Hs + Hs.conj().T)
+        ev, S = np.linalg.eigh(Hs)
+        theta = ev[:nroots]
+        Sx = S[:, :nroots]
+        Xr = (Sx.T @ Vm).reshape(nroots, *shape)
+        R = (Sx.T @ LVm).reshape(nroots, *shape) - theta[:, None, None] * Xr
+        rn = np.sqrt(np.sum(np.abs(R) ** 2, axis=(1, 2)))
+        if np.all(rn < tol):
+            return theta, Xr, it
+        cands = []
+        for i in range(nroots):
+            if rn[i] < tol:
+                continue
+            d = denom_base - theta[i]
+            d = np.where(np.abs(d) < 0.1, np.where(d < 0, -0.1, 0.1), d)
+            cands.append(R[i] / d)
+        if m + len(cands) > max_basis:
+            V = orth_add([], list(Xr))
+            LV = [sys.apply(v[None])[0] for v in V]
+        nV = len(V)
+        V = orth_add(V, cands)
+        LV += [sys.apply(v[None])[0] for v in V[nV:]]
+    return theta, Xr, max_iter
+
+
+def system_from_workload(wl, **kw) -> System:
+    """Build the oracle's System from a synthetic Workload."""
+    return System(wl.n, wl.a, wl.ecut, wl.phi_src, wl.eps_src, alpha=wl.alpha, kx_g0=wl.kx_g0,
+                  spin_flip=wl.spin_flip, phi_tgt=wl.phi_tgt if wl.spin_flip else None,
+                  vloc=wl.vloc, fxc=wl.fxc, **kw)

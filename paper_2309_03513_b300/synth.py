@@ -1,0 +1,158 @@
+"""Seeded synthetic inputs for the TDA Liouville operator.
+
+This module only draws random numbers and builds valid input arrays. It
+contains none of the operator's arithmetic, and it is the one module that both
+the CUDA path (through the bindings) and the FP64 oracle are fed from.
+
+Recipe (stand-ins for ground states of diamond / 4H-SiC supercells, which are
+not available here):
+
+* Orbitals: complex normal coefficients on the wavefunction sphere, made
+  orthonormal with a Householder QR (phases as returned by LAPACK).
+* Eigenvalues: uniform in [-0.5, 0] Ha, sorted ascending.
+* Trial vectors: for each batch entry b, the complex normal draws are made
+  orthogonal to the occupied orbitals of the target spin with a QR of
+  [phi_tgt | draws], the orthonormal complement block is mixed with a
+  complex normal matrix, and the batch entry is normalised so that
+  sum_v ||a_{b,v}||^2 = 1.
+* Smooth real fields (local potential, xc kernels): the real part of a sum of
+  plane waves exp(2 pi i m.j/N) with |m|^2 <= 4 and complex normal weights,
+  scaled to a stated maximum modulus.
+
+Array conventions shared by both sides:
+* plane-wave coefficient arrays are [..., npw] complex128 in the order of the
+  sphere (|m|^2, m_x, m_y, m_z ascending) that each side builds for itself;
+* real-space arrays are [N, N, N] indexed [j_z, j_y, j_x] (x fastest).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Workload:
+    """One synthetic system: sizes plus seeded input arrays (FP64 / complex128)."""
+
+    n: int
+    a: float
+    ecut: float
+    alpha: float
+    spin_flip: bool
+    nocc_src: int
+    nocc_tgt: int
+    nb: int
+    seed: int
+    kx_g0: float
+    phi_src: np.ndarray  # [nocc_src, npw]
+    phi_tgt: np.ndarray  # [nocc_tgt, npw] (same object as phi_src when not spin-flip)
+    eps_src: np.ndarray  # [nocc_src]
+    vloc: np.ndarray | None  # [N, N, N] real, target spin
+    fxc: np.ndarray | None  # [N, N, N] real (f_xc, or f_xc^SF for spin-flip)
+    X: np.ndarray  # [nb, nocc_src, npw]
+
+    @property
+    def npw(self) -> int:
+        return self.phi_src.shape[1]
+
+
+def random_orthonormal_rows(rng: np.random.Generator, nrows: int, ncols: int) -> np.ndarray:
+    """nrows orthonormal complex row vectors of length ncols (QR of normal draws)."""
+    if nrows > ncols:
+        raise ValueError("more orthonormal rows than columns requested")
+    z = rng.standard_normal((ncols, nrows)) + 1j * rng.standard_normal((ncols, nrows))
+    q, _ = np.linalg.qr(z)
+    return np.ascontiguousarray(q.T)
+
+
+def smooth_field(rng: np.random.Generator, n: int, max_abs: float, m2max: int = 4) -> np.ndarray:
+    """Real smooth field on the N^3 grid, indexed [j_z, j_y, j_x], max |f| = max_abs."""
+    j = np.arange(n)
+    f = np.zeros((n, n, n))
+    r = int(np.floor(np.sqrt(m2max)))
+    for mx in range(-r, r + 1):
+        for my in range(-r, r + 1):
+            for mz in range(-r, r + 1):
+                if mx * mx + my * my + mz * mz > m2max:
+                    continue
+                c = rng.standard_normal() + 1j * rng.standard_normal()
+                ex = np.exp(2j * np.pi * mx * j / n)
+                ey = np.exp(2j * np.pi * my * j / n)
+                ez = np.exp(2j * np.pi * mz * j / n)
+                f += (c * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).real
+    return f * (max_abs / np.abs(f).max())
+
+
+def trial_vectors(rng: np.random.Generator, phi_tgt: np.ndarray, nb: int, nocc_src: int) -> np.ndarray:
+    """nb batch entries of nocc_src coefficient vectors, each orthogonal to every row of phi_tgt."""
+    nocc_tgt, npw = phi_tgt.shape
+    if nocc_tgt + nocc_src > npw:
+        raise ValueError("sphere too small for the requested trial vectors")
+    X = np.empty((nb, nocc_src, npw), dtype=np.complex128)
+    for b in range(nb):
+        draws = rng.standard_normal((npw, nocc_src)) + 1j * rng.standard_normal((npw, nocc_src))
+        q, _ = np.linalg.qr(np.concatenate([phi_tgt.T, draws], axis=1))
+        comp = q[:, nocc_tgt:]  # orthonormal columns orthogonal to span(phi_tgt)
+        mix = rng.standard_normal((nocc_src, nocc_src)) + 1j * rng.standard_normal((nocc_src, nocc_src))
+        xb = (comp @ mix).T
+        X[b] = xb / np.sqrt(np.sum(np.abs(xb) ** 2))
+    return X
+
+
+def make_workload(
+    *,
+    n: int,
+    a: float,
+    ecut: float,
+    npw: int,
+    nocc_src: int,
+    nb: int,
+    seed: int,
+    alpha: float = 0.18,
+    spin_flip: bool = False,
+    nocc_tgt: int | None = None,
+    rc: float = 5.0,
+    with_vloc: bool = True,
+    with_fxc: bool = True,
+) -> Workload:
+    """Draw one synthetic system.
+
+    npw is the size of the wavefunction sphere for (n, a, ecut); the caller
+    obtains it from the side it is testing and both sides must agree.
+    Seeds: orbitals and eigenvalues from `seed`, V_loc from seed + 1000,
+    f_xc from seed + 2000 (f_xc^SF from seed + 3000), trial vectors from
+    seed + 4000.
+    """
+    rng = np.random.default_rng(seed)
+    if spin_flip:
+        if nocc_tgt is None:
+            raise ValueError("spin-flip needs nocc_tgt")
+        phi_src = random_orthonormal_rows(rng, nocc_src, npw)
+        phi_tgt = random_orthonormal_rows(rng, nocc_tgt, npw)
+    else:
+        nocc_tgt = nocc_src
+        phi_src = random_orthonormal_rows(rng, nocc_src, npw)
+        phi_tgt = phi_src
+    eps = np.sort(rng.uniform(-0.5, 0.0, size=nocc_src))
+    vloc = smooth_field(np.random.default_rng(seed + 1000), n, 0.1) if with_vloc else None
+    fxc = None
+    if with_fxc:
+        s = smooth_field(np.random.default_rng(seed + (3000 if spin_flip else 2000)), n, 1.0)
+        fxc = -0.3 * (1.0 + 0.5 * s)
+    X = trial_vectors(np.random.default_rng(seed + 4000), phi_tgt, nb, nocc_src)
+    return Workload(
+        n=n, a=a, ecut=ecut, alpha=alpha, spin_flip=spin_flip, nocc_src=nocc_src,
+        nocc_tgt=nocc_tgt, nb=nb, seed=seed, kx_g0=2.0 * np.pi * rc * rc,
+        phi_src=phi_src, phi_tgt=phi_tgt, eps_src=eps, vloc=vloc, fxc=fxc, X=X,
+    )
+
+
+# Named workloads: (n, a, ecut, nocc_src, nocc_tgt, nb, spin_flip).
+# 'tiny' is the 24^3 plain FP64 spin-conserving case; 'diamond64' the 64-atom
+# diamond-like cell at 25 Ha; 'sf216' the 216-atom spin-flip cell.
+WORKLOADS = {
+    "tiny": dict(n=24, a=10.0, ecut=10.0, nocc_src=8, nocc_tgt=8, nb=4, spin_flip=False, seed=0),
+    "diamond64": dict(n=72, a=13.48, ecut=25.0, nocc_src=128, nocc_tgt=128, nb=8, spin_flip=False, seed=0),
+    "sf216": dict(n=108, a=20.2, ecut=25.0, nocc_src=433, nocc_tgt=431, nb=16, spin_flip=True, seed=0),
+}

@@ -1,0 +1,363 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test fixes a part of the oracle to a closed form, a brute-force sum, an
+invariant of the operator or a library routine, so that a dropped term, a
+wrong sign, a missing conjugate or a transposed operand fails one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tddft_oracle as O
+from paper_2309_03513_b300 import synth
+
+
+# --------------------------------------------------------------------------
+# sphere and DFT mechanics
+# --------------------------------------------------------------------------
+
+def _count_ball(n, a, ecut):
+    """Lattice points with (1/2)(2 pi/a)^2 |m|^2 < ecut, counted column by column."""
+    r2 = 2.0 * ecut / (2.0 * math.pi / a) ** 2
+    h = n // 2
+    cnt = 0
+    for mx in range(-h, h):
+        for my in range(-h, h):
+            rest = r2 - mx * mx - my * my
+            if rest <= 0:
+                continue
+            k = math.isqrt(int(math.floor(rest)))
+            while k * k >= rest:
+                k -= 1
+            while (k + 1) * (k + 1) < rest:
+                k += 1
+            cnt += 2 * k + 1
+    return cnt
+
+
+@pytest.mark.parametrize("n,a,ecut,npw", [(24, 10.0, 10.0, 1503), (72, 13.48, 25.0, 14771),
+                                          (108, 20.2, 25.0, 49173)])
+def test_sphere_size(n, a, ecut, npw):
+    g = O.Grid(n, a, ecut)
+    assert g.npw == npw
+    assert _count_ball(n, a, ecut) == npw
+    m = g.miller
+    # ordering (|m|^2, mx, my, mz) and uniqueness
+    keys = [(int(x * x + y * y + z * z), int(x), int(y), int(z)) for x, y, z in m]
+    assert keys == sorted(keys)
+    assert len(set(keys)) == npw
+    # symmetric under m -> -m (Gamma point)
+    assert {tuple(v) for v in m} == {tuple(-v) for v in m}
+
+
+def test_dft_against_explicit_sums():
+    n = 6
+    g = O.Grid(n, 5.0, 2.0)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal((n,) * 3) + 1j * rng.standard_normal((n,) * 3)
+    j = np.array(list(itertools.product(range(n), repeat=3)))  # (jz, jy, jx)
+    mm = j.copy()
+    mm[mm >= n // 2] -= n
+    phase = np.exp(-2j * np.pi * (mm @ j.T) / n)  # [m, j]
+    F = phase @ f.reshape(-1)
+    assert np.allclose(g.fwd(f).reshape(-1), F, rtol=0, atol=1e-11)
+    Finv = phase.conj() @ f.reshape(-1)
+    assert np.allclose(g.inv(f).reshape(-1), Finv, rtol=0, atol=1e-11)
+
+
+def test_pw_to_real_is_the_plane_wave_sum():
+    n, a = 8, 7.0
+    g = O.Grid(n, a, 3.0)
+    rng = np.random.default_rng(2)
+    c = rng.standard_normal(g.npw) + 1j * rng.standard_normal(g.npw)
+    f = g.pw_to_real(c)
+    jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([jx, jy, jz], axis=-1) * (a / n)  # r_j = a j / N
+    G = g.miller * (2 * np.pi / a)
+    direct = np.einsum("g,zyxg->zyx", c, np.exp(1j * np.einsum("zyxk,gk->zyxg", r, G))) / math.sqrt(a ** 3)
+    assert np.allclose(f, direct, rtol=0, atol=1e-12)
+    assert np.allclose(g.real_to_pw(f), c, rtol=0, atol=1e-12)
+    # <f|f> over the grid equals sum |c|^2 (Parseval with weight Omega/N_r)
+    assert abs(g.inner(f, f).real - np.sum(np.abs(c) ** 2)) < 1e-10
+
+
+def test_convolution_against_brute_force_gaussian_images():
+    """Gaussian kernel kappa(G) = (pi/mu)^{3/2} exp(-G^2/4mu) is the Fourier
+    transform of exp(-mu r^2); Conv must equal the image sum over the lattice."""
+    n, a = 8, 6.0
+    g = O.Grid(n, a, 1.0)
+    mu = math.pi ** 2 * n * n / (144.0 * a * a)
+    kappa = (math.pi / mu) ** 1.5 * np.exp(-g.g2_cube / (4 * mu))
+    rng = np.random.default_rng(3)
+    rho = rng.standard_normal((n,) * 3) + 1j * rng.standard_normal((n,) * 3)
+    got = g.conv(rho, kappa)
+    j = np.array(list(itertools.product(range(n), repeat=3)), dtype=float)[:, ::-1]  # (jx, jy, jz)
+    r = j * (a / n)
+    K = 3
+    Rs = np.array(list(itertools.product(range(-K, K + 1), repeat=3)), dtype=float) * a
+    d = r[:, None, None, :] - r[None, :, None, :] + Rs[None, None, :, :]
+    kern = np.exp(-mu * np.sum(d * d, axis=-1)).sum(axis=2)  # [j, j']
+    want = (a ** 3 / n ** 3) * kern @ rho.reshape(-1)  # rho flattened (jz,jy,jx) = rows of j reversed
+    assert np.allclose(got.reshape(-1), want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_coulomb_energy_of_gaussian_charges():
+    """Grid Hartree energy of two periodic Gaussian charges vs the analytic
+    reciprocal-space sum (1/Omega) sum_{G!=0} 4pi/G^2 exp(-G^2(sa^2+sb^2)/2) cos(G.(Ra-Rb))."""
+    n, a = 24, 10.0
+    g = O.Grid(n, a, 5.0)
+    sa, sb = 1.1, 1.2
+    Ra = np.array([2.1, 3.3, 4.0])
+    Rb = np.array([6.5, 5.2, 7.7])
+    jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([jx, jy, jz], axis=-1) * (a / n)
+
+    def gauss(R, s):
+        out = np.zeros((n,) * 3)
+        for t in itertools.product((-1, 0, 1), repeat=3):
+            d = r - R - np.array(t) * a
+            out += np.exp(-np.sum(d * d, axis=-1) / (2 * s * s))
+        return out / (2 * math.pi * s * s) ** 1.5
+
+    ra, rb = gauss(Ra, sa), gauss(Rb, sb)
+    E_grid = g.inner(ra, g.conv(rb, g.coulomb(0.0))).real
+    M = 30
+    m = np.arange(-M, M + 1)
+    mx, my, mz = np.meshgrid(m, m, m, indexing="ij")
+    G = np.stack([mx, my, mz], axis=-1) * (2 * math.pi / a)
+    G2 = np.sum(G * G, axis=-1)
+    G2[M, M, M] = 1.0
+    terms = 4 * math.pi / G2 * np.exp(-G2 * (sa * sa + sb * sb) / 2) * np.cos(G @ (Ra - Rb))
+    terms[M, M, M] = 0.0
+    E_ana = terms.sum() / a ** 3
+    assert abs(E_grid - E_ana) < 1e-12 * max(1.0, abs(E_ana))
+    # self energy of one Gaussian against the same sum with Rb = Ra
+    E_self = g.inner(ra, g.conv(ra, g.coulomb(0.0))).real
+    t2 = 4 * math.pi / G2 * np.exp(-G2 * sa * sa)
+    t2[M, M, M] = 0.0
+    assert abs(E_self - t2.sum() / a ** 3) < 1e-12 * abs(E_self)
+
+
+# --------------------------------------------------------------------------
+# whole operator: free-electron closed form
+# --------------------------------------------------------------------------
+
+def _wrap(m, n):
+    return ((np.asarray(m) + n // 2) % n) - n // 2
+
+
+def test_free_electron_closed_form():
+    """Occupied orbitals = single plane waves. Every term of L then has a
+    closed form in plane waves (exact exchange of plane waves, shifted
+    plane-wave sums for K1e and K1d), written here without any FFT."""
+    n, a, ecut = 8, 6.0, 3.2
+    g = O.Grid(n, a, ecut)
+    npw = g.npw
+    mill = [tuple(int(t) for t in v) for v in g.miller]
+    pos = {m: i for i, m in enumerate(mill)}
+    occ = [(0, 0, 0), (1, 0, 0), (0, -1, 1)]
+    nocc = len(occ)
+    phi = np.zeros((nocc, npw), dtype=np.complex128)
+    for v, m in enumerate(occ):
+        phi[v, pos[m]] = 1.0
+    eps = np.array([-0.41, -0.23, -0.05])
+    alpha, g0, V0, cf = 0.37, 17.0, 0.13, -0.29
+    G0 = np.array([1, 1, 0])
+    jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vloc = 2 * V0 * np.cos(2 * np.pi * (G0[0] * jx + G0[1] * jy + G0[2] * jz) / n)
+    fxc = np.full((n,) * 3, cf)
+    S = O.System(n, a, ecut, phi, eps, alpha=alpha, kx_g0=g0, vloc=vloc, fxc=fxc)
+    rng = np.random.default_rng(4)
+    nb = 2
+    X = rng.standard_normal((nb, nocc, npw)) + 1j * rng.standard_normal((nb, nocc, npw))
+    for m in occ:
+        X[:, :, pos[m]] = 0.0  # orthogonal to the occupied plane waves
+    tp = 2 * math.pi / a
+    omega = a ** 3
+
+    def kap(m, g0val):
+        m = _wrap(m, n)
+        q2 = tp * tp * float(np.dot(m, m))
+        return g0val if q2 == 0 else 4 * math.pi / q2
+
+    want = np.zeros_like(X)
+    for b in range(nb):
+        for v in range(nocc):
+            out = np.zeros(npw, dtype=np.complex128)
+            Gv = np.array(occ[v])
+            for k, K in enumerate(mill):
+                K = np.array(K)
+                # kinetic and eigenvalue
+                out[k] += (0.5 * tp * tp * np.dot(K, K) - eps[v]) * X[b, v, k]
+                # local potential: shifts by +-G0
+                for s in (1, -1):
+                    t = tuple(_wrap(K + s * G0, n))
+                    if t in pos:
+                        out[pos[t]] += V0 * X[b, v, k]
+                # alpha V_X: exchange of plane waves
+                out[k] -= alpha / omega * sum(kap(K - np.array(Gw), g0) for Gw in occ) * X[b, v, k]
+                for vp in range(nocc):
+                    Gvp = np.array(occ[vp])
+                    # K1e: Hartree (kappa_H(0)=0) + constant f_xc
+                    t = tuple(_wrap(K - Gvp + Gv, n))
+                    if t in pos:
+                        out[pos[t]] += (kap(K - Gvp, 0.0) + cf) / omega * X[b, vp, k]
+                    # K1d
+                    t = tuple(_wrap(K + Gv - Gvp, n))
+                    if t in pos:
+                        out[pos[t]] -= alpha * kap(Gv - Gvp, g0) / omega * X[b, vp, k]
+            for m in occ:
+                out[pos[m]] = 0.0  # P^c removes the occupied plane waves
+            want[b, v] = out
+    got = S.apply(X)
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+# --------------------------------------------------------------------------
+# invariants on random systems
+# --------------------------------------------------------------------------
+
+def _tiny(spin_flip=False, n=12, a=7.0, ecut=4.0, nocc=4, nocc_tgt=3, nb=3, seed=5):
+    g = O.Grid(n, a, ecut)
+    wl = synth.make_workload(n=n, a=a, ecut=ecut, npw=g.npw, nocc_src=nocc, nb=nb, seed=seed,
+                             spin_flip=spin_flip, nocc_tgt=nocc_tgt if spin_flip else None)
+    return wl, O.system_from_workload(wl)
+
+
+@pytest.mark.parametrize("sf", [False, True])
+def test_hermiticity(sf):
+    wl, S = _tiny(spin_flip=sf)
+    A, B = wl.X[0:1], wl.X[1:2]
+    lhs = np.vdot(B, S.apply(A))
+    rhs = np.conj(np.vdot(A, S.apply(B)))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    # each term alone is Hermitian too (K1e, K1d, V_X and the diagonal part)
+    for t in (O.D_KIN | O.PROJ, O.D_VLOC | O.PROJ, O.D_EXX | O.PROJ, O.K1E_H | O.K1E_XC | O.PROJ, O.K1D | O.PROJ):
+        l1 = np.vdot(B, S.apply(A, t))
+        r1 = np.conj(np.vdot(A, S.apply(B, t)))
+        assert abs(l1 - r1) <= 1e-13 * max(abs(l1), 1e-300)
+
+
+def test_projector_and_inputs():
+    wl, S = _tiny()
+    P = wl.phi_src
+    assert np.abs(P.conj() @ P.T - np.eye(P.shape[0])).max() < 1e-13
+    assert np.abs(np.einsum("ug,bvg->buv", P.conj(), wl.X)).max() < 1e-13
+    Y = np.random.default_rng(6).standard_normal(wl.X.shape) + 0j
+    PY = S.project(Y)
+    assert np.allclose(S.project(PY), PY, atol=1e-13)
+    assert np.abs(np.einsum("ug,bvg->buv", P.conj(), PY)).max() < 1e-13
+    LX = S.apply(wl.X)
+    assert np.abs(np.einsum("ug,bvg->buv", P.conj(), LX)).max() < 1e-12
+    # Delta rho has zero mean: integral = sum_v <phi_v|a_v> = 0
+    a_r = S.grid.pw_to_real(wl.X[0])
+    assert abs(S.delta_rho(a_r).sum()) < 1e-12 * np.abs(S.delta_rho(a_r)).sum()
+
+
+def test_alpha_zero_removes_exchange():
+    wl, S = _tiny()
+    S0 = O.System(wl.n, wl.a, wl.ecut, wl.phi_src, wl.eps_src, alpha=0.0, kx_g0=wl.kx_g0,
+                  vloc=wl.vloc, fxc=wl.fxc)
+    full0 = S0.apply(wl.X)
+    rest = S.apply(wl.X, O.ALL_TERMS & ~(O.D_EXX | O.K1D))
+    assert np.allclose(full0, rest, atol=1e-14)
+    assert np.abs(S.apply(wl.X, O.D_EXX | O.K1D)).max() > 1e-3
+
+
+@pytest.mark.parametrize("sf", [False, True])
+def test_unitary_rotation_covariance(sf):
+    """phi_v = sum_n U_vn phit_n, at_n = sum_v' U*_v'n a_v' (Sec. 3.2, Eq. trunc):
+    (L A)_v = sum_m U_vm (Lt At)_m when all eps_v are equal."""
+    wl, S = _tiny(spin_flip=sf)
+    nocc = wl.nocc_src
+    rng = np.random.default_rng(7)
+    U, _ = np.linalg.qr(rng.standard_normal((nocc, nocc)) + 1j * rng.standard_normal((nocc, nocc)))
+    eps = np.full(nocc, -0.2)
+    phit = U.conj().T @ wl.phi_src  # phit_n = sum_v U*_vn phi_v
+    kw = dict(alpha=wl.alpha, kx_g0=wl.kx_g0, vloc=wl.vloc, fxc=wl.fxc, spin_flip=sf,
+              phi_tgt=wl.phi_tgt if sf else None)
+    S1 = O.System(wl.n, wl.a, wl.ecut, wl.phi_src, eps, **kw)
+    S2 = O.System(wl.n, wl.a, wl.ecut, phit, eps, **kw)
+    At = np.einsum("vn,bvg->bng", U.conj(), wl.X)
+    lhs = S1.apply(wl.X)
+    rhs = np.einsum("vm,bmg->bvg", U, S2.apply(At))
+    assert np.allclose(lhs, rhs, atol=1e-12 * np.abs(lhs).max())
+    # omega is invariant as well
+    assert np.allclose(S1.omega(wl.X), S2.omega(At), rtol=1e-12)
+
+
+def test_spin_flip_has_no_hartree_term():
+    wl, S = _tiny(spin_flip=True)
+    only_h = S.apply(wl.X, O.K1E_H | O.PROJ)
+    assert np.abs(only_h).max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# gradient: central finite differences (FP64, h = 1e-4)
+# --------------------------------------------------------------------------
+
+def test_gradient_against_finite_differences():
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=2, seed=8)
+    w = np.array([0.7, 1.3])
+    om, gphi, gv = S.omega_grad(wl.X, w)
+    assert np.allclose(om, S.omega(wl.X), rtol=1e-13)
+
+    def total(phi=None, vloc=None):
+        S2 = O.System(wl.n, wl.a, wl.ecut, wl.phi_src if phi is None else phi, wl.eps_src, alpha=wl.alpha,
+                      kx_g0=wl.kx_g0, vloc=wl.vloc if vloc is None else vloc, fxc=wl.fxc)
+        return float(np.dot(w, S2.omega(wl.X)))
+
+    h = 1e-4
+    rng = np.random.default_rng(9)
+    for _ in range(6):
+        u = int(rng.integers(wl.nocc_src))
+        k = int(rng.integers(S.grid.npw))
+        d = []
+        for step in (1.0, 1j):
+            p1 = wl.phi_src.copy()
+            p1[u, k] += h * step
+            p2 = wl.phi_src.copy()
+            p2[u, k] -= h * step
+            d.append((total(phi=p1) - total(phi=p2)) / (2 * h))
+        fd = d[0] + 1j * d[1]  # = 2 d/dc^*
+        assert abs(fd - 2 * gphi[u, k]) < 1e-7 * max(1.0, abs(fd)), (u, k, fd, 2 * gphi[u, k])
+    for _ in range(3):
+        j = tuple(int(t) for t in rng.integers(wl.n, size=3))
+        v1 = wl.vloc.copy()
+        v1[j] += h
+        v2 = wl.vloc.copy()
+        v2[j] -= h
+        fd = (total(vloc=v1) - total(vloc=v2)) / (2 * h)
+        assert abs(fd - gv[j]) < 1e-8 * max(1.0, abs(fd))
+
+
+def test_vloc_gradient_closed_form():
+    """d omega / d V_loc(r_j) = (Omega/N_r) sum_b w_b sum_v |x_{b,v}(r_j)|^2 for X orthogonal to phi."""
+    wl, S = _tiny(nb=2)
+    w = np.array([0.4, -1.1])
+    _, _, gv = S.omega_grad(wl.X, w)
+    dens = np.zeros((wl.n,) * 3)
+    for b in range(2):
+        for v in range(wl.nocc_src):
+            # the plane-wave sum written out directly
+            f = S.grid.pw_to_real(wl.X[b, v])
+            dens += w[b] * np.abs(f) ** 2
+    assert np.allclose(gv, dens * wl.a ** 3 / wl.n ** 3, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# dense operator and Davidson
+# --------------------------------------------------------------------------
+
+def test_davidson_matches_dense_diagonalisation():
+    wl, S = _tiny(n=8, a=6.0, ecut=2.5, nocc=2, nb=4, seed=10)
+    H, Qc = S.dense_matrix()
+    assert np.abs(H - H.conj().T).max() < 1e-12 * np.abs(H).max()
+    ev = np.linalg.eigvalsh(H)
+    theta, V, it = O.davidson(S, wl.X, nroots=3, tol=1e-9, max_iter=200)
+    assert np.allclose(theta, ev[:3], atol=1e-8), (theta, ev[:3])
+    # Ritz vectors are eigenvectors of L
+    LV = S.apply(V)
+    assert np.abs(LV - theta[:, None, None] * V).max() < 1e-7
