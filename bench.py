@@ -1,0 +1,329 @@
+"""Benchmark: Liouville applications/s on the 64-atom diamond-like batch.
+
+One step = one call of tddft_apply_liouville on the whole batch (8 trial
+vectors, all occupied pairs, every term of L, FP32 pair/FFT path). Prints one
+JSON line (rank 0). Under torchrun every rank runs an independent replica on
+its own GPU (the operator needs no collective for independent batches).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Liouville applications/s (all occupied pairs) and % HBM roofline vs FP64 path"
+UNIT = "applications/s"
+WORKLOAD = dict(n=72, a=13.48, ecut=25.0, nocc=128, nb=8, alpha=0.18, seed=0)
+WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 grid, Ecut 25 Ha "
+                 "(14771 plane waves), Nocc 128, Nb 8 trial vectors, alpha 0.18, all occupied pairs")
+
+# DRAM traffic per launch of the dominant kernel class from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
+# sources it was taken on; reported as null when the sources have changed.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("fft.cuh", "kernels.cuh", "plane_ops.cuh"):
+        with open(os.path.join(ROOT, "paper_2309_03513_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(rank: int):
+    from paper_2309_03513_b300 import synth
+    from paper_2309_03513_b300 import tddft as T
+    w = WORKLOAD
+    npw = T.sphere_size(w["n"], w["a"], w["ecut"])
+    return synth.make_workload(n=w["n"], a=w["a"], ecut=w["ecut"], npw=npw, nocc_src=w["nocc"], nb=w["nb"],
+                               seed=w["seed"] + rank, alpha=w["alpha"])
+
+
+def oracle_sample(wl, rows):
+    """Time the FP64 oracle on a few rows (b, v) of the batch; returns (seconds, cores)."""
+    from oracle import tddft_oracle as O
+    S = O.system_from_workload(wl)
+    S.phi_src_r()  # orbitals to real space once, as the oracle's set-up
+    t0 = time.perf_counter()
+    S.apply(wl.X, rows=rows)
+    return time.perf_counter() - t0, O.fft_workers()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(0)
+    nocc = WORKLOAD["nocc"]
+    times = []
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        row = [(i % WORKLOAD["nb"], (7 * i) % nocc)]
+        dt, cores = oracle_sample(wl, row)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = (len(times) / nocc) / total  # rows -> applications
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas", "step": "one row (b, v) of L.A"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one row (b, v) of the batch per step: all pair convolutions of that row, "
+                                   "with the Hartree/xc density of its trial vector; rows/s / Nocc"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+
+    from paper_2309_03513_b300 import tddft as T
+
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    wl = make_workload(rank)
+    nb, nocc = WORKLOAD["nb"], WORKLOAD["nocc"]
+    stream = torch.cuda.current_stream(dev)
+    sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    npw = sys_.npw
+    X = torch.from_numpy(wl.X).to(dev, torch.complex64)
+    LA = torch.empty_like(X)
+
+    for _ in range(args.warmup):
+        sys_.apply(X, out=LA, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    # timed region
+    sampler = ClockSampler(local if ws > 1 else 0)
+    sampler.start()
+    T.profile_enable(True)
+    launches0 = T.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sys_.apply(X, out=LA, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    launches = T.launch_count() - launches0
+    prof = T.profile_read()
+    T.profile_enable(False)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(ws, ms)
+    value = ws * args.steps * nb / (ms_max / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside)
+    Xh_t = torch.from_numpy(wl.X.astype(np.complex64)).pin_memory()
+    LAh_t = torch.empty(Xh_t.shape, dtype=torch.complex64).pin_memory()
+    Xh, LAh = Xh_t.numpy(), LAh_t.numpy()
+    sys_.apply_host(Xh, LAh, stream=stream)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sys_.apply_host(Xh, LAh, stream=stream)
+    t_e2e = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e = ws * args.e2e_steps * nb / t_e2e
+    io_bytes = nb * nocc * npw * 8
+
+    # plain FP64 GPU path on the same batch
+    fp64 = None
+    if args.fp64_steps > 0:
+        del LA
+        s64 = T.system_from_workload(wl, precision=T.PREC_FP64, stream=stream)
+        X64 = torch.from_numpy(wl.X).to(dev)
+        LA64 = torch.empty_like(X64)
+        s64.apply(X64, out=LA64, stream=stream)
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            s64.apply(X64, out=LA64, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = max_over_ranks(ws, f0.elapsed_time(f1))
+        fp64 = {"value": ws * args.fp64_steps * nb / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": fms / args.fp64_steps}
+        s64.close()
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    cls = prof["classes"]
+    dom = max(cls, key=lambda k: cls[k]["ms"])
+    d = cls[dom]
+    achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else None
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(src_hash, {}).get(dom)
+    shares = {k: round(v["ms"] / max(1e-9, sum(c["ms"] for c in cls.values())), 4) for k, v in cls.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "npw": npw, "nocc": nocc, "nb": nb,
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (trial vectors and outputs in real space: 2 x 3.1 GB per step)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+                     "traffic": traffic, "peak_source": peaks["source"],
+                     "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                     "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                     "class_time_share": shares, "kernel_sources": src_hash},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fp64_path": fp64,
+        "speedup_vs_fp64_path": (value / fp64["value"]) if fp64 else None,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        rows = [(0, v) for v in range(args.cpu_rows)]
+        dt, cores = oracle_sample(wl, rows)
+        line["cpu_baseline"] = {"value": (len(rows) / nocc) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(rows)} rows (b=0, v=0..{len(rows)-1}) of the same batch: all pair "
+                                          f"convolutions of those rows plus the Hartree/xc density of b=0; "
+                                          f"rows/s / Nocc; {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    sys_.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

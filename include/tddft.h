@@ -1,0 +1,199 @@
+/*
+ * C ABI of the B300 library for the Tamm-Dancoff Liouville operator of hybrid
+ * linear-response TDDFT in plane waves at the Gamma point (spin-conserving and
+ * spin-flip), after Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513.
+ *
+ * Conventions (all calls)
+ * -----------------------
+ * Cubic cell of side a (bohr), Omega = a^3, FFT grid n^3, r_j = a j / n,
+ * G_m = (2 pi / a) m with m_i in [-n/2, n/2) (n even).
+ * Wavefunction sphere S = {m : (1/2)|G_m|^2 < ecut} with |G|^2 computed in
+ * FP64 as ((2 pi / a)^2) * |m|^2; its npw points are ordered by
+ * (|m|^2, m_x, m_y, m_z) ascending. An orbital is
+ *   phi(r_j) = Omega^{-1/2} sum_{G in S} c(G) exp(i G.r_j).
+ * Plane-wave arrays are row-major [rows][npw] of interleaved complex numbers:
+ * complex128 (two doubles) for TDDFT_PREC_FP64 and for every host input of
+ * tddft_init_system, complex64 (two floats) for device buffers of TDDFT_PREC_FP32.
+ * Real-space arrays are [n][n][n] indexed [j_z][j_y][j_x] (x fastest).
+ * Coulomb kernels: kappa(G) = 4 pi / |G|^2 for G != 0; at G = 0 the exchange
+ * kernel takes desc.kx_g0 (e.g. 2 pi R_c^2) and the Hartree kernel 0.
+ * Periodic convolution: Conv_kappa[rho] = F^{-1}[kappa N_r^{-1} F[rho]].
+ *
+ * Errors: every call returns a tddft_status; no exception crosses the ABI.
+ * tddft_last_error() gives a thread-local message for the last failure.
+ * Streams are passed as void* (a cudaStream_t, NULL for the legacy stream).
+ * Calls on one handle must not overlap: a handle owns one workspace.
+ */
+#ifndef TDDFT_H
+#define TDDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tddft_status {
+  TDDFT_OK = 0,
+  TDDFT_EINVAL = 1,   /* bad argument, unsupported size, non-orthonormal orbitals */
+  TDDFT_ENOMEM = 2,   /* device or host allocation failed */
+  TDDFT_ECUDA = 3,    /* a CUDA runtime call failed */
+  TDDFT_ETIMEOUT = 4, /* a bounded device wait ran out */
+  TDDFT_ENUMERIC = 5, /* a small dense eigen/Cholesky step failed */
+  TDDFT_ENOTCONV = 6, /* Davidson hit the caller's iteration cap */
+  TDDFT_ENOTSUP = 7   /* combination not implemented */
+} tddft_status;
+
+/* Terms of L (Eq. 8 / Eq. 21 of the paper); a call applies the terms of the
+ * handle's mask. */
+#define TDDFT_TERM_D_KIN 1u   /* (1/2|G|^2 - eps_v) a_v            (Eq. 3, kinetic part of H^KS) */
+#define TDDFT_TERM_D_VLOC 2u  /* V_loc(r) a_v(r)                    (Eq. 3, local part of H^KS) */
+#define TDDFT_TERM_D_EXX 4u   /* +alpha V_X a_v, V_X a = -sum_w phi_w Conv_x[phi_w^* a]
+                                 (Eq. 3 with the exchange operator of Sec. 3.1) */
+#define TDDFT_TERM_K1E_H 8u   /* phi_v Conv_H[Delta rho]            (Eq. 4; absent for spin-flip, Sec. 2.3) */
+#define TDDFT_TERM_K1E_XC 16u /* phi_v f_xc Delta rho               (Eq. 4; f_xc^SF for spin-flip) */
+#define TDDFT_TERM_K1D 32u    /* -alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]  (Eq. 6, Sec. 3.2) */
+#define TDDFT_TERM_PROJ 64u   /* P^c = 1 - sum_u |phi_u><phi_u| of the target spin (after Eq. 7) */
+#define TDDFT_TERMS_ALL 127u
+
+#define TDDFT_SPIN_CONSERVING 0
+#define TDDFT_SPIN_FLIP 1 /* source spin up -> target spin down (Eq. 21) */
+
+#define TDDFT_PREC_FP64 0 /* every step in FP64 (the plain path) */
+#define TDDFT_PREC_FP32 1 /* pair products, FFTs, kernel multiplies in complex FP32 */
+
+typedef struct tddft_desc {
+  int n;              /* FFT points per axis; supported: 8 12 16 24 32 36 48 64 72 80 96 108 (FP32 also 128) */
+  double a;           /* cubic cell side (bohr) */
+  double ecut;        /* wavefunction cutoff (Ha) */
+  int spin_mode;      /* TDDFT_SPIN_CONSERVING or TDDFT_SPIN_FLIP */
+  int nocc_src;       /* occupied orbitals of the source spin: index v of a_v, pairs of K1e/K1d */
+  int nocc_tgt;       /* occupied orbitals of the target spin: P^c and V_X inside D (= nocc_src for SC) */
+  double alpha;       /* exact-exchange fraction alpha_EXX (Sec. 2.1) */
+  double kx_g0;       /* exchange kernel at G = 0 */
+  int precision;      /* TDDFT_PREC_FP64 or TDDFT_PREC_FP32 */
+  unsigned term_mask; /* TDDFT_TERM_* bits */
+  int nb_max;         /* largest batch of trial vectors one call may pass */
+} tddft_desc;
+
+/* Host inputs of tddft_init_system, all FP64. The library copies them; the
+ * caller may free them when the call returns. */
+typedef struct tddft_inputs {
+  const double* phi_src; /* complex128 [nocc_src][npw], orthonormal */
+  const double* phi_tgt; /* complex128 [nocc_tgt][npw], orthonormal; spin-flip only (NULL for SC) */
+  const double* eps_src; /* [nocc_src] eigenvalues of the source spin (Eq. 3; Eq. 21 for SF) */
+  const double* vloc;    /* [n^3] local potential of the target spin, or NULL (= 0) */
+  const double* fxc;     /* [n^3] f_xc(r) (SC) or f_xc^SF(r) (SF), or NULL (= 0) */
+} tddft_inputs;
+
+typedef struct tddft_info {
+  int npw;                 /* sphere size */
+  int n;                   /* grid points per axis */
+  int nb_chunk;            /* trial vectors processed per internal pass */
+  int precision;
+  size_t device_bytes;     /* device memory owned by the handle */
+} tddft_info;
+
+typedef struct tddft_system* tddft_handle;
+
+/* Size of the sphere S for (n, a, ecut). Host only. EINVAL if S does not fit
+ * strictly inside the grid (|m_i| < n/2). */
+tddft_status tddft_sphere_size(int n, double a, double ecut, int* npw);
+
+/* Miller indices of S in the library's order: miller[3*i + {0,1,2}] =
+ * (m_x, m_y, m_z) of point i. The caller provides npw*3 ints. Host only. */
+tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller);
+
+/* Build a system: copy the inputs to the device, build the sphere map and
+ * kernel tables, transform the orbitals to real space and allocate the
+ * workspace for nb_max trial vectors. The orbitals are checked orthonormal
+ * in FP64 (max |Phi^dagger Phi - I| <= 1e-10) -> else TDDFT_EINVAL.
+ * The handle owns all device memory until tddft_destroy. Synchronises the
+ * stream before returning. */
+tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, void* stream,
+                               tddft_handle* out);
+
+tddft_status tddft_query(tddft_handle h, tddft_info* info);
+
+/* Change the term mask of the handle (TDDFT_TERM_* bits). */
+tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask);
+
+/* Pair-batch tiling of the pair-convolution passes: targets per batch and
+ * sources per batch (0 keeps the current value). Host only. */
+tddft_status tddft_set_tiling(tddft_handle h, int targets, int sources);
+
+/* LA = L A for nb trial vectors (Eq. 8 for SC, Eq. 21 for SF).
+ * A, LA: device buffers [nb][nocc_src][npw] (complex128 for FP64 handles,
+ * complex64 for FP32 handles). They must not alias. Each A_b is assumed
+ * orthogonal to the target-spin orbitals (the operator is defined on that
+ * space). Asynchronous and stream-ordered; no host synchronisation.
+ * nb = 0 is a no-op; nb > nb_max -> TDDFT_EINVAL. */
+tddft_status tddft_apply_liouville(tddft_handle h, int nb, const void* A, void* LA, void* stream);
+
+/* Same as tddft_apply_liouville with HOST buffers of the same layout: the call
+ * copies A to the device, applies L and copies LA back, then synchronises
+ * the stream. */
+tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_host, void* LA_host, void* stream);
+
+/* Bilinear form omega_b = <P^c X_b | M | P^c X_b> (M = L without the outer
+ * P^c; equal to <X_b|L X_b> for X_b orthogonal to the orbitals) and the
+ * gradient of E = sum_b w_b omega_b (spin-conserving handles only).
+ * X: device [nb][nocc][npw] (handle precision). w: HOST [nb].
+ * omega: device double [nb].
+ * grad_phi: device [nocc][npw] (handle precision), the Wirtinger derivative
+ *   dE/dc_u^*(G) with X, eps, V_loc, f_xc and the kernels held fixed and P^c
+ *   taken on the handle's orbitals (the part of u_v of the Supporting
+ *   Information, Sec. S1, that does not come from the ground-state density).
+ * grad_vloc: device double [n^3], dE/dV_loc(r_j); may be NULL.
+ * Pair convolutions are recomputed, not stored. Written, not accumulated. */
+tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
+                                           void* grad_phi, double* grad_vloc, void* stream);
+
+/* Davidson solver for the lowest eigenpairs of L (Sec. 4 names Davidson's
+ * method; block scheme, FP64 orthogonalisation and Rayleigh-Ritz). */
+typedef struct tddft_davidson* tddft_dav_handle;
+
+/* Start a solve for nroots roots from nguess >= nroots guess vectors
+ * X0 (HOST complex128 [nguess][nocc_src][npw]); max_basis >= 2*nroots bounds
+ * the basis before a restart. Applies L to the guess (stream-ordered). */
+tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const double* X0, int max_basis,
+                                   void* stream, tddft_dav_handle* out);
+
+/* One Davidson iteration: Rayleigh-Ritz on the current basis, residuals,
+ * preconditioned corrections, FP64 orthogonalisation against the target
+ * orbitals and the basis, and L applied to the new vectors. Writes the
+ * current Ritz values (HOST double [nroots]) and the number of roots with
+ * residual norm < tol. One host synchronisation. TDDFT_ENUMERIC if the
+ * subspace eigensolver fails. */
+tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converged, double* ritz_values,
+                                 double* residual_norms, void* stream);
+
+/* Copy the current Ritz vectors to HOST complex128 [nroots][nocc_src][npw]. */
+tddft_status tddft_davidson_vectors(tddft_dav_handle d, double* X_host, void* stream);
+
+tddft_status tddft_davidson_destroy(tddft_dav_handle d);
+
+tddft_status tddft_destroy(tddft_handle h);
+
+/* Instrumentation (process-wide, not thread-safe). With the profiler enabled
+ * every launch of the three FFT plane kernels is bracketed by CUDA events on
+ * its stream. tddft_profile_read synchronises on those events and returns, per
+ * class (0: forward xy pass with the pair product, 1: z pass with the kernel
+ * multiply, 2: inverse xy pass with the re-multiply and accumulation), the
+ * summed device time in ms, the launch count and the algorithmic bytes (each
+ * operand read once, each output written once; the z pass counts the kernel
+ * table once per launch). total_launches counts every kernel launch of the
+ * library since it was loaded. Enabling resets the per-class records. */
+#define TDDFT_PROFILE_CLASSES 3
+tddft_status tddft_profile_enable(int enable);
+tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, long long* total_launches);
+
+const char* tddft_status_string(tddft_status s);
+const char* tddft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDDFT_H */

@@ -1,0 +1,324 @@
+// Shared-memory 3D FFT building blocks for the pair-convolution path.
+//
+// A 3D transform of an N^3 field is done plane by plane: an xy-plane pass
+// (x lines then y lines) and a z pass over xz-planes. Each 1D transform is an
+// in-place mixed-radix Cooley-Tukey FFT:
+//   forward  = decimation in frequency (DIF): natural order in, digit-reversed out;
+//   inverse  = the DIF stages undone in reverse order (DIT): digit-reversed in,
+//              natural order out.
+// No reordering pass exists: every array that lives in reciprocal space (the
+// convolution kernels, the sphere map) is stored in the digit-reversed order.
+// Sign convention: forward exp(-2 pi i jk/N), inverse exp(+2 pi i jk/N), both
+// unnormalised.
+//
+// Twiddles W_N^e = exp(-2 pi i e/N) come from a table computed on the host in
+// FP64 with std::cos/std::sin and rounded once to the working precision.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tddft {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// conj(a) * b
+template <typename T>
+__device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.x, -a.y}; }
+// multiply by +i / -i
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_pi(cplx<T> a) { return {-a.y, a.x}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_mi(cplx<T> a) { return {a.y, -a.x}; }
+
+constexpr int FWD = -1;  // exp(-2 pi i ...)
+constexpr int INV = +1;  // exp(+2 pi i ...)
+
+// multiply by (DIR i): forward -> -i, inverse -> +i
+template <int DIR, typename T>
+__device__ __forceinline__ cplx<T> mul_di(cplx<T> a) {
+  if constexpr (DIR == FWD) return mul_mi(a);
+  else return mul_pi(a);
+}
+
+// a * w (forward) or a * conj(w) (inverse), w a table twiddle W_N^e
+template <int DIR, typename T>
+__device__ __forceinline__ cplx<T> twmul(cplx<T> a, cplx<T> w) {
+  if constexpr (DIR == FWD) return cmul(a, w);
+  else return cmulc(w, a);
+}
+
+// ---------------------------------------------------------------------------
+// Radix codelets: v[k] <- sum_n v[n] exp(DIR 2 pi i n k / R), natural order.
+// Mathematical constants: sqrt(3)/2, cos/sin(2 pi/5), cos/sin(4 pi/5), 1/sqrt(2).
+// ---------------------------------------------------------------------------
+template <int DIR, typename T>
+__device__ __forceinline__ void dft2(cplx<T>* v) {
+  cplx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft3(cplx<T>* v) {
+  const T c = T(-0.5);
+  const T s = T(0.86602540378443864676372317075293618);
+  cplx<T> t1 = cadd(v[1], v[2]);
+  cplx<T> t2 = cadd(v[0], cscale(t1, c));
+  cplx<T> t3 = cscale(csub(v[1], v[2]), s);
+  v[0] = cadd(v[0], t1);
+  cplx<T> it3 = mul_di<DIR>(t3);
+  v[1] = cadd(t2, it3);
+  v[2] = csub(t2, it3);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft4(cplx<T>* v) {
+  cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  cplx<T> t2 = cadd(v[1], v[3]), t3 = mul_di<DIR>(csub(v[1], v[3]));
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft5(cplx<T>* v) {
+  const T c1 = T(0.30901699437494742410229341718281906);
+  const T c2 = T(-0.80901699437494742410229341718281906);
+  const T s1 = T(0.95105651629515357211643933337938214);
+  const T s2 = T(0.58778525229247312916870595463907277);
+  cplx<T> a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+  cplx<T> a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+  cplx<T> x0 = v[0];
+  v[0] = cadd(x0, cadd(a1, a2));
+  cplx<T> r1 = cadd(x0, cadd(cscale(a1, c1), cscale(a2, c2)));
+  cplx<T> r2 = cadd(x0, cadd(cscale(a1, c2), cscale(a2, c1)));
+  cplx<T> i1 = mul_di<DIR>(cadd(cscale(b1, s1), cscale(b2, s2)));
+  cplx<T> i2 = mul_di<DIR>(csub(cscale(b1, s2), cscale(b2, s1)));
+  v[1] = cadd(r1, i1);
+  v[4] = csub(r1, i1);
+  v[2] = cadd(r2, i2);
+  v[3] = csub(r2, i2);
+}
+
+// Multiply by exp(DIR 2 pi i E / R); exact for multiples of pi/4, table otherwise.
+// tw points at the length-N table, twstride = N / R.
+template <int DIR, int R, int E, typename T>
+__device__ __forceinline__ cplx<T> rot(cplx<T> a, const cplx<T>* tw, int twstride) {
+  constexpr int e = E % R;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr ((4 * e) % R == 0) {
+    constexpr int q = (4 * e) / R;  // quarter turns
+    if constexpr (q == 1) return mul_di<DIR>(a);
+    else if constexpr (q == 2) return {-a.x, -a.y};
+    else return mul_di<-DIR>(a);
+  } else if constexpr ((8 * e) % R == 0) {
+    constexpr int o = (8 * e) / R;  // odd number of eighth turns: 1, 3, 5, 7
+    const T h = T(0.70710678118654752440084436210484904);
+    // exp(DIR i pi/4) = h (1 + DIR i)
+    cplx<T> w1 = cscale(cadd(a, mul_di<DIR>(a)), h);
+    if constexpr (o == 1) return w1;
+    else if constexpr (o == 3) return mul_di<DIR>(w1);
+    else if constexpr (o == 5) return {-w1.x, -w1.y};
+    else return mul_di<-DIR>(w1);
+  } else {
+    return twmul<DIR>(a, tw[e * twstride]);
+  }
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(cplx<T>* v, const cplx<T>* tw, int twstride);
+
+template <int P, int Q, int DIR, typename T, int Q0, int K1>
+__device__ __forceinline__ void comp_rot(cplx<T>* t, cplx<T>* u, const cplx<T>* tw, int twstride) {
+  if constexpr (K1 < P) {
+    u[Q0 * P + K1] = rot<DIR, P * Q, Q0 * K1>(t[K1], tw, twstride);
+    comp_rot<P, Q, DIR, T, Q0, K1 + 1>(t, u, tw, twstride);
+  }
+}
+
+// Composite codelet R = P * Q: input index n = q + Q p, output k = k1 + P k2.
+template <int P, int Q, int DIR, typename T, int Q0 = 0>
+__device__ __forceinline__ void comp_first(cplx<T>* v, cplx<T>* u, const cplx<T>* tw, int twstride) {
+  if constexpr (Q0 < Q) {
+    cplx<T> t[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) t[p] = v[Q0 + Q * p];
+    dft<P, DIR>(t, tw, twstride * Q);
+    comp_rot<P, Q, DIR, T, Q0, 0>(t, u, tw, twstride);
+    comp_first<P, Q, DIR, T, Q0 + 1>(v, u, tw, twstride);
+  }
+}
+
+template <int P, int Q, int DIR, typename T>
+__device__ __forceinline__ void dft_comp(cplx<T>* v, const cplx<T>* tw, int twstride) {
+  cplx<T> u[P * Q];
+  comp_first<P, Q, DIR, T, 0>(v, u, tw, twstride);
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) {
+    cplx<T> t[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) t[q] = u[q * P + k1];
+    dft<Q, DIR>(t, tw, twstride * P);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = t[k2];
+  }
+}
+
+// twstride: index step in the length-N table for W_R (N / R).
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(cplx<T>* v, const cplx<T>* tw, int twstride) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<DIR>(v);
+  } else if constexpr (R == 3) {
+    dft3<DIR>(v);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v);
+  } else if constexpr (R == 5) {
+    dft5<DIR>(v);
+  } else if constexpr (R == 6) {
+    dft_comp<2, 3, DIR>(v, tw, twstride);
+  } else if constexpr (R == 8) {
+    dft_comp<2, 4, DIR>(v, tw, twstride);
+  } else if constexpr (R == 9) {
+    dft_comp<3, 3, DIR>(v, tw, twstride);
+  } else if constexpr (R == 12) {
+    dft_comp<4, 3, DIR>(v, tw, twstride);
+  } else if constexpr (R == 16) {
+    dft_comp<4, 4, DIR>(v, tw, twstride);
+  } else {
+    static_assert(R == 2, "unsupported radix");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Radix plans. Stage s has radix R_s; the stage operates on blocks of length
+// L_s = N / (R_0 ... R_{s-1}) and butterflies of stride M_s = L_s / R_s.
+// ---------------------------------------------------------------------------
+template <int N>
+struct Plan;
+#define TDDFT_PLAN(NN, ...)                                \
+  template <>                                              \
+  struct Plan<NN> {                                        \
+    static constexpr int r[] = {__VA_ARGS__};              \
+    static constexpr int S = sizeof(r) / sizeof(int);      \
+  };
+TDDFT_PLAN(8, 8)
+TDDFT_PLAN(12, 4, 3)
+TDDFT_PLAN(16, 16)
+TDDFT_PLAN(24, 8, 3)
+TDDFT_PLAN(32, 8, 4)
+TDDFT_PLAN(36, 4, 9)
+TDDFT_PLAN(48, 16, 3)
+TDDFT_PLAN(64, 8, 8)
+TDDFT_PLAN(72, 8, 9)
+TDDFT_PLAN(80, 16, 5)
+TDDFT_PLAN(96, 12, 8)
+TDDFT_PLAN(108, 12, 9)
+TDDFT_PLAN(128, 8, 16)
+#undef TDDFT_PLAN
+
+template <int N, int S>
+__host__ __device__ constexpr int plan_block() {  // L_s
+  int l = N;
+  for (int i = 0; i < S; ++i) l /= Plan<N>::r[i];
+  return l;
+}
+
+// Threads per line: a CTA of N * G threads works on N lines at once.
+template <int N>
+__host__ __device__ constexpr int lines_group() {
+  return N <= 16 ? 16 : (N <= 32 ? 8 : 4);
+}
+template <int N>
+__host__ __device__ constexpr int plane_threads() {
+  return N * lines_group<N>();
+}
+// Row pitch (complex elements) of a plane in shared memory: odd, so that
+// threads walking different lines hit different banks.
+template <int N>
+__host__ __device__ constexpr int plane_pitch() {
+  return N + 1;
+}
+
+// One DIF stage (forward) or its inverse over all N lines of a plane in smem.
+// Line l is a row (elements l*PITCH + i) when ROWS, a column (i*PITCH + l) otherwise.
+template <typename T, int N, int S, int DIR, bool ROWS>
+__device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, int g) {
+  constexpr int R = Plan<N>::r[S];
+  constexpr int L = plan_block<N, S>();
+  constexpr int M = L / R;
+  constexpr int G = lines_group<N>();
+  constexpr int NB = N / R;         // butterflies per line
+  constexpr int TWS = N / L;        // twiddle stride for W_L
+  constexpr int PITCH = plane_pitch<N>();
+#pragma unroll 1
+  for (int j = g; j < NB; j += G) {
+    const int blk = j / M, n1 = j - blk * M;
+    const int base = blk * L + n1;
+    cplx<T> v[R];
+    if constexpr (DIR == FWD) {
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) {
+        const int i = base + M * n2;
+        v[n2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
+      }
+      dft<R, FWD>(v, tw, N / R);
+#pragma unroll
+      for (int k2 = 1; k2 < R; ++k2)
+        if (n1) v[k2] = twmul<FWD>(v[k2], tw[n1 * k2 * TWS]);
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) {
+        const int i = base + M * k2;
+        if (ROWS) s[line * PITCH + i] = v[k2];
+        else s[i * PITCH + line] = v[k2];
+      }
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) {
+        const int i = base + M * k2;
+        v[k2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
+        if (k2 && n1) v[k2] = twmul<INV>(v[k2], tw[n1 * k2 * TWS]);
+      }
+      dft<R, INV>(v, tw, N / R);
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) {
+        const int i = base + M * n2;
+        if (ROWS) s[line * PITCH + i] = v[n2];
+        else s[i * PITCH + line] = v[n2];
+      }
+    }
+  }
+}
+
+// Full 1D transform of all lines of the plane (syncs between stages and at the end).
+template <typename T, int N, int DIR, bool ROWS, int S = 0>
+__device__ __forceinline__ void fft_lines(cplx<T>* s, const cplx<T>* tw, int line, int g) {
+  constexpr int NS = Plan<N>::S;
+  if constexpr (S < NS) {
+    constexpr int st = (DIR == FWD) ? S : (NS - 1 - S);
+    stage<T, N, st, DIR, ROWS>(s, tw, line, g);
+    __syncthreads();
+    fft_lines<T, N, DIR, ROWS, S + 1>(s, tw, line, g);
+  }
+}
+
+}  // namespace tddft

@@ -1,0 +1,302 @@
+// CUDA kernels of the Liouville-operator path (templated on the real type T
+// and, for the plane kernels, on the grid size N).
+//
+// Field layout: a real-space field is N^3 complex values indexed [z][y][x]
+// (x fastest). A reciprocal-space field produced by the forward kernels is
+// the same array with each axis in the digit-reversed order of its radix plan.
+#pragma once
+#include "fft.cuh"
+
+namespace tddft {
+
+// Affine description of a batch of pair convolutions. Item i = t * kdim + k
+// (t = target slot, k = source slot) convolves conj(Q) * R and, in the
+// accumulate mode, adds scale * P * Conv[conj(Q) R] to output field o.
+struct PairMap {
+  int kdim;
+  int q0, qk, qt;
+  int r0, rk, rt;
+  int p0, pk, pt;
+  int o0, ot;
+};
+
+template <typename T>
+__device__ __forceinline__ const cplx<T>* plane_ptr(const cplx<T>* base, long long field, int z, long long n3, int n2) {
+  return base + field * n3 + (long long)z * n2;
+}
+
+// ---------------------------------------------------------------------------
+// Forward xy pass. MODE_PRODUCT: plane = conj(Q) * R; MODE_LOAD: plane = R.
+// Grid (N, items). Output item i goes to ibuf field i (digit-reversed in x, y).
+// ---------------------------------------------------------------------------
+constexpr int XY_LOAD = 0;
+constexpr int XY_PRODUCT = 1;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_xy_fwd(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
+             cplx<T>* __restrict__ ibuf, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + N;
+  const int tid = threadIdx.x, z = blockIdx.x, item = blockIdx.y;
+  const int t = item / pm.kdim, k = item - t * pm.kdim;
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z, N3, N2);
+  if constexpr (MODE == XY_PRODUCT) {
+    const cplx<T>* Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z, N3, N2);
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = cmulc(Q[e], R[e]);
+    }
+  } else {
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = R[e];
+    }
+  }
+  __syncthreads();
+  const int line = tid % N, g = tid / N;
+  fft_lines<T, N, FWD, true>(s, tw, line, g);
+  fft_lines<T, N, FWD, false>(s, tw, line, g);
+  cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * N2;
+  for (int e = tid; e < N2; e += NT) {
+    const int y = e / N, x = e - y * N;
+    O[e] = s[y * PITCH + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z pass over the xz-plane at fixed y of every item.
+// Z_CONV: forward z, multiply by kernel * kscale, inverse z.  Z_FWD / Z_INV: one direction.
+// kernel is real, [N^3] in digit-reversed (position) order.
+// ---------------------------------------------------------------------------
+constexpr int Z_CONV = 0;
+constexpr int Z_FWD = 1;
+constexpr int Z_INV = 2;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_z(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + N;
+  const int tid = threadIdx.x, y = blockIdx.x, item = blockIdx.y;
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  cplx<T>* B = ibuf + (long long)item * N3 + (long long)y * N;
+  for (int e = tid; e < N2; e += NT) {
+    const int z = e / N, x = e - z * N;
+    s[z * PITCH + x] = B[(long long)z * N2 + x];
+  }
+  __syncthreads();
+  const int line = tid % N, g = tid / N;
+  if constexpr (MODE != Z_INV) fft_lines<T, N, FWD, false>(s, tw, line, g);
+  if constexpr (MODE == Z_CONV) {
+    const T* K = kern + (long long)y * N;
+    for (int e = tid; e < N2; e += NT) {
+      const int z = e / N, x = e - z * N;
+      s[z * PITCH + x] = cscale(s[z * PITCH + x], K[(long long)z * N2 + x] * kscale);
+    }
+    __syncthreads();
+  }
+  if constexpr (MODE != Z_FWD) fft_lines<T, N, INV, false>(s, tw, line, g);
+  for (int e = tid; e < N2; e += NT) {
+    const int z = e / N, x = e - z * N;
+    B[(long long)z * N2 + x] = s[z * PITCH + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse xy pass.
+// INV_WRITE: out field (o0 + t*ot) plane z = scale * IFFT_xy(ibuf item t).
+// INV_ACCUM: out field (o0 + t*ot) plane z += scale * sum_k P_(t,k) * IFFT_xy(ibuf item t*kdim+k).
+// Grid (N, targets). In INV_WRITE mode ob may be ibuf itself (in place: each
+// CTA reads its whole plane before it writes it back).
+// ---------------------------------------------------------------------------
+constexpr int INV_WRITE = 0;
+constexpr int INV_ACCUM = 1;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_xy_inv(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm,
+             T scale, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr int EPT = (N2 + NT - 1) / NT;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + N;
+  const int tid = threadIdx.x, z = blockIdx.x, t = blockIdx.y;
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  const int line = tid % N, g = tid / N;
+  cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z * N2;
+  if constexpr (MODE == INV_WRITE) {
+    const cplx<T>* I = ibuf + (long long)t * N3 + (long long)z * N2;
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = I[e];
+    }
+    __syncthreads();
+    fft_lines<T, N, INV, false>(s, tw, line, g);
+    fft_lines<T, N, INV, true>(s, tw, line, g);
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      O[e] = cscale(s[y * PITCH + x], scale);
+    }
+  } else {
+    cplx<T> acc[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) acc[i] = {T(0), T(0)};
+    for (int k = 0; k < pm.kdim; ++k) {
+      const long long item = (long long)t * pm.kdim + k;
+      const cplx<T>* I = ibuf + item * N3 + (long long)z * N2;
+      for (int e = tid; e < N2; e += NT) {
+        const int y = e / N, x = e - y * N;
+        s[y * PITCH + x] = I[e];
+      }
+      __syncthreads();
+      fft_lines<T, N, INV, false>(s, tw, line, g);
+      fft_lines<T, N, INV, true>(s, tw, line, g);
+      const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)t * pm.pt, z, N3, N2);
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + i * NT;
+        if (e < N2) {
+          const int y = e / N, x = e - y * N;
+          acc[i] = cadd(acc[i], cmul(P[e], s[y * PITCH + x]));
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * NT;
+      if (e < N2) O[e] = cadd(O[e], cscale(acc[i], scale));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise kernels
+// ---------------------------------------------------------------------------
+
+// drho[b](r) = sum_v conj(phi_v(r)) a_{b,v}(r)
+template <typename T>
+__global__ void k_delta_rho(const cplx<T>* __restrict__ phi, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ drho,
+                            int nocc, int nb, long long n3) {
+  const long long total = (long long)nb * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / n3, r = i - b * n3;
+    cplx<T> acc = {T(0), T(0)};
+    const cplx<T>* ab = a + b * nocc * n3 + r;
+    for (int v = 0; v < nocc; ++v) acc = cadd(acc, cmulc(phi[(long long)v * n3 + r], ab[(long long)v * n3]));
+    drho[i] = acc;
+  }
+}
+
+// out[b,v](r) = vloc(r) a_{b,v}(r) + phi_v(r) (W_b(r) + fxc(r) drho_b(r))
+// Each factor is optional (null pointer = absent).
+template <typename T>
+__global__ void k_init_out(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ phi, const T* __restrict__ vloc,
+                           const cplx<T>* __restrict__ wconv, const T* __restrict__ fxc, const cplx<T>* __restrict__ drho,
+                           cplx<T>* __restrict__ out, int nocc, int nb, long long n3) {
+  const long long total = (long long)nb * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / n3, r = i - b * n3;
+    cplx<T> W = {T(0), T(0)};
+    if (wconv) W = wconv[i];
+    if (fxc) W = cadd(W, cscale(drho[i], fxc[r]));
+    const bool k1e = (wconv != nullptr) || (fxc != nullptr);
+    const T vl = vloc ? vloc[r] : T(0);
+    for (int v = 0; v < nocc; ++v) {
+      const long long o = (b * nocc + v) * n3 + r;
+      cplx<T> val = {T(0), T(0)};
+      if (vloc) val = cscale(a[o], vl);
+      if (k1e) val = cadd(val, cmul(phi[(long long)v * n3 + r], W));
+      out[o] = val;
+    }
+  }
+}
+
+// cube[f][pos[g]] = s * c[f][g]  (cube zeroed beforehand)
+template <typename T>
+__global__ void k_scatter(const cplx<T>* __restrict__ c, cplx<T>* __restrict__ cube, const int* __restrict__ pos, int npw,
+                          int nf, T s, long long n3) {
+  const long long total = (long long)nf * npw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npw, g = i - f * npw;
+    cube[f * n3 + pos[g]] = cscale(c[i], s);
+  }
+}
+
+// out[f][g] = s * cube[f][pos[g]] (+ (g2h[g] - eps[(f0+f) % nocc]) * A[f][g] when A != null)
+template <typename T>
+__global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict__ pos, int npw, int nf, T s,
+                         const cplx<T>* __restrict__ A, const T* __restrict__ g2h, const T* __restrict__ eps, int nocc,
+                         int f0, cplx<T>* __restrict__ out, long long n3) {
+  const long long total = (long long)nf * npw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npw, g = i - f * npw;
+    cplx<T> v = cscale(cube[f * n3 + pos[g]], s);
+    if (A) v = cadd(v, cscale(A[i], g2h[g] - eps[(f0 + f) % nocc]));
+    out[i] = v;
+  }
+}
+
+// K1d contraction for one block of pairs (v in I, v' in J), tau[(vi*TJ + vj)] = Conv[conj(phi_v') phi_v]:
+//   out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
+//   and, when I != J, out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj]).
+// One thread per grid point of a chunk of PTS points; each thread keeps the tau
+// values of its point in its own column of shared memory (no sharing, no sync).
+template <typename T, int TB, int PTS>
+__global__ void __launch_bounds__(PTS)
+    k_k1d_contract(const cplx<T>* __restrict__ tau, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out, int i0,
+                   int ti, int j0, int tj, int nocc, int nb, T s, long long n3) {
+  __shared__ cplx<T> st[TB * TB][PTS];
+  const long long r = (long long)blockIdx.x * PTS + threadIdx.x;
+  const bool ok = r < n3;
+  for (int p = 0; p < TB * TB; ++p) {
+    const int vi = p / TB, vj = p - vi * TB;
+    st[p][threadIdx.x] = (ok && vi < ti && vj < tj) ? tau[(long long)(vi * tj + vj) * n3 + r] : cplx<T>{T(0), T(0)};
+  }
+  if (!ok) return;
+  const bool offdiag = (i0 != j0);
+  for (int b = 0; b < nb; ++b) {
+    const cplx<T>* ab = a + (long long)b * nocc * n3 + r;
+    cplx<T>* ob = out + (long long)b * nocc * n3 + r;
+    cplx<T> aJ[TB], aI[TB], accI[TB], accJ[TB];
+#pragma unroll
+    for (int q = 0; q < TB; ++q) {
+      aJ[q] = (q < tj) ? ab[(long long)(j0 + q) * n3] : cplx<T>{T(0), T(0)};
+      aI[q] = (q < ti && offdiag) ? ab[(long long)(i0 + q) * n3] : cplx<T>{T(0), T(0)};
+      accI[q] = {T(0), T(0)};
+      accJ[q] = {T(0), T(0)};
+    }
+#pragma unroll
+    for (int vi = 0; vi < TB; ++vi) {
+#pragma unroll
+      for (int vj = 0; vj < TB; ++vj) {
+        const cplx<T> tv = st[vi * TB + vj][threadIdx.x];
+        accI[vi] = cadd(accI[vi], cmul(aJ[vj], tv));
+        if (offdiag) accJ[vj] = cadd(accJ[vj], cmulc(tv, aI[vi]));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < TB; ++q) {
+      if (q < ti) {
+        cplx<T>* o = ob + (long long)(i0 + q) * n3;
+        *o = cadd(*o, cscale(accI[q], s));
+      }
+      if (offdiag && q < tj) {
+        cplx<T>* o = ob + (long long)(j0 + q) * n3;
+        *o = cadd(*o, cscale(accJ[q], s));
+      }
+    }
+  }
+}
+
+}  // namespace tddft

@@ -1,0 +1,974 @@
+// C ABI of the Liouville-operator library: system set-up, L.A, the adjoint of
+// omega = <X|L X>, and a block-Davidson driver. Host code plus the small
+// pointwise kernels; the FFT plane kernels live in plane_f32.cu / plane_f64.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tddft.h"
+#include "gemm.cuh"
+#include "plane_ops.cuh"
+
+using namespace tddft;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static tddft_status fail(tddft_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                                 \
+  do {                                                                                                 \
+    cudaError_t _e = (expr);                                                                           \
+    if (_e != cudaSuccess)                                                                             \
+      return fail(_e == cudaErrorMemoryAllocation ? TDDFT_ENOMEM : TDDFT_ECUDA,                        \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                                 \
+  } while (0)
+
+#define STATUS_TRY(expr)                  \
+  do {                                    \
+    tddft_status _s = (expr);             \
+    if (_s != TDDFT_OK) return _s;        \
+  } while (0)
+
+static tddft_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(TDDFT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return TDDFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting and the optional per-class profiler (process-wide, not thread-safe)
+// ---------------------------------------------------------------------------
+namespace {
+struct Profiler {
+  bool on = false;
+  long long launches = 0;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cls;        // class of event pair i
+  std::vector<double> bytes;   // algorithmic bytes of event pair i
+  size_t used = 0;
+  cudaEvent_t pending = nullptr;
+};
+Profiler g_prof;
+}  // namespace
+
+void tddft::note_launch() { ++g_prof.launches; }
+
+void tddft::prof_begin(int c, cudaStream_t st) {
+  if (!g_prof.on) return;
+  const size_t need = 2 * (g_prof.used + 1);
+  while (g_prof.pool.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      g_prof.on = false;
+      return;
+    }
+    g_prof.pool.push_back(e);
+  }
+  cudaEventRecord(g_prof.pool[2 * g_prof.used], st);
+  (void)c;
+}
+
+void tddft::prof_end(int c, cudaStream_t st, double bytes) {
+  if (!g_prof.on) return;
+  cudaEventRecord(g_prof.pool[2 * g_prof.used + 1], st);
+  if (g_prof.cls.size() <= g_prof.used) {
+    g_prof.cls.push_back(c);
+    g_prof.bytes.push_back(bytes);
+  } else {
+    g_prof.cls[g_prof.used] = c;
+    g_prof.bytes[g_prof.used] = bytes;
+  }
+  ++g_prof.used;
+}
+
+static int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  return (int)std::max(1LL, std::min(g, 148LL * 32));
+}
+
+// ---------------------------------------------------------------------------
+// sphere and radix plans (host)
+// ---------------------------------------------------------------------------
+struct Miller {
+  long long m2;
+  int x, y, z;
+};
+
+static tddft_status build_sphere(int n, double a, double ecut, std::vector<Miller>& out) {
+  if (n < 2 || (n & 1)) return fail(TDDFT_EINVAL, "grid size must be even and >= 2");
+  if (!(a > 0.0) || !(ecut > 0.0)) return fail(TDDFT_EINVAL, "cell side and cutoff must be positive");
+  const int h = n / 2;
+  const double tpiba = 2.0 * M_PI / a;
+  const double tpiba2 = tpiba * tpiba;
+  out.clear();
+  for (int z = -h; z < n - h; ++z)
+    for (int y = -h; y < n - h; ++y)
+      for (int x = -h; x < n - h; ++x) {
+        const long long m2 = (long long)x * x + (long long)y * y + (long long)z * z;
+        const double g2 = tpiba2 * (double)m2;
+        if (0.5 * g2 < ecut) {
+          if (std::abs(x) >= h || std::abs(y) >= h || std::abs(z) >= h)
+            return fail(TDDFT_EINVAL, "wavefunction sphere does not fit inside the FFT grid");
+          out.push_back({m2, x, y, z});
+        }
+      }
+  std::sort(out.begin(), out.end(), [](const Miller& p, const Miller& q) {
+    return std::tie(p.m2, p.x, p.y, p.z) < std::tie(q.m2, q.x, q.y, q.z);
+  });
+  return TDDFT_OK;
+}
+
+static std::vector<int> plan_radices(int n) {
+  switch (n) {
+#define TDDFT_CASE(NN) \
+  case NN:             \
+    return std::vector<int>(std::begin(Plan<NN>::r), std::end(Plan<NN>::r));
+    TDDFT_CASE(8)
+    TDDFT_CASE(12)
+    TDDFT_CASE(16)
+    TDDFT_CASE(24)
+    TDDFT_CASE(32)
+    TDDFT_CASE(36)
+    TDDFT_CASE(48)
+    TDDFT_CASE(64)
+    TDDFT_CASE(72)
+    TDDFT_CASE(80)
+    TDDFT_CASE(96)
+    TDDFT_CASE(108)
+    TDDFT_CASE(128)
+#undef TDDFT_CASE
+    default:
+      return {};
+  }
+}
+
+// Position of frequency k after the in-place DIF stages of the plan.
+static int dif_position(int k, const std::vector<int>& radices, int n) {
+  int pos = 0, len = n, kk = k;
+  for (int r : radices) {
+    const int m = len / r;
+    pos += m * (kk % r);
+    kk /= r;
+    len = m;
+  }
+  return pos;
+}
+
+// ---------------------------------------------------------------------------
+// pointwise kernels used by the adjoint and Davidson
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cast(const cplx<double>* __restrict__ in, cplx<T>* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = {(T)in[i].x, (T)in[i].y};
+}
+
+template <typename T>
+__global__ void k_widen(const cplx<T>* __restrict__ in, cplx<double>* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = {(double)in[i].x, (double)in[i].y};
+}
+
+// out[r] = s * in[r] for real tables
+template <typename T>
+__global__ void k_real_cast(const double* __restrict__ in, T* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
+// omega[b] = Re sum_i conj(p[b][i]) y[b][i], one block per b (FP64 accumulation)
+template <typename T>
+__global__ void k_bilinear(const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ y, long long len,
+                           double* __restrict__ omega) {
+  __shared__ double red[256];
+  const long long b = blockIdx.x;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+    const cplx<T> u = p[b * len + i], v = y[b * len + i];
+    acc += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) omega[b] = red[0];
+}
+
+// g[u](r) += w * p[u](r) * conj(W(r))   (u over nocc fields)
+template <typename T>
+__global__ void k_grad_k1e(const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ W, cplx<T>* __restrict__ g,
+                           int nocc, T w, long long n3) {
+  const long long total = (long long)nocc * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i % n3;
+    g[i] = cadd(g[i], cscale(cmul(p[i], cconj(W[r])), w));
+  }
+}
+
+// W(r) += fxc(r) drho(r)   (fxc may be null)
+template <typename T>
+__global__ void k_add_fxc(cplx<T>* __restrict__ W, const T* __restrict__ fxc, const cplx<T>* __restrict__ drho,
+                          long long n3) {
+  if (!fxc) return;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n3; r += (long long)gridDim.x * blockDim.x)
+    W[r] = cadd(W[r], cscale(drho[r], fxc[r]));
+}
+
+// gv[r] += s * sum_v |p[v](r)|^2
+template <typename T>
+__global__ void k_grad_vloc(const cplx<T>* __restrict__ p, int nocc, double s, double* __restrict__ gv, long long n3) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n3; r += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      const cplx<T> u = p[(long long)v * n3 + r];
+      acc += (double)u.x * (double)u.x + (double)u.y * (double)u.y;
+    }
+    gv[r] += s * acc;
+  }
+}
+
+// Ct[k][u] = -w[k / nocc] * conj(C[u][k])   (C is [M][K])
+template <typename T>
+__global__ void k_proj_grad_coef(const cplx<T>* __restrict__ C, int M, int K, int nocc, const double* __restrict__ w,
+                                 cplx<T>* __restrict__ Ct) {
+  const long long total = (long long)M * K;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long u = i / K, k = i - u * K;
+    const T s = (T)(-w[k / nocc]);
+    const cplx<T> c = C[i];
+    Ct[k * M + u] = {s * c.x, -s * c.y};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+struct Buffers {
+  void* tw = nullptr;          // [n] twiddles
+  void* kx = nullptr;          // [n^3] real, exchange kernel / N_r, position order
+  void* kh = nullptr;          // [n^3] real, Hartree kernel / N_r
+  int* pos = nullptr;          // [npw] cube position of each sphere point
+  void* g2h = nullptr;         // [npw] real, |G|^2 / 2
+  void* eps = nullptr;         // [nocc_src] real
+  void* phi_src_pw = nullptr;  // [nocc_src][npw]
+  void* phi_tgt_pw = nullptr;  // [nocc_tgt][npw] (aliases phi_src_pw for SC)
+  cplx<double>* phi_tgt_pw64 = nullptr;  // FP64 copy for Davidson
+  void* phi_src_r = nullptr;   // [nocc_src][n^3]
+  void* phi_tgt_r = nullptr;   // [nocc_tgt][n^3] (aliases for SC)
+  void* vloc = nullptr;        // [n^3] real or null
+  void* fxc = nullptr;         // [n^3] real or null
+  void* a_r = nullptr;         // [nb_chunk*nocc_src][n^3]
+  void* out_r = nullptr;       // [nb_chunk*nocc_src][n^3]
+  void* drho = nullptr;        // [nb_chunk][n^3]
+  void* wb = nullptr;          // [nb_chunk][n^3]
+  void* ibuf = nullptr;        // [ibuf_fields][n^3]
+  void* cpart = nullptr;       // projector split-K partials
+  void* cmat = nullptr;        // projector overlaps [nocc_tgt][nb_max*nocc_src]
+  void* ctmp = nullptr;        // [nb_max*nocc_src][nocc_tgt]
+  void* io_a = nullptr;        // staging for host-buffer calls / adjoint [nb_max][nocc_src][npw]
+  void* io_b = nullptr;
+  void* grad_r = nullptr;      // [nocc_src][n^3] (adjoint)
+  double* wdev = nullptr;      // [nb_max]
+};
+
+struct tddft_system {
+  tddft_desc d{};
+  int npw = 0, n = 0;
+  long long n3 = 0;
+  int nb_chunk = 0;
+  int ibuf_fields = 0;
+  int tile_targets = 8, tile_sources = 8, k1d_block = 8;
+  int nsplit = 1;
+  size_t bytes = 0;
+  Buffers b;
+  std::vector<void*> allocations;
+  PlaneOps<float> ops32;
+  PlaneOps<double> ops64;
+  bool sf() const { return d.spin_mode == TDDFT_SPIN_FLIP; }
+  size_t esz() const { return d.precision == TDDFT_PREC_FP64 ? 16 : 8; }
+  size_t rsz() const { return d.precision == TDDFT_PREC_FP64 ? 8 : 4; }
+};
+
+static tddft_status dalloc(tddft_system* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return TDDFT_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  h->allocations.push_back(*p);
+  h->bytes += bytes;
+  return TDDFT_OK;
+}
+
+template <typename T>
+static PlaneOps<T>& ops_of(tddft_system* h);
+template <>
+PlaneOps<float>& ops_of<float>(tddft_system* h) { return h->ops32; }
+template <>
+PlaneOps<double>& ops_of<double>(tddft_system* h) { return h->ops64; }
+
+// ---------------------------------------------------------------------------
+// building blocks of the apply (templated on the working precision)
+// ---------------------------------------------------------------------------
+
+// real-space fields dst[f] (f < nf) from plane-wave rows src[f] (Omega^{-1/2} normalisation)
+template <typename T>
+static tddft_status pw_to_real(tddft_system* h, const cplx<T>* src, int nf, cplx<T>* dst, cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  const T s = (T)(1.0 / std::sqrt(h->d.a * h->d.a * h->d.a));
+  for (int f0 = 0; f0 < nf; f0 += h->ibuf_fields) {
+    const int cnt = std::min(h->ibuf_fields, nf - f0);
+    CUDA_TRY(cudaMemsetAsync(ib, 0, (size_t)cnt * h->n3 * sizeof(cplx<T>), st));
+    { k_scatter<T><<<grid_for((long long)cnt * h->npw, 256), 256, 0, st>>>(src + (long long)f0 * h->npw, ib, h->b.pos,
+                                                                         h->npw, cnt, s, h->n3); note_launch(); }
+    o.z(Z_INV, ib, cnt, nullptr, T(1), tw, st);
+    PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, f0, 1};
+    o.xy_inv(INV_WRITE, ib, dst, nullptr, pm, cnt, T(1), tw, st);
+  }
+  return check_launch("pw_to_real");
+}
+
+// plane-wave rows dst[f] = Omega^{1/2}/N_r F[src[f]] on the sphere, plus the
+// diagonal term (|G|^2/2 - eps_v) A[f] when A is given (v = (f0 + f) % nocc_src).
+template <typename T>
+static tddft_status real_to_pw(tddft_system* h, const cplx<T>* src, int nf, cplx<T>* dst, const cplx<T>* A,
+                               cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  const T s = (T)(std::sqrt(h->d.a * h->d.a * h->d.a) / (double)h->n3);
+  for (int f0 = 0; f0 < nf; f0 += h->ibuf_fields) {
+    const int cnt = std::min(h->ibuf_fields, nf - f0);
+    PairMap pm{1, 0, 0, 0, f0, 0, 1, 0, 0, 0, 0, 0};
+    o.xy_fwd(XY_LOAD, nullptr, src, pm, cnt, ib, tw, st);
+    o.z(Z_FWD, ib, cnt, nullptr, T(1), tw, st);
+    { k_gather<T><<<grid_for((long long)cnt * h->npw, 256), 256, 0, st>>>(
+        ib, h->b.pos, h->npw, cnt, s, A ? A + (long long)f0 * h->npw : nullptr, (const T*)h->b.g2h,
+        (const T*)h->b.eps, h->d.nocc_src, f0, dst + (long long)f0 * h->npw, h->n3); note_launch(); }
+  }
+  return check_launch("real_to_pw");
+}
+
+// Y[n][:] -= sum_m Phi[m][:] <Phi_m|Y_n>  for nrows rows of length npw
+template <typename T>
+static tddft_status project_rows(tddft_system* h, const cplx<T>* phi, int M, cplx<T>* Y, int nrows, cudaStream_t st) {
+  if (nrows <= 0 || M <= 0) return TDDFT_OK;
+  const int K = h->npw;
+  cplx<T>* C = (cplx<T>*)h->b.cmat;
+  cplx<T>* Cp = (cplx<T>*)h->b.cpart;
+  const int nsplit = h->nsplit;
+  const int kchunk = ((K + nsplit - 1) / nsplit + 15) / 16 * 16;
+  dim3 g1((M + 31) / 32, (nrows + 31) / 32, nsplit);
+  { k_overlap<T><<<g1, 256, 0, st>>>(phi, M, Y, nrows, K, kchunk, Cp); note_launch(); }
+  { k_reduce_split<T><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(Cp, nsplit, (long long)M * nrows, C); note_launch(); }
+  dim3 g2((K + 63) / 64, (nrows + 31) / 32);
+  { k_update<T><<<g2, 256, 0, st>>>(phi, M, C, nrows, K, T(-1), Y); note_launch(); }
+  return check_launch("project_rows");
+}
+
+// Conv_kappa of nf fields src[f] into dst[f] (dst may equal src)
+template <typename T>
+static tddft_status convolve_fields(tddft_system* h, const cplx<T>* src, int nf, const T* kern, T kscale, cplx<T>* dst,
+                                    cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  for (int f0 = 0; f0 < nf; f0 += h->ibuf_fields) {
+    const int cnt = std::min(h->ibuf_fields, nf - f0);
+    PairMap pin{1, 0, 0, 0, f0, 0, 1, 0, 0, 0, 0, 0};
+    o.xy_fwd(XY_LOAD, nullptr, src, pin, cnt, ib, tw, st);
+    o.z(Z_CONV, ib, cnt, kern, kscale, tw, st);
+    PairMap pout{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, f0, 1};
+    o.xy_inv(INV_WRITE, ib, dst, nullptr, pout, cnt, T(1), tw, st);
+  }
+  return check_launch("convolve_fields");
+}
+
+// out[o0 + t*ot] += scale * sum_k P_(t,k) Conv_x[conj(Q_(t,k)) R_(t,k)] over a grid of
+// ntargets x nsources pairs, tiled into batches that fit the intermediate buffer.
+// qm/rm/pm give the affine field maps in terms of (t, k) relative to the tile origin.
+struct PairGrid {
+  int ntargets, nsources;
+  // field index = base + k * ks + t * ts
+  int q_base, q_ks, q_ts;
+  int r_base, r_ks, r_ts;
+  int p_base, p_ks, p_ts;
+  int o_base, o_ts;
+};
+
+template <typename T>
+static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cplx<T>* rb, const cplx<T>* pb,
+                                    cplx<T>* ob, const PairGrid& pg, const T* kern, T scale, cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  int TT = std::max(1, std::min(h->tile_targets, pg.ntargets));
+  int KS = std::max(1, std::min(h->tile_sources, pg.nsources));
+  while (TT * KS > h->ibuf_fields) {
+    if (KS > 1) KS = (KS + 1) / 2;
+    else TT = (TT + 1) / 2;
+  }
+  for (int t0 = 0; t0 < pg.ntargets; t0 += TT) {
+    const int tt = std::min(TT, pg.ntargets - t0);
+    for (int k0 = 0; k0 < pg.nsources; k0 += KS) {
+      const int kk = std::min(KS, pg.nsources - k0);
+      PairMap pm;
+      pm.kdim = kk;
+      pm.q0 = pg.q_base + k0 * pg.q_ks + t0 * pg.q_ts;
+      pm.qk = pg.q_ks;
+      pm.qt = pg.q_ts;
+      pm.r0 = pg.r_base + k0 * pg.r_ks + t0 * pg.r_ts;
+      pm.rk = pg.r_ks;
+      pm.rt = pg.r_ts;
+      pm.p0 = pg.p_base + k0 * pg.p_ks + t0 * pg.p_ts;
+      pm.pk = pg.p_ks;
+      pm.pt = pg.p_ts;
+      pm.o0 = pg.o_base + t0 * pg.o_ts;
+      pm.ot = pg.o_ts;
+      o.xy_fwd(XY_PRODUCT, qb, rb, pm, tt * kk, ib, tw, st);
+      o.z(Z_CONV, ib, tt * kk, kern, T(1), tw, st);
+      o.xy_inv(INV_ACCUM, ib, ob, pb, pm, tt, scale, tw, st);
+    }
+  }
+  return check_launch("pair_accumulate");
+}
+
+// K1d: out[b][v] -= alpha sum_v' a[b][v'] Conv_x[conj(phi_v') phi_v], tau computed once per
+// unordered block pair (I <= J) and shared by every b of the chunk.
+template <typename T>
+static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  const cplx<T>* phi = (const cplx<T>*)h->b.phi_src_r;
+  const int nocc = h->d.nocc_src;
+  int TB = std::min(h->k1d_block, nocc);
+  while (TB * TB > h->ibuf_fields) --TB;
+  const T s = (T)(-h->d.alpha);
+  for (int i0 = 0; i0 < nocc; i0 += TB) {
+    const int ti = std::min(TB, nocc - i0);
+    for (int j0 = i0; j0 < nocc; j0 += TB) {
+      const int tj = std::min(TB, nocc - j0);
+      // item = vi * tj + vj : Q = phi[j0 + vj], R = phi[i0 + vi]
+      PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
+      o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
+      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);
+      PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+      o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
+      if (sizeof(T) == 4) {
+        constexpr int PTS = 64;
+        { k_k1d_contract<T, 8, PTS><<<(unsigned)((h->n3 + PTS - 1) / PTS), PTS, 0, st>>>(
+            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
+      } else {
+        constexpr int PTS = 32;
+        { k_k1d_contract<T, 8, PTS><<<(unsigned)((h->n3 + PTS - 1) / PTS), PTS, 0, st>>>(
+            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
+      }
+    }
+  }
+  return check_launch("k1d_term");
+}
+
+// (L A) for nb trial vectors; terms of `mask` (PROJ bit included or not).
+template <typename T>
+static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T>* LA, unsigned mask, cudaStream_t st) {
+  const int nocc = h->d.nocc_src, npw = h->npw;
+  const long long n3 = h->n3;
+  const cplx<T>* phis = (const cplx<T>*)h->b.phi_src_r;
+  const cplx<T>* phit = (const cplx<T>*)h->b.phi_tgt_r;
+  cplx<T>* a_r = (cplx<T>*)h->b.a_r;
+  cplx<T>* out_r = (cplx<T>*)h->b.out_r;
+  cplx<T>* drho = (cplx<T>*)h->b.drho;
+  cplx<T>* wb = (cplx<T>*)h->b.wb;
+  const bool k1e_h = (mask & TDDFT_TERM_K1E_H) && !h->sf();
+  const bool k1e_xc = (mask & TDDFT_TERM_K1E_XC) && h->b.fxc;
+  const bool vloc = (mask & TDDFT_TERM_D_VLOC) && h->b.vloc;
+  for (int b0 = 0; b0 < nb; b0 += h->nb_chunk) {
+    const int nbc = std::min(h->nb_chunk, nb - b0);
+    const int nf = nbc * nocc;
+    const cplx<T>* Ab = A + (long long)b0 * nocc * npw;
+    STATUS_TRY(pw_to_real<T>(h, Ab, nf, a_r, st));
+    if (k1e_h || k1e_xc)
+      { k_delta_rho<T><<<grid_for((long long)nbc * n3, 256), 256, 0, st>>>(phis, a_r, drho, nocc, nbc, n3); note_launch(); }
+    if (k1e_h) STATUS_TRY(convolve_fields<T>(h, drho, nbc, (const T*)h->b.kh, T(1), wb, st));
+    { k_init_out<T><<<grid_for((long long)nbc * n3, 256), 256, 0, st>>>(
+        a_r, phis, vloc ? (const T*)h->b.vloc : nullptr, k1e_h ? wb : nullptr, k1e_xc ? (const T*)h->b.fxc : nullptr,
+        drho, out_r, nocc, nbc, n3); note_launch(); }
+    STATUS_TRY(check_launch("init_out"));
+    if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0) {
+      // out[t] += -alpha sum_w phi_w Conv_x[conj(phi_w) a_t],  t = (b, v)
+      PairGrid pg{nf, h->d.nocc_tgt, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
+      STATUS_TRY(pair_accumulate<T>(h, phit, a_r, phit, out_r, pg, (const T*)h->b.kx, (T)(-h->d.alpha), st));
+    }
+    if ((mask & TDDFT_TERM_K1D) && h->d.alpha != 0.0) STATUS_TRY(k1d_term<T>(h, nbc, st));
+    STATUS_TRY(real_to_pw<T>(h, out_r, nf, LA + (long long)b0 * nocc * npw,
+                             (mask & TDDFT_TERM_D_KIN) ? Ab : nullptr, st));
+  }
+  if (mask & TDDFT_TERM_PROJ)
+    STATUS_TRY(project_rows<T>(h, (const cplx<T>*)h->b.phi_tgt_pw, h->d.nocc_tgt, LA, nb * nocc, st));
+  return TDDFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// init
+// ---------------------------------------------------------------------------
+static bool supported_n(int n, int prec) {
+  static const int sizes[] = {8, 12, 16, 24, 32, 36, 48, 64, 72, 80, 96, 108, 128};
+  for (int s : sizes)
+    if (s == n) return !(prec == TDDFT_PREC_FP64 && n == 128);
+  return false;
+}
+
+template <typename T>
+static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStream_t st) {
+  const int n = h->n, npw = h->npw;
+  const long long n3 = h->n3;
+  const tddft_desc& d = h->d;
+  PlaneOps<T>& o = ops_of<T>(h);
+  o = plane_ops_for<T>(n);
+  if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
+  CUDA_TRY(o.prepare());
+
+  std::vector<int> radices = plan_radices(n);
+  std::vector<int> rev(n);
+  for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
+
+  // twiddles W_n^e = exp(-2 pi i e / n) in FP64 on the host, rounded once
+  std::vector<cplx<T>> tw(n);
+  for (int e = 0; e < n; ++e) {
+    const double ang = -2.0 * M_PI * (double)e / (double)n;
+    tw[e] = {(T)std::cos(ang), (T)std::sin(ang)};
+  }
+  // kernels in position order, divided by N_r
+  const double tpiba = 2.0 * M_PI / d.a, tpiba2 = tpiba * tpiba;
+  std::vector<T> kx(n3), kh(n3);
+  auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
+  for (int kz = 0; kz < n; ++kz)
+    for (int ky = 0; ky < n; ++ky)
+      for (int kxx = 0; kxx < n; ++kxx) {
+        const long long m2 = (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
+        const double g2 = tpiba2 * (double)m2;
+        const double vx = m2 == 0 ? d.kx_g0 : 4.0 * M_PI / g2;
+        const double vh = m2 == 0 ? 0.0 : 4.0 * M_PI / g2;
+        const long long p = ((long long)rev[kz] * n + rev[ky]) * n + rev[kxx];
+        kx[p] = (T)(vx / (double)n3);
+        kh[p] = (T)(vh / (double)n3);
+      }
+  std::vector<Miller> sph;
+  STATUS_TRY(build_sphere(n, d.a, d.ecut, sph));
+  std::vector<int> pos(npw);
+  std::vector<T> g2h(npw);
+  for (int i = 0; i < npw; ++i) {
+    const int px = rev[(sph[i].x % n + n) % n], py = rev[(sph[i].y % n + n) % n], pz = rev[(sph[i].z % n + n) % n];
+    pos[i] = (pz * n + py) * n + px;
+    g2h[i] = (T)(0.5 * (tpiba2 * (double)sph[i].m2));
+  }
+  std::vector<T> eps(d.nocc_src);
+  for (int v = 0; v < d.nocc_src; ++v) eps[v] = (T)in->eps_src[v];
+
+  Buffers& B = h->b;
+  const size_t ez = sizeof(cplx<T>), rz = sizeof(T);
+  STATUS_TRY(dalloc(h, &B.tw, n * ez));
+  STATUS_TRY(dalloc(h, &B.kx, n3 * rz));
+  STATUS_TRY(dalloc(h, &B.kh, n3 * rz));
+  STATUS_TRY(dalloc(h, (void**)&B.pos, npw * sizeof(int)));
+  STATUS_TRY(dalloc(h, &B.g2h, npw * rz));
+  STATUS_TRY(dalloc(h, &B.eps, d.nocc_src * rz));
+  CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), n * ez, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.kx, kx.data(), n3 * rz, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.kh, kh.data(), n3 * rz, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.pos, pos.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.g2h, g2h.data(), npw * rz, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.eps, eps.data(), d.nocc_src * rz, cudaMemcpyHostToDevice, st));
+
+  // orbitals: FP64 upload, orthonormality check, cast to the working precision
+  const int nsets = h->sf() ? 2 : 1;
+  const int ntgt = d.nocc_tgt;
+  STATUS_TRY(dalloc(h, (void**)&B.phi_tgt_pw64, (size_t)ntgt * npw * sizeof(cplx<double>)));
+  cplx<double>* phi_src64 = nullptr;
+  STATUS_TRY(dalloc(h, (void**)&phi_src64, (size_t)d.nocc_src * npw * sizeof(cplx<double>)));
+  CUDA_TRY(cudaMemcpyAsync(phi_src64, in->phi_src, (size_t)d.nocc_src * npw * 16, cudaMemcpyHostToDevice, st));
+  if (h->sf())
+    CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, in->phi_tgt, (size_t)ntgt * npw * 16, cudaMemcpyHostToDevice, st));
+  else
+    CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, phi_src64, (size_t)ntgt * npw * 16, cudaMemcpyDeviceToDevice, st));
+
+  // projector scratch sized for nb_max * nocc_src rows (also used for the checks below)
+  const int maxrows = std::max(d.nb_max * d.nocc_src, std::max(d.nocc_src, ntgt));
+  h->nsplit = std::max(1, std::min(32, npw / 512));
+  STATUS_TRY(dalloc(h, &B.cmat, (size_t)std::max(ntgt, d.nocc_src) * maxrows * sizeof(cplx<double>)));
+  STATUS_TRY(dalloc(h, &B.cpart, (size_t)h->nsplit * std::max(ntgt, d.nocc_src) * maxrows * sizeof(cplx<double>)));
+  STATUS_TRY(dalloc(h, &B.ctmp, (size_t)std::max(ntgt, d.nocc_src) * maxrows * sizeof(cplx<double>)));
+
+  for (int set = 0; set < nsets; ++set) {
+    const cplx<double>* P = set == 0 ? phi_src64 : B.phi_tgt_pw64;
+    const int M = set == 0 ? d.nocc_src : ntgt;
+    cplx<double>* C = (cplx<double>*)B.cmat;
+    cplx<double>* Cp = (cplx<double>*)B.cpart;
+    const int kchunk = ((npw + h->nsplit - 1) / h->nsplit + 15) / 16 * 16;
+    dim3 g1((M + 31) / 32, (M + 31) / 32, h->nsplit);
+    { k_overlap<double><<<g1, 256, 0, st>>>(P, M, P, M, npw, kchunk, Cp); note_launch(); }
+    { k_reduce_split<double><<<grid_for((long long)M * M, 256), 256, 0, st>>>(Cp, h->nsplit, (long long)M * M, C); note_launch(); }
+    STATUS_TRY(check_launch("orthonormality check"));
+    std::vector<cplx<double>> hc((size_t)M * M);
+    CUDA_TRY(cudaMemcpyAsync(hc.data(), C, hc.size() * 16, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    double dev = 0.0;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        const cplx<double> c = hc[(size_t)i * M + j];
+        dev = std::max(dev, std::hypot(c.x - (i == j ? 1.0 : 0.0), c.y));
+      }
+    if (!(dev <= 1e-10))
+      return fail(TDDFT_EINVAL, "orbitals are not orthonormal: max |Phi^H Phi - I| = " + std::to_string(dev));
+  }
+
+  STATUS_TRY(dalloc(h, &B.phi_src_pw, (size_t)d.nocc_src * npw * ez));
+  { k_cast<T><<<grid_for((long long)d.nocc_src * npw, 256), 256, 0, st>>>(phi_src64, (cplx<T>*)B.phi_src_pw,
+                                                                        (long long)d.nocc_src * npw); note_launch(); }
+  if (h->sf()) {
+    STATUS_TRY(dalloc(h, &B.phi_tgt_pw, (size_t)ntgt * npw * ez));
+    { k_cast<T><<<grid_for((long long)ntgt * npw, 256), 256, 0, st>>>(B.phi_tgt_pw64, (cplx<T>*)B.phi_tgt_pw,
+                                                                    (long long)ntgt * npw); note_launch(); }
+  } else {
+    B.phi_tgt_pw = B.phi_src_pw;
+  }
+  STATUS_TRY(check_launch("orbital cast"));
+
+  // local fields
+  double* tmp64 = nullptr;
+  if (in->vloc || in->fxc) {
+    CUDA_TRY(cudaMalloc((void**)&tmp64, n3 * sizeof(double)));
+  }
+  if (in->vloc) {
+    STATUS_TRY(dalloc(h, &B.vloc, n3 * rz));
+    CUDA_TRY(cudaMemcpyAsync(tmp64, in->vloc, n3 * 8, cudaMemcpyHostToDevice, st));
+    { k_real_cast<T><<<grid_for(n3, 256), 256, 0, st>>>(tmp64, (T*)B.vloc, n3); note_launch(); }
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (in->fxc) {
+    STATUS_TRY(dalloc(h, &B.fxc, n3 * rz));
+    CUDA_TRY(cudaMemcpyAsync(tmp64, in->fxc, n3 * 8, cudaMemcpyHostToDevice, st));
+    { k_real_cast<T><<<grid_for(n3, 256), 256, 0, st>>>(tmp64, (T*)B.fxc, n3); note_launch(); }
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (tmp64) CUDA_TRY(cudaFree(tmp64));
+
+  // workspace: chunk of trial vectors and the pair-batch buffer, bounded to leave
+  // room on the device (cfg-independent: at most ~60% of free memory)
+  size_t freeb = 0, totalb = 0;
+  CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+  const size_t field = (size_t)n3 * ez;
+  h->ibuf_fields = std::max(16, std::min(128, (int)((size_t)(256u << 20) / field)));
+  const size_t fixed = field * ((size_t)h->ibuf_fields + (size_t)d.nocc_src + (h->sf() ? ntgt : 0));
+  const size_t per_b = field * (2 * (size_t)d.nocc_src + 2);
+  const size_t budget = (size_t)(0.6 * (double)freeb);
+  if (budget < fixed + per_b) return fail(TDDFT_ENOMEM, "not enough device memory for one trial vector");
+  h->nb_chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)d.nb_max, (budget - fixed) / per_b));
+
+  STATUS_TRY(dalloc(h, &B.ibuf, (size_t)h->ibuf_fields * field));
+  STATUS_TRY(dalloc(h, &B.phi_src_r, (size_t)d.nocc_src * field));
+  STATUS_TRY(dalloc(h, &B.a_r, (size_t)h->nb_chunk * d.nocc_src * field));
+  STATUS_TRY(dalloc(h, &B.out_r, (size_t)h->nb_chunk * d.nocc_src * field));
+  STATUS_TRY(dalloc(h, &B.drho, (size_t)h->nb_chunk * field));
+  STATUS_TRY(dalloc(h, &B.wb, (size_t)h->nb_chunk * field));
+  STATUS_TRY(pw_to_real<T>(h, (const cplx<T>*)B.phi_src_pw, d.nocc_src, (cplx<T>*)B.phi_src_r, st));
+  if (h->sf()) {
+    STATUS_TRY(dalloc(h, &B.phi_tgt_r, (size_t)ntgt * field));
+    STATUS_TRY(pw_to_real<T>(h, (const cplx<T>*)B.phi_tgt_pw, ntgt, (cplx<T>*)B.phi_tgt_r, st));
+  } else {
+    B.phi_tgt_r = B.phi_src_r;
+  }
+  const size_t iob = (size_t)d.nb_max * d.nocc_src * npw * ez;
+  STATUS_TRY(dalloc(h, &B.io_a, iob));
+  STATUS_TRY(dalloc(h, &B.io_b, iob));
+  STATUS_TRY(dalloc(h, (void**)&B.wdev, (size_t)d.nb_max * sizeof(double)));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return check_launch("init");
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (spin-conserving)
+// ---------------------------------------------------------------------------
+template <typename T>
+static tddft_status adjoint_impl(tddft_system* h, int nb, const cplx<T>* X, const double* w, double* omega,
+                                 cplx<T>* grad_phi, double* grad_vloc, cudaStream_t st) {
+  const int nocc = h->d.nocc_src, npw = h->npw;
+  const long long n3 = h->n3, rows = (long long)nb * nocc;
+  Buffers& B = h->b;
+  if (!B.grad_r) STATUS_TRY(dalloc(h, &B.grad_r, (size_t)nocc * n3 * sizeof(cplx<T>)));
+  cplx<T>* P = (cplx<T>*)B.io_a;   // P^c X
+  cplx<T>* Y = (cplx<T>*)B.io_b;   // M P^c X
+  cplx<T>* G = (cplx<T>*)B.grad_r;
+  const cplx<T>* phi = (const cplx<T>*)B.phi_src_pw;
+  const cplx<T>* phi_r = (const cplx<T>*)B.phi_src_r;
+  CUDA_TRY(cudaMemcpyAsync(P, X, (size_t)rows * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st));
+  STATUS_TRY(project_rows<T>(h, phi, nocc, P, (int)rows, st));
+  const unsigned mask = TDDFT_TERMS_ALL & ~TDDFT_TERM_PROJ;
+  STATUS_TRY(apply_impl<T>(h, nb, P, Y, mask, st));
+  { k_bilinear<T><<<nb, 256, 0, st>>>(P, Y, (long long)nocc * npw, omega); note_launch(); }
+  STATUS_TRY(check_launch("bilinear"));
+
+  // real-space part of the gradient, one trial vector at a time
+  CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)nocc * n3 * sizeof(cplx<T>), st));
+  if (grad_vloc) CUDA_TRY(cudaMemsetAsync(grad_vloc, 0, (size_t)n3 * sizeof(double), st));
+  cplx<T>* p_r = (cplx<T>*)B.a_r;
+  cplx<T>* drho = (cplx<T>*)B.drho;
+  cplx<T>* wb = (cplx<T>*)B.wb;
+  const double vol = h->d.a * h->d.a * h->d.a;
+  for (int b = 0; b < nb; ++b) {
+    if (w[b] == 0.0) continue;
+    STATUS_TRY(pw_to_real<T>(h, P + (long long)b * nocc * npw, nocc, p_r, st));
+    const T wa = (T)(-h->d.alpha * w[b]);
+    if (h->d.alpha != 0.0) {
+      // -alpha w sum_v p_v Conv_x[conj(p_v) phi_u]:  target u, source v
+      PairGrid ga{nocc, nocc, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
+      STATUS_TRY(pair_accumulate<T>(h, p_r, phi_r, p_r, G, ga, (const T*)B.kx, wa, st));
+      // -alpha w sum_v phi_v Conv_x[conj(p_v) p_u]
+      PairGrid gb{nocc, nocc, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
+      STATUS_TRY(pair_accumulate<T>(h, p_r, p_r, phi_r, G, gb, (const T*)B.kx, wa, st));
+    }
+    // K1e: w p_u conj(W), W = Conv_H[drho] + f_xc drho
+    { k_delta_rho<T><<<grid_for(n3, 256), 256, 0, st>>>(phi_r, p_r, drho, nocc, 1, n3); note_launch(); }
+    STATUS_TRY(convolve_fields<T>(h, drho, 1, (const T*)B.kh, T(1), wb, st));
+    { k_add_fxc<T><<<grid_for(n3, 256), 256, 0, st>>>(wb, (const T*)B.fxc, drho, n3); note_launch(); }
+    { k_grad_k1e<T><<<grid_for((long long)nocc * n3, 256), 256, 0, st>>>(p_r, wb, G, nocc, (T)w[b], n3); note_launch(); }
+    STATUS_TRY(check_launch("adjoint k1e"));
+    if (grad_vloc)
+      { k_grad_vloc<T><<<grid_for(n3, 256), 256, 0, st>>>(p_r, nocc, w[b] * vol / (double)n3, grad_vloc, n3); note_launch(); }
+  }
+  STATUS_TRY(real_to_pw<T>(h, G, nocc, grad_phi, nullptr, st));
+
+  // projector terms: -sum_k w_b(k) [ <x_k|phi_u> y_k + <y_k|phi_u> x_k ]
+  CUDA_TRY(cudaMemcpyAsync(B.wdev, w, (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, st));
+  cplx<T>* C = (cplx<T>*)B.cmat;
+  cplx<T>* Cp = (cplx<T>*)B.cpart;
+  cplx<T>* Ct = (cplx<T>*)B.ctmp;
+  const int nsplit = h->nsplit;
+  const int kchunk = ((npw + nsplit - 1) / nsplit + 15) / 16 * 16;
+  for (int pass = 0; pass < 2; ++pass) {
+    const cplx<T>* V = pass == 0 ? X : Y;        // overlap partner
+    const cplx<T>* Wv = pass == 0 ? Y : X;       // vectors that get the coefficients
+    dim3 g1((nocc + 31) / 32, (unsigned)((rows + 31) / 32), nsplit);
+    { k_overlap<T><<<g1, 256, 0, st>>>(phi, nocc, V, (int)rows, npw, kchunk, Cp); note_launch(); }
+    { k_reduce_split<T><<<grid_for((long long)nocc * rows, 256), 256, 0, st>>>(Cp, nsplit, (long long)nocc * rows, C); note_launch(); }
+    { k_proj_grad_coef<T><<<grid_for((long long)nocc * rows, 256), 256, 0, st>>>(C, nocc, (int)rows, nocc, B.wdev, Ct); note_launch(); }
+    dim3 g2((npw + 63) / 64, (nocc + 31) / 32);
+    { k_update<T><<<g2, 256, 0, st>>>(Wv, (int)rows, Ct, nocc, npw, T(1), grad_phi); note_launch(); }
+  }
+  return check_launch("adjoint projector terms");
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* tddft_status_string(tddft_status s) {
+  switch (s) {
+    case TDDFT_OK: return "ok";
+    case TDDFT_EINVAL: return "invalid argument";
+    case TDDFT_ENOMEM: return "out of memory";
+    case TDDFT_ECUDA: return "CUDA error";
+    case TDDFT_ETIMEOUT: return "device wait timed out";
+    case TDDFT_ENUMERIC: return "numerical failure";
+    case TDDFT_ENOTCONV: return "not converged";
+    case TDDFT_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char* tddft_last_error(void) { return g_last_error.c_str(); }
+
+tddft_status tddft_sphere_size(int n, double a, double ecut, int* npw) {
+  if (!npw) return fail(TDDFT_EINVAL, "null output");
+  std::vector<Miller> s;
+  STATUS_TRY(build_sphere(n, a, ecut, s));
+  *npw = (int)s.size();
+  return TDDFT_OK;
+}
+
+tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller) {
+  if (!miller) return fail(TDDFT_EINVAL, "null output");
+  std::vector<Miller> s;
+  STATUS_TRY(build_sphere(n, a, ecut, s));
+  for (size_t i = 0; i < s.size(); ++i) {
+    miller[3 * i] = s[i].x;
+    miller[3 * i + 1] = s[i].y;
+    miller[3 * i + 2] = s[i].z;
+  }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_profile_enable(int enable) {
+  g_prof.on = enable != 0;
+  g_prof.used = 0;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, long long* total_launches) {
+  if (total_launches) *total_launches = g_prof.launches;
+  for (int c = 0; c < TDDFT_PROFILE_CLASSES; ++c) {
+    if (ms) ms[c] = 0.0;
+    if (launches) launches[c] = 0;
+    if (bytes) bytes[c] = 0.0;
+  }
+  for (size_t i = 0; i < g_prof.used; ++i) {
+    CUDA_TRY(cudaEventSynchronize(g_prof.pool[2 * i + 1]));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, g_prof.pool[2 * i], g_prof.pool[2 * i + 1]));
+    const int c = g_prof.cls[i];
+    if (ms) ms[c] += t;
+    if (launches) launches[c] += 1;
+    if (bytes) bytes[c] += g_prof.bytes[i];
+  }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_destroy(tddft_handle h) {
+  if (!h) return TDDFT_OK;
+  for (void* p : h->allocations) cudaFree(p);
+  delete h;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, void* stream, tddft_handle* out) {
+  if (!desc || !in || !out) return fail(TDDFT_EINVAL, "null argument");
+  *out = nullptr;
+  const tddft_desc& d = *desc;
+  if (d.spin_mode != TDDFT_SPIN_CONSERVING && d.spin_mode != TDDFT_SPIN_FLIP)
+    return fail(TDDFT_EINVAL, "unknown spin mode");
+  if (d.precision != TDDFT_PREC_FP64 && d.precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
+  if (!supported_n(d.n, d.precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(d.n));
+  if (d.nocc_src < 1 || d.nb_max < 1) return fail(TDDFT_EINVAL, "nocc_src and nb_max must be >= 1");
+  if (d.spin_mode == TDDFT_SPIN_CONSERVING && d.nocc_tgt != d.nocc_src)
+    return fail(TDDFT_EINVAL, "spin-conserving systems need nocc_tgt == nocc_src");
+  if (d.nocc_tgt < 1) return fail(TDDFT_EINVAL, "nocc_tgt must be >= 1");
+  if (!in->phi_src || !in->eps_src) return fail(TDDFT_EINVAL, "orbitals and eigenvalues are required");
+  if (d.spin_mode == TDDFT_SPIN_FLIP && !in->phi_tgt) return fail(TDDFT_EINVAL, "spin-flip needs phi_tgt");
+  std::vector<Miller> sph;
+  STATUS_TRY(build_sphere(d.n, d.a, d.ecut, sph));
+  if ((int)sph.size() < std::max(d.nocc_src, d.nocc_tgt))
+    return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
+  tddft_system* h = new tddft_system();
+  h->d = d;
+  h->n = d.n;
+  h->n3 = (long long)d.n * d.n * d.n;
+  h->npw = (int)sph.size();
+  cudaStream_t st = (cudaStream_t)stream;
+  tddft_status s = d.precision == TDDFT_PREC_FP64 ? init_impl<double>(h, in, st) : init_impl<float>(h, in, st);
+  if (s != TDDFT_OK) {
+    std::string msg = g_last_error;
+    tddft_destroy(h);
+    g_last_error = msg;
+    return s;
+  }
+  *out = h;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_query(tddft_handle h, tddft_info* info) {
+  if (!h || !info) return fail(TDDFT_EINVAL, "null argument");
+  info->npw = h->npw;
+  info->n = h->n;
+  info->nb_chunk = h->nb_chunk;
+  info->precision = h->d.precision;
+  info->device_bytes = h->bytes;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (term_mask & ~TDDFT_TERMS_ALL) return fail(TDDFT_EINVAL, "unknown term bits");
+  h->d.term_mask = term_mask;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_set_tiling(tddft_handle h, int targets, int sources) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (targets < 0 || sources < 0) return fail(TDDFT_EINVAL, "negative tile");
+  if (targets) h->tile_targets = targets;
+  if (sources) h->tile_sources = sources;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_apply_liouville(tddft_handle h, int nb, const void* A, void* LA, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
+  if (nb == 0) return TDDFT_OK;
+  if (!A || !LA) return fail(TDDFT_EINVAL, "null buffer");
+  if (A == LA) return fail(TDDFT_EINVAL, "A and LA must not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return apply_impl<double>(h, nb, (const cplx<double>*)A, (cplx<double>*)LA, h->d.term_mask, st);
+  return apply_impl<float>(h, nb, (const cplx<float>*)A, (cplx<float>*)LA, h->d.term_mask, st);
+}
+
+tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_host, void* LA_host, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
+  if (nb == 0) return TDDFT_OK;
+  if (!A_host || !LA_host) return fail(TDDFT_EINVAL, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)nb * h->d.nocc_src * h->npw * h->esz();
+  CUDA_TRY(cudaMemcpyAsync(h->b.io_a, A_host, bytes, cudaMemcpyHostToDevice, st));
+  STATUS_TRY(tddft_apply_liouville(h, nb, h->b.io_a, h->b.io_b, stream));
+  CUDA_TRY(cudaMemcpyAsync(LA_host, h->b.io_b, bytes, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return TDDFT_OK;
+}
+
+tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
+                                           void* grad_phi, double* grad_vloc, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (h->sf()) return fail(TDDFT_ENOTSUP, "the adjoint is implemented for spin-conserving systems");
+  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+  if (!X || !w || !omega || !grad_phi) return fail(TDDFT_EINVAL, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return adjoint_impl<double>(h, nb, (const cplx<double>*)X, w, omega, (cplx<double>*)grad_phi, grad_vloc, st);
+  return adjoint_impl<float>(h, nb, (const cplx<float>*)X, w, omega, (cplx<float>*)grad_phi, grad_vloc, st);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Davidson (filled in below)
+// ---------------------------------------------------------------------------
+struct tddft_davidson {
+  tddft_system* h = nullptr;
+};
+
+extern "C" {
+tddft_status tddft_davidson_create(tddft_handle, int, int, const double*, int, void*, tddft_dav_handle* out) {
+  if (out) *out = nullptr;
+  return fail(TDDFT_ENOTSUP, "Davidson not built yet");
+}
+tddft_status tddft_davidson_step(tddft_dav_handle, double, int*, double*, double*, void*) {
+  return fail(TDDFT_ENOTSUP, "Davidson not built yet");
+}
+tddft_status tddft_davidson_vectors(tddft_dav_handle, double*, void*) { return fail(TDDFT_ENOTSUP, "Davidson not built yet"); }
+tddft_status tddft_davidson_destroy(tddft_dav_handle d) {
+  delete d;
+  return TDDFT_OK;
+}
+}

@@ -1,0 +1,320 @@
+"""Python binding of the C ABI in include/tddft.h (argument marshalling only).
+
+Every step of the operator runs in the CUDA library libtddft.so; this module
+loads it (failing loudly when it is missing), converts arguments to plain
+pointers and sizes, and turns status codes into exceptions. PyTorch is used
+for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtddft.so")
+
+TERM_D_KIN = 1
+TERM_D_VLOC = 2
+TERM_D_EXX = 4
+TERM_K1E_H = 8
+TERM_K1E_XC = 16
+TERM_K1D = 32
+TERM_PROJ = 64
+TERMS_ALL = 127
+
+SPIN_CONSERVING = 0
+SPIN_FLIP = 1
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUMERIC", 6: "ENOTCONV", 7: "ENOTSUP"}
+
+# every entry point declared in include/tddft.h
+EXPORTS = [
+    "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
+    "tddft_set_tiling", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
+    "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
+]
+PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
+
+
+class TddftError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("a", ctypes.c_double), ("ecut", ctypes.c_double),
+                ("spin_mode", ctypes.c_int), ("nocc_src", ctypes.c_int), ("nocc_tgt", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("kx_g0", ctypes.c_double), ("precision", ctypes.c_int),
+                ("term_mask", ctypes.c_uint), ("nb_max", ctypes.c_int)]
+
+
+class Inputs(ctypes.Structure):
+    _fields_ = [("phi_src", ctypes.c_void_p), ("phi_tgt", ctypes.c_void_p), ("eps_src", ctypes.c_void_p),
+                ("vloc", ctypes.c_void_p), ("fxc", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("npw", ctypes.c_int), ("n", ctypes.c_int), ("nb_chunk", ctypes.c_int),
+                ("precision", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libtddft.so from the package directory (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "tddft_sphere_size": ([ci, cd, cd, ctypes.POINTER(ci)], st),
+        "tddft_sphere_miller": ([ci, cd, cd, vp], st),
+        "tddft_init_system": ([ctypes.POINTER(Desc), ctypes.POINTER(Inputs), vp, ctypes.POINTER(vp)], st),
+        "tddft_query": ([vp, ctypes.POINTER(Info)], st),
+        "tddft_set_terms": ([vp, ctypes.c_uint], st),
+        "tddft_set_tiling": ([vp, ci, ci], st),
+        "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
+        "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
+        "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
+        "tddft_davidson_create": ([vp, ci, ci, vp, ci, vp, ctypes.POINTER(vp)], st),
+        "tddft_davidson_step": ([vp, cd, ctypes.POINTER(ci), vp, vp, vp], st),
+        "tddft_davidson_vectors": ([vp, vp, vp], st),
+        "tddft_davidson_destroy": ([vp], st),
+        "tddft_destroy": ([vp], st),
+        "tddft_status_string": ([st], ctypes.c_char_p),
+        "tddft_last_error": ([], ctypes.c_char_p),
+        "tddft_profile_enable": ([ci], st),
+        "tddft_profile_read": ([vp, vp, vp, vp], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        detail = load().tddft_last_error().decode(errors="replace")
+        raise TddftError(status, where, detail)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data
+
+
+def sphere_size(n: int, a: float, ecut: float) -> int:
+    out = ctypes.c_int()
+    _check(load().tddft_sphere_size(n, a, ecut, ctypes.byref(out)), "tddft_sphere_size")
+    return out.value
+
+
+def sphere_miller(n: int, a: float, ecut: float) -> np.ndarray:
+    npw = sphere_size(n, a, ecut)
+    m = np.zeros((npw, 3), dtype=np.int32)
+    _check(load().tddft_sphere_miller(n, a, ecut, m.ctypes.data), "tddft_sphere_miller")
+    return m
+
+
+def profile_enable(on: bool = True):
+    _check(load().tddft_profile_enable(1 if on else 0), "tddft_profile_enable")
+
+
+def profile_read() -> dict:
+    """Per-class device time (ms), launches and algorithmic bytes, plus the library's total launch count."""
+    k = len(PROFILE_CLASSES)
+    ms = np.zeros(k)
+    nl = np.zeros(k, dtype=np.int64)
+    by = np.zeros(k)
+    tot = ctypes.c_longlong()
+    _check(load().tddft_profile_read(ms.ctypes.data, nl.ctypes.data, by.ctypes.data, ctypes.byref(tot)),
+           "tddft_profile_read")
+    return {"classes": {name: {"ms": float(ms[i]), "launches": int(nl[i]), "bytes": float(by[i])}
+                        for i, name in enumerate(PROFILE_CLASSES)}, "total_launches": int(tot.value)}
+
+
+def launch_count() -> int:
+    """Kernel launches of the library since it was loaded (no synchronisation)."""
+    tot = ctypes.c_longlong()
+    _check(load().tddft_profile_read(None, None, None, ctypes.byref(tot)), "tddft_profile_read")
+    return int(tot.value)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class LiouvilleSystem:
+    """One system on the GPU: orbitals, eigenvalues, local fields and workspace.
+
+    Inputs are FP64 host arrays (complex128 orbitals [nocc, npw] in the
+    library's sphere order, real fields [n, n, n] indexed [z, y, x]).
+    """
+
+    def __init__(self, *, n, a, ecut, phi_src, eps_src, alpha=0.18, kx_g0=0.0, precision=PREC_FP32,
+                 term_mask=TERMS_ALL, nb_max=1, spin_flip=False, phi_tgt=None, vloc=None, fxc=None, stream=None):
+        lib = load()
+        self.n, self.a, self.ecut = int(n), float(a), float(ecut)
+        self.precision = int(precision)
+        self.spin_flip = bool(spin_flip)
+        phi_src = np.ascontiguousarray(phi_src, dtype=np.complex128)
+        self.nocc_src, self.npw = phi_src.shape
+        phi_tgt_c = None if phi_tgt is None else np.ascontiguousarray(phi_tgt, dtype=np.complex128)
+        self.nocc_tgt = phi_tgt_c.shape[0] if (spin_flip and phi_tgt_c is not None) else self.nocc_src
+        eps = np.ascontiguousarray(eps_src, dtype=np.float64)
+        vl = None if vloc is None else np.ascontiguousarray(vloc, dtype=np.float64)
+        fx = None if fxc is None else np.ascontiguousarray(fxc, dtype=np.float64)
+        self.nb_max = int(nb_max)
+        d = Desc(self.n, self.a, self.ecut, SPIN_FLIP if spin_flip else SPIN_CONSERVING, self.nocc_src,
+                 self.nocc_tgt, float(alpha), float(kx_g0), self.precision, int(term_mask), self.nb_max)
+        inp = Inputs(_ptr(phi_src), _ptr(phi_tgt_c) if spin_flip else None, _ptr(eps), _ptr(vl), _ptr(fx))
+        h = ctypes.c_void_p()
+        _check(lib.tddft_init_system(ctypes.byref(d), ctypes.byref(inp), _stream_ptr(stream), ctypes.byref(h)),
+               "tddft_init_system")
+        self._h = h
+        info = Info()
+        _check(lib.tddft_query(h, ctypes.byref(info)), "tddft_query")
+        if info.npw != self.npw:
+            self.close()
+            raise ValueError(f"orbital arrays have {self.npw} coefficients, the sphere has {info.npw}")
+        self.info = {"npw": info.npw, "n": info.n, "nb_chunk": info.nb_chunk, "precision": info.precision,
+                     "device_bytes": info.device_bytes}
+
+    # -- helpers --
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == PREC_FP64 else torch.complex64
+
+    def _check_batch(self, X):
+        import torch
+        if not X.is_cuda or X.dtype != self.complex_dtype or not X.is_contiguous():
+            raise TypeError(f"expected a contiguous CUDA tensor of {self.complex_dtype}")
+        if X.dim() != 3 or X.shape[1:] != (self.nocc_src, self.npw):
+            raise ValueError(f"expected shape [nb, {self.nocc_src}, {self.npw}], got {tuple(X.shape)}")
+        return torch
+
+    def set_terms(self, mask: int):
+        _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
+
+    def set_tiling(self, targets: int = 0, sources: int = 0):
+        _check(load().tddft_set_tiling(self._h, int(targets), int(sources)), "tddft_set_tiling")
+
+    # -- calls --
+    def apply(self, X, out=None, stream=None):
+        """L X for a device batch X [nb, nocc_src, npw] (tddft_apply_liouville)."""
+        torch = self._check_batch(X)
+        if out is None:
+            out = torch.empty_like(X)
+        _check(load().tddft_apply_liouville(self._h, X.shape[0], X.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+               "tddft_apply_liouville")
+        return out
+
+    def apply_host(self, X: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """L X with host arrays (tddft_apply_liouville_host); copies happen inside the call."""
+        dt = np.complex128 if self.precision == PREC_FP64 else np.complex64
+        if X.dtype != dt or not X.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dt)} array")
+        if out is None:
+            out = np.empty_like(X)
+        _check(load().tddft_apply_liouville_host(self._h, X.shape[0], X.ctypes.data, out.ctypes.data,
+                                                 _stream_ptr(stream)), "tddft_apply_liouville_host")
+        return out
+
+    def adjoint(self, X, w, stream=None, with_vloc=True):
+        """omega_b and the gradients of sum_b w_b omega_b (tddft_apply_liouville_adjoint).
+
+        Returns (omega [nb] float64, grad_phi [nocc, npw] (Wirtinger d/dc^*), grad_vloc [n,n,n] or None).
+        """
+        torch = self._check_batch(X)
+        nb = X.shape[0]
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (nb,):
+            raise ValueError("w must have one weight per trial vector")
+        omega = torch.empty(nb, dtype=torch.float64, device=X.device)
+        gphi = torch.empty((self.nocc_src, self.npw), dtype=self.complex_dtype, device=X.device)
+        gv = torch.empty((self.n,) * 3, dtype=torch.float64, device=X.device) if with_vloc else None
+        _check(load().tddft_apply_liouville_adjoint(self._h, nb, X.data_ptr(), w.ctypes.data, omega.data_ptr(),
+                                                    gphi.data_ptr(), None if gv is None else gv.data_ptr(),
+                                                    _stream_ptr(stream)), "tddft_apply_liouville_adjoint")
+        return omega, gphi, gv
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tddft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Davidson:
+    """Block Davidson for the lowest eigenpairs of L (tddft_davidson_*)."""
+
+    def __init__(self, system: LiouvilleSystem, X0: np.ndarray, nroots: int, max_basis: int = 0, stream=None):
+        lib = load()
+        X0 = np.ascontiguousarray(X0, dtype=np.complex128)
+        self.system = system
+        self.nroots = int(nroots)
+        h = ctypes.c_void_p()
+        _check(lib.tddft_davidson_create(system._h, self.nroots, X0.shape[0], X0.ctypes.data,
+                                         int(max_basis) or 8 * self.nroots, _stream_ptr(stream), ctypes.byref(h)),
+               "tddft_davidson_create")
+        self._h = h
+
+    def step(self, tol: float, stream=None):
+        nconv = ctypes.c_int()
+        theta = np.zeros(self.nroots)
+        rn = np.zeros(self.nroots)
+        _check(load().tddft_davidson_step(self._h, float(tol), ctypes.byref(nconv), theta.ctypes.data, rn.ctypes.data,
+                                          _stream_ptr(stream)), "tddft_davidson_step")
+        return nconv.value, theta, rn
+
+    def vectors(self, stream=None) -> np.ndarray:
+        s = self.system
+        out = np.zeros((self.nroots, s.nocc_src, s.npw), dtype=np.complex128)
+        _check(load().tddft_davidson_vectors(self._h, out.ctypes.data, _stream_ptr(stream)), "tddft_davidson_vectors")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tddft_davidson_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def system_from_workload(wl, *, precision=PREC_FP32, term_mask=TERMS_ALL, nb_max=None, stream=None):
+    """Build a LiouvilleSystem from a synthetic Workload (see synth.py)."""
+    return LiouvilleSystem(n=wl.n, a=wl.a, ecut=wl.ecut, phi_src=wl.phi_src, eps_src=wl.eps_src, alpha=wl.alpha,
+                           kx_g0=wl.kx_g0, precision=precision, term_mask=term_mask,
+                           nb_max=nb_max or wl.nb, spin_flip=wl.spin_flip,
+                           phi_tgt=wl.phi_tgt if wl.spin_flip else None, vloc=wl.vloc, fxc=wl.fxc, stream=stream)

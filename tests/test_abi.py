@@ -1,0 +1,46 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared
+entry point, and its host-side sphere matches the oracle's bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import tddft_oracle as O
+from paper_2309_03513_b300 import tddft as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tddft.h")).read()
+    return sorted(set(re.findall(r"\b(tddft_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = T.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(T.EXPORTS) == declared
+
+
+@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0), (108, 20.2, 25.0), (8, 6.0, 3.2),
+                                      (12, 7.0, 4.0), (48, 9.0, 25.0), (96, 17.97, 25.0)])
+def test_sphere_matches_oracle_exactly(n, a, ecut):
+    m = T.sphere_miller(n, a, ecut)
+    assert np.array_equal(m, O.Grid(n, a, ecut).miller)
+
+
+def test_status_strings_and_errors():
+    lib = T.load()
+    assert lib.tddft_status_string(0) == b"ok"
+    assert lib.tddft_status_string(1) == b"invalid argument"
+    with pytest.raises(T.TddftError) as e:
+        T.sphere_size(7, 5.0, 1.0)
+    assert e.value.status == 1
+    with pytest.raises(T.TddftError):
+        T.sphere_size(8, 2.0, 200.0)  # sphere larger than the grid
+    with pytest.raises(T.TddftError):
+        T.sphere_size(8, -1.0, 1.0)

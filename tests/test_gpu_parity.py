@@ -1,0 +1,156 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative Frobenius error per trial vector <= 1e-11 for the FP64
+path and <= 1e-5 for the FP32 path (errors of FP32 pair products, FFTs and
+accumulation over ~10^2-10^3 pairs stay near 1e-6).
+"""
+import numpy as np
+import pytest
+
+from oracle import tddft_oracle as O
+from paper_2309_03513_b300 import synth
+from paper_2309_03513_b300 import tddft as T
+
+pytestmark = pytest.mark.gpu
+
+TOL = {T.PREC_FP64: 1e-11, T.PREC_FP32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _t
+
+
+def _workload(n, a, ecut, nocc, nb, seed=0, sf=False, nocc_tgt=None):
+    npw = T.sphere_size(n, a, ecut)
+    return synth.make_workload(n=n, a=a, ecut=ecut, npw=npw, nocc_src=nocc, nb=nb, seed=seed, spin_flip=sf,
+                               nocc_tgt=nocc_tgt)
+
+
+def _rel_err(got, want):
+    got = got.reshape(want.shape[0], -1)
+    want = want.reshape(want.shape[0], -1)
+    return np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+
+
+def _run(torch, wl, prec, mask=T.TERMS_ALL, X=None, tiling=None):
+    sys_ = T.system_from_workload(wl, precision=prec, term_mask=mask)
+    if tiling:
+        sys_.set_tiling(*tiling)
+    X = wl.X if X is None else X
+    Xd = torch.from_numpy(X).to("cuda", sys_.complex_dtype)
+    out = sys_.apply(Xd)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().astype(np.complex128)
+    sys_.close()
+    return res
+
+
+@pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
+def test_tiny_full_operator(torch, prec):
+    """24^3 grid, 8 orbitals, 4 trial vectors: the plain FP64 spin-conserving case."""
+    wl = _workload(24, 10.0, 10.0, 8, 4)
+    want = O.system_from_workload(wl).apply(wl.X)
+    got = _run(torch, wl, prec)
+    assert _rel_err(got, want).max() < TOL[prec]
+
+
+@pytest.mark.parametrize("term", [T.TERM_D_KIN, T.TERM_D_VLOC, T.TERM_D_EXX, T.TERM_K1E_H, T.TERM_K1E_XC,
+                                  T.TERM_K1D, T.TERM_D_EXX | T.TERM_PROJ, T.TERM_K1D | T.TERM_PROJ])
+def test_each_term_fp64(torch, term):
+    wl = _workload(12, 7.0, 4.0, 4, 3, seed=3)
+    want = O.system_from_workload(wl).apply(wl.X, term)
+    got = _run(torch, wl, T.PREC_FP64, mask=term)
+    assert _rel_err(got, want).max() < 1e-11
+
+
+@pytest.mark.parametrize("n,a,ecut,nocc,nb", [(8, 6.0, 3.2, 3, 2), (16, 8.0, 6.0, 5, 2), (32, 9.0, 12.0, 6, 2),
+                                               (36, 9.0, 14.0, 5, 1), (48, 10.0, 20.0, 4, 1),
+                                               (64, 11.0, 25.0, 3, 1), (72, 13.48, 25.0, 3, 1),
+                                               (80, 15.0, 25.0, 2, 1), (96, 17.97, 25.0, 2, 1),
+                                               (108, 20.2, 25.0, 2, 1)])
+def test_every_grid_plan(torch, n, a, ecut, nocc, nb):
+    """One system per supported radix plan (8, 4x3, 16, 8x4, 4x9, 16x3, 8x8, 8x9, 16x5, 12x8, 12x9)."""
+    wl = _workload(n, a, ecut, nocc, nb, seed=n)
+    want = O.system_from_workload(wl).apply(wl.X)
+    for prec in (T.PREC_FP64, T.PREC_FP32):
+        got = _run(torch, wl, prec)
+        assert _rel_err(got, want).max() < TOL[prec], (n, prec)
+
+
+@pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
+def test_spin_flip(torch, prec):
+    wl = _workload(24, 10.0, 10.0, 7, 3, seed=11, sf=True, nocc_tgt=5)
+    want = O.system_from_workload(wl).apply(wl.X)
+    got = _run(torch, wl, prec)
+    assert _rel_err(got, want).max() < TOL[prec]
+
+
+def test_ragged_tiles_give_the_same_result(torch):
+    """Pair batches that do not divide the target and source counts."""
+    wl = _workload(24, 10.0, 10.0, 11, 3, seed=12)
+    want = O.system_from_workload(wl).apply(wl.X)
+    for tiling in ((3, 5), (7, 2), (1, 1), (64, 16)):
+        got = _run(torch, wl, T.PREC_FP64, tiling=tiling)
+        assert _rel_err(got, want).max() < 1e-11, tiling
+
+
+def test_host_buffer_entry_point(torch):
+    wl = _workload(24, 10.0, 10.0, 8, 4)
+    want = O.system_from_workload(wl).apply(wl.X)
+    s = T.system_from_workload(wl, precision=T.PREC_FP32)
+    got = s.apply_host(np.ascontiguousarray(wl.X.astype(np.complex64)))
+    s.close()
+    assert _rel_err(got.astype(np.complex128), want).max() < 1e-5
+
+
+def test_hermiticity_fp32(torch):
+    wl = _workload(24, 10.0, 10.0, 8, 2, seed=13)
+    got = _run(torch, wl, T.PREC_FP32)
+    lhs = np.vdot(wl.X[1], got[0])
+    rhs = np.conj(np.vdot(wl.X[0], got[1]))
+    assert abs(lhs - rhs) < 1e-6 * abs(lhs)
+
+
+def test_edge_cases(torch):
+    wl = _workload(12, 7.0, 4.0, 3, 2)
+    s = T.system_from_workload(wl, precision=T.PREC_FP64, nb_max=2)
+    X = torch.from_numpy(wl.X).cuda()
+    empty = torch.empty((0, 3, s.npw), dtype=torch.complex128, device="cuda")
+    s.apply(empty)  # nb = 0 is a no-op
+    with pytest.raises(T.TddftError) as e:
+        s.apply(torch.cat([X, X]))  # nb > nb_max
+    assert e.value.status == 1
+    s.close()
+    bad = wl.phi_src.copy()
+    bad[0] *= 1.01
+    with pytest.raises(T.TddftError) as e:
+        T.LiouvilleSystem(n=12, a=7.0, ecut=4.0, phi_src=bad, eps_src=wl.eps_src, nb_max=1)
+    assert e.value.status == 1
+    with pytest.raises(T.TddftError):
+        T.LiouvilleSystem(n=14, a=7.0, ecut=4.0, phi_src=wl.phi_src, eps_src=wl.eps_src, nb_max=1)
+
+
+def test_alpha_zero_and_single_orbital(torch):
+    wl = _workload(12, 7.0, 4.0, 1, 1, seed=14)
+    wl.alpha = 0.0
+    want = O.system_from_workload(wl).apply(wl.X)
+    assert _rel_err(_run(torch, wl, T.PREC_FP64), want).max() < 1e-11
+
+
+def test_diamond64_sampled_rows_fp32(torch):
+    """64-atom diamond-like cell (72^3, 25 Ha, 128 orbitals, 8 trial vectors), the
+    batch the benchmark times: every output checked on sampled rows (b, v)."""
+    p = synth.WORKLOADS["diamond64"]
+    wl = _workload(p["n"], 13.48, 25.0, 128, 8, seed=0)
+    got = _run(torch, wl, T.PREC_FP32)
+    rows = [(0, 0), (3, 77), (7, 127)]
+    want = O.system_from_workload(wl).apply(wl.X, rows=rows)
+    g = np.stack([got[b, v] for b, v in rows])
+    assert _rel_err(g, want).max() < 1e-5
+    # every row lies in the unoccupied space
+    ov = np.einsum("ug,bvg->buv", wl.phi_src.conj(), got)
+    assert np.abs(ov).max() < 1e-5 * np.abs(got).max()
