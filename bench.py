@@ -242,7 +242,7 @@ def run_native(args):
     for _ in range(args.e2e_steps):
         sys_.apply_host(Xh, LAh, stream=stream)
     t_e2e = max_over_ranks(ws, time.perf_counter() - t0)
-    e2e = ws * args.e2e_steps * nb / t_e2e
+    e2e = ws * args.e2e_steps * nb / t_e2e if args.e2e_steps > 0 else None
     io_bytes = nb * nocc * npw * 8
 
     # plain FP64 GPU path on the same batch
@@ -316,7 +316,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
+                    help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()
+    WORKLOAD["nb"] = args.nb
     if args.warmup < 3 and args.impl == "native":
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
