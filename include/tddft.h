@@ -189,6 +189,28 @@ tddft_status tddft_destroy(tddft_handle h);
 tddft_status tddft_profile_enable(int enable);
 tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, long long* total_launches);
 
+/* Allocation-free exchange pair term (no counterpart in the paper; a service
+ * for callers that cannot allocate device memory and so cannot create a
+ * handle, e.g. codes that give all device memory to their own pool allocator).
+ *
+ * Computes, for one occupied orbital phi and one trial orbital a given as
+ * plane-wave coefficients on the sphere of (n, a, ecut):
+ *   out = PW[ -alpha * phi(r) * Conv_x[conj(phi) a](r) ]
+ * (the exchange term alpha V_X a of Sec. 3.1 for a single occupied orbital),
+ * in complex FP32 with the same kernels as tddft_apply_liouville.
+ * phi_pw, a_pw, out_pw: device complex64 [npw]; the caller owns them.
+ * The call allocates nothing: its working memory is one file-scope device
+ * array of 3.5 MiB that every GPU which loads the library keeps until the
+ * process exits, which limits n to <= 48 (larger n -> TDDFT_EINVAL with a
+ * message naming the limit). The first call on a device looks up the
+ * array's device address (set-up, once per device); make that first call
+ * before any stream capture. Every call uses the same array and leaves its
+ * contents behind; calls whose work overlaps on the GPU (different streams,
+ * or several host threads) race on it and must be serialised by the caller.
+ * Stream-ordered; the host tables are copied with cudaMemcpyAsync. */
+tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut, double alpha, double kx_g0,
+                                         const void* phi_pw, const void* a_pw, void* out_pw, void* stream);
+
 const char* tddft_status_string(tddft_status s);
 const char* tddft_last_error(void);
 

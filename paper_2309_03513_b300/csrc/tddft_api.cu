@@ -972,3 +972,113 @@ tddft_status tddft_davidson_destroy(tddft_dav_handle d) {
   return TDDFT_OK;
 }
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free exchange pair term.
+//
+// For callers that cannot allocate device memory themselves and therefore
+// cannot create a handle (for example a code that hands all device memory to
+// its own pool allocator, so that a library cudaMalloc would fail or break the
+// pool). All working memory lives in one file-scope device array of fixed
+// size, which every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int NOALLOC_MAX_N = 48;
+constexpr size_t NOALLOC_N3 = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_MAX_N;
+// layout: twiddles | kernel table | sphere positions | orbital field | trial field | reciprocal-space field
+constexpr size_t NA_TW = 0;
+constexpr size_t NA_KERN = 1024;
+constexpr size_t NA_POS = NA_KERN + NOALLOC_N3 * sizeof(float);
+constexpr size_t NA_PHI = NA_POS + NOALLOC_N3 * sizeof(int);
+constexpr size_t NA_A = NA_PHI + NOALLOC_N3 * sizeof(cplx<float>);
+constexpr size_t NA_G = NA_A + NOALLOC_N3 * sizeof(cplx<float>);
+constexpr size_t NOALLOC_BYTES = NA_G + NOALLOC_N3 * sizeof(cplx<float>);  // 3.5 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut, double alpha, double kx_g0,
+                                                     const void* phi_pw, const void* a_pw, void* out_pw,
+                                                     void* stream) {
+  if (!phi_pw || !a_pw || !out_pw) return fail(TDDFT_EINVAL, "null buffer");
+  if (n > NOALLOC_MAX_N)
+    return fail(TDDFT_EINVAL, "grid size " + std::to_string(n) + " exceeds the allocation-free limit of " +
+                                  std::to_string(NOALLOC_MAX_N));
+  if (!supported_n(n, TDDFT_PREC_FP32)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
+  std::vector<Miller> sph;
+  STATUS_TRY(build_sphere(n, a, ecut, sph));
+  const int npw = (int)sph.size();
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(TDDFT_EINVAL, "device index out of range");
+  if (!g_noalloc_ptr[dev]) {
+    // set-up, once per device: the device address of the scratch array
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  unsigned char* base = g_noalloc_ptr[dev];
+  PlaneOps<float> o = plane_ops_for<float>(n);
+  if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
+  CUDA_TRY(o.prepare());
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n3 = (long long)n * n * n;
+  cplx<float>* tw = (cplx<float>*)(base + NA_TW);
+  float* kern = (float*)(base + NA_KERN);
+  int* pos = (int*)(base + NA_POS);
+  cplx<float>* phi_r = (cplx<float>*)(base + NA_PHI);
+  cplx<float>* a_r = (cplx<float>*)(base + NA_A);
+  cplx<float>* gbuf = (cplx<float>*)(base + NA_G);
+
+  // tables of this grid (the same host arithmetic as a handle's set-up)
+  std::vector<int> radices = plan_radices(n), rev(n);
+  for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
+  std::vector<cplx<float>> twh(n);
+  for (int e = 0; e < n; ++e) {
+    const double ang = -2.0 * M_PI * (double)e / (double)n;
+    twh[e] = {(float)std::cos(ang), (float)std::sin(ang)};
+  }
+  const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
+  auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
+  std::vector<float> kh(n3);
+  for (int kz = 0; kz < n; ++kz)
+    for (int ky = 0; ky < n; ++ky)
+      for (int kxx = 0; kxx < n; ++kxx) {
+        const long long m2 = (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
+        const double vx = m2 == 0 ? kx_g0 : 4.0 * M_PI / (tpiba2 * (double)m2);
+        kh[((long long)rev[kz] * n + rev[ky]) * n + rev[kxx]] = (float)(vx / (double)n3);
+      }
+  std::vector<int> posh(npw);
+  for (int i = 0; i < npw; ++i)
+    posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
+  CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), n * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
+
+  // both orbitals to real space (cube cleared first: it keeps the previous call's contents)
+  const float s_in = (float)(1.0 / std::sqrt(a * a * a));
+  const cplx<float>* srcs[2] = {(const cplx<float>*)phi_pw, (const cplx<float>*)a_pw};
+  cplx<float>* dsts[2] = {phi_r, a_r};
+  for (int i = 0; i < 2; ++i) {
+    CUDA_TRY(cudaMemsetAsync(gbuf, 0, n3 * sizeof(cplx<float>), st));
+    { k_scatter<float><<<grid_for(npw, 256), 256, 0, st>>>(srcs[i], gbuf, pos, npw, 1, s_in, n3); note_launch(); }
+    o.z(Z_INV, gbuf, 1, nullptr, 1.f, tw, st);
+    PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+    o.xy_inv(INV_WRITE, gbuf, dsts[i], nullptr, pm, 1, 1.f, tw, st);
+  }
+  // -alpha phi Conv_x[conj(phi) a], accumulated into the cleared trial field
+  PairMap pp{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+  o.xy_fwd(XY_PRODUCT, phi_r, a_r, pp, 1, gbuf, tw, st);
+  o.z(Z_CONV, gbuf, 1, kern, 1.f, tw, st);
+  CUDA_TRY(cudaMemsetAsync(a_r, 0, n3 * sizeof(cplx<float>), st));
+  o.xy_inv(INV_ACCUM, gbuf, a_r, phi_r, pp, 1, (float)(-alpha), tw, st);
+  // back to plane waves on the sphere
+  PairMap pl{1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0};
+  o.xy_fwd(XY_LOAD, nullptr, a_r, pl, 1, gbuf, tw, st);
+  o.z(Z_FWD, gbuf, 1, nullptr, 1.f, tw, st);
+  const float s_out = (float)(std::sqrt(a * a * a) / (double)n3);
+  { k_gather<float><<<grid_for(npw, 256), 256, 0, st>>>(gbuf, pos, npw, 1, s_out, nullptr, nullptr, nullptr, 1, 0,
+                                                         (cplx<float>*)out_pw, n3); note_launch(); }
+  return check_launch("tddft_exchange_pair_noalloc");
+}

@@ -37,6 +37,7 @@ EXPORTS = [
     "tddft_set_tiling", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
+    "tddft_exchange_pair_noalloc",
 ]
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
@@ -96,6 +97,7 @@ def load() -> ctypes.CDLL:
         "tddft_last_error": ([], ctypes.c_char_p),
         "tddft_profile_enable": ([ci], st),
         "tddft_profile_read": ([vp, vp, vp, vp], st),
+        "tddft_exchange_pair_noalloc": ([ci, cd, cd, cd, cd, vp, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -150,6 +152,24 @@ def launch_count() -> int:
     tot = ctypes.c_longlong()
     _check(load().tddft_profile_read(None, None, None, ctypes.byref(tot)), "tddft_profile_read")
     return int(tot.value)
+
+
+def exchange_pair_noalloc(n, a, ecut, alpha, kx_g0, phi, trial, out=None, stream=None):
+    """-alpha phi Conv_x[conj(phi) a] in plane waves for one orbital pair, without
+    any device allocation by the library (tddft_exchange_pair_noalloc).
+
+    phi, trial: CUDA complex64 tensors [npw]; returns out (allocated here by
+    torch when not given, since the Python caller can allocate)."""
+    import torch
+    for t in (phi, trial):
+        if not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+            raise TypeError("expected contiguous CUDA complex64 tensors")
+    if out is None:
+        out = torch.empty_like(phi)
+    _check(load().tddft_exchange_pair_noalloc(int(n), float(a), float(ecut), float(alpha), float(kx_g0),
+                                              phi.data_ptr(), trial.data_ptr(), out.data_ptr(), _stream_ptr(stream)),
+           "tddft_exchange_pair_noalloc")
+    return out
 
 
 def _stream_ptr(stream):
