@@ -119,9 +119,23 @@ tddft_status tddft_query(tddft_handle h, tddft_info* info);
 /* Change the term mask of the handle (TDDFT_TERM_* bits). */
 tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask);
 
-/* Pair-batch tiling of the pair-convolution passes: targets per batch and
- * sources per batch (0 keeps the current value). Host only. */
-tddft_status tddft_set_tiling(tddft_handle h, int targets, int sources);
+/* Schedule of the pair-convolution passes (results agree to rounding for
+ * every choice). A batch convolves `targets` x `sources` pairs at once
+ * (bounded by batch_fields, the intermediate buffer of the handle); K1d
+ * builds tau for k1d_block x k1d_block orbital pairs at a time and shares it
+ * by every trial vector. accumulate = 0: one CTA per (target, plane) sums its
+ * sources in a fixed order; 1: one CTA per pair with atomic accumulation
+ * (order not fixed). In set_tuning, 0 (or -1 for accumulate) keeps a value and
+ * batch_fields is ignored. Host only. */
+typedef struct tddft_tuning {
+  int targets;
+  int sources;
+  int k1d_block;    /* 1..8 */
+  int accumulate;   /* 0 or 1 */
+  int batch_fields; /* read-only */
+} tddft_tuning;
+tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
+tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);
 
 /* LA = L A for nb trial vectors (Eq. 8 for SC, Eq. 21 for SF).
  * A, LA: device buffers [nb][nocc_src][npw] (complex128 for FP64 handles,

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(plane_threads<N>())
   const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z, N3, N2);
   if constexpr (MODE == XY_PRODUCT) {
     const cplx<T>* Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z, N3, N2);
+#pragma unroll 4
     for (int e = tid; e < N2; e += NT) {
       const int y = e / N, x = e - y * N;
       s[y * PITCH + x] = cmulc(Q[e], R[e]);
@@ -114,11 +115,26 @@ __global__ void __launch_bounds__(plane_threads<N>())
 // Inverse xy pass.
 // INV_WRITE: out field (o0 + t*ot) plane z = scale * IFFT_xy(ibuf item t).
 // INV_ACCUM: out field (o0 + t*ot) plane z += scale * sum_k P_(t,k) * IFFT_xy(ibuf item t*kdim+k).
-// Grid (N, targets). In INV_WRITE mode ob may be ibuf itself (in place: each
+//            Grid (N, targets); each CTA loops over the sources of its target.
+// INV_ATOMIC: the same sum with one CTA per item (grid (N, targets*kdim)),
+//            added to the output with atomics (summation order not fixed). In INV_WRITE mode ob may be ibuf itself (in place: each
 // CTA reads its whole plane before it writes it back).
 // ---------------------------------------------------------------------------
 constexpr int INV_WRITE = 0;
 constexpr int INV_ACCUM = 1;
+constexpr int INV_ATOMIC = 2;  // one CTA per pair item, atomic accumulation into the target
+
+template <typename T>
+__device__ __forceinline__ void atomic_cadd(cplx<T>* p, cplx<T> v);
+template <>
+__device__ __forceinline__ void atomic_cadd<float>(cplx<float>* p, cplx<float> v) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
+}
+template <>
+__device__ __forceinline__ void atomic_cadd<double>(cplx<double>* p, cplx<double> v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
 
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(plane_threads<N>())
@@ -146,6 +162,25 @@ __global__ void __launch_bounds__(plane_threads<N>())
     for (int e = tid; e < N2; e += NT) {
       const int y = e / N, x = e - y * N;
       O[e] = cscale(s[y * PITCH + x], scale);
+    }
+  } else if constexpr (MODE == INV_ATOMIC) {
+    const int item = t;
+    const int tt = item / pm.kdim, k = item - tt * pm.kdim;
+    const cplx<T>* I = ibuf + (long long)item * N3 + (long long)z * N2;
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = I[e];
+    }
+    __syncthreads();
+    fft_lines<T, N, INV, false>(s, tw, line, g);
+    fft_lines<T, N, INV, true>(s, tw, line, g);
+    const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)tt * pm.pt, z, N3, N2);
+    cplx<T>* Oa = ob + (long long)(pm.o0 + (long long)tt * pm.ot) * N3 + (long long)z * N2;
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      atomic_cadd(Oa + e, cscale(cmul(P[e], s[y * PITCH + x]), scale));
     }
   } else {
     cplx<T> acc[EPT];

@@ -42,7 +42,21 @@ struct PlaneLaunch {
     TDDFT_ATTR((k_z<T, N, Z_INV>))
     TDDFT_ATTR((k_xy_inv<T, N, INV_WRITE>))
     TDDFT_ATTR((k_xy_inv<T, N, INV_ACCUM>))
+    TDDFT_ATTR((k_xy_inv<T, N, INV_ATOMIC>))
 #undef TDDFT_ATTR
+    // prefer shared memory over L1 so that several plane CTAs fit on an SM
+#define TDDFT_CARVE(K)                                                                                   \
+  e = cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared); \
+  if (e != cudaSuccess) return e;
+    TDDFT_CARVE((k_xy_fwd<T, N, XY_LOAD>))
+    TDDFT_CARVE((k_xy_fwd<T, N, XY_PRODUCT>))
+    TDDFT_CARVE((k_z<T, N, Z_CONV>))
+    TDDFT_CARVE((k_z<T, N, Z_FWD>))
+    TDDFT_CARVE((k_z<T, N, Z_INV>))
+    TDDFT_CARVE((k_xy_inv<T, N, INV_WRITE>))
+    TDDFT_CARVE((k_xy_inv<T, N, INV_ACCUM>))
+    TDDFT_CARVE((k_xy_inv<T, N, INV_ATOMIC>))
+#undef TDDFT_CARVE
     return cudaSuccess;
   }
 
@@ -78,15 +92,17 @@ struct PlaneLaunch {
   static void xy_inv(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
                      const cplx<T>* tw, cudaStream_t st) {
     if (targets <= 0) return;
-    dim3 grid(N, targets);
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
     prof_begin(KC_XY_INV, st);
-    if (mode == INV_ACCUM)
-      k_xy_inv<T, N, INV_ACCUM><<<grid, NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
-    else
-      k_xy_inv<T, N, INV_WRITE><<<grid, NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    if (mode == INV_ACCUM) {
+      k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    } else if (mode == INV_ATOMIC) {
+      k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    } else {
+      k_xy_inv<T, N, INV_WRITE><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    }
     note_launch();
-    prof_end(KC_XY_INV, st, mode == INV_ACCUM ? (2.0 * pm.kdim + 2.0) * F * targets : 2.0 * F * targets);
+    prof_end(KC_XY_INV, st, mode == INV_WRITE ? 2.0 * F * targets : (2.0 * pm.kdim + 2.0) * F * targets);
   }
 
   static PlaneOps<T> ops() {

@@ -293,6 +293,7 @@ struct tddft_system {
   int nb_chunk = 0;
   int ibuf_fields = 0;
   int tile_targets = 8, tile_sources = 8, k1d_block = 8;
+  int accumulate = INV_ATOMIC;
   int nsplit = 1;
   size_t bytes = 0;
   Buffers b;
@@ -446,7 +447,7 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
       pm.ot = pg.o_ts;
       o.xy_fwd(XY_PRODUCT, qb, rb, pm, tt * kk, ib, tw, st);
       o.z(Z_CONV, ib, tt * kk, kern, T(1), tw, st);
-      o.xy_inv(INV_ACCUM, ib, ob, pb, pm, tt, scale, tw, st);
+      o.xy_inv(h->accumulate, ib, ob, pb, pm, tt, scale, tw, st);
     }
   }
   return check_launch("pair_accumulate");
@@ -903,11 +904,25 @@ tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
   return TDDFT_OK;
 }
 
-tddft_status tddft_set_tiling(tddft_handle h, int targets, int sources) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (targets < 0 || sources < 0) return fail(TDDFT_EINVAL, "negative tile");
-  if (targets) h->tile_targets = targets;
-  if (sources) h->tile_sources = sources;
+tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
+  if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
+  if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 8)
+    return fail(TDDFT_EINVAL, "tile sizes must be >= 0 and k1d_block <= 8");
+  if (t->accumulate < -1 || t->accumulate > 1) return fail(TDDFT_EINVAL, "accumulate must be -1, 0 or 1");
+  if (t->targets) h->tile_targets = t->targets;
+  if (t->sources) h->tile_sources = t->sources;
+  if (t->k1d_block) h->k1d_block = t->k1d_block;
+  if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
+  if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
+  t->targets = h->tile_targets;
+  t->sources = h->tile_sources;
+  t->k1d_block = h->k1d_block;
+  t->accumulate = h->accumulate == INV_ATOMIC ? 1 : 0;
+  t->batch_fields = h->ibuf_fields;
   return TDDFT_OK;
 }
 

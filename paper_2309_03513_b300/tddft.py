@@ -34,7 +34,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUM
 # every entry point declared in include/tddft.h
 EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
-    "tddft_set_tiling", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_set_tuning", "tddft_get_tuning", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -58,6 +58,11 @@ class Desc(ctypes.Structure):
 class Inputs(ctypes.Structure):
     _fields_ = [("phi_src", ctypes.c_void_p), ("phi_tgt", ctypes.c_void_p), ("eps_src", ctypes.c_void_p),
                 ("vloc", ctypes.c_void_p), ("fxc", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
+                ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -84,7 +89,8 @@ def load() -> ctypes.CDLL:
         "tddft_init_system": ([ctypes.POINTER(Desc), ctypes.POINTER(Inputs), vp, ctypes.POINTER(vp)], st),
         "tddft_query": ([vp, ctypes.POINTER(Info)], st),
         "tddft_set_terms": ([vp, ctypes.c_uint], st),
-        "tddft_set_tiling": ([vp, ci, ci], st),
+        "tddft_set_tuning": ([vp, ctypes.POINTER(Tuning)], st),
+        "tddft_get_tuning": ([vp, ctypes.POINTER(Tuning)], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -232,8 +238,17 @@ class LiouvilleSystem:
     def set_terms(self, mask: int):
         _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
 
+    def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1):
+        t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0)
+        _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(load().tddft_get_tuning(self._h, ctypes.byref(t)), "tddft_get_tuning")
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
     def set_tiling(self, targets: int = 0, sources: int = 0):
-        _check(load().tddft_set_tiling(self._h, int(targets), int(sources)), "tddft_set_tiling")
+        self.set_tuning(targets=targets, sources=sources)
 
     # -- calls --
     def apply(self, X, out=None, stream=None):

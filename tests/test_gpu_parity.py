@@ -39,7 +39,7 @@ def _rel_err(got, want):
 def _run(torch, wl, prec, mask=T.TERMS_ALL, X=None, tiling=None):
     sys_ = T.system_from_workload(wl, precision=prec, term_mask=mask)
     if tiling:
-        sys_.set_tiling(*tiling)
+        sys_.set_tuning(*tiling)
     X = wl.X if X is None else X
     Xd = torch.from_numpy(X).to("cuda", sys_.complex_dtype)
     out = sys_.apply(Xd)
@@ -93,9 +93,11 @@ def test_ragged_tiles_give_the_same_result(torch):
     """Pair batches that do not divide the target and source counts."""
     wl = _workload(24, 10.0, 10.0, 11, 3, seed=12)
     want = O.system_from_workload(wl).apply(wl.X)
-    for tiling in ((3, 5), (7, 2), (1, 1), (64, 16)):
+    for tiling in ((3, 5, 0, 0), (7, 2, 3, 1), (1, 1, 1, 0), (64, 16, 8, 1), (5, 3, 5, 1)):
         got = _run(torch, wl, T.PREC_FP64, tiling=tiling)
         assert _rel_err(got, want).max() < 1e-11, tiling
+    got = _run(torch, wl, T.PREC_FP32, tiling=(4, 4, 4, 1))
+    assert _rel_err(got, want).max() < 1e-5
 
 
 def test_host_buffer_entry_point(torch):
