@@ -130,12 +130,20 @@ tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask);
 typedef struct tddft_tuning {
   int targets;
   int sources;
-  int k1d_block;    /* 1..8 */
+  int k1d_block;    /* 1..16 */
   int accumulate;   /* 0 or 1 */
   int batch_fields; /* read-only */
+  int graph;        /* 1: tddft_apply_liouville captures its launches into a CUDA
+                       graph on first use for a given (nb, A, LA, term mask) and
+                       replays it on the caller's stream; 0: plain launches */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);
+
+/* Time a fixed set of schedules (batch shapes, accumulate mode, K1d block) on
+ * nb trial vectors A (device, handle precision; LA is scratch output), keep
+ * the fastest on the handle and return it in *best (may be NULL). Synchronises. */
+tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, void* stream, tddft_tuning* best);
 
 /* LA = L A for nb trial vectors (Eq. 8 for SC, Eq. 21 for SF).
  * A, LA: device buffers [nb][nocc_src][npw] (complex128 for FP64 handles,
@@ -149,6 +157,16 @@ tddft_status tddft_apply_liouville(tddft_handle h, int nb, const void* A, void* 
  * copies A to the device, applies L and copies LA back, then synchronises
  * the stream. */
 tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_host, void* LA_host, void* stream);
+
+/* Several independent systems (any sizes, spin modes, precisions) in one CUDA
+ * graph launch: system i applies L_i to nb[i] trial vectors A[i] -> LA[i]
+ * (device buffers, layouts as in tddft_apply_liouville). Each system runs as
+ * its own branch of the graph, so uneven systems overlap on the GPU. The graph
+ * is captured on the first call and replayed while the argument lists are
+ * unchanged (process-wide cache of one graph; not thread-safe). A handle may
+ * appear once. Stream-ordered on `stream`. */
+tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
+                                         void* const* LA, void* stream);
 
 /* Bilinear form omega_b = <P^c X_b | M | P^c X_b> (M = L without the outer
  * P^c; equal to <X_b|L X_b> for X_b orthogonal to the orbitals) and the

@@ -282,55 +282,44 @@ __global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict
   }
 }
 
-// K1d contraction for one block of pairs (v in I, v' in J), tau[(vi*TJ + vj)] = Conv[conj(phi_v') phi_v]:
-//   out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
-//   and, when I != J, out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj]).
-// One thread per grid point of a chunk of PTS points; each thread keeps the tau
-// values of its point in its own column of shared memory (no sharing, no sync).
-template <typename T, int TB, int PTS>
-__global__ void __launch_bounds__(PTS)
+// K1d contraction for one block of pairs (v in I = [i0, i0+ti), v' in J = [j0, j0+tj)),
+// tau[(vi*tj + vj)] = Conv_x[conj(phi_v') phi_v] in real space.
+//   SIDE 0:  out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
+//   SIDE 1:  out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj])   (blocks with I != J;
+//            tau_{v'v} = conj(tau_{vv'}) because the kernel is real and even)
+// Block of TB x PTS threads: thread (q, p) owns orbital q of its side and grid
+// point r = blockIdx.x * PTS + p; it keeps its TB tau values in registers and
+// loops over the trial vectors b. Each (b, orbital, point) is written once.
+template <typename T, int TB, int PTS, int SIDE>
+__global__ void __launch_bounds__(TB * PTS)
     k_k1d_contract(const cplx<T>* __restrict__ tau, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out, int i0,
                    int ti, int j0, int tj, int nocc, int nb, T s, long long n3) {
-  __shared__ cplx<T> st[TB * TB][PTS];
-  const long long r = (long long)blockIdx.x * PTS + threadIdx.x;
-  const bool ok = r < n3;
-  for (int p = 0; p < TB * TB; ++p) {
-    const int vi = p / TB, vj = p - vi * TB;
-    st[p][threadIdx.x] = (ok && vi < ti && vj < tj) ? tau[(long long)(vi * tj + vj) * n3 + r] : cplx<T>{T(0), T(0)};
+  const int q = threadIdx.x / PTS, p = threadIdx.x - q * PTS;
+  const long long r = (long long)blockIdx.x * PTS + p;
+  const int nq = SIDE == 0 ? ti : tj;   // outputs on this side
+  const int nk = SIDE == 0 ? tj : ti;   // summed index
+  if (q >= nq || r >= n3) return;
+  cplx<T> tv[TB];
+#pragma unroll
+  for (int k = 0; k < TB; ++k) {
+    if (k < nk) {
+      const long long item = SIDE == 0 ? (long long)q * tj + k : (long long)k * tj + q;
+      const cplx<T> t = tau[item * n3 + r];
+      tv[k] = SIDE == 0 ? t : cconj(t);
+    } else {
+      tv[k] = {T(0), T(0)};
+    }
   }
-  if (!ok) return;
-  const bool offdiag = (i0 != j0);
+  const int src0 = SIDE == 0 ? j0 : i0;
+  const int dst = (SIDE == 0 ? i0 : j0) + q;
   for (int b = 0; b < nb; ++b) {
-    const cplx<T>* ab = a + (long long)b * nocc * n3 + r;
-    cplx<T>* ob = out + (long long)b * nocc * n3 + r;
-    cplx<T> aJ[TB], aI[TB], accI[TB], accJ[TB];
+    const cplx<T>* ab = a + ((long long)b * nocc + src0) * n3 + r;
+    cplx<T> acc = {T(0), T(0)};
 #pragma unroll
-    for (int q = 0; q < TB; ++q) {
-      aJ[q] = (q < tj) ? ab[(long long)(j0 + q) * n3] : cplx<T>{T(0), T(0)};
-      aI[q] = (q < ti && offdiag) ? ab[(long long)(i0 + q) * n3] : cplx<T>{T(0), T(0)};
-      accI[q] = {T(0), T(0)};
-      accJ[q] = {T(0), T(0)};
-    }
-#pragma unroll
-    for (int vi = 0; vi < TB; ++vi) {
-#pragma unroll
-      for (int vj = 0; vj < TB; ++vj) {
-        const cplx<T> tv = st[vi * TB + vj][threadIdx.x];
-        accI[vi] = cadd(accI[vi], cmul(aJ[vj], tv));
-        if (offdiag) accJ[vj] = cadd(accJ[vj], cmulc(tv, aI[vi]));
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < TB; ++q) {
-      if (q < ti) {
-        cplx<T>* o = ob + (long long)(i0 + q) * n3;
-        *o = cadd(*o, cscale(accI[q], s));
-      }
-      if (offdiag && q < tj) {
-        cplx<T>* o = ob + (long long)(j0 + q) * n3;
-        *o = cadd(*o, cscale(accJ[q], s));
-      }
-    }
+    for (int k = 0; k < TB; ++k)
+      if (k < nk) acc = cadd(acc, cmul(ab[(long long)k * n3], tv[k]));
+    cplx<T>* o = out + ((long long)b * nocc + dst) * n3 + r;
+    *o = cadd(*o, cscale(acc, s));
   }
 }
 

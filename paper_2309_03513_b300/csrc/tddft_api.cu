@@ -292,11 +292,21 @@ struct tddft_system {
   long long n3 = 0;
   int nb_chunk = 0;
   int ibuf_fields = 0;
-  int tile_targets = 8, tile_sources = 8, k1d_block = 8;
+  int tile_targets = 8, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int nsplit = 1;
   size_t bytes = 0;
   Buffers b;
+  // CUDA-graph replay of tddft_apply_liouville (tuning.graph): the launch
+  // sequence is captured on the handle's own stream once per (nb, A, LA, mask)
+  // and replayed on the caller's stream.
+  bool use_graph = false;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_nb = -1;
+  const void* g_A = nullptr;
+  void* g_LA = nullptr;
+  unsigned g_mask = 0;
   std::vector<void*> allocations;
   PlaneOps<float> ops32;
   PlaneOps<double> ops64;
@@ -475,14 +485,14 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
-      if (sizeof(T) == 4) {
-        constexpr int PTS = 64;
-        { k_k1d_contract<T, 8, PTS><<<(unsigned)((h->n3 + PTS - 1) / PTS), PTS, 0, st>>>(
+      {
+        constexpr int KB = 16, PTS = 16;
+        const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
+        { k_k1d_contract<T, KB, PTS, 0><<<blocks, KB * PTS, 0, st>>>(
             ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
-      } else {
-        constexpr int PTS = 32;
-        { k_k1d_contract<T, 8, PTS><<<(unsigned)((h->n3 + PTS - 1) / PTS), PTS, 0, st>>>(
-            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
+        if (i0 != j0)
+          { k_k1d_contract<T, KB, PTS, 1><<<blocks, KB * PTS, 0, st>>>(
+              ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
       }
     }
   }
@@ -679,7 +689,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   size_t freeb = 0, totalb = 0;
   CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
   const size_t field = (size_t)n3 * ez;
-  h->ibuf_fields = std::max(16, std::min(128, (int)((size_t)(256u << 20) / field)));
+  h->ibuf_fields = std::max(16, std::min(512, (int)((size_t)(1u << 30) / field)));
   const size_t fixed = field * ((size_t)h->ibuf_fields + (size_t)d.nocc_src + (h->sf() ? ntgt : 0));
   const size_t per_b = field * (2 * (size_t)d.nocc_src + 2);
   const size_t budget = (size_t)(0.6 * (double)freeb);
@@ -779,6 +789,112 @@ static tddft_status adjoint_impl(tddft_system* h, int nb, const cplx<T>* X, cons
   return check_launch("adjoint projector terms");
 }
 
+static tddft_status apply_dispatch(tddft_system* h, int nb, const void* A, void* LA, unsigned mask, cudaStream_t st) {
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return apply_impl<double>(h, nb, (const cplx<double>*)A, (cplx<double>*)LA, mask, st);
+  return apply_impl<float>(h, nb, (const cplx<float>*)A, (cplx<float>*)LA, mask, st);
+}
+
+static tddft_status ensure_capture_stream(tddft_system* h) {
+  if (!h->cap) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  return TDDFT_OK;
+}
+
+// Capture one apply of h into a graph (on h->cap), returning the graph.
+static tddft_status capture_apply(tddft_system* h, int nb, const void* A, void* LA, cudaGraph_t* g) {
+  STATUS_TRY(ensure_capture_stream(h));
+  CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  tddft_status s = apply_dispatch(h, nb, A, LA, h->d.term_mask, h->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+  if (s != TDDFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(TDDFT_ECUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  *g = graph;
+  return TDDFT_OK;
+}
+
+static tddft_status apply_graph(tddft_system* h, int nb, const void* A, void* LA, cudaStream_t st) {
+  if (!(h->gexec && h->g_nb == nb && h->g_A == A && h->g_LA == LA && h->g_mask == h->d.term_mask)) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    // work queued earlier on the caller's stream must finish before the
+    // capture stream is used for the capture itself (capture launches nothing)
+    cudaGraph_t g = nullptr;
+    STATUS_TRY(capture_apply(h, nb, A, LA, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      return fail(TDDFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    h->g_nb = nb;
+    h->g_A = A;
+    h->g_LA = LA;
+    h->g_mask = h->d.term_mask;
+  }
+  CUDA_TRY(cudaGraphLaunch(h->gexec, st));
+  return TDDFT_OK;
+}
+
+// One graph for several systems: each system's apply is a branch forked from
+// the first handle's capture stream, so that independent systems of uneven
+// size run concurrently when replayed with a single graph launch.
+namespace {
+struct MultiKey {
+  std::vector<const void*> k;
+  bool operator==(const MultiKey& o) const { return k == o.k; }
+};
+struct MultiGraph {
+  MultiKey key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> events;
+};
+MultiGraph g_multi;
+}  // namespace
+
+static tddft_status build_multi_graph(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
+                                      void* const* LA, cudaGraphExec_t* out, std::vector<cudaEvent_t>& events) {
+  for (int i = 0; i < nsys; ++i) STATUS_TRY(ensure_capture_stream(hs[i]));
+  while ((int)events.size() < nsys + 1) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    events.push_back(e);
+  }
+  cudaStream_t origin = hs[0]->cap;
+  CUDA_TRY(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+  tddft_status s = TDDFT_OK;
+  cudaError_t e = cudaEventRecord(events[nsys], origin);
+  for (int i = 0; i < nsys && s == TDDFT_OK && e == cudaSuccess; ++i) {
+    cudaStream_t si = hs[i]->cap;
+    if (si != origin) e = cudaStreamWaitEvent(si, events[nsys], 0);
+    if (e != cudaSuccess) break;
+    if (nb[i] > 0) s = apply_dispatch(hs[i], nb[i], A[i], LA[i], hs[i]->d.term_mask, si);
+    if (s == TDDFT_OK && si != origin) {
+      e = cudaEventRecord(events[i], si);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, events[i], 0);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+  if (s != TDDFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(TDDFT_ECUDA, std::string("multi-system capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  cudaError_t e3 = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return fail(TDDFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  return TDDFT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -847,6 +963,14 @@ tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, 
 
 tddft_status tddft_destroy(tddft_handle h) {
   if (!h) return TDDFT_OK;
+  // a cached multi-system graph that refers to this handle is dropped
+  if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
+    cudaGraphExecDestroy(g_multi.exec);
+    g_multi.exec = nullptr;
+    g_multi.key.k.clear();
+  }
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocations) cudaFree(p);
   delete h;
   return TDDFT_OK;
@@ -900,19 +1024,30 @@ tddft_status tddft_query(tddft_handle h, tddft_info* info) {
 tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
   if (!h) return fail(TDDFT_EINVAL, "null handle");
   if (term_mask & ~TDDFT_TERMS_ALL) return fail(TDDFT_EINVAL, "unknown term bits");
-  h->d.term_mask = term_mask;
+  h->d.term_mask = term_mask;  // a cached graph is re-captured when the mask differs
   return TDDFT_OK;
 }
 
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
   if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
-  if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 8)
-    return fail(TDDFT_EINVAL, "tile sizes must be >= 0 and k1d_block <= 8");
+  if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 16)
+    return fail(TDDFT_EINVAL, "tile sizes must be >= 0 and k1d_block <= 16");
   if (t->accumulate < -1 || t->accumulate > 1) return fail(TDDFT_EINVAL, "accumulate must be -1, 0 or 1");
+  if (t->graph < -1 || t->graph > 1) return fail(TDDFT_EINVAL, "graph must be -1, 0 or 1");
   if (t->targets) h->tile_targets = t->targets;
   if (t->sources) h->tile_sources = t->sources;
   if (t->k1d_block) h->k1d_block = t->k1d_block;
   if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
+  if (t->graph >= 0) h->use_graph = t->graph == 1;
+  if (h->gexec) {  // the schedule changed: the next graph call captures again
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
+    cudaGraphExecDestroy(g_multi.exec);
+    g_multi.exec = nullptr;
+    g_multi.key.k.clear();
+  }
   return TDDFT_OK;
 }
 
@@ -923,6 +1058,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->k1d_block = h->k1d_block;
   t->accumulate = h->accumulate == INV_ATOMIC ? 1 : 0;
   t->batch_fields = h->ibuf_fields;
+  t->graph = h->use_graph ? 1 : 0;
   return TDDFT_OK;
 }
 
@@ -933,9 +1069,8 @@ tddft_status tddft_apply_liouville(tddft_handle h, int nb, const void* A, void* 
   if (!A || !LA) return fail(TDDFT_EINVAL, "null buffer");
   if (A == LA) return fail(TDDFT_EINVAL, "A and LA must not alias");
   cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64)
-    return apply_impl<double>(h, nb, (const cplx<double>*)A, (cplx<double>*)LA, h->d.term_mask, st);
-  return apply_impl<float>(h, nb, (const cplx<float>*)A, (cplx<float>*)LA, h->d.term_mask, st);
+  if (h->use_graph) return apply_graph(h, nb, A, LA, st);
+  return apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
 }
 
 tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_host, void* LA_host, void* stream) {
@@ -949,6 +1084,91 @@ tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_ho
   STATUS_TRY(tddft_apply_liouville(h, nb, h->b.io_a, h->b.io_b, stream));
   CUDA_TRY(cudaMemcpyAsync(LA_host, h->b.io_b, bytes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return TDDFT_OK;
+}
+
+tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
+                                         void* const* LA, void* stream) {
+  if (nsys < 1 || !hs || !nb || !A || !LA) return fail(TDDFT_EINVAL, "null or empty argument");
+  for (int i = 0; i < nsys; ++i) {
+    if (!hs[i]) return fail(TDDFT_EINVAL, "null handle in the list");
+    if (nb[i] < 0 || nb[i] > hs[i]->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max] for system " + std::to_string(i));
+    if (nb[i] > 0 && (!A[i] || !LA[i] || A[i] == LA[i])) return fail(TDDFT_EINVAL, "bad buffers for system " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(TDDFT_EINVAL, "a handle appears twice (one workspace per handle)");
+  }
+  MultiKey key;
+  for (int i = 0; i < nsys; ++i) {
+    key.k.push_back(hs[i]);
+    key.k.push_back((const void*)(size_t)nb[i]);
+    key.k.push_back(A[i]);
+    key.k.push_back(LA[i]);
+    key.k.push_back((const void*)(size_t)hs[i]->d.term_mask);
+  }
+  if (!(g_multi.exec && g_multi.key == key)) {
+    if (g_multi.exec) {
+      cudaGraphExecDestroy(g_multi.exec);
+      g_multi.exec = nullptr;
+    }
+    STATUS_TRY(build_multi_graph(nsys, hs, nb, A, LA, &g_multi.exec, g_multi.events));
+    g_multi.key = key;
+  }
+  CUDA_TRY(cudaGraphLaunch(g_multi.exec, (cudaStream_t)stream));
+  return TDDFT_OK;
+}
+
+tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, void* stream, tddft_tuning* best) {
+  if (!h || !A || !LA) return fail(TDDFT_EINVAL, "null argument");
+  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+  cudaStream_t st = (cudaStream_t)stream;
+  struct Cand {
+    int tt, ks, acc, kb;
+  };
+  const Cand cands[] = {{8, 8, 1, 16}, {16, 4, 1, 16}, {4, 16, 1, 16}, {16, 8, 1, 16}, {32, 2, 1, 16},
+                        {8, 8, 0, 16},  {16, 8, 0, 16}, {8, 8, 1, 8}};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const bool graph = h->use_graph;
+  h->use_graph = false;
+  float best_ms = 1e30f;
+  Cand bc = cands[0];
+  tddft_status s = TDDFT_OK;
+  for (const Cand& c : cands) {
+    h->tile_targets = c.tt;
+    h->tile_sources = c.ks;
+    h->accumulate = c.acc ? INV_ATOMIC : INV_ACCUM;
+    h->k1d_block = c.kb;
+    s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);  // warm
+    if (s != TDDFT_OK) break;
+    cudaEventRecord(e0, st);
+    s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
+    if (s != TDDFT_OK) break;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      s = fail(TDDFT_ECUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      bc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->use_graph = graph;
+  h->tile_targets = bc.tt;
+  h->tile_sources = bc.ks;
+  h->accumulate = bc.acc ? INV_ATOMIC : INV_ACCUM;
+  h->k1d_block = bc.kb;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (s != TDDFT_OK) return s;
+  if (best) STATUS_TRY(tddft_get_tuning(h, best));
   return TDDFT_OK;
 }
 
@@ -967,21 +1187,351 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Davidson (filled in below)
+// Davidson: block scheme with FP64 basis, orthogonalisation and Rayleigh-Ritz
 // ---------------------------------------------------------------------------
+
+// Hermitian eigenproblem of a small dense matrix (row-major, n x n) by cyclic
+// complex Jacobi rotations. Eigenvalues ascending in w, eigenvectors in the
+// columns of V (row-major). Returns false if the sweeps do not converge.
+static bool herm_eig(int n, std::vector<std::complex<double>> A, std::vector<double>& w,
+                     std::vector<std::complex<double>>& V) {
+  using C = std::complex<double>;
+  V.assign((size_t)n * n, C(0.0, 0.0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  auto at = [&](int i, int j) -> C& { return A[(size_t)i * n + j]; };
+  double fro = 0.0;
+  for (auto& z : A) fro += std::norm(z);
+  bool ok = false;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += std::norm(at(p, q));
+    if (off <= 1e-30 * std::max(fro, 1e-300)) {
+      ok = true;
+      break;
+    }
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const C apq = at(p, q);
+        const double r = std::abs(apq);
+        if (r < 1e-300) continue;
+        const C ph = apq / r;  // exp(i phi)
+        const double app = at(p, p).real(), aqq = at(q, q).real();
+        const double tau = (aqq - app) / (2.0 * r);
+        const double t = tau == 0.0 ? 1.0 : (tau > 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        // U = diag(1, conj(ph)) [[c, sn], [-sn, c]] acting on (p, q)
+        const C upp = c, upq = sn, uqp = -sn * std::conj(ph), uqq = c * std::conj(ph);
+        for (int k = 0; k < n; ++k) {  // A <- A U
+          const C akp = at(k, p), akq = at(k, q);
+          at(k, p) = akp * upp + akq * uqp;
+          at(k, q) = akp * upq + akq * uqq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- U^H A
+          const C apk = at(p, k), aqk = at(q, k);
+          at(p, k) = std::conj(upp) * apk + std::conj(uqp) * aqk;
+          at(q, k) = std::conj(upq) * apk + std::conj(uqq) * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // V <- V U
+          const C vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = vkp * upp + vkq * uqp;
+          V[(size_t)k * n + q] = vkp * upq + vkq * uqq;
+        }
+      }
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return at(x, x).real() < at(y, y).real(); });
+  std::vector<std::complex<double>> Vs((size_t)n * n);
+  w.resize(n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = at(idx[j], idx[j]).real();
+    for (int k = 0; k < n; ++k) Vs[(size_t)k * n + j] = V[(size_t)k * n + idx[j]];
+  }
+  V.swap(Vs);
+  return ok;
+}
+
+// y[i] = a[i] - theta * x[i]
+__global__ void k_residual(const cplx<double>* __restrict__ a, const cplx<double>* __restrict__ x, double theta,
+                           cplx<double>* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = {a[i].x - theta * x[i].x, a[i].y - theta * x[i].y};
+}
+
+// nrm[b] = ||x_b||_2 (one block per row of length len)
+__global__ void k_row_norms(const cplx<double>* __restrict__ x, long long len, double* __restrict__ nrm) {
+  __shared__ double red[256];
+  const long long b = blockIdx.x;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+    const cplx<double> u = x[b * len + i];
+    acc += u.x * u.x + u.y * u.y;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) nrm[b] = sqrt(red[0]);
+}
+
+// x /= max(||x||, tiny) with the norm from k_row_norms
+__global__ void k_normalize(cplx<double>* __restrict__ x, const double* __restrict__ nrm, long long len) {
+  const double s = 1.0 / fmax(nrm[0], 1e-300);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    x[i] = {x[i].x * s, x[i].y * s};
+}
+
+// t = r / d with d = |G|^2/2 - eps_v - theta, |d| clamped to >= 0.1 Ha (sign kept)
+__global__ void k_precondition(const cplx<double>* __restrict__ r, const double* __restrict__ g2h,
+                               const double* __restrict__ eps, double theta, int npw, long long len,
+                               cplx<double>* __restrict__ t) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    const long long v = i / npw, g = i - v * npw;
+    double d = g2h[g] - eps[v] - theta;
+    if (fabs(d) < 0.1) d = d < 0.0 ? -0.1 : 0.1;
+    t[i] = {r[i].x / d, r[i].y / d};
+  }
+}
+
 struct tddft_davidson {
   tddft_system* h = nullptr;
+  int nroots = 0, max_basis = 0, m = 0;
+  long long len = 0;  // nocc_src * npw
+  std::vector<void*> allocs;
+  cplx<double>* V = nullptr;   // [max_basis][len]
+  cplx<double>* LV = nullptr;  // [max_basis][len]
+  cplx<double>* X = nullptr;   // [nroots][len] Ritz vectors
+  cplx<double>* W = nullptr;   // [nroots][len] L applied to the Ritz vectors
+  cplx<double>* R = nullptr;   // [nroots][len] residuals, then corrections
+  void* tin = nullptr;         // [nroots][len] working precision
+  void* tout = nullptr;
+  cplx<double>* part = nullptr;   // split-K partials [nsplit][max_basis][max_basis]
+  cplx<double>* small = nullptr;  // [max_basis][max_basis]
+  double* g2h = nullptr;          // [npw]
+  double* eps = nullptr;          // [nocc_src]
+  double* nrm = nullptr;          // [max_basis]
+  int nsplit = 1;
+  std::vector<double> theta;
+  ~tddft_davidson() {
+    for (void* p : allocs) cudaFree(p);
+  }
 };
 
+static tddft_status dav_alloc(tddft_davidson* d, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  d->allocs.push_back(*p);
+  return TDDFT_OK;
+}
+
+// C[i][j] = <A_i|B_j> over rows of length len (i < ma, j < mb) into d->small
+static void dav_overlap(tddft_davidson* d, const cplx<double>* A, int ma, const cplx<double>* B, int mb,
+                        cudaStream_t st) {
+  const int kchunk = (int)(((d->len + d->nsplit - 1) / d->nsplit + 15) / 16 * 16);
+  dim3 g1((ma + 31) / 32, (mb + 31) / 32, d->nsplit);
+  { k_overlap<double><<<g1, 256, 0, st>>>(A, ma, B, mb, (int)d->len, kchunk, d->part); note_launch(); }
+  { k_reduce_split<double><<<grid_for((long long)ma * mb, 256), 256, 0, st>>>(d->part, d->nsplit, (long long)ma * mb,
+                                                                             d->small); note_launch(); }
+}
+
+// Y[n] += s * sum_m A[m] C[m][n]  (rows of length len, C is [ma][nn] in d->small or given)
+static void dav_combine(tddft_davidson* d, const cplx<double>* A, int ma, const cplx<double>* C, int nn, double s,
+                        cplx<double>* Y, cudaStream_t st) {
+  dim3 g2((unsigned)((d->len + 63) / 64), (nn + 31) / 32);
+  { k_update<double><<<g2, 256, 0, st>>>(A, ma, C, nn, (int)d->len, s, Y); note_launch(); }
+}
+
+// Orthogonalise t against the target orbitals (each of its nocc_src rows) and
+// the current basis, twice; normalise; append to the basis.
+static tddft_status dav_append(tddft_davidson* d, cplx<double>* t, cudaStream_t st) {
+  tddft_system* h = d->h;
+  for (int pass = 0; pass < 2; ++pass) {
+    STATUS_TRY(project_rows<double>(h, h->b.phi_tgt_pw64, h->d.nocc_tgt, t, h->d.nocc_src, st));
+    if (d->m > 0) {
+      dav_overlap(d, d->V, d->m, t, 1, st);
+      dav_combine(d, d->V, d->m, d->small, 1, -1.0, t, st);
+    }
+  }
+  { k_row_norms<<<1, 256, 0, st>>>(t, d->len, d->nrm); note_launch(); }
+  { k_normalize<<<grid_for(d->len, 256), 256, 0, st>>>(t, d->nrm, d->len); note_launch(); }
+  cplx<double>* dst = d->V + (long long)d->m * d->len;
+  if (dst != t) CUDA_TRY(cudaMemcpyAsync(dst, t, d->len * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, st));
+  d->m += 1;
+  return check_launch("davidson append");
+}
+
+// LV[m0 .. m) = L V[m0 .. m) through the handle's apply (working precision)
+template <typename T>
+static tddft_status dav_apply_new(tddft_davidson* d, int m0, cudaStream_t st) {
+  tddft_system* h = d->h;
+  for (int b0 = m0; b0 < d->m; b0 += d->h->d.nb_max) {
+    const int nb = std::min(d->h->d.nb_max, d->m - b0);
+    const long long cnt = (long long)nb * d->len;
+    { k_cast<T><<<grid_for(cnt, 256), 256, 0, st>>>(d->V + (long long)b0 * d->len, (cplx<T>*)d->tin, cnt); note_launch(); }
+    STATUS_TRY(apply_impl<T>(h, nb, (const cplx<T>*)d->tin, (cplx<T>*)d->tout, h->d.term_mask, st));
+    { k_widen<T><<<grid_for(cnt, 256), 256, 0, st>>>((const cplx<T>*)d->tout, d->LV + (long long)b0 * d->len, cnt); note_launch(); }
+  }
+  return check_launch("davidson apply");
+}
+
+static tddft_status dav_apply(tddft_davidson* d, int m0, cudaStream_t st) {
+  return d->h->d.precision == TDDFT_PREC_FP64 ? dav_apply_new<double>(d, m0, st) : dav_apply_new<float>(d, m0, st);
+}
+
 extern "C" {
-tddft_status tddft_davidson_create(tddft_handle, int, int, const double*, int, void*, tddft_dav_handle* out) {
-  if (out) *out = nullptr;
-  return fail(TDDFT_ENOTSUP, "Davidson not built yet");
+
+tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const double* X0, int max_basis,
+                                   void* stream, tddft_dav_handle* out) {
+  if (!h || !X0 || !out) return fail(TDDFT_EINVAL, "null argument");
+  *out = nullptr;
+  if (nroots < 1 || nguess < nroots) return fail(TDDFT_EINVAL, "need 1 <= nroots <= nguess");
+  if (max_basis < 2 * nroots || max_basis < nguess) return fail(TDDFT_EINVAL, "max_basis must be >= 2*nroots and >= nguess");
+  if (h->d.nb_max < nroots) return fail(TDDFT_EINVAL, "the handle's nb_max must be >= nroots");
+  if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "Davidson needs the projector term");
+  cudaStream_t st = (cudaStream_t)stream;
+  tddft_davidson* d = new tddft_davidson();
+  d->h = h;
+  d->nroots = nroots;
+  d->max_basis = max_basis;
+  d->len = (long long)h->d.nocc_src * h->npw;
+  d->nsplit = (int)std::max<long long>(1, std::min<long long>(64, d->len / 4096));
+  const size_t vb = (size_t)d->len * sizeof(cplx<double>);
+  tddft_status s = TDDFT_OK;
+  auto A = [&](void** p, size_t b) {
+    if (s == TDDFT_OK) s = dav_alloc(d, p, b);
+  };
+  A((void**)&d->V, vb * max_basis);
+  A((void**)&d->LV, vb * max_basis);
+  A((void**)&d->X, vb * nroots);
+  A((void**)&d->W, vb * nroots);
+  A((void**)&d->R, vb * std::max(nroots, nguess));
+  A(&d->tin, (size_t)d->len * h->esz() * h->d.nb_max);
+  A(&d->tout, (size_t)d->len * h->esz() * h->d.nb_max);
+  A((void**)&d->part, sizeof(cplx<double>) * d->nsplit * max_basis * max_basis);
+  A((void**)&d->small, sizeof(cplx<double>) * max_basis * max_basis);
+  A((void**)&d->g2h, sizeof(double) * h->npw);
+  A((void**)&d->eps, sizeof(double) * h->d.nocc_src);
+  A((void**)&d->nrm, sizeof(double) * max_basis);
+  if (s != TDDFT_OK) {
+    delete d;
+    return s;
+  }
+  // FP64 preconditioner tables
+  std::vector<Miller> sph;
+  tddft_status sb = build_sphere(h->n, h->d.a, h->d.ecut, sph);
+  if (sb != TDDFT_OK) {
+    delete d;
+    return sb;
+  }
+  const double tpiba = 2.0 * M_PI / h->d.a, tpiba2 = tpiba * tpiba;
+  std::vector<double> g2h(h->npw);
+  for (int i = 0; i < h->npw; ++i) g2h[i] = 0.5 * (tpiba2 * (double)sph[i].m2);
+  // the handle keeps eps in the working precision; Davidson keeps its own FP64 copy
+  std::vector<double> eps(h->d.nocc_src);
+  if (h->d.precision == TDDFT_PREC_FP64) {
+    cudaMemcpy(eps.data(), h->b.eps, eps.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  } else {
+    std::vector<float> e32(h->d.nocc_src);
+    cudaMemcpy(e32.data(), h->b.eps, e32.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < e32.size(); ++i) eps[i] = e32[i];
+  }
+  cudaMemcpyAsync(d->g2h, g2h.data(), g2h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d->eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d->R, X0, vb * nguess, cudaMemcpyHostToDevice, st);
+  for (int i = 0; i < nguess && s == TDDFT_OK; ++i) s = dav_append(d, d->R + (long long)i * d->len, st);
+  if (s == TDDFT_OK) s = dav_apply(d, 0, st);
+  if (s == TDDFT_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = fail(TDDFT_ECUDA, std::string("davidson create: ") + cudaGetErrorString(e));
+  }
+  if (s != TDDFT_OK) {
+    delete d;
+    return s;
+  }
+  *out = d;
+  return TDDFT_OK;
 }
-tddft_status tddft_davidson_step(tddft_dav_handle, double, int*, double*, double*, void*) {
-  return fail(TDDFT_ENOTSUP, "Davidson not built yet");
+
+tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converged, double* ritz_values,
+                                 double* residual_norms, void* stream) {
+  if (!d || !n_converged || !ritz_values) return fail(TDDFT_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m = d->m, nr = d->nroots;
+  // Rayleigh-Ritz: H = V^H L V (FP64), diagonalised on the host
+  dav_overlap(d, d->V, m, d->LV, m, st);
+  std::vector<std::complex<double>> H((size_t)m * m);
+  CUDA_TRY(cudaMemcpyAsync(H.data(), d->small, H.size() * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < m; ++i)
+    for (int j = i; j < m; ++j) {
+      const std::complex<double> a = 0.5 * (H[(size_t)i * m + j] + std::conj(H[(size_t)j * m + i]));
+      H[(size_t)i * m + j] = a;
+      H[(size_t)j * m + i] = std::conj(a);
+    }
+  std::vector<double> w;
+  std::vector<std::complex<double>> S;
+  if (!herm_eig(m, H, w, S)) return fail(TDDFT_ENUMERIC, "subspace eigensolver did not converge");
+  d->theta.assign(w.begin(), w.begin() + nr);
+  // S restricted to the lowest nr columns, [m][nr] row-major, to the device
+  std::vector<std::complex<double>> Sx((size_t)m * nr);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < nr; ++j) Sx[(size_t)i * nr + j] = S[(size_t)i * m + j];
+  CUDA_TRY(cudaMemcpyAsync(d->small, Sx.data(), Sx.size() * sizeof(cplx<double>), cudaMemcpyHostToDevice, st));
+  const size_t vb = (size_t)d->len * sizeof(cplx<double>);
+  CUDA_TRY(cudaMemsetAsync(d->X, 0, vb * nr, st));
+  CUDA_TRY(cudaMemsetAsync(d->W, 0, vb * nr, st));
+  dav_combine(d, d->V, m, d->small, nr, 1.0, d->X, st);
+  dav_combine(d, d->LV, m, d->small, nr, 1.0, d->W, st);
+  for (int i = 0; i < nr; ++i)
+    { k_residual<<<grid_for(d->len, 256), 256, 0, st>>>(d->W + (long long)i * d->len, d->X + (long long)i * d->len,
+                                                       d->theta[i], d->R + (long long)i * d->len, d->len); note_launch(); }
+  { k_row_norms<<<nr, 256, 0, st>>>(d->R, d->len, d->nrm); note_launch(); }
+  std::vector<double> rn(nr);
+  CUDA_TRY(cudaMemcpyAsync(rn.data(), d->nrm, nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  STATUS_TRY(check_launch("davidson step"));
+  int nconv = 0;
+  for (int i = 0; i < nr; ++i) nconv += rn[i] < tol;
+  for (int i = 0; i < nr; ++i) {
+    ritz_values[i] = d->theta[i];
+    if (residual_norms) residual_norms[i] = rn[i];
+  }
+  *n_converged = nconv;
+  if (nconv == nr) return TDDFT_OK;
+  // corrections for the unconverged roots
+  std::vector<int> todo;
+  for (int i = 0; i < nr; ++i)
+    if (!(rn[i] < tol)) todo.push_back(i);
+  for (int i : todo)
+    { k_precondition<<<grid_for(d->len, 256), 256, 0, st>>>(d->R + (long long)i * d->len, d->g2h, d->eps, d->theta[i],
+                                                           d->h->npw, d->len, d->R + (long long)i * d->len); note_launch(); }
+  // restart on the Ritz vectors when the basis would overflow
+  if (d->m + (int)todo.size() > d->max_basis) {
+    CUDA_TRY(cudaMemcpyAsync(d->V, d->X, vb * nr, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d->LV, d->W, vb * nr, cudaMemcpyDeviceToDevice, st));
+    d->m = nr;
+  }
+  const int m0 = d->m;
+  for (int i : todo) STATUS_TRY(dav_append(d, d->R + (long long)i * d->len, st));
+  STATUS_TRY(dav_apply(d, m0, st));
+  return TDDFT_OK;
 }
-tddft_status tddft_davidson_vectors(tddft_dav_handle, double*, void*) { return fail(TDDFT_ENOTSUP, "Davidson not built yet"); }
+
+tddft_status tddft_davidson_vectors(tddft_dav_handle d, double* X_host, void* stream) {
+  if (!d || !X_host) return fail(TDDFT_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(X_host, d->X, (size_t)d->nroots * d->len * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return TDDFT_OK;
+}
+
 tddft_status tddft_davidson_destroy(tddft_dav_handle d) {
   delete d;
   return TDDFT_OK;

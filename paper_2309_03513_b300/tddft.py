@@ -34,7 +34,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUM
 # every entry point declared in include/tddft.h
 EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
-    "tddft_set_tuning", "tddft_get_tuning", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -62,7 +62,7 @@ class Inputs(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
-                ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int)]
+                ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
         "tddft_set_terms": ([vp, ctypes.c_uint], st),
         "tddft_set_tuning": ([vp, ctypes.POINTER(Tuning)], st),
         "tddft_get_tuning": ([vp, ctypes.POINTER(Tuning)], st),
+        "tddft_autotune": ([vp, ci, vp, vp, vp, ctypes.POINTER(Tuning)], st),
+        "tddft_apply_liouville_multi": ([ci, vp, vp, vp, vp, vp], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -238,13 +240,24 @@ class LiouvilleSystem:
     def set_terms(self, mask: int):
         _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
 
-    def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1):
-        t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0)
+    def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
+                   graph: int = -1):
+        t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 
     def get_tuning(self) -> dict:
         t = Tuning()
         _check(load().tddft_get_tuning(self._h, ctypes.byref(t)), "tddft_get_tuning")
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def autotune(self, X, out=None, stream=None) -> dict:
+        """Time the library's candidate schedules on the batch X and keep the fastest."""
+        torch = self._check_batch(X)
+        if out is None:
+            out = torch.empty_like(X)
+        t = Tuning()
+        _check(load().tddft_autotune(self._h, X.shape[0], X.data_ptr(), out.data_ptr(), _stream_ptr(stream),
+                                     ctypes.byref(t)), "tddft_autotune")
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def set_tiling(self, targets: int = 0, sources: int = 0):
@@ -305,6 +318,22 @@ class LiouvilleSystem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def apply_multi(systems, Xs, outs=None, stream=None):
+    """L_i X_i for several systems in one graph launch (tddft_apply_liouville_multi)."""
+    n = len(systems)
+    if outs is None:
+        outs = [X.new_empty(X.shape) for X in Xs]
+    for s, X, o in zip(systems, Xs, outs):
+        s._check_batch(X)
+        s._check_batch(o)
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in systems])
+    nb = (ctypes.c_int * n)(*[X.shape[0] for X in Xs])
+    A = (ctypes.c_void_p * n)(*[X.data_ptr() for X in Xs])
+    LA = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(load().tddft_apply_liouville_multi(n, hs, nb, A, LA, _stream_ptr(stream)), "tddft_apply_liouville_multi")
+    return outs
 
 
 class Davidson:
