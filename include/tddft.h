@@ -45,7 +45,7 @@ typedef enum tddft_status {
   TDDFT_ENOTSUP = 7   /* combination not implemented */
 } tddft_status;
 
-/* Terms of L (Eq. 8 / Eq. 21 of the paper); a call applies the terms of the
+/* Terms of L (Eq. 9 / Eq. 21 of the paper); a call applies the terms of the
  * handle's mask. */
 #define TDDFT_TERM_D_KIN 1u   /* (1/2|G|^2 - eps_v) a_v            (Eq. 3, kinetic part of H^KS) */
 #define TDDFT_TERM_D_VLOC 2u  /* V_loc(r) a_v(r)                    (Eq. 3, local part of H^KS) */
@@ -145,7 +145,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);
  * the fastest on the handle and return it in *best (may be NULL). Synchronises. */
 tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, void* stream, tddft_tuning* best);
 
-/* LA = L A for nb trial vectors (Eq. 8 for SC, Eq. 21 for SF).
+/* LA = L A for nb trial vectors (Eq. 9 for SC, Eq. 21 for SF).
  * A, LA: device buffers [nb][nocc_src][npw] (complex128 for FP64 handles,
  * complex64 for FP32 handles). They must not alias. Each A_b is assumed
  * orthogonal to the target-spin orbitals (the operator is defined on that

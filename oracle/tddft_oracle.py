@@ -7,7 +7,7 @@ library and never imports it.
 What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
 
 * the Tamm-Dancoff eigen-operator L = D + K1e - K1d applied to a batch of
-  trial vectors A (Eq. 8), with D from Eq. 3 (H^KS contains the hybrid
+  trial vectors A (Eq. 9), with D from Eq. 3 (H^KS contains the hybrid
   exact exchange alpha*V_X of the exchange-operator equation in Sec. 3.1),
   K1e from Eq. 4 and K1d from Eq. 6, and the projector P^c = 1 - sum |phi><phi|
   stated after Eq. 7;
@@ -15,7 +15,7 @@ What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
   Hartree part, K1d^SF over source-spin pairs; Sec. 2.3);
 * the bilinear form omega = <X|L X> (the excitation energy of Sec. 2.2) and
   its gradient with respect to the occupied orbitals and the local potential
-  (the u_v ingredient of the Z-vector equation, Eq. 16, Supporting Information
+  (the u_v ingredient of the Z-vector equation, Eq. 19, defined in Eq. 20 and the Supporting Information
   Sec. S1), with X, eps, f_xc and the Coulomb kernels held fixed;
 * a dense matrix of L on tiny systems and a plain block-Davidson solver
   (Sec. 4 names Davidson's method for diagonalising L).
@@ -256,7 +256,7 @@ class System:
         return out
 
     def apply(self, X: np.ndarray, terms: int = ALL_TERMS, rows=None) -> np.ndarray:
-        """L X for X [nb, nocc_src, npw] (Eq. 8 / Eq. 21).
+        """L X for X [nb, nocc_src, npw] (Eq. 9 / Eq. 21).
 
         rows: optional list of (b, v) pairs; then only those rows are
         computed and returned as [len(rows), npw] (K1e still uses all v).
@@ -283,7 +283,7 @@ class System:
         """omega_b = <P^c X_b | M | P^c X_b>, M = the bracket of L without P^c.
 
         For X orthogonal to the occupied orbitals this is <X_b | L X_b>
-        (Eq. 8); written this way it stays real when the orbitals move, which
+        (Eq. 9); written this way it stays real when the orbitals move, which
         is what the gradient and the finite-difference checks differentiate.
         """
         P = self.project(np.asarray(X, dtype=np.complex128))

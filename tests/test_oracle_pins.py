@@ -268,7 +268,7 @@ def test_alpha_zero_removes_exchange():
 
 @pytest.mark.parametrize("sf", [False, True])
 def test_unitary_rotation_covariance(sf):
-    """phi_v = sum_n U_vn phit_n, at_n = sum_v' U*_v'n a_v' (Sec. 3.2, Eq. trunc):
+    """phi_v = sum_n U_vn phit_n, at_n = sum_v' U*_v'n a_v' (Sec. 3.2, Eq. 31):
     (L A)_v = sum_m U_vm (Lt At)_m when all eps_v are equal."""
     wl, S = _tiny(spin_flip=sf)
     nocc = wl.nocc_src
