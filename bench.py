@@ -245,6 +245,28 @@ def run_native(args):
     e2e = ws * args.e2e_steps * nb / t_e2e if args.e2e_steps > 0 else None
     io_bytes = nb * nocc * npw * 8
 
+    # per-term split (one step each, same batch): K1d-only apps/s etc.
+    term_ms = {}
+    if args.term_split:
+        for name, mask in (("D_exchange", T.TERM_D_EXX), ("K1d", T.TERM_K1D), ("K1e", T.TERM_K1E_H | T.TERM_K1E_XC),
+                           ("diagonal_and_projector", T.TERM_D_KIN | T.TERM_D_VLOC | T.TERM_PROJ)):
+            sys_.set_terms(mask)
+            sys_.apply(X, out=LA, stream=stream)
+            t0e = torch.cuda.Event(enable_timing=True)
+            t1e = torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            sys_.apply(X, out=LA, stream=stream)
+            t1e.record(stream)
+            torch.cuda.synchronize(dev)
+            term_ms[name] = t0e.elapsed_time(t1e)
+        sys_.set_terms(T.TERMS_ALL)
+
+    extras = {}
+    if "uneven" in args.extra:
+        extras["uneven12"] = bench_uneven(torch, T, dev, stream)
+    if "sf216" in args.extra:
+        extras["sf216"] = bench_sf216(torch, T, dev, stream)
+
     # plain FP64 GPU path on the same batch
     fp64 = None
     if args.fp64_steps > 0:
@@ -292,6 +314,9 @@ def run_native(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
         "clocks": clocks,
+        "terms_ms_per_step": term_ms or None,
+        "k1d_only_apps_per_s": (nb / (term_ms["K1d"] / 1e3)) if term_ms else None,
+        "extras": extras or None,
         "fp64_path": fp64,
         "speedup_vs_fp64_path": (value / fp64["value"]) if fp64 else None,
     }
@@ -306,6 +331,63 @@ def run_native(args):
     sys_.close()
 
 
+def bench_uneven(torch, T, dev, stream, steps=2):
+    """12 uneven systems (grids 48..96, 32..256 orbitals, 4..16 trial vectors, mixed
+    spin-conserving / spin-flip) in one CUDA-graph launch; applications/s over all systems."""
+    from paper_2309_03513_b300 import synth
+    systems, Xs = [], []
+    total_nb = 0
+    for i in range(1, 13):
+        n = [48, 64, 80, 96][(i - 1) % 4]
+        a = n * (13.48 / 72)
+        nocc = 32 + round(224 * (i - 1) / 11)
+        nbi = 4 * (1 + (i - 1) % 4)
+        sf = (i % 2 == 0)
+        wl = synth.make_workload(n=n, a=a, ecut=25.0, npw=T.sphere_size(n, a, 25.0), nocc_src=nocc, nb=nbi, seed=i,
+                                 spin_flip=sf, nocc_tgt=nocc - 2 if sf else None)
+        s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+        systems.append(s)
+        Xs.append(torch.from_numpy(wl.X).to(dev, torch.complex64))
+        total_nb += nbi
+    outs = [torch.empty_like(X) for X in Xs]
+    T.apply_multi(systems, Xs, outs, stream=stream)  # capture + first run
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        T.apply_multi(systems, Xs, outs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    for s in systems:
+        s.close()
+    return {"value": total_nb / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "trial_vectors": total_nb,
+            "steps": steps, "systems": 12, "note": "one CUDA-graph launch per step, one branch per system"}
+
+
+def bench_sf216(torch, T, dev, stream, steps=1):
+    """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path."""
+    from paper_2309_03513_b300 import synth
+    n, a = 108, 20.2
+    wl = synth.make_workload(n=n, a=a, ecut=25.0, npw=T.sphere_size(n, a, 25.0), nocc_src=433, nb=16, seed=0,
+                             spin_flip=True, nocc_tgt=431)
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    X = torch.from_numpy(wl.X).to(dev, torch.complex64)
+    LA = torch.empty_like(X)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        s.apply(X, out=LA, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    return {"value": 16 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": 0,
+            "pairs_per_step": 16 * 433 * 431 + 433 * 434 // 2}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +398,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")
+    ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip)")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()
