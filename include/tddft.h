@@ -136,6 +136,10 @@ typedef struct tddft_tuning {
   int graph;        /* 1: tddft_apply_liouville captures its launches into a CUDA
                        graph on first use for a given (nb, A, LA, term mask) and
                        replays it on the caller's stream; 0: plain launches */
+  int xy_kernel;    /* xy passes: 0 shared-memory radix stages; 1, 2, 4 register-resident
+                       lines with that many z-planes per CTA (FP32, n <= 80) */
+  int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
+                       (FP32, n <= 80). -1 keeps the value in set_tuning */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

@@ -63,6 +63,15 @@ __device__ __forceinline__ cplx<T> twmul(cplx<T> a, cplx<T> w) {
   else return cmulc(w, a);
 }
 
+// Twiddle accessors: tw(e) = W_N^e = exp(-2 pi i e / N) for the N of the transform.
+// TwPtr reads a table in shared memory; TwConst (below) reads the constant-memory
+// table, where a compile-time index becomes an immediate constant operand.
+template <typename T>
+struct TwPtr {
+  const cplx<T>* p;
+  __device__ __forceinline__ cplx<T> operator()(int e) const { return p[e]; }
+};
+
 // ---------------------------------------------------------------------------
 // Radix codelets: v[k] <- sum_n v[n] exp(DIR 2 pi i n k / R), natural order.
 // Mathematical constants: sqrt(3)/2, cos/sin(2 pi/5), cos/sin(4 pi/5), 1/sqrt(2).
@@ -119,8 +128,8 @@ __device__ __forceinline__ void dft5(cplx<T>* v) {
 
 // Multiply by exp(DIR 2 pi i E / R); exact for multiples of pi/4, table otherwise.
 // tw points at the length-N table, twstride = N / R.
-template <int DIR, int R, int E, typename T>
-__device__ __forceinline__ cplx<T> rot(cplx<T> a, const cplx<T>* tw, int twstride) {
+template <int DIR, int R, int E, typename T, typename TW>
+__device__ __forceinline__ cplx<T> rot(cplx<T> a, const TW& tw, int twstride) {
   constexpr int e = E % R;
   if constexpr (e == 0) {
     return a;
@@ -139,15 +148,15 @@ __device__ __forceinline__ cplx<T> rot(cplx<T> a, const cplx<T>* tw, int twstrid
     else if constexpr (o == 5) return {-w1.x, -w1.y};
     else return mul_di<-DIR>(w1);
   } else {
-    return twmul<DIR>(a, tw[e * twstride]);
+    return twmul<DIR>(a, tw(e * twstride));
   }
 }
 
-template <int R, int DIR, typename T>
-__device__ __forceinline__ void dft(cplx<T>* v, const cplx<T>* tw, int twstride);
+template <int R, int DIR, typename T, typename TW>
+__device__ __forceinline__ void dft(cplx<T>* v, const TW& tw, int twstride);
 
-template <int P, int Q, int DIR, typename T, int Q0, int K1>
-__device__ __forceinline__ void comp_rot(cplx<T>* t, cplx<T>* u, const cplx<T>* tw, int twstride) {
+template <int P, int Q, int DIR, typename T, int Q0, int K1, typename TW>
+__device__ __forceinline__ void comp_rot(cplx<T>* t, cplx<T>* u, const TW& tw, int twstride) {
   if constexpr (K1 < P) {
     u[Q0 * P + K1] = rot<DIR, P * Q, Q0 * K1>(t[K1], tw, twstride);
     comp_rot<P, Q, DIR, T, Q0, K1 + 1>(t, u, tw, twstride);
@@ -155,8 +164,8 @@ __device__ __forceinline__ void comp_rot(cplx<T>* t, cplx<T>* u, const cplx<T>* 
 }
 
 // Composite codelet R = P * Q: input index n = q + Q p, output k = k1 + P k2.
-template <int P, int Q, int DIR, typename T, int Q0 = 0>
-__device__ __forceinline__ void comp_first(cplx<T>* v, cplx<T>* u, const cplx<T>* tw, int twstride) {
+template <int P, int Q, int DIR, typename T, int Q0 = 0, typename TW>
+__device__ __forceinline__ void comp_first(cplx<T>* v, cplx<T>* u, const TW& tw, int twstride) {
   if constexpr (Q0 < Q) {
     cplx<T> t[P];
 #pragma unroll
@@ -167,8 +176,8 @@ __device__ __forceinline__ void comp_first(cplx<T>* v, cplx<T>* u, const cplx<T>
   }
 }
 
-template <int P, int Q, int DIR, typename T>
-__device__ __forceinline__ void dft_comp(cplx<T>* v, const cplx<T>* tw, int twstride) {
+template <int P, int Q, int DIR, typename T, typename TW>
+__device__ __forceinline__ void dft_comp(cplx<T>* v, const TW& tw, int twstride) {
   cplx<T> u[P * Q];
   comp_first<P, Q, DIR, T, 0>(v, u, tw, twstride);
 #pragma unroll
@@ -183,8 +192,8 @@ __device__ __forceinline__ void dft_comp(cplx<T>* v, const cplx<T>* tw, int twst
 }
 
 // twstride: index step in the length-N table for W_R (N / R).
-template <int R, int DIR, typename T>
-__device__ __forceinline__ void dft(cplx<T>* v, const cplx<T>* tw, int twstride) {
+template <int R, int DIR, typename T, typename TW>
+__device__ __forceinline__ void dft(cplx<T>* v, const TW& tw, int twstride) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     dft2<DIR>(v);
@@ -281,7 +290,7 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
         const int i = base + M * n2;
         v[n2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
       }
-      dft<R, FWD>(v, tw, N / R);
+      dft<R, FWD>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2)
         if (n1) v[k2] = twmul<FWD>(v[k2], tw[n1 * k2 * TWS]);
@@ -298,7 +307,7 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
         v[k2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
         if (k2 && n1) v[k2] = twmul<INV>(v[k2], tw[n1 * k2 * TWS]);
       }
-      dft<R, INV>(v, tw, N / R);
+      dft<R, INV>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll
       for (int n2 = 0; n2 < R; ++n2) {
         const int i = base + M * n2;
@@ -318,6 +327,73 @@ __device__ __forceinline__ void fft_lines(cplx<T>* s, const cplx<T>* tw, int lin
     stage<T, N, st, DIR, ROWS>(s, tw, line, g);
     __syncthreads();
     fft_lines<T, N, DIR, ROWS, S + 1>(s, tw, line, g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Constant-memory twiddle tables (one per translation unit; filled by the
+// launchers' prepare()) and the register-resident 1D transform.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int tw_offset(int n) {
+  constexpr int sizes[] = {8, 12, 16, 24, 32, 36, 48, 64, 72, 80, 96, 108, 128};
+  int off = 0;
+  for (int s : sizes) {
+    if (s == n) return off;
+    off += s;
+  }
+  return -1;
+}
+constexpr int TW_TOTAL = 724;  // sum of the supported sizes
+static __constant__ cplx<float> c_tw_f32[TW_TOTAL];
+static __constant__ cplx<double> c_tw_f64[TW_TOTAL];
+
+template <typename T, int N>
+struct TwConst {
+  __device__ __forceinline__ cplx<T> operator()(int e) const {
+    if constexpr (sizeof(T) == 4) return c_tw_f32[tw_offset(N) + e];
+    else return c_tw_f64[tw_offset(N) + e];
+  }
+};
+
+// Whole length-N transform of v[0..N) held in registers: forward = DIF
+// (natural in, digit-reversed out), inverse = DIT (digit-reversed in, natural out).
+template <typename T, int N, int DIR, typename TW, int S = 0>
+__device__ __forceinline__ void fft_reg(cplx<T>* v, const TW& tw) {
+  constexpr int NS = Plan<N>::S;
+  if constexpr (S < NS) {
+    constexpr int st = (DIR == FWD) ? S : (NS - 1 - S);
+    constexpr int R = Plan<N>::r[st];
+    constexpr int L = plan_block<N, st>();
+    constexpr int M = L / R;
+    constexpr int TWS = N / L;
+#pragma unroll
+    for (int blk = 0; blk < N / L; ++blk) {
+#pragma unroll
+      for (int n1 = 0; n1 < M; ++n1) {
+        const int base = blk * L + n1;
+        cplx<T> x[R];
+        if constexpr (DIR == FWD) {
+#pragma unroll
+          for (int n2 = 0; n2 < R; ++n2) x[n2] = v[base + M * n2];
+          dft<R, FWD>(x, tw, N / R);
+#pragma unroll
+          for (int k2 = 1; k2 < R; ++k2)
+            if (n1) x[k2] = twmul<FWD>(x[k2], tw(n1 * k2 * TWS));
+#pragma unroll
+          for (int k2 = 0; k2 < R; ++k2) v[base + M * k2] = x[k2];
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < R; ++k2) {
+            x[k2] = v[base + M * k2];
+            if (k2 && n1) x[k2] = twmul<INV>(x[k2], tw(n1 * k2 * TWS));
+          }
+          dft<R, INV>(x, tw, N / R);
+#pragma unroll
+          for (int n2 = 0; n2 < R; ++n2) v[base + M * n2] = x[n2];
+        }
+      }
+    }
+    fft_reg<T, N, DIR, TW, S + 1>(v, tw);
   }
 }
 

@@ -111,6 +111,39 @@ __global__ void __launch_bounds__(plane_threads<N>())
   }
 }
 
+// Register-resident z pass: one thread per (x, y) column holds the whole
+// column of N values, so the transform needs neither shared memory nor a
+// barrier; loads and stores of a warp cover 32 consecutive columns of one
+// z-plane (coalesced). Used where the column fits the register file.
+template <typename T, int N>
+__host__ __device__ constexpr bool z_in_registers() {
+  return sizeof(T) == 4 && N >= 8 && N <= 80;
+}
+constexpr int ZREG_THREADS = 128;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ZREG_THREADS)
+    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale) {
+  constexpr int N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  const int c = blockIdx.x * ZREG_THREADS + threadIdx.x;
+  if (c >= N2) return;
+  cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + c;
+  cplx<T> v[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = B[(long long)z * N2];
+  TwConst<T, N> tw;
+  if constexpr (MODE != Z_INV) fft_reg<T, N, FWD>(v, tw);
+  if constexpr (MODE == Z_CONV) {
+    const T* K = kern + c;
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = cscale(v[z], K[(long long)z * N2] * kscale);
+  }
+  if constexpr (MODE != Z_FWD) fft_reg<T, N, INV>(v, tw);
+#pragma unroll
+  for (int z = 0; z < N; ++z) B[(long long)z * N2] = v[z];
+}
+
 // ---------------------------------------------------------------------------
 // Inverse xy pass.
 // INV_WRITE: out field (o0 + t*ot) plane z = scale * IFFT_xy(ibuf item t).
@@ -216,6 +249,117 @@ __global__ void __launch_bounds__(plane_threads<N>())
 }
 
 // ---------------------------------------------------------------------------
+// Register-line xy passes (used where z_in_registers holds): a CTA works on
+// XY_PLANES consecutive z-planes of one item with one thread per line. A
+// plane makes one round trip through shared memory (the transpose between the
+// x and the y transform); each 1D transform runs in registers.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int XY_PLANES>
+__host__ __device__ constexpr int xyreg_threads() {
+  return (N * XY_PLANES + 31) / 32 * 32;
+}
+template <typename T, int N, int XY_PLANES>
+__host__ __device__ constexpr size_t xyreg_smem() {
+  return (size_t)XY_PLANES * N * plane_pitch<N>() * sizeof(cplx<T>);
+}
+
+template <typename T, int N, int MODE, int XY_PLANES>
+__global__ void __launch_bounds__(xyreg_threads<T, N, XY_PLANES>())
+    k_xy_fwd_reg(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
+                 cplx<T>* __restrict__ ibuf) {
+  constexpr int NT = xyreg_threads<T, N, XY_PLANES>(), PITCH = plane_pitch<N>(), N2 = N * N, PS = N * PITCH;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int tid = threadIdx.x, z0 = blockIdx.x * XY_PLANES, item = blockIdx.y;
+  const int t = item / pm.kdim, k = item - t * pm.kdim;
+  const bool active = tid < N * XY_PLANES;
+  const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z0, N3, N2);
+  const cplx<T>* Q = nullptr;
+  if constexpr (MODE == XY_PRODUCT) Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z0, N3, N2);
+  // coalesced load of XY_PLANES consecutive planes (contiguous in memory)
+#pragma unroll 4
+  for (int e = tid; e < XY_PLANES * N2; e += NT) {
+    const int p = e / N2, r = e - p * N2, y = r / N, x = r - y * N;
+    s[p * PS + y * PITCH + x] = (MODE == XY_PRODUCT) ? cmulc(Q[e], R[e]) : R[e];
+  }
+  __syncthreads();
+  const int p = active ? tid / N : 0, l = active ? tid - p * N : 0;
+  cplx<T>* sp = s + p * PS;
+  TwConst<T, N> tw;
+  cplx<T> v[N];
+  // x transform: thread = row l
+  if (active) {
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = sp[l * PITCH + x];
+    fft_reg<T, N, FWD>(v, tw);
+#pragma unroll
+    for (int x = 0; x < N; ++x) sp[l * PITCH + x] = v[x];
+  }
+  __syncthreads();
+  if (!active) return;
+  // y transform: thread = column l, written straight to global (coalesced over l)
+#pragma unroll
+  for (int y = 0; y < N; ++y) v[y] = sp[y * PITCH + l];
+  fft_reg<T, N, FWD>(v, tw);
+  cplx<T>* O = ibuf + (long long)item * N3 + (long long)(z0 + p) * N2 + l;
+#pragma unroll
+  for (int y = 0; y < N; ++y) O[y * N] = v[y];
+}
+
+template <typename T, int N, int MODE, int XY_PLANES>
+__global__ void __launch_bounds__(xyreg_threads<T, N, XY_PLANES>())
+    k_xy_inv_reg(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm, T scale) {
+  constexpr int NT = xyreg_threads<T, N, XY_PLANES>(), PITCH = plane_pitch<N>(), N2 = N * N, PS = N * PITCH;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int tid = threadIdx.x, z0 = blockIdx.x * XY_PLANES, item = blockIdx.y;
+  const bool active = tid < N * XY_PLANES;
+  const int p = active ? tid / N : 0, l = active ? tid - p * N : 0;
+  cplx<T>* sp = s + p * PS;
+  TwConst<T, N> tw;
+  cplx<T> v[N];
+  if (active) {
+    // y transform: thread = column l, read straight from global (coalesced over l)
+    const cplx<T>* I = ibuf + (long long)item * N3 + (long long)(z0 + p) * N2 + l;
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = I[y * N];
+    fft_reg<T, N, INV>(v, tw);
+#pragma unroll
+    for (int y = 0; y < N; ++y) sp[y * PITCH + l] = v[y];
+  }
+  __syncthreads();
+  if (active) {
+    // x transform: thread = row l
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = sp[l * PITCH + x];
+    fft_reg<T, N, INV>(v, tw);
+#pragma unroll
+    for (int x = 0; x < N; ++x) sp[l * PITCH + x] = v[x];
+  }
+  __syncthreads();
+  // coalesced epilogue over the XY_PLANES planes
+  if constexpr (MODE == INV_WRITE) {
+    cplx<T>* O = ob + (long long)(pm.o0 + (long long)item * pm.ot) * N3 + (long long)z0 * N2;
+#pragma unroll 4
+    for (int e = tid; e < XY_PLANES * N2; e += NT) {
+      const int pp = e / N2, r = e - pp * N2, y = r / N, x = r - y * N;
+      O[e] = cscale(s[pp * PS + y * PITCH + x], scale);
+    }
+  } else {  // INV_ATOMIC: item = t * kdim + k
+    const int t = item / pm.kdim, k = item - t * pm.kdim;
+    const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)t * pm.pt, z0, N3, N2);
+    cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z0 * N2;
+#pragma unroll 4
+    for (int e = tid; e < XY_PLANES * N2; e += NT) {
+      const int pp = e / N2, r = e - pp * N2, y = r / N, x = r - y * N;
+      atomic_cadd(O + e, cscale(cmul(P[e], s[pp * PS + y * PITCH + x]), scale));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Pointwise kernels
 // ---------------------------------------------------------------------------
 
@@ -289,8 +433,9 @@ __global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict
 //            tau_{v'v} = conj(tau_{vv'}) because the kernel is real and even)
 // Block of TB x PTS threads: thread (q, p) owns orbital q of its side and grid
 // point r = blockIdx.x * PTS + p; it keeps its TB tau values in registers and
-// loops over the trial vectors b. Each (b, orbital, point) is written once.
-template <typename T, int TB, int PTS, int SIDE>
+// accumulates BB trial vectors at once, so that all loads of a chunk are
+// independent. Each (b, orbital, point) is written once.
+template <typename T, int TB, int PTS, int SIDE, int BB>
 __global__ void __launch_bounds__(TB * PTS)
     k_k1d_contract(const cplx<T>* __restrict__ tau, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out, int i0,
                    int ti, int j0, int tj, int nocc, int nb, T s, long long n3) {
@@ -312,14 +457,26 @@ __global__ void __launch_bounds__(TB * PTS)
   }
   const int src0 = SIDE == 0 ? j0 : i0;
   const int dst = (SIDE == 0 ? i0 : j0) + q;
-  for (int b = 0; b < nb; ++b) {
-    const cplx<T>* ab = a + ((long long)b * nocc + src0) * n3 + r;
-    cplx<T> acc = {T(0), T(0)};
+  for (int b0 = 0; b0 < nb; b0 += BB) {
+    const int bn = min(BB, nb - b0);
+    cplx<T> acc[BB];
 #pragma unroll
-    for (int k = 0; k < TB; ++k)
-      if (k < nk) acc = cadd(acc, cmul(ab[(long long)k * n3], tv[k]));
-    cplx<T>* o = out + ((long long)b * nocc + dst) * n3 + r;
-    *o = cadd(*o, cscale(acc, s));
+    for (int bb = 0; bb < BB; ++bb) acc[bb] = {T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < TB; ++k) {
+      if (k < nk) {
+#pragma unroll
+        for (int bb = 0; bb < BB; ++bb)
+          if (bb < bn) acc[bb] = cadd(acc[bb], cmul(a[((long long)(b0 + bb) * nocc + src0 + k) * n3 + r], tv[k]));
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < BB; ++bb) {
+      if (bb < bn) {
+        cplx<T>* o = out + ((long long)(b0 + bb) * nocc + dst) * n3 + r;
+        *o = cadd(*o, cscale(acc[bb], s));
+      }
+    }
   }
 }
 

@@ -292,7 +292,7 @@ struct tddft_system {
   long long n3 = 0;
   int nb_chunk = 0;
   int ibuf_fields = 0;
-  int tile_targets = 8, tile_sources = 8, k1d_block = 16;
+  int tile_targets = 16, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int nsplit = 1;
   size_t bytes = 0;
@@ -488,10 +488,10 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       {
         constexpr int KB = 16, PTS = 16;
         const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
-        { k_k1d_contract<T, KB, PTS, 0><<<blocks, KB * PTS, 0, st>>>(
+        { k_k1d_contract<T, KB, PTS, 0, 1><<<blocks, KB * PTS, 0, st>>>(
             ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
         if (i0 != j0)
-          { k_k1d_contract<T, KB, PTS, 1><<<blocks, KB * PTS, 0, st>>>(
+          { k_k1d_contract<T, KB, PTS, 1, 1><<<blocks, KB * PTS, 0, st>>>(
               ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
       }
     }
@@ -1039,6 +1039,21 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
   if (t->k1d_block) h->k1d_block = t->k1d_block;
   if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
   if (t->graph >= 0) h->use_graph = t->graph == 1;
+  if (t->xy_kernel >= 0) {
+    if (!(t->xy_kernel == 0 || t->xy_kernel == 1 || t->xy_kernel == 2 || t->xy_kernel == 4))
+      return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 4");
+    const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
+    if (t->xy_kernel && !reg) return fail(TDDFT_EINVAL, "register-resident passes need FP32 and n <= 80");
+    h->ops32.kc.xy = t->xy_kernel;
+    h->ops64.kc.xy = t->xy_kernel;
+  }
+  if (t->z_kernel >= 0) {
+    if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
+    const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
+    if (t->z_kernel && !reg) return fail(TDDFT_EINVAL, "register-resident passes need FP32 and n <= 80");
+    h->ops32.kc.z = t->z_kernel;
+    h->ops64.kc.z = t->z_kernel;
+  }
   if (h->gexec) {  // the schedule changed: the next graph call captures again
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -1059,6 +1074,9 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->accumulate = h->accumulate == INV_ATOMIC ? 1 : 0;
   t->batch_fields = h->ibuf_fields;
   t->graph = h->use_graph ? 1 : 0;
+  const KernelChoice kc = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.kc : h->ops64.kc;
+  t->xy_kernel = kc.xy;
+  t->z_kernel = kc.z;
   return TDDFT_OK;
 }
 
@@ -1124,8 +1142,8 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
   struct Cand {
     int tt, ks, acc, kb;
   };
-  const Cand cands[] = {{8, 8, 1, 16}, {16, 4, 1, 16}, {4, 16, 1, 16}, {16, 8, 1, 16}, {32, 2, 1, 16},
-                        {8, 8, 0, 16},  {16, 8, 0, 16}, {8, 8, 1, 8}};
+  const Cand cands[] = {{16, 8, 1, 16}, {8, 8, 1, 16}, {32, 4, 1, 16}, {16, 4, 1, 16}, {4, 16, 1, 16},
+                        {16, 8, 0, 16},  {8, 8, 1, 8}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));

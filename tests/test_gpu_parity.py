@@ -100,6 +100,19 @@ def test_ragged_tiles_give_the_same_result(torch):
     assert _rel_err(got, want).max() < 1e-5
 
 
+@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0)])
+def test_kernel_variants_fp32(torch, n, a, ecut):
+    """Every plane-pass variant (staged / register-resident xy with 1, 2, 4 planes per
+    CTA, staged / register-resident z, loop / atomic accumulation) gives the oracle's L."""
+    wl = _workload(n, a, ecut, 6, 2, seed=15)
+    want = O.system_from_workload(wl).apply(wl.X)
+    for xy in (0, 1, 2, 4):
+        for z in (0, 1):
+            for acc in (0, 1):
+                got = _run(torch, wl, T.PREC_FP32, tiling=(3, 4, 5, acc, -1, xy, z))
+                assert _rel_err(got, want).max() < 1e-5, (xy, z, acc)
+
+
 def test_host_buffer_entry_point(torch):
     wl = _workload(24, 10.0, 10.0, 8, 4)
     want = O.system_from_workload(wl).apply(wl.X)
