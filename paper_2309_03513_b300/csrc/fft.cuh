@@ -252,6 +252,30 @@ __host__ __device__ constexpr int plan_block() {  // L_s
   return l;
 }
 
+// Per-stage twiddle tables: stage s stores W_{L_s}^{n1 k2} at [k2 * M_s + n1]
+// (k2 < R_s, n1 < M_s), L_s entries, so that lanes with consecutive n1 read
+// consecutive words. The tables of all stages follow each other.
+template <int N, int S>
+__host__ __device__ constexpr int stage_tw_off() {
+  int off = 0;
+  for (int i = 0; i < S; ++i) {
+    int l = N;
+    for (int j = 0; j < i; ++j) l /= Plan<N>::r[j];
+    off += l;
+  }
+  return off;
+}
+template <int N>
+__host__ __device__ constexpr int stage_tw_len() {
+  return stage_tw_off<N, Plan<N>::S>();
+}
+// Shared-memory twiddle region of the staged kernels: the length-N table
+// followed by the per-stage tables.
+template <int N>
+__host__ __device__ constexpr int tw_table_len() {
+  return N + stage_tw_len<N>();
+}
+
 // Threads per line: a CTA of N * G threads works on N lines at once.
 template <int N>
 __host__ __device__ constexpr int lines_group() {
@@ -277,8 +301,8 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
   constexpr int M = L / R;
   constexpr int G = lines_group<N>();
   constexpr int NB = N / R;         // butterflies per line
-  constexpr int TWS = N / L;        // twiddle stride for W_L
   constexpr int PITCH = plane_pitch<N>();
+  const cplx<T>* stw = tw + N + stage_tw_off<N, S>();  // [k2 * M + n1]
 #pragma unroll 1
   for (int j = g; j < NB; j += G) {
     const int blk = j / M, n1 = j - blk * M;
@@ -293,7 +317,7 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
       dft<R, FWD>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2)
-        if (n1) v[k2] = twmul<FWD>(v[k2], tw[n1 * k2 * TWS]);
+        if (n1) v[k2] = twmul<FWD>(v[k2], stw[k2 * M + n1]);
 #pragma unroll
       for (int k2 = 0; k2 < R; ++k2) {
         const int i = base + M * k2;
@@ -305,7 +329,7 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
       for (int k2 = 0; k2 < R; ++k2) {
         const int i = base + M * k2;
         v[k2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
-        if (k2 && n1) v[k2] = twmul<INV>(v[k2], tw[n1 * k2 * TWS]);
+        if (k2 && n1) v[k2] = twmul<INV>(v[k2], stw[k2 * M + n1]);
       }
       dft<R, INV>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll

@@ -40,10 +40,10 @@ __global__ void __launch_bounds__(plane_threads<N>())
   constexpr long long N3 = (long long)N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* s = tw + N;
+  cplx<T>* s = tw + tw_table_len<N>();
   const int tid = threadIdx.x, z = blockIdx.x, item = blockIdx.y;
   const int t = item / pm.kdim, k = item - t * pm.kdim;
-  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
   const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z, N3, N2);
   if constexpr (MODE == XY_PRODUCT) {
     const cplx<T>* Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z, N3, N2);
@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(plane_threads<N>())
   constexpr long long N3 = (long long)N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* s = tw + N;
+  cplx<T>* s = tw + tw_table_len<N>();
   const int tid = threadIdx.x, y = blockIdx.x, item = blockIdx.y;
-  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
   cplx<T>* B = ibuf + (long long)item * N3 + (long long)y * N;
   for (int e = tid; e < N2; e += NT) {
     const int z = e / N, x = e - z * N;
@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(plane_threads<N>())
   constexpr long long N3 = (long long)N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* s = tw + N;
+  cplx<T>* s = tw + tw_table_len<N>();
   const int tid = threadIdx.x, z = blockIdx.x, t = blockIdx.y;
-  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
   const int line = tid % N, g = tid / N;
   cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z * N2;
   if constexpr (MODE == INV_WRITE) {
@@ -427,54 +427,61 @@ __global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict
 }
 
 // K1d contraction for one block of pairs (v in I = [i0, i0+ti), v' in J = [j0, j0+tj)),
-// tau[(vi*tj + vj)] = Conv_x[conj(phi_v') phi_v] in real space.
-//   SIDE 0:  out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
-//   SIDE 1:  out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj])   (blocks with I != J;
-//            tau_{v'v} = conj(tau_{vv'}) because the kernel is real and even)
-// Block of TB x PTS threads: thread (q, p) owns orbital q of its side and grid
-// point r = blockIdx.x * PTS + p; it keeps its TB tau values in registers and
-// accumulates BB trial vectors at once, so that all loads of a chunk are
-// independent. Each (b, orbital, point) is written once.
-template <typename T, int TB, int PTS, int SIDE, int BB>
-__global__ void __launch_bounds__(TB * PTS)
+// tau[(vi*tj + vj)] = Conv_x[conj(phi_v') phi_v] in real space:
+//   out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
+//   and, when I != J, out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj])
+//   (tau_{v'v} = conj(tau_{vv'}) because the kernel is real and even).
+// A CTA of 256 threads takes PTS consecutive grid points: the tau values of
+// those points are staged once in shared memory with coalesced loads, then
+// thread (q, l) computes orbital q of each side for the points l + 16 j, for
+// every trial vector b. Each (b, orbital, point) is written once.
+constexpr int K1D_THREADS = 256;
+template <typename T, int TB, int PTS>
+__global__ void __launch_bounds__(K1D_THREADS)
     k_k1d_contract(const cplx<T>* __restrict__ tau, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out, int i0,
                    int ti, int j0, int tj, int nocc, int nb, T s, long long n3) {
-  const int q = threadIdx.x / PTS, p = threadIdx.x - q * PTS;
-  const long long r = (long long)blockIdx.x * PTS + p;
-  const int nq = SIDE == 0 ? ti : tj;   // outputs on this side
-  const int nk = SIDE == 0 ? tj : ti;   // summed index
-  if (q >= nq || r >= n3) return;
-  cplx<T> tv[TB];
-#pragma unroll
-  for (int k = 0; k < TB; ++k) {
-    if (k < nk) {
-      const long long item = SIDE == 0 ? (long long)q * tj + k : (long long)k * tj + q;
-      const cplx<T> t = tau[item * n3 + r];
-      tv[k] = SIDE == 0 ? t : cconj(t);
-    } else {
-      tv[k] = {T(0), T(0)};
-    }
+  static_assert(K1D_THREADS == TB * 16 && PTS % 16 == 0, "thread layout");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* st = reinterpret_cast<cplx<T>*>(smem_raw);  // [TB*TB][PTS]
+  const long long r0 = (long long)blockIdx.x * PTS;
+  const int npts = (int)min((long long)PTS, n3 - r0);
+  // the whole TB x TB tile is written (zeros outside ti x tj and past the last point)
+  for (int e = threadIdx.x; e < TB * TB * PTS; e += K1D_THREADS) {
+    const int slot = e / PTS, p = e - slot * PTS;
+    const int vi = slot / TB, vj = slot - vi * TB;
+    st[e] = (vi < ti && vj < tj && p < npts) ? tau[(long long)(vi * tj + vj) * n3 + r0 + p] : cplx<T>{T(0), T(0)};
   }
-  const int src0 = SIDE == 0 ? j0 : i0;
-  const int dst = (SIDE == 0 ? i0 : j0) + q;
-  for (int b0 = 0; b0 < nb; b0 += BB) {
-    const int bn = min(BB, nb - b0);
-    cplx<T> acc[BB];
+  __syncthreads();
+  const int q = threadIdx.x / 16, l = threadIdx.x - q * 16;
+  constexpr int PPT = PTS / 16;
+  const bool offdiag = (i0 != j0);
+  for (int side = 0; side < (offdiag ? 2 : 1); ++side) {
+    const int nq = side == 0 ? ti : tj, nk = side == 0 ? tj : ti;
+    if (q >= nq) continue;
+    const int src0 = side == 0 ? j0 : i0, dst = (side == 0 ? i0 : j0) + q;
+    for (int b = 0; b < nb; ++b) {
+      const cplx<T>* ab = a + ((long long)b * nocc + src0) * n3 + r0;
+      cplx<T>* ob = out + ((long long)b * nocc + dst) * n3 + r0;
+      // issue every load of this (side, b) before using any of them
+      cplx<T> av[PPT][TB], ov[PPT];
 #pragma unroll
-    for (int bb = 0; bb < BB; ++bb) acc[bb] = {T(0), T(0)};
+      for (int j = 0; j < PPT; ++j) {
+        const int p = l + 16 * j;
+        const bool okp = p < npts;
+        ov[j] = okp ? ob[p] : cplx<T>{T(0), T(0)};
 #pragma unroll
-    for (int k = 0; k < TB; ++k) {
-      if (k < nk) {
-#pragma unroll
-        for (int bb = 0; bb < BB; ++bb)
-          if (bb < bn) acc[bb] = cadd(acc[bb], cmul(a[((long long)(b0 + bb) * nocc + src0 + k) * n3 + r], tv[k]));
+        for (int k = 0; k < TB; ++k) av[j][k] = (okp && k < nk) ? ab[(long long)k * n3 + p] : cplx<T>{T(0), T(0)};
       }
-    }
 #pragma unroll
-    for (int bb = 0; bb < BB; ++bb) {
-      if (bb < bn) {
-        cplx<T>* o = out + ((long long)(b0 + bb) * nocc + dst) * n3 + r;
-        *o = cadd(*o, cscale(acc[bb], s));
+      for (int j = 0; j < PPT; ++j) {
+        const int p = l + 16 * j;
+        cplx<T> acc = {T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < TB; ++k) {
+          const cplx<T> tv = side == 0 ? st[(q * TB + k) * PTS + p] : cconj(st[(k * TB + q) * PTS + p]);
+          acc = cadd(acc, cmul(av[j][k], tv));
+        }
+        if (p < npts) ob[p] = cadd(ov[j], cscale(acc, s));
       }
     }
   }

@@ -54,7 +54,7 @@ struct PlaneOps {
 template <typename T, int N>
 struct PlaneLaunch {
   static constexpr int NT = plane_threads<N>();
-  static constexpr size_t SMEM = (size_t)(N + N * plane_pitch<N>()) * sizeof(cplx<T>);
+  static constexpr size_t SMEM = (size_t)(tw_table_len<N>() + N * plane_pitch<N>()) * sizeof(cplx<T>);
 
   static cudaError_t prepare() {
     cudaError_t e;
@@ -232,6 +232,27 @@ struct PlaneLaunch {
     return o;
   }
 };
+
+// Host twiddle table of the staged kernels for grid size N (see tw_table_len):
+// W_N^e for e < N, then per stage W_{L_s}^{n1 k2} at [k2 * M_s + n1]; FP64
+// std::cos / std::sin, rounded once to T.
+template <typename T>
+std::vector<cplx<T>> host_twiddles(int n, const std::vector<int>& radices) {
+  std::vector<cplx<T>> t;
+  auto w = [n](long long e) {
+    const double ang = -2.0 * M_PI * (double)e / (double)n;
+    return cplx<T>{(T)std::cos(ang), (T)std::sin(ang)};
+  };
+  for (int e = 0; e < n; ++e) t.push_back(w(e));
+  int l = n;
+  for (int r : radices) {
+    const int m = l / r, tws = n / l;
+    for (int k2 = 0; k2 < r; ++k2)
+      for (int n1 = 0; n1 < m; ++n1) t.push_back(w((long long)n1 * k2 * tws));
+    l = m;
+  }
+  return t;
+}
 
 // Dispatch by grid size; returns ops with n == 0 for an unsupported size.
 template <typename T>

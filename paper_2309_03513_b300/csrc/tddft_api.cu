@@ -486,13 +486,11 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
       {
-        constexpr int KB = 16, PTS = 16;
+        constexpr int KB = 16, PTS = 32;
+        const size_t smem = (size_t)KB * KB * PTS * sizeof(cplx<T>);
         const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
-        { k_k1d_contract<T, KB, PTS, 0, 1><<<blocks, KB * PTS, 0, st>>>(
+        { k_k1d_contract<T, KB, PTS><<<blocks, K1D_THREADS, smem, st>>>(
             ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
-        if (i0 != j0)
-          { k_k1d_contract<T, KB, PTS, 1, 1><<<blocks, KB * PTS, 0, st>>>(
-              ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
       }
     }
   }
@@ -558,17 +556,15 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   o = plane_ops_for<T>(n);
   if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
   CUDA_TRY(o.prepare());
+  CUDA_TRY(cudaFuncSetAttribute(k_k1d_contract<T, 16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(16 * 16 * 32 * sizeof(cplx<T>))));
 
   std::vector<int> radices = plan_radices(n);
   std::vector<int> rev(n);
   for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
 
-  // twiddles W_n^e = exp(-2 pi i e / n) in FP64 on the host, rounded once
-  std::vector<cplx<T>> tw(n);
-  for (int e = 0; e < n; ++e) {
-    const double ang = -2.0 * M_PI * (double)e / (double)n;
-    tw[e] = {(T)std::cos(ang), (T)std::sin(ang)};
-  }
+  // twiddles W_n^e = exp(-2 pi i e / n) and the per-stage tables, FP64 on the host, rounded once
+  std::vector<cplx<T>> tw = host_twiddles<T>(n, radices);
   // kernels in position order, divided by N_r
   const double tpiba = 2.0 * M_PI / d.a, tpiba2 = tpiba * tpiba;
   std::vector<T> kx(n3), kh(n3);
@@ -598,13 +594,13 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
 
   Buffers& B = h->b;
   const size_t ez = sizeof(cplx<T>), rz = sizeof(T);
-  STATUS_TRY(dalloc(h, &B.tw, n * ez));
+  STATUS_TRY(dalloc(h, &B.tw, tw.size() * ez));
   STATUS_TRY(dalloc(h, &B.kx, n3 * rz));
   STATUS_TRY(dalloc(h, &B.kh, n3 * rz));
   STATUS_TRY(dalloc(h, (void**)&B.pos, npw * sizeof(int)));
   STATUS_TRY(dalloc(h, &B.g2h, npw * rz));
   STATUS_TRY(dalloc(h, &B.eps, d.nocc_src * rz));
-  CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), n * ez, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * ez, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kx, kx.data(), n3 * rz, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kh, kh.data(), n3 * rz, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.pos, pos.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1569,8 +1565,8 @@ namespace {
 constexpr int NOALLOC_MAX_N = 48;
 constexpr size_t NOALLOC_N3 = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_MAX_N;
 // layout: twiddles | kernel table | sphere positions | orbital field | trial field | reciprocal-space field
-constexpr size_t NA_TW = 0;
-constexpr size_t NA_KERN = 1024;
+constexpr size_t NA_TW = 0;       // up to 3 * NOALLOC_MAX_N twiddles
+constexpr size_t NA_KERN = 2048;
 constexpr size_t NA_POS = NA_KERN + NOALLOC_N3 * sizeof(float);
 constexpr size_t NA_PHI = NA_POS + NOALLOC_N3 * sizeof(int);
 constexpr size_t NA_A = NA_PHI + NOALLOC_N3 * sizeof(cplx<float>);
@@ -1617,11 +1613,7 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
   // tables of this grid (the same host arithmetic as a handle's set-up)
   std::vector<int> radices = plan_radices(n), rev(n);
   for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
-  std::vector<cplx<float>> twh(n);
-  for (int e = 0; e < n; ++e) {
-    const double ang = -2.0 * M_PI * (double)e / (double)n;
-    twh[e] = {(float)std::cos(ang), (float)std::sin(ang)};
-  }
+  std::vector<cplx<float>> twh = host_twiddles<float>(n, radices);
   const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
   auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
   std::vector<float> kh(n3);
@@ -1635,7 +1627,7 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
   std::vector<int> posh(npw);
   for (int i = 0; i < npw; ++i)
     posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
-  CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), n * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
 
