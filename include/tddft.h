@@ -114,6 +114,9 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller);
 tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, void* stream,
                                tddft_handle* out);
 
+/* Sizes of the handle. Also synchronises the legacy stream and reports
+ * TDDFT_ETIMEOUT if a bounded device wait of the library ran out since the
+ * last check (the flag is then cleared). */
 tddft_status tddft_query(tddft_handle h, tddft_info* info);
 
 /* Change the term mask of the handle (TDDFT_TERM_* bits). */
@@ -140,6 +143,10 @@ typedef struct tddft_tuning {
                        lines with that many z-planes per CTA (FP32, n <= 80) */
   int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
                        (FP32, n <= 80). -1 keeps the value in set_tuning */
+  int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with
+                       split-precision TF32 products (hi*hi + hi*lo + lo*hi, FP32
+                       accumulation in tensor memory); 0 SIMT FP32. FP64 handles
+                       always use SIMT FP64. -1 keeps the value in set_tuning */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

@@ -15,6 +15,7 @@
 #include "../../include/tddft.h"
 #include "gemm.cuh"
 #include "plane_ops.cuh"
+#include "umma.cuh"
 
 using namespace tddft;
 
@@ -284,6 +285,7 @@ struct Buffers {
   void* io_b = nullptr;
   void* grad_r = nullptr;      // [nocc_src][n^3] (adjoint)
   double* wdev = nullptr;      // [nb_max]
+  int* dev_err = nullptr;      // set by a device wait that ran out of polls
 };
 
 struct tddft_system {
@@ -294,6 +296,7 @@ struct tddft_system {
   int ibuf_fields = 0;
   int tile_targets = 16, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
+  int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
   int nsplit = 1;
   size_t bytes = 0;
   Buffers b;
@@ -380,9 +383,49 @@ static tddft_status real_to_pw(tddft_system* h, const cplx<T>* src, int nf, cplx
 }
 
 // Y[n][:] -= sum_m Phi[m][:] <Phi_m|Y_n>  for nrows rows of length npw
+// Projector on tcgen05 tensor cores (FP32 data, 3xTF32 products, FP32 accumulation).
+static tddft_status project_rows_tc(tddft_system* h, const cplx<float>* phi, int M, cplx<float>* Y, int nrows,
+                                    cudaStream_t st) {
+  const int K = h->npw;
+  const int Kp = (K + UMMA_KC - 1) / UMMA_KC * UMMA_KC;
+  const int Rp = (nrows + UMMA_N - 1) / UMMA_N * UMMA_N;
+  const int kchunks = 2 * Kp / UMMA_KC;
+  const int mt = (M + UMMA_M - 1) / UMMA_M;
+  const int nt = 2 * Rp / UMMA_N;
+  int splits = std::max(1, std::min(kchunks, 296 / std::max(1, nt * mt)));
+  splits = std::min(splits, 2 * h->nsplit);
+  const int per = (kchunks + splits - 1) / splits;
+  splits = (kchunks + per - 1) / per;
+  cplx<float>* part = (cplx<float>*)h->b.cpart;
+  cplx<float>* C = (cplx<float>*)h->b.cmat;
+  {
+    OvA la{phi, M, K, Kp};
+    OvB lb{Y, nrows, Rp, K, Kp};
+    OvEp ep{part, M, nrows, Rp};
+    k_umma_gemm<OvA, OvB, OvEp><<<dim3(nt, mt, splits), 128, UMMA_SMEM, st>>>(la, lb, ep, kchunks, per, h->b.dev_err);
+    note_launch();
+  }
+  { k_reduce_split<float><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(part, splits, (long long)M * nrows, C); note_launch(); }
+  {
+    const int Up = (M + UMMA_KC - 1) / UMMA_KC * UMMA_KC;
+    const int Gp = (K + UMMA_N - 1) / UMMA_N * UMMA_N;
+    UpA la{C, M, Up, nrows};
+    UpB lb{phi, M, Up, K, Gp};
+    UpEp ep{Y, nrows, K, Gp};
+    const int kc2 = 2 * Up / UMMA_KC;
+    k_umma_gemm<UpA, UpB, UpEp><<<dim3(2 * Gp / UMMA_N, (nrows + UMMA_M - 1) / UMMA_M, 1), 128, UMMA_SMEM, st>>>(
+        la, lb, ep, kc2, kc2, h->b.dev_err);
+    note_launch();
+  }
+  return check_launch("projector (tensor cores)");
+}
+
 template <typename T>
 static tddft_status project_rows(tddft_system* h, const cplx<T>* phi, int M, cplx<T>* Y, int nrows, cudaStream_t st) {
   if (nrows <= 0 || M <= 0) return TDDFT_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (h->projector_tc) return project_rows_tc(h, phi, M, Y, nrows, st);
+  }
   const int K = h->npw;
   cplx<T>* C = (cplx<T>*)h->b.cmat;
   cplx<T>* Cp = (cplx<T>*)h->b.cpart;
@@ -558,6 +601,10 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   CUDA_TRY(o.prepare());
   CUDA_TRY(cudaFuncSetAttribute(k_k1d_contract<T, 16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(16 * 16 * 32 * sizeof(cplx<T>))));
+  CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<OvA, OvB, OvEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
+  CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<UpA, UpB, UpEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
+  STATUS_TRY(dalloc(h, (void**)&h->b.dev_err, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(h->b.dev_err, 0, sizeof(int), st));
 
   std::vector<int> radices = plan_radices(n);
   std::vector<int> rev(n);
@@ -891,6 +938,19 @@ static tddft_status build_multi_graph(int nsys, const tddft_handle* hs, const in
   return TDDFT_OK;
 }
 
+// Reads (and clears) the device error flag; synchronises the stream.
+static tddft_status check_device_flag(tddft_system* h, cudaStream_t st) {
+  if (!h->b.dev_err) return TDDFT_OK;
+  int flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flag, h->b.dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (flag) {
+    CUDA_TRY(cudaMemsetAsync(h->b.dev_err, 0, sizeof(int), st));
+    return fail(TDDFT_ETIMEOUT, "a bounded device wait (tensor-core projector) ran out; results of the call are invalid");
+  }
+  return TDDFT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1009,6 +1069,7 @@ tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, v
 
 tddft_status tddft_query(tddft_handle h, tddft_info* info) {
   if (!h || !info) return fail(TDDFT_EINVAL, "null argument");
+  STATUS_TRY(check_device_flag(h, nullptr));
   info->npw = h->npw;
   info->n = h->n;
   info->nb_chunk = h->nb_chunk;
@@ -1043,6 +1104,10 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->ops32.kc.xy = t->xy_kernel;
     h->ops64.kc.xy = t->xy_kernel;
   }
+  if (t->projector >= 0) {
+    if (t->projector > 1) return fail(TDDFT_EINVAL, "projector must be 0 or 1");
+    h->projector_tc = t->projector;
+  }
   if (t->z_kernel >= 0) {
     if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
     const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
@@ -1073,6 +1138,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   const KernelChoice kc = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.kc : h->ops64.kc;
   t->xy_kernel = kc.xy;
   t->z_kernel = kc.z;
+  t->projector = h->projector_tc;
   return TDDFT_OK;
 }
 
@@ -1098,7 +1164,7 @@ tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_ho
   STATUS_TRY(tddft_apply_liouville(h, nb, h->b.io_a, h->b.io_b, stream));
   CUDA_TRY(cudaMemcpyAsync(LA_host, h->b.io_b, bytes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  return TDDFT_OK;
+  return check_device_flag(h, st);
 }
 
 tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
@@ -1512,6 +1578,7 @@ tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converge
   CUDA_TRY(cudaStreamSynchronize(st));
   STATUS_TRY(check_launch("davidson step"));
   int nconv = 0;
+  STATUS_TRY(check_device_flag(d->h, st));
   for (int i = 0; i < nr; ++i) nconv += rn[i] < tol;
   for (int i = 0; i < nr; ++i) {
     ritz_values[i] = d->theta[i];

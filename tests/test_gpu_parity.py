@@ -113,6 +113,19 @@ def test_kernel_variants_fp32(torch, n, a, ecut):
                 assert _rel_err(got, want).max() < 1e-5, (xy, z, acc)
 
 
+def test_projector_tensor_cores_match_simt(torch):
+    """The tcgen05 projector (3xTF32 products, FP32 accumulation) against the SIMT
+    FP32 projector and the oracle, on a batch whose rows exceed one 128-row tile."""
+    wl = _workload(24, 10.0, 10.0, 40, 5, seed=16)
+    want = O.system_from_workload(wl).apply(wl.X)
+    tc = _run(torch, wl, T.PREC_FP32, tiling=(0, 0, 0, -1, -1, -1, -1, 1))
+    simt = _run(torch, wl, T.PREC_FP32, tiling=(0, 0, 0, -1, -1, -1, -1, 0))
+    assert _rel_err(tc, want).max() < 1e-5
+    assert _rel_err(tc, simt).max() < 2e-6
+    only_proj = _run(torch, wl, T.PREC_FP32, mask=T.TERM_D_KIN | T.TERM_PROJ, tiling=(0, 0, 0, -1, -1, -1, -1, 1))
+    assert _rel_err(only_proj, O.system_from_workload(wl).apply(wl.X, T.TERM_D_KIN | T.TERM_PROJ)).max() < 1e-5
+
+
 def test_host_buffer_entry_point(torch):
     wl = _workload(24, 10.0, 10.0, 8, 4)
     want = O.system_from_workload(wl).apply(wl.X)
