@@ -139,8 +139,12 @@ typedef struct tddft_tuning {
   int graph;        /* 1: tddft_apply_liouville captures its launches into a CUDA
                        graph on first use for a given (nb, A, LA, term mask) and
                        replays it on the caller's stream; 0: plain launches */
-  int xy_kernel;    /* xy passes: 0 shared-memory radix stages; 1, 2, 4 register-resident
-                       lines with that many z-planes per CTA (FP32, n <= 80) */
+  int prune;        /* 1: the z pass of pair convolutions transforms only the (k_x, k_y)
+                       columns inside the disc of radius 2 G_max and writes zeros to the
+                       others, which are exactly zero for products of two sphere
+                       functions when the grid does not alias them (checked at set-up;
+                       otherwise every column is transformed); 0: off. Register-
+                       resident z pass only. -1 keeps the value in set_tuning */
   int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
                        (FP32, n <= 80). -1 keeps the value in set_tuning */
   int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with

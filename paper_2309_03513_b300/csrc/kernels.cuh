@@ -121,14 +121,25 @@ __host__ __device__ constexpr bool z_in_registers() {
 }
 constexpr int ZREG_THREADS = 128;
 
+// cols (optional): the N^2 column positions with the nact columns that can be
+// non-zero first (ascending), then the others (ascending). Threads of the
+// first kind transform their column; threads of the second kind only write
+// zeros, which is what the transform of an all-zero column gives exactly.
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(ZREG_THREADS)
-    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale) {
+    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, const int* __restrict__ cols,
+            int nact) {
   constexpr int N2 = N * N;
   constexpr long long N3 = (long long)N * N * N;
-  const int c = blockIdx.x * ZREG_THREADS + threadIdx.x;
-  if (c >= N2) return;
+  const int i = blockIdx.x * ZREG_THREADS + threadIdx.x;
+  if (i >= N2) return;
+  const int c = cols ? cols[i] : i;
   cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + c;
+  if (cols && i >= nact) {
+#pragma unroll 8
+    for (int z = 0; z < N; ++z) B[(long long)z * N2] = cplx<T>{T(0), T(0)};
+    return;
+  }
   cplx<T> v[N];
 #pragma unroll
   for (int z = 0; z < N; ++z) v[z] = B[(long long)z * N2];
@@ -244,117 +255,6 @@ __global__ void __launch_bounds__(plane_threads<N>())
     for (int i = 0; i < EPT; ++i) {
       const int e = tid + i * NT;
       if (e < N2) O[e] = cadd(O[e], cscale(acc[i], scale));
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Register-line xy passes (used where z_in_registers holds): a CTA works on
-// XY_PLANES consecutive z-planes of one item with one thread per line. A
-// plane makes one round trip through shared memory (the transpose between the
-// x and the y transform); each 1D transform runs in registers.
-// ---------------------------------------------------------------------------
-template <typename T, int N, int XY_PLANES>
-__host__ __device__ constexpr int xyreg_threads() {
-  return (N * XY_PLANES + 31) / 32 * 32;
-}
-template <typename T, int N, int XY_PLANES>
-__host__ __device__ constexpr size_t xyreg_smem() {
-  return (size_t)XY_PLANES * N * plane_pitch<N>() * sizeof(cplx<T>);
-}
-
-template <typename T, int N, int MODE, int XY_PLANES>
-__global__ void __launch_bounds__(xyreg_threads<T, N, XY_PLANES>())
-    k_xy_fwd_reg(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
-                 cplx<T>* __restrict__ ibuf) {
-  constexpr int NT = xyreg_threads<T, N, XY_PLANES>(), PITCH = plane_pitch<N>(), N2 = N * N, PS = N * PITCH;
-  constexpr long long N3 = (long long)N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int tid = threadIdx.x, z0 = blockIdx.x * XY_PLANES, item = blockIdx.y;
-  const int t = item / pm.kdim, k = item - t * pm.kdim;
-  const bool active = tid < N * XY_PLANES;
-  const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z0, N3, N2);
-  const cplx<T>* Q = nullptr;
-  if constexpr (MODE == XY_PRODUCT) Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z0, N3, N2);
-  // coalesced load of XY_PLANES consecutive planes (contiguous in memory)
-#pragma unroll 4
-  for (int e = tid; e < XY_PLANES * N2; e += NT) {
-    const int p = e / N2, r = e - p * N2, y = r / N, x = r - y * N;
-    s[p * PS + y * PITCH + x] = (MODE == XY_PRODUCT) ? cmulc(Q[e], R[e]) : R[e];
-  }
-  __syncthreads();
-  const int p = active ? tid / N : 0, l = active ? tid - p * N : 0;
-  cplx<T>* sp = s + p * PS;
-  TwConst<T, N> tw;
-  cplx<T> v[N];
-  // x transform: thread = row l
-  if (active) {
-#pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = sp[l * PITCH + x];
-    fft_reg<T, N, FWD>(v, tw);
-#pragma unroll
-    for (int x = 0; x < N; ++x) sp[l * PITCH + x] = v[x];
-  }
-  __syncthreads();
-  if (!active) return;
-  // y transform: thread = column l, written straight to global (coalesced over l)
-#pragma unroll
-  for (int y = 0; y < N; ++y) v[y] = sp[y * PITCH + l];
-  fft_reg<T, N, FWD>(v, tw);
-  cplx<T>* O = ibuf + (long long)item * N3 + (long long)(z0 + p) * N2 + l;
-#pragma unroll
-  for (int y = 0; y < N; ++y) O[y * N] = v[y];
-}
-
-template <typename T, int N, int MODE, int XY_PLANES>
-__global__ void __launch_bounds__(xyreg_threads<T, N, XY_PLANES>())
-    k_xy_inv_reg(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm, T scale) {
-  constexpr int NT = xyreg_threads<T, N, XY_PLANES>(), PITCH = plane_pitch<N>(), N2 = N * N, PS = N * PITCH;
-  constexpr long long N3 = (long long)N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int tid = threadIdx.x, z0 = blockIdx.x * XY_PLANES, item = blockIdx.y;
-  const bool active = tid < N * XY_PLANES;
-  const int p = active ? tid / N : 0, l = active ? tid - p * N : 0;
-  cplx<T>* sp = s + p * PS;
-  TwConst<T, N> tw;
-  cplx<T> v[N];
-  if (active) {
-    // y transform: thread = column l, read straight from global (coalesced over l)
-    const cplx<T>* I = ibuf + (long long)item * N3 + (long long)(z0 + p) * N2 + l;
-#pragma unroll
-    for (int y = 0; y < N; ++y) v[y] = I[y * N];
-    fft_reg<T, N, INV>(v, tw);
-#pragma unroll
-    for (int y = 0; y < N; ++y) sp[y * PITCH + l] = v[y];
-  }
-  __syncthreads();
-  if (active) {
-    // x transform: thread = row l
-#pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = sp[l * PITCH + x];
-    fft_reg<T, N, INV>(v, tw);
-#pragma unroll
-    for (int x = 0; x < N; ++x) sp[l * PITCH + x] = v[x];
-  }
-  __syncthreads();
-  // coalesced epilogue over the XY_PLANES planes
-  if constexpr (MODE == INV_WRITE) {
-    cplx<T>* O = ob + (long long)(pm.o0 + (long long)item * pm.ot) * N3 + (long long)z0 * N2;
-#pragma unroll 4
-    for (int e = tid; e < XY_PLANES * N2; e += NT) {
-      const int pp = e / N2, r = e - pp * N2, y = r / N, x = r - y * N;
-      O[e] = cscale(s[pp * PS + y * PITCH + x], scale);
-    }
-  } else {  // INV_ATOMIC: item = t * kdim + k
-    const int t = item / pm.kdim, k = item - t * pm.kdim;
-    const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)t * pm.pt, z0, N3, N2);
-    cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z0 * N2;
-#pragma unroll 4
-    for (int e = tid; e < XY_PLANES * N2; e += NT) {
-      const int pp = e / N2, r = e - pp * N2, y = r / N, x = r - y * N;
-      atomic_cadd(O + e, cscale(cmul(P[e], s[pp * PS + y * PITCH + x]), scale));
     }
   }
 }

@@ -17,37 +17,40 @@ void note_launch();
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double bytes);
 
-// Kernel variants of the plane passes (KernelChoice, chosen per handle):
-// xy = 0: shared-memory staged radix stages; 1, 2, 4: register-resident lines
-// with that many z-planes per CTA (FP32 grids up to 80 only).
-// z = 0: shared-memory staged; 1: register-resident columns (same limit).
+// z = 0: shared-memory staged z pass; 1: register-resident columns (FP32, n <= 80).
 struct KernelChoice {
-  int xy = 0;
   int z = 1;
+};
+
+// Columns of the z pass that can be non-zero (see k_z_reg); nullptr = all.
+struct ColumnList {
+  const int* cols = nullptr;
+  int nact = 0;
 };
 
 template <typename T>
 struct PlaneOps {
   int n = 0;
-  bool reg_ok = false;  // register-resident variants exist for this (T, N)
+  bool reg_ok = false;  // the register-resident z pass exists for this (T, N)
   KernelChoice kc;
   cudaError_t (*prepare)() = nullptr;
-  void (*f_xy_fwd)(KernelChoice kc, int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items,
-                   cplx<T>* ibuf, const cplx<T>* tw, cudaStream_t st) = nullptr;
+  void (*f_xy_fwd)(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
+                   const cplx<T>* tw, cudaStream_t st) = nullptr;
   void (*f_z)(KernelChoice kc, int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw,
-              cudaStream_t st) = nullptr;
-  void (*f_xy_inv)(KernelChoice kc, int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm,
-                   int targets, T scale, const cplx<T>* tw, cudaStream_t st) = nullptr;
+              ColumnList cl, cudaStream_t st) = nullptr;
+  void (*f_xy_inv)(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
+                   const cplx<T>* tw, cudaStream_t st) = nullptr;
   void xy_fwd(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
               const cplx<T>* tw, cudaStream_t st) const {
-    f_xy_fwd(kc, mode, qb, rb, pm, items, ibuf, tw, st);
+    f_xy_fwd(mode, qb, rb, pm, items, ibuf, tw, st);
   }
-  void z(int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw, cudaStream_t st) const {
-    f_z(kc, mode, ibuf, items, kern, kscale, tw, st);
+  void z(int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw, cudaStream_t st,
+         ColumnList cl = ColumnList{}) const {
+    f_z(kc, mode, ibuf, items, kern, kscale, tw, cl, st);
   }
   void xy_inv(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
               const cplx<T>* tw, cudaStream_t st) const {
-    f_xy_inv(kc, mode, ibuf, ob, pb, pm, targets, scale, tw, st);
+    f_xy_inv(mode, ibuf, ob, pb, pm, targets, scale, tw, st);
   }
 };
 
@@ -83,23 +86,6 @@ struct PlaneLaunch {
     TDDFT_CARVE((k_xy_inv<T, N, INV_ACCUM>))
     TDDFT_CARVE((k_xy_inv<T, N, INV_ATOMIC>))
 #undef TDDFT_CARVE
-    if constexpr (z_in_registers<T, N>()) {
-#define TDDFT_ATTR2(K, PL)                                                                     \
-  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xyreg_smem<T, N, PL>()); \
-  if (e != cudaSuccess) return e;                                                              \
-  e = cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared); \
-  if (e != cudaSuccess) return e;
-#define TDDFT_ATTR_PL(PL)                                     \
-      TDDFT_ATTR2((k_xy_fwd_reg<T, N, XY_LOAD, PL>), PL)      \
-      TDDFT_ATTR2((k_xy_fwd_reg<T, N, XY_PRODUCT, PL>), PL)   \
-      TDDFT_ATTR2((k_xy_inv_reg<T, N, INV_WRITE, PL>), PL)    \
-      TDDFT_ATTR2((k_xy_inv_reg<T, N, INV_ATOMIC, PL>), PL)
-      TDDFT_ATTR_PL(1)
-      TDDFT_ATTR_PL(2)
-      TDDFT_ATTR_PL(4)
-#undef TDDFT_ATTR_PL
-#undef TDDFT_ATTR2
-    }
     // constant-memory twiddles W_N^e for the register-resident transforms,
     // computed in FP64 on the host and rounded once
     std::vector<cplx<T>> t(N);
@@ -114,44 +100,22 @@ struct PlaneLaunch {
     return e;
   }
 
-  template <int PL>
-  static void xy_fwd_reg_launch(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
-                                cudaStream_t st) {
-    dim3 g(N / PL, items);
-    constexpr int RT = xyreg_threads<T, N, PL>();
-    constexpr size_t RS = xyreg_smem<T, N, PL>();
-    if (mode == XY_PRODUCT)
-      k_xy_fwd_reg<T, N, XY_PRODUCT, PL><<<g, RT, RS, st>>>(qb, rb, pm, ibuf);
-    else
-      k_xy_fwd_reg<T, N, XY_LOAD, PL><<<g, RT, RS, st>>>(qb, rb, pm, ibuf);
-  }
-
-  static void xy_fwd(KernelChoice kc, int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items,
-                     cplx<T>* ibuf, const cplx<T>* tw, cudaStream_t st) {
+  static void xy_fwd(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
+                     const cplx<T>* tw, cudaStream_t st) {
     if (items <= 0) return;
     dim3 grid(N, items);
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
     prof_begin(KC_XY_FWD, st);
-    bool done = false;
-    if constexpr (z_in_registers<T, N>()) {
-      done = true;
-      if (kc.xy == 1) xy_fwd_reg_launch<1>(mode, qb, rb, pm, items, ibuf, st);
-      else if (kc.xy == 2) xy_fwd_reg_launch<2>(mode, qb, rb, pm, items, ibuf, st);
-      else if (kc.xy == 4) xy_fwd_reg_launch<4>(mode, qb, rb, pm, items, ibuf, st);
-      else done = false;
-    }
-    if (!done) {
-      if (mode == XY_PRODUCT)
-        k_xy_fwd<T, N, XY_PRODUCT><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
-      else
-        k_xy_fwd<T, N, XY_LOAD><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
-    }
+    if (mode == XY_PRODUCT)
+      k_xy_fwd<T, N, XY_PRODUCT><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
+    else
+      k_xy_fwd<T, N, XY_LOAD><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
     note_launch();
     prof_end(KC_XY_FWD, st, (mode == XY_PRODUCT ? 3.0 : 2.0) * F * items);
   }
 
   static void zl(KernelChoice kc, int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw,
-                 cudaStream_t st) {
+                 ColumnList cl, cudaStream_t st) {
     if (items <= 0) return;
     dim3 grid(N, items);
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
@@ -162,11 +126,11 @@ struct PlaneLaunch {
         done = true;
         dim3 g((N * N + ZREG_THREADS - 1) / ZREG_THREADS, items);
         if (mode == Z_CONV)
-          k_z_reg<T, N, Z_CONV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale);
+          k_z_reg<T, N, Z_CONV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, cl.cols, cl.nact);
         else if (mode == Z_FWD)
-          k_z_reg<T, N, Z_FWD><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale);
+          k_z_reg<T, N, Z_FWD><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, nullptr, 0);
         else
-          k_z_reg<T, N, Z_INV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale);
+          k_z_reg<T, N, Z_INV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, nullptr, 0);
       }
     }
     if (!done) {
@@ -181,40 +145,17 @@ struct PlaneLaunch {
     prof_end(KC_Z, st, 2.0 * F * items + (mode == Z_CONV ? F / 2.0 : 0.0));
   }
 
-  template <int PL>
-  static void xy_inv_reg_launch(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm,
-                                int targets, T scale, cudaStream_t st) {
-    constexpr int RT = xyreg_threads<T, N, PL>();
-    constexpr size_t RS = xyreg_smem<T, N, PL>();
-    if (mode == INV_ATOMIC)
-      k_xy_inv_reg<T, N, INV_ATOMIC, PL><<<dim3(N / PL, targets * pm.kdim), RT, RS, st>>>(ibuf, ob, pb, pm, scale);
-    else
-      k_xy_inv_reg<T, N, INV_WRITE, PL><<<dim3(N / PL, targets), RT, RS, st>>>(ibuf, ob, pb, pm, scale);
-  }
-
-  static void xy_inv(KernelChoice kc, int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm,
-                     int targets, T scale, const cplx<T>* tw, cudaStream_t st) {
+  static void xy_inv(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
+                     const cplx<T>* tw, cudaStream_t st) {
     if (targets <= 0) return;
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
     prof_begin(KC_XY_INV, st);
-    bool done = false;
-    if constexpr (z_in_registers<T, N>()) {
-      if (mode != INV_ACCUM && (kc.xy == 1 || kc.xy == 2 || kc.xy == 4)) {
-        done = true;
-        if (kc.xy == 1) xy_inv_reg_launch<1>(mode, ibuf, ob, pb, pm, targets, scale, st);
-        else if (kc.xy == 2) xy_inv_reg_launch<2>(mode, ibuf, ob, pb, pm, targets, scale, st);
-        else xy_inv_reg_launch<4>(mode, ibuf, ob, pb, pm, targets, scale, st);
-      }
-    }
-    if (!done) {
-      if (mode == INV_ACCUM) {
-        k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
-      } else if (mode == INV_ATOMIC) {
-        k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
-      } else {
-        k_xy_inv<T, N, INV_WRITE><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
-      }
-    }
+    if (mode == INV_ACCUM)
+      k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    else if (mode == INV_ATOMIC)
+      k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+    else
+      k_xy_inv<T, N, INV_WRITE><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
     note_launch();
     prof_end(KC_XY_INV, st, mode == INV_WRITE ? 2.0 * F * targets : (2.0 * pm.kdim + 2.0) * F * targets);
   }
@@ -223,7 +164,6 @@ struct PlaneLaunch {
     PlaneOps<T> o;
     o.n = N;
     o.reg_ok = z_in_registers<T, N>();
-    o.kc.xy = 0;
     o.kc.z = o.reg_ok ? 1 : 0;
     o.prepare = &prepare;
     o.f_xy_fwd = &xy_fwd;

@@ -286,6 +286,7 @@ struct Buffers {
   void* grad_r = nullptr;      // [nocc_src][n^3] (adjoint)
   double* wdev = nullptr;      // [nb_max]
   int* dev_err = nullptr;      // set by a device wait that ran out of polls
+  int* zcols = nullptr;        // [n*n] z-pass column positions, the ncols_act possibly non-zero ones first
 };
 
 struct tddft_system {
@@ -297,6 +298,8 @@ struct tddft_system {
   int tile_targets = 16, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
+  bool prune = false;    // z pass of pair convolutions only on the columns a pair density can occupy
+  int ncols_act = 0;     // number of such columns (0 = no list: the grid aliases pair densities)
   int nsplit = 1;
   size_t bytes = 0;
   Buffers b;
@@ -317,6 +320,17 @@ struct tddft_system {
   size_t esz() const { return d.precision == TDDFT_PREC_FP64 ? 16 : 8; }
   size_t rsz() const { return d.precision == TDDFT_PREC_FP64 ? 8 : 4; }
 };
+
+// Column list of the z pass of pair convolutions (all columns when pruning is off
+// or the grid would alias a pair density).
+static ColumnList pair_columns(const tddft_system* h) {
+  ColumnList cl;
+  if (h->prune && h->b.zcols) {
+    cl.cols = h->b.zcols;
+    cl.nact = h->ncols_act;
+  }
+  return cl;
+}
 
 static tddft_status dalloc(tddft_system* h, void** p, size_t bytes) {
   *p = nullptr;
@@ -450,7 +464,7 @@ static tddft_status convolve_fields(tddft_system* h, const cplx<T>* src, int nf,
     const int cnt = std::min(h->ibuf_fields, nf - f0);
     PairMap pin{1, 0, 0, 0, f0, 0, 1, 0, 0, 0, 0, 0};
     o.xy_fwd(XY_LOAD, nullptr, src, pin, cnt, ib, tw, st);
-    o.z(Z_CONV, ib, cnt, kern, kscale, tw, st);
+    o.z(Z_CONV, ib, cnt, kern, kscale, tw, st, pair_columns(h));  // the fields are pair densities
     PairMap pout{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, f0, 1};
     o.xy_inv(INV_WRITE, ib, dst, nullptr, pout, cnt, T(1), tw, st);
   }
@@ -499,7 +513,7 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
       pm.o0 = pg.o_base + t0 * pg.o_ts;
       pm.ot = pg.o_ts;
       o.xy_fwd(XY_PRODUCT, qb, rb, pm, tt * kk, ib, tw, st);
-      o.z(Z_CONV, ib, tt * kk, kern, T(1), tw, st);
+      o.z(Z_CONV, ib, tt * kk, kern, T(1), tw, st, pair_columns(h));
       o.xy_inv(h->accumulate, ib, ob, pb, pm, tt, scale, tw, st);
     }
   }
@@ -525,7 +539,7 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       // item = vi * tj + vj : Q = phi[j0 + vj], R = phi[i0 + vi]
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
       o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
-      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);
+      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st, pair_columns(h));
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
       {
@@ -638,6 +652,27 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   }
   std::vector<T> eps(d.nocc_src);
   for (int v = 0; v < d.nocc_src; ++v) eps[v] = (T)in->eps_src[v];
+  // z-pass columns of pair densities: the product of two sphere functions has
+  // |m| < 2 R_m (R_m = sqrt(2 ecut) / tpiba); without aliasing (2 max|m_i| <=
+  // n/2 - 1) every (k_x, k_y) column with m_x^2 + m_y^2 > 4 R_m^2 is exactly
+  // zero. Positions are digit-reversed; the list holds the others after them.
+  int mmax = 0;
+  for (const Miller& q : sph) mmax = std::max(mmax, std::max(std::abs(q.x), std::max(std::abs(q.y), std::abs(q.z))));
+  std::vector<int> zcols;
+  if (2 * mmax <= n / 2 - 1) {
+    std::vector<int> irev(n);
+    for (int k = 0; k < n; ++k) irev[rev[k]] = k;
+    const double r2 = 4.0 * (2.0 * d.ecut / tpiba2) * (1.0 + 1e-12);
+    std::vector<int> rest;
+    for (int py = 0; py < n; ++py)
+      for (int px = 0; px < n; ++px) {
+        const double mx = mof(irev[px]), my = mof(irev[py]);
+        if (mx * mx + my * my <= r2) zcols.push_back(py * n + px);
+        else rest.push_back(py * n + px);
+      }
+    h->ncols_act = (int)zcols.size();
+    zcols.insert(zcols.end(), rest.begin(), rest.end());
+  }
 
   Buffers& B = h->b;
   const size_t ez = sizeof(cplx<T>), rz = sizeof(T);
@@ -647,6 +682,10 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   STATUS_TRY(dalloc(h, (void**)&B.pos, npw * sizeof(int)));
   STATUS_TRY(dalloc(h, &B.g2h, npw * rz));
   STATUS_TRY(dalloc(h, &B.eps, d.nocc_src * rz));
+  if (!zcols.empty()) {
+    STATUS_TRY(dalloc(h, (void**)&B.zcols, zcols.size() * sizeof(int)));
+    CUDA_TRY(cudaMemcpyAsync(B.zcols, zcols.data(), zcols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * ez, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kx, kx.data(), n3 * rz, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kh, kh.data(), n3 * rz, cudaMemcpyHostToDevice, st));
@@ -1096,17 +1135,9 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
   if (t->k1d_block) h->k1d_block = t->k1d_block;
   if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
   if (t->graph >= 0) h->use_graph = t->graph == 1;
-  if (t->xy_kernel >= 0) {
-    if (!(t->xy_kernel == 0 || t->xy_kernel == 1 || t->xy_kernel == 2 || t->xy_kernel == 4))
-      return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 4");
-    const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
-    if (t->xy_kernel && !reg) return fail(TDDFT_EINVAL, "register-resident passes need FP32 and n <= 80");
-    h->ops32.kc.xy = t->xy_kernel;
-    h->ops64.kc.xy = t->xy_kernel;
-  }
-  if (t->projector >= 0) {
-    if (t->projector > 1) return fail(TDDFT_EINVAL, "projector must be 0 or 1");
-    h->projector_tc = t->projector;
+  if (t->prune >= 0) {
+    if (t->prune > 1) return fail(TDDFT_EINVAL, "prune must be 0 or 1");
+    h->prune = t->prune == 1;
   }
   if (t->z_kernel >= 0) {
     if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
@@ -1136,7 +1167,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->batch_fields = h->ibuf_fields;
   t->graph = h->use_graph ? 1 : 0;
   const KernelChoice kc = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.kc : h->ops64.kc;
-  t->xy_kernel = kc.xy;
+  t->prune = h->prune ? 1 : 0;
   t->z_kernel = kc.z;
   t->projector = h->projector_tc;
   return TDDFT_OK;

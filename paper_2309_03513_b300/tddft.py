@@ -63,7 +63,7 @@ class Inputs(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
-                ("xy_kernel", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int)]
+                ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -242,8 +242,8 @@ class LiouvilleSystem:
         _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
-                   graph: int = -1, xy_kernel: int = -1, z_kernel: int = -1, projector: int = -1):
-        t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(xy_kernel),
+                   graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1):
+        t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
                    int(z_kernel), int(projector))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 

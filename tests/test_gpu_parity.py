@@ -100,17 +100,20 @@ def test_ragged_tiles_give_the_same_result(torch):
     assert _rel_err(got, want).max() < 1e-5
 
 
-@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0)])
+@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0), (32, 9.0, 12.0)])
 def test_kernel_variants_fp32(torch, n, a, ecut):
-    """Every plane-pass variant (staged / register-resident xy with 1, 2, 4 planes per
-    CTA, staged / register-resident z, loop / atomic accumulation) gives the oracle's L."""
+    """Every plane-pass variant (column pruning on / off, staged / register-resident
+    z pass, loop / atomic accumulation) gives the oracle's L. The 24^3 grid aliases
+    pair densities (pruning stays off there); 72^3 and 32^3 do not."""
     wl = _workload(n, a, ecut, 6, 2, seed=15)
     want = O.system_from_workload(wl).apply(wl.X)
-    for xy in (0, 1, 2, 4):
+    for prune in (0, 1):
         for z in (0, 1):
             for acc in (0, 1):
-                got = _run(torch, wl, T.PREC_FP32, tiling=(3, 4, 5, acc, -1, xy, z))
-                assert _rel_err(got, want).max() < 1e-5, (xy, z, acc)
+                got = _run(torch, wl, T.PREC_FP32, tiling=(3, 4, 5, acc, -1, prune, z))
+                assert _rel_err(got, want).max() < 1e-5, (prune, z, acc)
+    got = _run(torch, wl, T.PREC_FP64, tiling=(3, 4, 5, 1, -1, 1, 0))
+    assert _rel_err(got, want).max() < 1e-11
 
 
 def test_projector_tensor_cores_match_simt(torch):
