@@ -33,7 +33,11 @@ WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 
 # DRAM traffic per launch of the dominant kernel class from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
 # sources it was taken on; reported as null when the sources have changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/plane_kernels_traffic_diamond64.md: one 128-pair launch of each class
+    "2e0796f04ca0": {"xy_fwd_pair_product": 437.4e6, "z_kernel_multiply": 704.0e6,
+                     "xy_inv_remultiply_accumulate": 523.9e6},
+}
 
 
 def kernel_source_hash() -> str:
