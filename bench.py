@@ -156,13 +156,22 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x: float) -> float:
+    """Largest value over the ranks (the slowest rank's time); CPU tensor under gloo."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws: int, units_per_rank: float, local_seconds: float) -> tuple[float, float]:
+    """Whole-job rate for independent replicas: units of all ranks / slowest rank's time.
+    Returns (rate, max seconds)."""
+    t = max_over_ranks(ws, local_seconds)
+    return ws * units_per_rank / t, t
 
 
 def run_reference(args):
@@ -233,8 +242,8 @@ def run_native(args):
     prof = T.profile_read()
     T.profile_enable(False)
     clocks = sampler.stop()
-    ms_max = max_over_ranks(ws, ms)
-    value = ws * args.steps * nb / (ms_max / 1e3)
+    value, sec_max = job_throughput(ws, args.steps * nb, ms / 1e3)
+    ms_max = sec_max * 1e3
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     Xh_t = torch.from_numpy(wl.X.astype(np.complex64)).pin_memory()

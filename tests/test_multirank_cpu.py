@@ -1,0 +1,44 @@
+"""The multi-rank (replica) aggregation of bench.py on two gloo ranks on the CPU:
+every rank reports its own time, the job rate is the units of all ranks over the
+slowest rank's time, and the barrier/all-reduce path runs without a GPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    local = [2.0, 3.0][rank]  # seconds each replica took
+    bench.barrier(ws)
+    rate, tmax = bench.job_throughput(ws, units_per_rank=8.0, local_seconds=local)
+    q.put((rank, rate, tmax))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, rate, tmax in out:
+        assert tmax == pytest.approx(3.0)
+        assert rate == pytest.approx(2 * 8.0 / 3.0)
