@@ -189,6 +189,8 @@ class System:
             raise ValueError("orbital arrays do not match the sphere size")
         self._phi_src_r = None
         self._phi_tgt_r = None
+        self.use_ace = False   # D_EXX through V_X^ACE (after ace_build) instead of the exact V_X
+        self.ace_xi = None
 
     @property
     def nocc_src(self):
@@ -215,6 +217,47 @@ class System:
         P = self.phi_tgt
         return Y - np.einsum("ug,...u->...g", P, np.einsum("ug,...g->...u", P.conj(), Y))
 
+    # -- exact exchange and its adaptively compressed form (Sec. 3.1) --
+    def exchange_pw(self, psi: np.ndarray) -> np.ndarray:
+        """V_X psi for plane-wave rows psi [..., npw]: -sum_w phi_w Conv_x[phi_w^* psi] -> PW
+        (the exchange-operator equation of Sec. 3.1, target-spin orbitals)."""
+        g = self.grid
+        psi = np.asarray(psi, dtype=np.complex128)
+        flat = psi.reshape(-1, g.npw)
+        out = np.empty_like(flat)
+        phit = self.phi_tgt_r()
+        for i, row in enumerate(flat):
+            f = g.pw_to_real(row)
+            acc = np.zeros_like(f)
+            for w in range(self.nocc_tgt):
+                acc -= phit[w] * g.conv(phit[w].conj() * f, self.kx)
+            out[i] = g.real_to_pw(acc)
+        return out.reshape(psi.shape)
+
+    def ace_build(self, extra: np.ndarray | None = None) -> np.ndarray:
+        """ACE projection vectors xi [N_ACE, npw] (Sec. 3.1, Eqs. 29-30).
+
+        The build set Psi is the target-spin occupied orbitals followed by the
+        rows of `extra` (orthonormal and orthogonal to them). W_i = V_X psi_i,
+        M = Psi^dagger W (negative definite), -M = L L^dagger (Cholesky),
+        xi = W L^{-dagger}, so that V_X^ACE = -sum_k |xi_k><xi_k| equals V_X on
+        span(Psi).
+        """
+        Psi = self.phi_tgt if extra is None else np.concatenate([self.phi_tgt, np.asarray(extra)], axis=0)
+        W = self.exchange_pw(Psi)
+        M = Psi.conj() @ W.T
+        M = 0.5 * (M + M.conj().T)
+        L = np.linalg.cholesky(-M)
+        # xi_k = sum_i W_i (L^{-dagger})_{ik}: as rows, xi = conj(L^{-1}) W
+        xi = np.conj(np.linalg.inv(L)) @ W
+        self.ace_xi = xi
+        return xi
+
+    def exchange_ace_pw(self, psi: np.ndarray) -> np.ndarray:
+        """V_X^ACE psi = -sum_k xi_k <xi_k|psi> for plane-wave rows psi [..., npw]."""
+        xi = self.ace_xi
+        return -np.einsum("kg,...k->...g", xi, np.einsum("kg,...g->...k", xi.conj(), psi))
+
     # -- pieces of the operator --
     def delta_rho(self, a_r: np.ndarray) -> np.ndarray:
         """Delta rho(r) = sum_v phi_v^*(r) a_v(r) (Eq. 2 diagonal; Sec. 2.3 for SF)."""
@@ -238,7 +281,7 @@ class System:
         out_r = np.zeros(a_r.shape[1:], dtype=np.complex128)
         if (terms & D_VLOC) and self.vloc is not None:
             out_r += self.vloc * a_r[v]
-        if terms & D_EXX:
+        if (terms & D_EXX) and not self.use_ace:
             # alpha V_X a_v = -alpha sum_w phi_w Conv_x[phi_w^* a_v]   (Sec. 3.1, exchange operator)
             phit = self.phi_tgt_r()
             for w in range(self.nocc_tgt):
@@ -253,6 +296,8 @@ class System:
         out = g.real_to_pw(out_r)
         if terms & D_KIN:
             out += (0.5 * g.g2_sphere - self.eps_src[v]) * Xb[v]
+        if (terms & D_EXX) and self.use_ace:
+            out += self.alpha * self.exchange_ace_pw(Xb[v])
         return out
 
     def apply(self, X: np.ndarray, terms: int = ALL_TERMS, rows=None) -> np.ndarray:

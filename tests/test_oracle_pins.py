@@ -361,3 +361,51 @@ def test_davidson_matches_dense_diagonalisation():
     # Ritz vectors are eigenvectors of L
     LV = S.apply(V)
     assert np.abs(LV - theta[:, None, None] * V).max() < 1e-7
+
+
+# --------------------------------------------------------------------------
+# adaptively compressed exchange (Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def _orthonormal_complement_rows(rng, phi, k):
+    x = synth.trial_vectors(rng, phi, 1, k)[0]
+    q, _ = np.linalg.qr(x.T)
+    return q.T
+
+
+def test_ace_is_exact_on_its_build_span():
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=2, seed=21)
+    extra = _orthonormal_complement_rows(np.random.default_rng(1), wl.phi_tgt, 6)
+    S.ace_build(extra)
+    Psi = np.concatenate([wl.phi_tgt, extra])
+    exact = S.exchange_pw(Psi)
+    assert np.abs(S.exchange_ace_pw(Psi) - exact).max() < 1e-12 * np.abs(exact).max()
+    # V_X is negative definite: <psi|V_X|psi> < 0 for every build vector
+    assert np.all(np.einsum("ig,ig->i", Psi.conj(), exact).real < 0)
+
+
+def test_ace_with_a_complete_basis_is_the_exact_operator():
+    """Built on every plane-wave direction (occupied orbitals plus a basis of their
+    complement), V_X^ACE = V_X on any vector, and L with ACE equals L."""
+    wl, S = _tiny(n=8, a=6.0, ecut=2.5, nocc=2, nb=2, seed=22)
+    S.ace_build(S.complement_basis().T)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((3, S.grid.npw)) + 1j * rng.standard_normal((3, S.grid.npw))
+    exact = S.exchange_pw(v)
+    assert np.abs(S.exchange_ace_pw(v) - exact).max() < 1e-11 * np.abs(exact).max()
+    full = S.apply(wl.X)
+    S.use_ace = True
+    assert np.allclose(S.apply(wl.X), full, atol=1e-11 * np.abs(full).max())
+
+
+def test_ace_error_decreases_with_more_build_vectors():
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=1, seed=23)
+    extra = _orthonormal_complement_rows(np.random.default_rng(3), wl.phi_tgt, 40)
+    a = wl.X[0]
+    exact = S.exchange_pw(a)
+    errs = []
+    for k in (0, 10, 20, 40):
+        S.ace_build(extra[:k] if k else None)
+        errs.append(np.linalg.norm(S.exchange_ace_pw(a) - exact))
+    assert all(e2 <= e1 * (1 + 1e-12) for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 0.7 * errs[0]
