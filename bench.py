@@ -279,6 +279,8 @@ def run_native(args):
         extras["uneven12"] = bench_uneven(torch, T, dev, stream)
     if "sf216" in args.extra:
         extras["sf216"] = bench_sf216(torch, T, dev, stream)
+    if "ace" in args.extra:
+        extras["ace"] = bench_ace(torch, T, dev, stream, wl, X, LA)
 
     # plain FP64 GPU path on the same batch
     fp64 = None
@@ -379,6 +381,47 @@ def bench_uneven(torch, T, dev, stream, steps=2):
             "steps": steps, "systems": 12, "note": "one CUDA-graph launch per step, one branch per system"}
 
 
+def bench_ace(torch, T, dev, stream, wl, X, LA, steps=3):
+    """The same batch with the exchange inside D through the compressed operator
+    built on N_ACE = 4 N_occ vectors (the occupied orbitals plus 3 N_occ random
+    orthonormal rows orthogonal to them, standing in for unoccupied orbitals).
+    An approximation of L: its relative deviation from the exact operator on this
+    batch is reported beside the rate."""
+    from paper_2309_03513_b300 import synth
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    s.apply(X, out=LA, stream=stream)
+    exact = LA.clone()
+    nocc = wl.phi_tgt.shape[0]
+    extra = synth.complement_rows(np.random.default_rng(1234), wl.phi_tgt, 3 * nocc)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.ace_build(extra, stream=stream)
+    build_s = time.perf_counter() - t0
+    s.apply(X, out=LA, stream=stream)
+    torch.cuda.synchronize(dev)
+    dev_rel = float(torch.linalg.vector_norm(LA - exact) / torch.linalg.vector_norm(exact))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        s.apply(X, out=LA, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    s.set_terms(T.TERM_D_EXX)
+    s.apply(X, out=LA, stream=stream)
+    e0.record(stream)
+    s.apply(X, out=LA, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    d_ms = e0.elapsed_time(e1)
+    s.close()
+    nb = X.shape[0]
+    return {"value": nb / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "n_ace": 4 * nocc,
+            "build_s": build_s, "D_exchange_ms": d_ms, "rel_deviation_from_exact_L": dev_rel,
+            "note": "approximate operator (compressed exchange inside D); not the bench metric"}
+
+
 def bench_sf216(torch, T, dev, stream, steps=1):
     """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path."""
     from paper_2309_03513_b300 import synth
@@ -412,7 +455,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")
-    ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip)")
+    ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
+                                             "ace (compressed exchange on the bench batch)")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()

@@ -183,6 +183,23 @@ tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_ho
 tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
                                          void* const* LA, void* stream);
 
+/* Adaptively compressed exchange (ACE, Sec. 3.1, Eqs. 29-30) for the exchange
+ * term inside D: V_X^ACE = -sum_k |xi_k><xi_k| with xi = W L^{-dagger},
+ * W = V_X Psi (exact pair convolutions), -Psi^dagger W = L L^dagger (FP64
+ * Cholesky on the host). Psi = the target-spin occupied orbitals followed by
+ * n_extra HOST complex128 rows extra[n_extra][npw] (orthonormal and orthogonal
+ * to the orbitals; max deviation 1e-10, else TDDFT_EINVAL; NULL if n_extra = 0),
+ * e.g. low unoccupied orbitals (the paper uses N_ACE = N_occ + 20 up to
+ * 4 N_occ). V_X^ACE equals V_X on span(Psi) and approaches it as the set grows;
+ * elsewhere it is an approximation. After a successful build the handle's
+ * exchange term uses V_X^ACE: two GEMMs in plane waves (tensor cores for FP32)
+ * instead of N_b N_occ N_occ,tgt pair convolutions. TDDFT_ENUMERIC if
+ * -Psi^dagger W is not positive definite. Synchronises the stream. */
+tddft_status tddft_ace_build(tddft_handle h, int n_extra, const double* extra, void* stream);
+
+/* Switch the built ACE operator on (1) or back to the exact exchange (0). */
+tddft_status tddft_ace_enable(tddft_handle h, int enable);
+
 /* Bilinear form omega_b = <P^c X_b | M | P^c X_b> (M = L without the outer
  * P^c; equal to <X_b|L X_b> for X_b orthogonal to the orbitals) and the
  * gradient of E = sum_b w_b omega_b (spin-conserving handles only).
@@ -193,7 +210,8 @@ tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const
  *   taken on the handle's orbitals (the part of u_v of the Supporting
  *   Information, Sec. S1, that does not come from the ground-state density).
  * grad_vloc: device double [n^3], dE/dV_loc(r_j); may be NULL.
- * Pair convolutions are recomputed, not stored. Written, not accumulated. */
+ * Pair convolutions are recomputed, not stored. Written, not accumulated.
+ * TDDFT_ENOTSUP while ACE is switched on (the gradient is of the exact exchange). */
 tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
                                            void* grad_phi, double* grad_vloc, void* stream);
 

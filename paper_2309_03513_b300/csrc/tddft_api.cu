@@ -299,6 +299,12 @@ struct tddft_system {
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
   bool prune = false;    // z pass of pair convolutions only on the columns a pair density can occupy
+  // adaptively compressed exchange for the exchange term inside D (tddft_ace_build)
+  bool ace_on = false;
+  int n_ace = 0;
+  void* ace_xi = nullptr;    // [n_ace][npw] working precision
+  void* ace_c = nullptr;     // [n_ace][nb_max * nocc_src]
+  void* ace_part = nullptr;  // split-K partials [2 * nsplit][n_ace][nb_max * nocc_src]
   int ncols_act = 0;     // number of such columns (0 = no list: the grid aliases pair densities)
   int nsplit = 1;
   size_t bytes = 0;
@@ -397,60 +403,87 @@ static tddft_status real_to_pw(tddft_system* h, const cplx<T>* src, int nf, cplx
 }
 
 // Y[n][:] -= sum_m Phi[m][:] <Phi_m|Y_n>  for nrows rows of length npw
-// Projector on tcgen05 tensor cores (FP32 data, 3xTF32 products, FP32 accumulation).
-static tddft_status project_rows_tc(tddft_system* h, const cplx<float>* phi, int M, cplx<float>* Y, int nrows,
-                                    cudaStream_t st) {
+// Complex GEMMs on tcgen05 tensor cores (FP32 data, 3xTF32 products, FP32 accumulation).
+// At most 256 chunks of 32 real K values (8192 products) accumulate in one TMEM
+// accumulator chain: the accumulator's rounding error grows about linearly with
+// the chain length (measured: 3e-5 relative on a projected 49k-plane-wave row with
+// one split of the whole K, 4e-6 with nine), so long K is always split.
+constexpr int TC_CHAIN_CHUNKS = 256;
+
+// overlap: C[u][r] = sum_g conj(P[u][g]) Y[r][g]   (C: [M][nrows], split-K partials in part)
+
+static tddft_status tc_overlap(tddft_system* h, const cplx<float>* P, int M, const cplx<float>* Y, int nrows,
+                               cplx<float>* part, int max_splits, cplx<float>* C, cudaStream_t st) {
   const int K = h->npw;
   const int Kp = (K + UMMA_KC - 1) / UMMA_KC * UMMA_KC;
   const int Rp = (nrows + UMMA_N - 1) / UMMA_N * UMMA_N;
   const int kchunks = 2 * Kp / UMMA_KC;
   const int mt = (M + UMMA_M - 1) / UMMA_M;
   const int nt = 2 * Rp / UMMA_N;
-  int splits = std::max(1, std::min(kchunks, 296 / std::max(1, nt * mt)));
-  splits = std::min(splits, 2 * h->nsplit);
+  const int min_splits = (kchunks + TC_CHAIN_CHUNKS - 1) / TC_CHAIN_CHUNKS;
+  int splits = std::max(min_splits, std::min(kchunks, 296 / std::max(1, nt * mt)));
+  splits = std::max(1, std::min(splits, max_splits));
   const int per = (kchunks + splits - 1) / splits;
   splits = (kchunks + per - 1) / per;
-  cplx<float>* part = (cplx<float>*)h->b.cpart;
-  cplx<float>* C = (cplx<float>*)h->b.cmat;
-  {
-    OvA la{phi, M, K, Kp};
-    OvB lb{Y, nrows, Rp, K, Kp};
-    OvEp ep{part, M, nrows, Rp};
-    k_umma_gemm<OvA, OvB, OvEp><<<dim3(nt, mt, splits), 128, UMMA_SMEM, st>>>(la, lb, ep, kchunks, per, h->b.dev_err);
-    note_launch();
-  }
+  OvA la{P, M, K, Kp};
+  OvB lb{Y, nrows, Rp, K, Kp};
+  OvEp ep{part, M, nrows, Rp};
+  { k_umma_gemm<OvA, OvB, OvEp><<<dim3(nt, mt, splits), 128, UMMA_SMEM, st>>>(la, lb, ep, kchunks, per, h->b.dev_err); note_launch(); }
   { k_reduce_split<float><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(part, splits, (long long)M * nrows, C); note_launch(); }
-  {
-    const int Up = (M + UMMA_KC - 1) / UMMA_KC * UMMA_KC;
-    const int Gp = (K + UMMA_N - 1) / UMMA_N * UMMA_N;
-    UpA la{C, M, Up, nrows};
-    UpB lb{phi, M, Up, K, Gp};
-    UpEp ep{Y, nrows, K, Gp};
-    const int kc2 = 2 * Up / UMMA_KC;
-    k_umma_gemm<UpA, UpB, UpEp><<<dim3(2 * Gp / UMMA_N, (nrows + UMMA_M - 1) / UMMA_M, 1), 128, UMMA_SMEM, st>>>(
-        la, lb, ep, kc2, kc2, h->b.dev_err);
-    note_launch();
-  }
-  return check_launch("projector (tensor cores)");
+  return check_launch("overlap (tensor cores)");
 }
 
+// update: Y[r][g] += s * sum_u P[u][g] C[u][r]
+static tddft_status tc_update(tddft_system* h, const cplx<float>* P, int M, const cplx<float>* C, cplx<float>* Y,
+                              int nrows, float s, cudaStream_t st) {
+  const int K = h->npw;
+  const int Up = (M + UMMA_KC - 1) / UMMA_KC * UMMA_KC;
+  const int Gp = (K + UMMA_N - 1) / UMMA_N * UMMA_N;
+  UpA la{C, M, Up, nrows};
+  UpB lb{P, M, Up, K, Gp};
+  UpEp ep{Y, nrows, K, Gp, s};
+  const int kc2 = 2 * Up / UMMA_KC;
+  { k_umma_gemm<UpA, UpB, UpEp><<<dim3(2 * Gp / UMMA_N, (nrows + UMMA_M - 1) / UMMA_M, 1), 128, UMMA_SMEM, st>>>(
+        la, lb, ep, kc2, kc2, h->b.dev_err); note_launch(); }
+  return check_launch("update (tensor cores)");
+}
+
+// C[u][r] = sum_g conj(P[u][g]) Y[r][g] for u < M, r < nrows (tensor cores for FP32 when enabled)
 template <typename T>
-static tddft_status project_rows(tddft_system* h, const cplx<T>* phi, int M, cplx<T>* Y, int nrows, cudaStream_t st) {
-  if (nrows <= 0 || M <= 0) return TDDFT_OK;
+static tddft_status gemm_overlap(tddft_system* h, const cplx<T>* P, int M, const cplx<T>* Y, int nrows, cplx<T>* part,
+                                 cplx<T>* C, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (h->projector_tc) return project_rows_tc(h, phi, M, Y, nrows, st);
+    if (h->projector_tc) return tc_overlap(h, P, M, Y, nrows, part, 2 * h->nsplit, C, st);
   }
   const int K = h->npw;
-  cplx<T>* C = (cplx<T>*)h->b.cmat;
-  cplx<T>* Cp = (cplx<T>*)h->b.cpart;
   const int nsplit = h->nsplit;
   const int kchunk = ((K + nsplit - 1) / nsplit + 15) / 16 * 16;
   dim3 g1((M + 31) / 32, (nrows + 31) / 32, nsplit);
-  { k_overlap<T><<<g1, 256, 0, st>>>(phi, M, Y, nrows, K, kchunk, Cp); note_launch(); }
-  { k_reduce_split<T><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(Cp, nsplit, (long long)M * nrows, C); note_launch(); }
+  { k_overlap<T><<<g1, 256, 0, st>>>(P, M, Y, nrows, K, kchunk, part); note_launch(); }
+  { k_reduce_split<T><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(part, nsplit, (long long)M * nrows, C); note_launch(); }
+  return check_launch("overlap");
+}
+
+// Y[r][g] += s * sum_u P[u][g] C[u][r]
+template <typename T>
+static tddft_status gemm_update(tddft_system* h, const cplx<T>* P, int M, const cplx<T>* C, cplx<T>* Y, int nrows,
+                                T s, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (h->projector_tc) return tc_update(h, P, M, C, Y, nrows, s, st);
+  }
+  const int K = h->npw;
   dim3 g2((K + 63) / 64, (nrows + 31) / 32);
-  { k_update<T><<<g2, 256, 0, st>>>(phi, M, C, nrows, K, T(-1), Y); note_launch(); }
-  return check_launch("project_rows");
+  { k_update<T><<<g2, 256, 0, st>>>(P, M, C, nrows, K, s, Y); note_launch(); }
+  return check_launch("update");
+}
+
+// Y[n][:] -= sum_m Phi[m][:] <Phi_m|Y_n>  for nrows rows of length npw
+template <typename T>
+static tddft_status project_rows(tddft_system* h, const cplx<T>* phi, int M, cplx<T>* Y, int nrows, cudaStream_t st) {
+  if (nrows <= 0 || M <= 0) return TDDFT_OK;
+  cplx<T>* C = (cplx<T>*)h->b.cmat;
+  STATUS_TRY(gemm_overlap<T>(h, phi, M, Y, nrows, (cplx<T>*)h->b.cpart, C, st));
+  return gemm_update<T>(h, phi, M, C, Y, nrows, T(-1), st);
 }
 
 // Conv_kappa of nf fields src[f] into dst[f] (dst may equal src)
@@ -580,7 +613,7 @@ static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T
         a_r, phis, vloc ? (const T*)h->b.vloc : nullptr, k1e_h ? wb : nullptr, k1e_xc ? (const T*)h->b.fxc : nullptr,
         drho, out_r, nocc, nbc, n3); note_launch(); }
     STATUS_TRY(check_launch("init_out"));
-    if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0) {
+    if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0 && !h->ace_on) {
       // out[t] += -alpha sum_w phi_w Conv_x[conj(phi_w) a_t],  t = (b, v)
       PairGrid pg{nf, h->d.nocc_tgt, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
       STATUS_TRY(pair_accumulate<T>(h, phit, a_r, phit, out_r, pg, (const T*)h->b.kx, (T)(-h->d.alpha), st));
@@ -588,6 +621,13 @@ static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T
     if ((mask & TDDFT_TERM_K1D) && h->d.alpha != 0.0) STATUS_TRY(k1d_term<T>(h, nbc, st));
     STATUS_TRY(real_to_pw<T>(h, out_r, nf, LA + (long long)b0 * nocc * npw,
                              (mask & TDDFT_TERM_D_KIN) ? Ab : nullptr, st));
+  }
+  if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0 && h->ace_on) {
+    // alpha V_X^ACE a = -alpha sum_k xi_k <xi_k|a>, in plane waves
+    const cplx<T>* xi = (const cplx<T>*)h->ace_xi;
+    cplx<T>* C = (cplx<T>*)h->ace_c;
+    STATUS_TRY(gemm_overlap<T>(h, xi, h->n_ace, A, nb * nocc, (cplx<T>*)h->ace_part, C, st));
+    STATUS_TRY(gemm_update<T>(h, xi, h->n_ace, C, LA, nb * nocc, (T)(-h->d.alpha), st));
   }
   if (mask & TDDFT_TERM_PROJ)
     STATUS_TRY(project_rows<T>(h, (const cplx<T>*)h->b.phi_tgt_pw, h->d.nocc_tgt, LA, nb * nocc, st));
@@ -800,6 +840,157 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
+// adaptively compressed exchange (Sec. 3.1)
+// ---------------------------------------------------------------------------
+
+// A = L L^dagger for Hermitian positive definite A (row-major n x n, lower L
+// returned in A); false if a pivot is not positive.
+static bool cholesky_lower(int n, std::vector<std::complex<double>>& A) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(A[(size_t)j * n + k]);
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    A[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      std::complex<double> v = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * std::conj(A[(size_t)j * n + k]);
+      A[(size_t)i * n + j] = v / ljj;
+    }
+    for (int i = 0; i < j; ++i) A[(size_t)i * n + j] = 0.0;
+  }
+  return true;
+}
+
+// inverse of a lower-triangular L (row-major), by forward substitution per column
+static std::vector<std::complex<double>> lower_inverse(int n, const std::vector<std::complex<double>>& L) {
+  std::vector<std::complex<double>> X((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      std::complex<double> v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= L[(size_t)i * n + k] * X[(size_t)k * n + c];
+      X[(size_t)i * n + c] = v / L[(size_t)i * n + i];
+    }
+  }
+  return X;
+}
+
+namespace {
+// temporaries of one ACE build, released on every exit path
+struct TempAllocs {
+  std::vector<void*> p;
+  tddft_status get(void** out, size_t bytes) {
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    p.push_back(*out);
+    return TDDFT_OK;
+  }
+  ~TempAllocs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+}  // namespace
+
+template <typename T>
+static tddft_status ace_build_impl(tddft_system* h, int n_extra, const double* extra, cudaStream_t st) {
+  const int nt = h->d.nocc_tgt, na = nt + n_extra, npw = h->npw;
+  const size_t row64 = (size_t)npw * sizeof(cplx<double>), rowT = (size_t)npw * sizeof(cplx<T>);
+  TempAllocs tmp;
+  cplx<double>* psi64 = nullptr;
+  cplx<double>* w64 = nullptr;
+  cplx<T>* psi = nullptr;
+  cplx<T>* W = nullptr;
+  cplx<double>* m64 = nullptr;
+  cplx<double>* p64 = nullptr;
+  cplx<T>* cm = nullptr;
+  STATUS_TRY(tmp.get((void**)&psi64, row64 * na));
+  STATUS_TRY(tmp.get((void**)&w64, row64 * na));
+  STATUS_TRY(tmp.get((void**)&psi, rowT * na));
+  STATUS_TRY(tmp.get((void**)&W, rowT * na));
+  STATUS_TRY(tmp.get((void**)&m64, sizeof(cplx<double>) * na * na));
+  STATUS_TRY(tmp.get((void**)&p64, sizeof(cplx<double>) * h->nsplit * na * na));
+  STATUS_TRY(tmp.get((void**)&cm, sizeof(cplx<T>) * na * na));
+  CUDA_TRY(cudaMemcpyAsync(psi64, h->b.phi_tgt_pw64, row64 * nt, cudaMemcpyDeviceToDevice, st));
+  if (n_extra) CUDA_TRY(cudaMemcpyAsync(psi64 + (size_t)nt * npw, extra, row64 * n_extra, cudaMemcpyHostToDevice, st));
+  const int kchunk = ((npw + h->nsplit - 1) / h->nsplit + 15) / 16 * 16;
+  auto overlap64 = [&](const cplx<double>* A, const cplx<double>* B, std::vector<std::complex<double>>& out) -> tddft_status {
+    dim3 g1((na + 31) / 32, (na + 31) / 32, h->nsplit);
+    { k_overlap<double><<<g1, 256, 0, st>>>(A, na, B, na, npw, kchunk, p64); note_launch(); }
+    { k_reduce_split<double><<<grid_for((long long)na * na, 256), 256, 0, st>>>(p64, h->nsplit, (long long)na * na, m64); note_launch(); }
+    STATUS_TRY(check_launch("ace overlap"));
+    out.resize((size_t)na * na);
+    CUDA_TRY(cudaMemcpyAsync(out.data(), m64, out.size() * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDDFT_OK;
+  };
+  // the build set must be orthonormal (the occupied orbitals followed by the extra rows)
+  std::vector<std::complex<double>> S;
+  STATUS_TRY(overlap64(psi64, psi64, S));
+  double dev = 0.0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < na; ++j) dev = std::max(dev, std::abs(S[(size_t)i * na + j] - (i == j ? 1.0 : 0.0)));
+  if (!(dev <= 1e-10))
+    return fail(TDDFT_EINVAL, "ACE build vectors are not orthonormal and orthogonal to the orbitals: max dev " +
+                                  std::to_string(dev));
+  { k_cast<T><<<grid_for((long long)na * npw, 256), 256, 0, st>>>(psi64, psi, (long long)na * npw); note_launch(); }
+  // W = V_X Psi with the exact pair convolutions, in chunks of the real-space workspace
+  const int cap = h->nb_chunk * h->d.nocc_src;
+  cplx<T>* a_r = (cplx<T>*)h->b.a_r;
+  cplx<T>* out_r = (cplx<T>*)h->b.out_r;
+  const cplx<T>* phit = (const cplx<T>*)h->b.phi_tgt_r;
+  for (int r0 = 0; r0 < na; r0 += cap) {
+    const int cnt = std::min(cap, na - r0);
+    STATUS_TRY(pw_to_real<T>(h, psi + (size_t)r0 * npw, cnt, a_r, st));
+    CUDA_TRY(cudaMemsetAsync(out_r, 0, (size_t)cnt * h->n3 * sizeof(cplx<T>), st));
+    PairGrid pg{cnt, nt, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
+    STATUS_TRY(pair_accumulate<T>(h, phit, a_r, phit, out_r, pg, (const T*)h->b.kx, T(-1), st));
+    STATUS_TRY(real_to_pw<T>(h, out_r, cnt, W + (size_t)r0 * npw, nullptr, st));
+  }
+  { k_widen<T><<<grid_for((long long)na * npw, 256), 256, 0, st>>>(W, w64, (long long)na * npw); note_launch(); }
+  // M = Psi^dagger W (FP64), -M = L L^dagger, xi = W L^{-dagger}
+  std::vector<std::complex<double>> M;
+  STATUS_TRY(overlap64(psi64, w64, M));
+  std::vector<std::complex<double>> negM((size_t)na * na);
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < na; ++j)
+      negM[(size_t)i * na + j] = -0.5 * (M[(size_t)i * na + j] + std::conj(M[(size_t)j * na + i]));
+  if (!cholesky_lower(na, negM)) return fail(TDDFT_ENUMERIC, "-Psi^dagger V_X Psi is not positive definite");
+  const std::vector<std::complex<double>> Linv = lower_inverse(na, negM);
+  // xi[k][g] = sum_i conj(Linv[k][i]) W[i][g]  ->  update with C[i][k] = conj(Linv[k][i])
+  std::vector<cplx<T>> ch((size_t)na * na);
+  for (int i = 0; i < na; ++i)
+    for (int k = 0; k < na; ++k) {
+      const std::complex<double> c = std::conj(Linv[(size_t)k * na + i]);
+      ch[(size_t)i * na + k] = {(T)c.real(), (T)c.imag()};
+    }
+  CUDA_TRY(cudaMemcpyAsync(cm, ch.data(), ch.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+  // persistent buffers (replaced on a rebuild)
+  const int rows = h->d.nb_max * h->d.nocc_src;
+  for (void** q : {&h->ace_xi, &h->ace_c, &h->ace_part}) {
+    if (*q) {
+      cudaFree(*q);
+      h->allocations.erase(std::remove(h->allocations.begin(), h->allocations.end(), *q), h->allocations.end());
+      *q = nullptr;
+    }
+  }
+  h->ace_on = false;
+  STATUS_TRY(dalloc(h, &h->ace_xi, rowT * na));
+  STATUS_TRY(dalloc(h, &h->ace_c, sizeof(cplx<T>) * (size_t)na * rows));
+  STATUS_TRY(dalloc(h, &h->ace_part, sizeof(cplx<T>) * (size_t)2 * h->nsplit * na * rows));
+  CUDA_TRY(cudaMemsetAsync(h->ace_xi, 0, rowT * na, st));
+  { dim3 g2((npw + 63) / 64, (na + 31) / 32);
+    k_update<T><<<g2, 256, 0, st>>>(W, na, cm, na, npw, T(1), (cplx<T>*)h->ace_xi); note_launch(); }
+  STATUS_TRY(check_launch("ace build"));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  h->n_ace = na;
+  h->ace_on = true;
+  return TDDFT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // adjoint (spin-conserving)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -937,6 +1128,19 @@ struct MultiGraph {
   std::vector<cudaEvent_t> events;
 };
 MultiGraph g_multi;
+
+// Forget the captured graphs that contain h's launches.
+void drop_graphs(tddft_system* h) {
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
+    cudaGraphExecDestroy(g_multi.exec);
+    g_multi.exec = nullptr;
+    g_multi.key.k.clear();
+  }
+}
 }  // namespace
 
 static tddft_status build_multi_graph(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
@@ -1139,6 +1343,10 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     if (t->prune > 1) return fail(TDDFT_EINVAL, "prune must be 0 or 1");
     h->prune = t->prune == 1;
   }
+  if (t->projector >= 0) {
+    if (t->projector > 1) return fail(TDDFT_EINVAL, "projector must be 0 or 1");
+    h->projector_tc = t->projector;
+  }
   if (t->z_kernel >= 0) {
     if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
     const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
@@ -1146,15 +1354,7 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->ops32.kc.z = t->z_kernel;
     h->ops64.kc.z = t->z_kernel;
   }
-  if (h->gexec) {  // the schedule changed: the next graph call captures again
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
-    cudaGraphExecDestroy(g_multi.exec);
-    g_multi.exec = nullptr;
-    g_multi.key.k.clear();
-  }
+  drop_graphs(h);  // the schedule changed: the next graph call captures again
   return TDDFT_OK;
 }
 
@@ -1228,6 +1428,24 @@ tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const
   return TDDFT_OK;
 }
 
+tddft_status tddft_ace_build(tddft_handle h, int n_extra, const double* extra, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (n_extra < 0 || (n_extra > 0 && !extra)) return fail(TDDFT_EINVAL, "bad extra rows");
+  if (h->d.nocc_tgt + n_extra > h->npw) return fail(TDDFT_EINVAL, "more ACE vectors than plane waves");
+  cudaStream_t st = (cudaStream_t)stream;
+  drop_graphs(h);  // a captured graph would keep the old exchange path
+  if (h->d.precision == TDDFT_PREC_FP64) return ace_build_impl<double>(h, n_extra, extra, st);
+  return ace_build_impl<float>(h, n_extra, extra, st);
+}
+
+tddft_status tddft_ace_enable(tddft_handle h, int enable) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (enable && !h->ace_xi) return fail(TDDFT_EINVAL, "ACE has not been built");
+  h->ace_on = enable != 0;
+  drop_graphs(h);
+  return TDDFT_OK;
+}
+
 tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, void* stream, tddft_tuning* best) {
   if (!h || !A || !LA) return fail(TDDFT_EINVAL, "null argument");
   if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
@@ -1287,6 +1505,7 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
                                            void* grad_phi, double* grad_vloc, void* stream) {
   if (!h) return fail(TDDFT_EINVAL, "null handle");
   if (h->sf()) return fail(TDDFT_ENOTSUP, "the adjoint is implemented for spin-conserving systems");
+  if (h->ace_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact exchange; disable ACE first");
   if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
   if (!X || !w || !omega || !grad_phi) return fail(TDDFT_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;

@@ -261,14 +261,15 @@ struct UpB {
   }
 };
 struct UpEp {
-  cplx<float>* y;  // [R][G], updated in place: y -= D
+  cplx<float>* y;  // [R][G], updated in place: y += s * D
   int R, G, Gp;
+  float s;
   __device__ __forceinline__ void operator()(int r, int n, float v, int) const {
     const bool im = n >= Gp;
     const int g = im ? n - Gp : n;
     if (r >= R || g >= G) return;
     float* d = reinterpret_cast<float*>(y + (long long)r * G + g);
-    d[im ? 1 : 0] -= v;
+    d[im ? 1 : 0] += s * v;
   }
 };
 

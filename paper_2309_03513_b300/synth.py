@@ -100,6 +100,17 @@ def trial_vectors(rng: np.random.Generator, phi_tgt: np.ndarray, nb: int, nocc_s
     return X
 
 
+def complement_rows(rng: np.random.Generator, phi_tgt: np.ndarray, k: int) -> np.ndarray:
+    """k orthonormal rows orthogonal to every row of phi_tgt (QR of [phi_tgt^T | normal draws]);
+    stand-ins for low unoccupied orbitals as extra build vectors of the compressed exchange."""
+    nocc_tgt, npw = phi_tgt.shape
+    if nocc_tgt + k > npw:
+        raise ValueError("sphere too small for the requested rows")
+    draws = rng.standard_normal((npw, k)) + 1j * rng.standard_normal((npw, k))
+    q, _ = np.linalg.qr(np.concatenate([phi_tgt.T, draws], axis=1))
+    return np.ascontiguousarray(q[:, nocc_tgt:].T)
+
+
 def make_workload(
     *,
     n: int,

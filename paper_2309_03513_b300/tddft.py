@@ -34,7 +34,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUM
 # every entry point declared in include/tddft.h
 EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
-    "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi",
+    "tddft_ace_build", "tddft_ace_enable", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -94,6 +95,8 @@ def load() -> ctypes.CDLL:
         "tddft_get_tuning": ([vp, ctypes.POINTER(Tuning)], st),
         "tddft_autotune": ([vp, ci, vp, vp, vp, ctypes.POINTER(Tuning)], st),
         "tddft_apply_liouville_multi": ([ci, vp, vp, vp, vp, vp], st),
+        "tddft_ace_build": ([vp, ci, vp, vp], st),
+        "tddft_ace_enable": ([vp, ci], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -266,6 +269,19 @@ class LiouvilleSystem:
         _check(load().tddft_autotune(self._h, X.shape[0], X.data_ptr(), out.data_ptr(), _stream_ptr(stream),
                                      ctypes.byref(t)), "tddft_autotune")
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def ace_build(self, extra=None, stream=None):
+        """Build V_X^ACE from the target orbitals plus the rows of `extra` (host complex128
+        [n, npw], orthonormal and orthogonal to the orbitals) and switch it on."""
+        if extra is None:
+            n, ptr, keep = 0, None, None
+        else:
+            keep = np.ascontiguousarray(extra, dtype=np.complex128)
+            n, ptr = keep.shape[0], keep.ctypes.data
+        _check(load().tddft_ace_build(self._h, n, ptr, _stream_ptr(stream)), "tddft_ace_build")
+
+    def ace_enable(self, on: bool = True):
+        _check(load().tddft_ace_enable(self._h, 1 if on else 0), "tddft_ace_enable")
 
     def set_tiling(self, targets: int = 0, sources: int = 0):
         self.set_tuning(targets=targets, sources=sources)

@@ -129,6 +129,24 @@ def test_projector_tensor_cores_match_simt(torch):
     assert _rel_err(only_proj, O.system_from_workload(wl).apply(wl.X, T.TERM_D_KIN | T.TERM_PROJ)).max() < 1e-5
 
 
+def test_tuning_fields_round_trip(torch):
+    """Every writable field of tddft_tuning takes effect and reads back; -1 / 0 keep the value."""
+    wl = _workload(24, 10.0, 10.0, 8, 2, seed=17)
+    s = T.system_from_workload(wl, precision=T.PREC_FP32)
+    for kw in (dict(targets=4), dict(sources=2), dict(k1d_block=8), dict(accumulate=0), dict(accumulate=1),
+               dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
+               dict(projector=0), dict(projector=1)):
+        before = s.get_tuning()
+        s.set_tuning(**kw)
+        after = s.get_tuning()
+        (k, v), = kw.items()
+        assert after[k] == v, (kw, after)
+        assert {x: after[x] for x in after if x != k} == {x: before[x] for x in before if x != k}, (kw, before, after)
+    with pytest.raises(T.TddftError):
+        s.set_tuning(projector=2)
+    s.close()
+
+
 def test_host_buffer_entry_point(torch):
     wl = _workload(24, 10.0, 10.0, 8, 4)
     want = O.system_from_workload(wl).apply(wl.X)
