@@ -18,7 +18,11 @@ What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
   (the u_v ingredient of the Z-vector equation, Eq. 19, defined in Eq. 20 and the Supporting Information
   Sec. S1), with X, eps, f_xc and the Coulomb kernels held fixed;
 * a dense matrix of L on tiny systems and a plain block-Davidson solver
-  (Sec. 4 names Davidson's method for diagonalising L).
+  (Sec. 4 names Davidson's method for diagonalising L);
+* the K2e and K2d terms (Eqs. 5 and 7) of the full operator of the Z-vector
+  equation (Eq. 19) and its conjugate-gradient solution with the inexact
+  Krylov switch of Sec. 3.3 (exact operator while the residual norm is at
+  least lambda_thr, then the operator without K2d);
 
 Discretisation (the paper works in plane waves at the Gamma point, Sec. 2):
 cubic cell of side a, Omega = a^3, grid N^3 (N_r points), r_j = a j / N,
@@ -55,7 +59,11 @@ K1E_H = 8     # phi_v Conv_H[Delta rho]                    (Eq. 4, Coulomb part 
 K1E_XC = 16   # phi_v f_xc Delta rho                       (Eq. 4, local xc kernel)
 K1D = 32      # -alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]  (Eq. 6)
 PROJ = 64     # P^c = 1 - sum_u |phi_u><phi_u|             (after Eq. 7)
-ALL_TERMS = 127
+ALL_TERMS = 127   # the Tamm-Dancoff operator of Eq. 9
+K2E_H = 128   # phi_v Conv_H[sum_v' a_v'^* phi_v']         (Eq. 5, Coulomb part of f_Hxc)
+K2E_XC = 256  # phi_v f_xc sum_v' a_v'^* phi_v'            (Eq. 5, local xc kernel)
+K2D = 512     # -alpha sum_v' phi_v' Conv_x[a_v'^* phi_v]  (Eq. 7)
+ZVEC_TERMS = 1023  # D + K1e - K1d + K2e - K2d, the operator of the Z-vector equation (Eq. 19)
 
 _WORKERS = int(os.environ.get("ORACLE_FFT_WORKERS", os.cpu_count() or 1))
 
@@ -264,12 +272,21 @@ class System:
         return np.einsum("vzyx,vzyx->zyx", self.phi_src_r().conj(), a_r)
 
     def k1e_potential(self, drho: np.ndarray, terms: int) -> np.ndarray:
-        """W = Conv_H[Delta rho] + f_xc Delta rho (Eq. 4); SF: f_xc^SF Delta rho only (Sec. 2.3)."""
+        """W = Conv_H[Delta rho] + f_xc Delta rho (Eq. 4); SF: f_xc^SF Delta rho only (Sec. 2.3).
+
+        With the K2e bits (Eq. 5) the density of the conjugated trial vectors,
+        sum_v' a_v'^* phi_v' = conj(Delta rho), enters the same way."""
+        if self.spin_flip and terms & (K2E_H | K2E_XC | K2D):
+            raise NotImplementedError("K2 terms are defined here for the spin-conserving operator")
         W = np.zeros_like(drho)
         if (terms & K1E_H) and not self.spin_flip:
             W += self.grid.conv(drho, self.kh)
         if (terms & K1E_XC) and self.fxc is not None:
             W += self.fxc * drho
+        if terms & K2E_H:
+            W += self.grid.conv(drho.conj(), self.kh)
+        if (terms & K2E_XC) and self.fxc is not None:
+            W += self.fxc * drho.conj()
         return W
 
     def unprojected_row(self, a_r, Xb, W, v, terms, tau_row=None) -> np.ndarray:
@@ -286,13 +303,20 @@ class System:
             phit = self.phi_tgt_r()
             for w in range(self.nocc_tgt):
                 out_r -= self.alpha * phit[w] * g.conv(phit[w].conj() * a_r[v], self.kx)
-        if terms & (K1E_H | K1E_XC):
+        if terms & (K1E_H | K1E_XC | K2E_H | K2E_XC):
             out_r += self.phi_src_r()[v] * W
         if terms & K1D:
             phis = self.phi_src_r()
             for vp in range(self.nocc_src):
                 tau = g.conv(phis[vp].conj() * phis[v], self.kx)  # tau_{v v'} (Sec. 3.2)
                 out_r -= self.alpha * a_r[vp] * tau
+        if terms & K2D:
+            # alpha sum_v' phi_v' Conv_x[a_v'^* phi_v]   (Eq. 7)
+            if self.spin_flip:
+                raise NotImplementedError("K2 terms are defined here for the spin-conserving operator")
+            phis = self.phi_src_r()
+            for vp in range(self.nocc_src):
+                out_r -= self.alpha * phis[vp] * g.conv(a_r[vp].conj() * phis[v], self.kx)
         out = g.real_to_pw(out_r)
         if terms & D_KIN:
             out += (0.5 * g.g2_sphere - self.eps_src[v]) * Xb[v]
@@ -315,7 +339,8 @@ class System:
         out = np.zeros((len(want), self.grid.npw), dtype=np.complex128)
         for b, items in by_b.items():
             a_r = self.grid.pw_to_real(X[b])
-            W = self.k1e_potential(self.delta_rho(a_r), terms) if terms & (K1E_H | K1E_XC) else None
+            W = (self.k1e_potential(self.delta_rho(a_r), terms)
+                 if terms & (K1E_H | K1E_XC | K2E_H | K2E_XC) else None)
             for i, v in items:
                 row = self.unprojected_row(a_r, X[b], W, v, terms)
                 out[i] = self.project(row) if terms & PROJ else row
@@ -418,6 +443,45 @@ class System:
             H[:, j0:j0 + batch.shape[0]] = coeff.reshape(batch.shape[0], dim).T
         return H, Qc
 
+    def dense_real_matrix(self, terms: int = ZVEC_TERMS) -> tuple[np.ndarray, np.ndarray]:
+        """Real matrix of the (real-linear) operator on the unoccupied space.
+
+        With the K2 terms the operator acts on conj(Z) as well as Z, so it is
+        linear over the reals only. Coordinates: z = sum_(v,k) (s + i t) q_k e_v
+        with real s, t; returns (R, Qc) with R acting on [s; t]. Tiny systems only.
+        """
+        Qc = self.complement_basis()
+        nc = Qc.shape[1]
+        nocc = self.nocc_src
+        dim = nocc * nc
+        R = np.zeros((2 * dim, 2 * dim))
+        cols = []
+        for ph in (1.0, 1j):
+            for vp in range(nocc):
+                for k in range(nc):
+                    x = np.zeros((nocc, self.grid.npw), dtype=np.complex128)
+                    x[vp] = ph * Qc[:, k]
+                    cols.append(x)
+        for j0 in range(0, 2 * dim, 64):
+            batch = np.stack(cols[j0:j0 + 64])
+            LX = self.apply(batch, terms)
+            coeff = np.einsum("gk,bvg->bvk", Qc.conj(), LX).reshape(batch.shape[0], dim)
+            R[:dim, j0:j0 + batch.shape[0]] = coeff.real.T
+            R[dim:, j0:j0 + batch.shape[0]] = coeff.imag.T
+        return R, Qc
+
+    def zvector_rhs(self, X: np.ndarray) -> np.ndarray:
+        """Right-hand sides of Eq. 19 for the states X [nb, nocc, npw]:
+        U_s = -P^c u_s, u_s = d omega_s / d phi^* (Eq. 20) as computed by omega_grad
+        (the parts of u that do not come from H^KS, eps and V_xc depending on the
+        ground-state density, which are inputs here)."""
+        X = np.asarray(X, dtype=np.complex128)
+        U = np.empty_like(X)
+        for b in range(X.shape[0]):
+            _, g, _ = self.omega_grad(X[b:b + 1], np.ones(1))
+            U[b] = -self.project(g)
+        return U
+
 
 # --------------------------------------------------------------------------
 # Davidson (the paper only names the method; this follows Davidson's block scheme)
@@ -492,3 +556,68 @@ def system_from_workload(wl, **kw) -> System:
     return System(wl.n, wl.a, wl.ecut, wl.phi_src, wl.eps_src, alpha=wl.alpha, kx_g0=wl.kx_g0,
                   spin_flip=wl.spin_flip, phi_tgt=wl.phi_tgt if wl.spin_flip else None,
                   vloc=wl.vloc, fxc=wl.fxc, **kw)
+
+
+# --------------------------------------------------------------------------
+# Z-vector equation (Eq. 19) by conjugate gradients with the inexact Krylov
+# switch of Sec. 3.3
+# --------------------------------------------------------------------------
+
+def zvector_cg(sys: System, U: np.ndarray, lam_thr: float, tol: float, max_iter: int = 200,
+               precondition: bool = False):
+    """Solve (D + K1e - K1d + K2e - K2d) Z_s = U_s for each state s by CG.
+
+    The operator is linear over the reals and self-adjoint for the real inner
+    product Re<x|y>, so CG runs with that inner product and real step sizes.
+    For each state: the exact operator is applied while the residual norm
+    ||r|| is at least lam_thr; below it the operator without K2d (Sec. 3.3).
+    A state stops once ||r|| < tol. Optional diagonal preconditioner:
+    P^c [r_v / (1/2|G|^2 - eps_v)] with the denominator clamped to >= 0.1 Ha.
+    Starts from Z = 0. Returns (Z, iterations [nb], exact_iterations [nb],
+    residual norms [nb], converged [nb]); the residual is the recursively
+    updated one.
+    """
+    g = sys.grid
+    U = np.asarray(U, dtype=np.complex128)
+    nb = U.shape[0]
+    den = 0.5 * g.g2_sphere[None, :] - sys.eps_src[:, None]
+    den = np.where(np.abs(den) < 0.1, np.where(den < 0, -0.1, 0.1), den)
+
+    def prec(r):
+        return sys.project(r / den) if precondition else r
+
+    def ip(x, y):
+        return float(np.vdot(x, y).real)
+
+    exact_terms = ZVEC_TERMS
+    approx_terms = ZVEC_TERMS & ~K2D
+    Z = np.zeros_like(U)
+    iters = np.zeros(nb, dtype=int)
+    n_exact = np.zeros(nb, dtype=int)
+    res = np.zeros(nb)
+    conv = np.zeros(nb, dtype=bool)
+    for b in range(nb):
+        r = U[b].copy()
+        sv = prec(r)
+        p = sv.copy()
+        rs = ip(r, sv)
+        for it in range(max_iter):
+            rn = np.sqrt(ip(r, r))
+            if rn < tol:
+                conv[b] = True
+                break
+            exact = rn >= lam_thr
+            q = sys.apply(p[None], exact_terms if exact else approx_terms)[0]
+            step = rs / ip(p, q)
+            Z[b] += step * p
+            r = r - step * q
+            sv = prec(r)
+            rs_new = ip(r, sv)
+            p = sv + (rs_new / rs) * p
+            rs = rs_new
+            iters[b] += 1
+            n_exact[b] += int(exact)
+        else:
+            conv[b] = np.sqrt(ip(r, r)) < tol
+        res[b] = np.sqrt(ip(r, r))
+    return Z, iters, n_exact, res, conv

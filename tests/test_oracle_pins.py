@@ -409,3 +409,136 @@ def test_ace_error_decreases_with_more_build_vectors():
         errs.append(np.linalg.norm(S.exchange_ace_pw(a) - exact))
     assert all(e2 <= e1 * (1 + 1e-12) for e1, e2 in zip(errs, errs[1:])), errs
     assert errs[-1] < 0.7 * errs[0]
+
+
+# --------------------------------------------------------------------------
+# K2 terms (Eqs. 5, 7) and the Z-vector equation (Eq. 19)
+# --------------------------------------------------------------------------
+
+def test_free_electron_k2_closed_form():
+    """Single-plane-wave orbitals: a trial orbital a_v' = x e^{iK.r}/sqrt(Omega) gives
+    K2e_v = (kappa_H(G_v'-K) + f_xc) conj(x)/Omega at G_v + G_v' - K and
+    K2d_v = alpha kappa_x(G_v - K) conj(x)/Omega at the same plane wave, written
+    here without any FFT."""
+    n, a, ecut = 8, 6.0, 3.2
+    g = O.Grid(n, a, ecut)
+    npw = g.npw
+    mill = [tuple(int(t) for t in v) for v in g.miller]
+    pos = {m: i for i, m in enumerate(mill)}
+    occ = [(0, 0, 0), (1, 0, 0), (0, -1, 1)]
+    nocc = len(occ)
+    phi = np.zeros((nocc, npw), dtype=np.complex128)
+    for v, m in enumerate(occ):
+        phi[v, pos[m]] = 1.0
+    alpha, g0, cf = 0.37, 17.0, -0.29
+    fxc = np.full((n,) * 3, cf)
+    S = O.System(n, a, ecut, phi, np.array([-0.41, -0.23, -0.05]), alpha=alpha, kx_g0=g0, fxc=fxc)
+    rng = np.random.default_rng(24)
+    X = rng.standard_normal((2, nocc, npw)) + 1j * rng.standard_normal((2, nocc, npw))
+    for m in occ:
+        X[:, :, pos[m]] = 0.0
+    tp = 2 * math.pi / a
+    omega = a ** 3
+
+    def kap(m, g0val):
+        m = _wrap(m, n)
+        q2 = tp * tp * float(np.dot(m, m))
+        return g0val if q2 == 0 else 4 * math.pi / q2
+
+    for terms in (O.K2E_H, O.K2E_XC, O.K2D, O.K2E_H | O.K2E_XC | O.K2D):
+        want = np.zeros_like(X)
+        for b in range(2):
+            for v in range(nocc):
+                Gv = np.array(occ[v])
+                out = np.zeros(npw, dtype=np.complex128)
+                for vp in range(nocc):
+                    Gvp = np.array(occ[vp])
+                    for k, K in enumerate(mill):
+                        K = np.array(K)
+                        t = tuple(_wrap(Gv + Gvp - K, n))
+                        if t not in pos:
+                            continue
+                        c = np.conj(X[b, vp, k]) / omega
+                        if terms & O.K2E_H:
+                            out[pos[t]] += kap(Gvp - K, 0.0) * c
+                        if terms & O.K2E_XC:
+                            out[pos[t]] += cf * c
+                        if terms & O.K2D:
+                            out[pos[t]] -= alpha * kap(Gv - K, g0) * c
+                for m in occ:
+                    out[pos[m]] = 0.0
+                want[b, v] = out
+        got = S.apply(X, terms | O.PROJ)
+        assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max()), terms
+
+
+@pytest.mark.parametrize("terms", [O.K2E_H, O.K2E_XC, O.K2D])
+def test_k2_terms_are_conjugate_linear(terms):
+    """K2(c z) = conj(c) K2(z) for complex c, while the K1 counterpart is linear."""
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=1, seed=25)
+    z = wl.X
+    c = 0.6 - 1.3j
+    k2 = S.apply(z, terms | O.PROJ)
+    assert np.abs(k2).max() > 1e-7
+    assert np.allclose(S.apply(c * z, terms | O.PROJ), np.conj(c) * k2, atol=1e-13 * np.abs(k2).max())
+    k1 = {O.K2E_H: O.K1E_H, O.K2E_XC: O.K1E_XC, O.K2D: O.K1D}[terms]
+    l1 = S.apply(z, k1 | O.PROJ)
+    assert np.allclose(S.apply(c * z, k1 | O.PROJ), c * l1, atol=1e-13 * np.abs(l1).max())
+
+
+def test_zvector_operator_is_real_symmetric_and_definite():
+    """The real matrix of D + K1e - K1d + K2e - K2d on the unoccupied space is
+    symmetric (each K2 term alone too) and positive definite on the tiny test system."""
+    wl, S = _tiny(n=8, a=6.0, ecut=2.5, nocc=2, nb=1, seed=26)
+    R, _ = S.dense_real_matrix()
+    assert np.abs(R - R.T).max() < 1e-13 * np.abs(R).max()
+    assert np.linalg.eigvalsh(0.5 * (R + R.T)).min() > 0
+    for t in (O.K2E_H, O.K2E_XC, O.K2D):
+        Rt, _ = S.dense_real_matrix(t | O.PROJ)
+        assert np.abs(Rt).max() > 1e-4
+        assert np.abs(Rt - Rt.T).max() < 1e-13 * np.abs(Rt).max()
+
+
+def _real_coords(Qc, Z):
+    c = np.einsum("gk,vg->vk", Qc.conj(), Z).reshape(-1)
+    return np.concatenate([c.real, c.imag])
+
+
+@pytest.mark.parametrize("precondition", [False, True])
+def test_zvector_cg_matches_dense_solve(precondition):
+    """CG with the exact operator throughout (lambda_thr = 0) against numpy's dense
+    solve of the real system; with lambda_thr = inf against the solve of the
+    system without K2d (Sec. 3.3)."""
+    wl, S = _tiny(n=8, a=6.0, ecut=2.5, nocc=2, nb=2, seed=27)
+    U = S.zvector_rhs(wl.X)
+    R, Qc = S.dense_real_matrix()
+    Ra, _ = S.dense_real_matrix(O.ZVEC_TERMS & ~O.K2D)
+    for lam, M in ((0.0, R), (np.inf, Ra)):
+        Z, it, nex, res, conv = O.zvector_cg(S, U, lam, 1e-11, max_iter=400, precondition=precondition)
+        assert conv.all(), (it, res)
+        assert (nex == (it if lam == 0.0 else 0)).all()
+        for b in range(2):
+            want = np.linalg.solve(M, _real_coords(Qc, U[b]))
+            got = _real_coords(Qc, Z[b])
+            assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+            # Z stays in the unoccupied space
+            assert np.abs(wl.phi_tgt.conj() @ Z[b].T).max() < 1e-12
+
+
+def test_inexact_krylov_error_shrinks_with_the_threshold():
+    """The switch to the operator without K2d at ||r|| < lambda_thr: fewer exact
+    applications for larger thresholds, and the error of Z against the exact
+    solution shrinks as the threshold is lowered (Sec. 3.3)."""
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=1, seed=28)
+    U = S.zvector_rhs(wl.X)
+    Z0, *_ = O.zvector_cg(S, U, 0.0, 1e-12, max_iter=400)
+    nrm = np.linalg.norm(U)
+    errs, nexs = [], []
+    for lam in (1e-1, 1e-2, 1e-3, 1e-4):
+        Z, it, nex, res, conv = O.zvector_cg(S, U, lam * nrm, 1e-12, max_iter=400)
+        assert conv.all()
+        errs.append(np.linalg.norm(Z - Z0) / np.linalg.norm(Z0))
+        nexs.append(int(nex[0]))
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
+    assert all(n2 >= n1 for n1, n2 in zip(nexs, nexs[1:])), nexs
+    assert errs[-1] < 1e-4 and errs[0] > 1e-6, errs
