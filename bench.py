@@ -262,7 +262,9 @@ def run_native(args):
     term_ms = {}
     if args.term_split:
         for name, mask in (("D_exchange", T.TERM_D_EXX), ("K1d", T.TERM_K1D), ("K1e", T.TERM_K1E_H | T.TERM_K1E_XC),
-                           ("diagonal_and_projector", T.TERM_D_KIN | T.TERM_D_VLOC | T.TERM_PROJ)):
+                           ("diagonal_and_projector", T.TERM_D_KIN | T.TERM_D_VLOC | T.TERM_PROJ),
+                           ("K2d (Z-vector operator only)", T.TERM_K2D),
+                           ("K2e (Z-vector operator only)", T.TERM_K2E_H | T.TERM_K2E_XC)):
             sys_.set_terms(mask)
             sys_.apply(X, out=LA, stream=stream)
             t0e = torch.cuda.Event(enable_timing=True)
@@ -281,6 +283,8 @@ def run_native(args):
         extras["sf216"] = bench_sf216(torch, T, dev, stream)
     if "ace" in args.extra:
         extras["ace"] = bench_ace(torch, T, dev, stream, wl, X, LA)
+    if "zvector" in args.extra:
+        extras["zvector"] = bench_zvector(torch, T, dev, stream, wl, X)
 
     # plain FP64 GPU path on the same batch
     fp64 = None
@@ -422,6 +426,43 @@ def bench_ace(torch, T, dev, stream, wl, X, LA, steps=3):
             "note": "approximate operator (compressed exchange inside D); not the bench metric"}
 
 
+def bench_zvector(torch, T, dev, stream, wl, X, max_iter=40):
+    """Z-vector equation (Eq. 19) for the bench batch's states: right-hand sides
+    from the adjoint, then preconditioned CG with the inexact Krylov switch at
+    lambda_thr = 1e-4 (Sec. 3.3) to a residual norm of 1e-6, FP32 operator.
+    Reports the time of one exact and one approximate operator application."""
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    nb = X.shape[0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    U = s.zvector_rhs(X, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rhs_ms = e0.elapsed_time(e1)
+    Y = torch.empty_like(X)
+    op_ms = {}
+    for name, mask in (("exact", T.TERMS_ZVEC), ("approx_no_K2d", T.TERMS_ZVEC & ~T.TERM_K2D)):
+        s.set_terms(mask)
+        s.apply(U, out=Y, stream=stream)
+        e0.record(stream)
+        s.apply(U, out=Y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        op_ms[name] = e0.elapsed_time(e1)
+    s.set_terms(T.TERMS_ALL)
+    t0 = time.perf_counter()
+    Z, it, ex, res = s.zvector_solve(U, lambda_thr=1e-4, tol=1e-6, max_iter=max_iter, precondition=True,
+                                     stream=stream, require_convergence=False)
+    torch.cuda.synchronize(dev)
+    solve_s = time.perf_counter() - t0
+    s.close()
+    return {"states": nb, "rhs_ms": rhs_ms, "operator_ms_per_batch": op_ms, "solve_s": solve_s,
+            "iterations": it.tolist(), "exact_iterations": ex.tolist(), "residual": res.tolist(),
+            "lambda_thr": 1e-4, "tol": 1e-6, "max_iter": max_iter,
+            "note": "preconditioned CG; per state the exact operator while ||r|| >= lambda_thr"}
+
+
 def bench_sf216(torch, T, dev, stream, steps=1):
     """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path."""
     from paper_2309_03513_b300 import synth
@@ -456,7 +497,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")
     ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
-                                             "ace (compressed exchange on the bench batch)")
+                                             "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch)")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()

@@ -55,7 +55,15 @@ typedef enum tddft_status {
 #define TDDFT_TERM_K1E_XC 16u /* phi_v f_xc Delta rho               (Eq. 4; f_xc^SF for spin-flip) */
 #define TDDFT_TERM_K1D 32u    /* -alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]  (Eq. 6, Sec. 3.2) */
 #define TDDFT_TERM_PROJ 64u   /* P^c = 1 - sum_u |phi_u><phi_u| of the target spin (after Eq. 7) */
-#define TDDFT_TERMS_ALL 127u
+#define TDDFT_TERMS_ALL 127u  /* the Tamm-Dancoff operator L = D + K1e - K1d (Eq. 9 / Eq. 21) */
+/* Terms of the full operator of the Z-vector equation (Eq. 19), spin-conserving
+ * handles only (TDDFT_ENOTSUP on spin-flip handles). They act on the complex
+ * conjugate of the trial vectors, so with them the operator is linear over the
+ * reals only (it is self-adjoint for Re<x|y>); Davidson rejects them. */
+#define TDDFT_TERM_K2E_H 128u  /* phi_v Conv_H[sum_v' a_v'^* phi_v']          (Eq. 5) */
+#define TDDFT_TERM_K2E_XC 256u /* phi_v f_xc sum_v' a_v'^* phi_v'             (Eq. 5) */
+#define TDDFT_TERM_K2D 512u    /* -alpha sum_v' phi_v' Conv_x[a_v'^* phi_v]   (Eq. 7) */
+#define TDDFT_TERMS_ZVEC 1023u /* D + K1e - K1d + K2e - K2d */
 
 #define TDDFT_SPIN_CONSERVING 0
 #define TDDFT_SPIN_FLIP 1 /* source spin up -> target spin down (Eq. 21) */
@@ -119,7 +127,8 @@ tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, v
  * last check (the flag is then cleared). */
 tddft_status tddft_query(tddft_handle h, tddft_info* info);
 
-/* Change the term mask of the handle (TDDFT_TERM_* bits). */
+/* Change the term mask of the handle (TDDFT_TERM_* bits; K2 bits on a
+ * spin-flip handle -> TDDFT_ENOTSUP). */
 tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask);
 
 /* Schedule of the pair-convolution passes (results agree to rounding for
@@ -182,6 +191,42 @@ tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_ho
  * appear once. Stream-ordered on `stream`. */
 tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
                                          void* const* LA, void* stream);
+
+/* Z-vector equation (Eq. 19): (D + K1e - K1d + K2e - K2d) Z_s = U_s, solved
+ * for each state s by conjugate gradients (Sec. 3.3). Spin-conserving handles
+ * with the projector term (else TDDFT_ENOTSUP / TDDFT_EINVAL).
+ * The operator is the handle's Tamm-Dancoff mask plus the K2 counterpart of
+ * every K1 term in it (K1e_H -> K2e_H, K1e_XC -> K2e_XC, K1d -> K2d). With the
+ * K2 terms it acts on conj(Z) too: it is linear over the reals and
+ * self-adjoint for Re<x|y>, so CG uses that inner product and real steps.
+ * Inexact Krylov switch: a state's search direction gets the exact operator
+ * while its residual norm ||r_s||_2 (recursively updated, all v and G) is at
+ * least lambda_thr, afterwards the operator without K2d. lambda_thr = 0: always
+ * exact. A state stops once ||r_s|| < tol; Z starts at 0. precondition = 1:
+ * s = P^c [r_v / (1/2|G|^2 - eps_v)], |denominator| clamped to >= 0.1 Ha.
+ * U, Z: device [nb][nocc_src][npw] in the handle's precision (nb <= nb_max, no
+ * aliasing); Z is written. iterations, exact_iterations, residual: optional
+ * host arrays [nb] (CG steps per state, steps with the exact operator, final
+ * ||r_s||). Host-driven: two small device->host reads per iteration.
+ * TDDFT_ENOTCONV if a state has not reached tol after max_iter steps (Z holds
+ * the last iterate); TDDFT_ENUMERIC if <p|L p> <= 0 (the operator is not
+ * positive definite on the search space). */
+typedef struct {
+  double lambda_thr;
+  double tol;
+  int max_iter;
+  int precondition;
+} tddft_zvector_opts;
+tddft_status tddft_zvector_solve(tddft_handle h, int nb, const void* U, void* Z, const tddft_zvector_opts* opts,
+                                 int* iterations, int* exact_iterations, double* residual, void* stream);
+
+/* Right-hand sides of Eq. 19 for nb states X (device [nb][nocc_src][npw]):
+ * U_s = -P^c u_s with u_s = d omega_s / d phi^* from the adjoint
+ * (tddft_apply_liouville_adjoint with weight 1 on state s alone; Eq. 20,
+ * without the parts that come from H^KS, eps and V_xc depending on the
+ * ground-state density, which are inputs here). U: device, same layout,
+ * written. Spin-conserving handles with ACE off (else TDDFT_ENOTSUP). */
+tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, void* stream);
 
 /* Adaptively compressed exchange (ACE, Sec. 3.1, Eqs. 29-30) for the exchange
  * term inside D: V_X^ACE = -sum_k |xi_k><xi_k| with xi = W L^{-dagger},

@@ -277,19 +277,31 @@ __global__ void k_delta_rho(const cplx<T>* __restrict__ phi, const cplx<T>* __re
   }
 }
 
-// out[b,v](r) = vloc(r) a_{b,v}(r) + phi_v(r) (W_b(r) + fxc(r) drho_b(r))
-// Each factor is optional (null pointer = absent).
+// out[b,v](r) = vloc(r) a_{b,v}(r) + phi_v(r) W_b(r), where
+// W_b = [Conv_H drho_b] and/or its conjugate (hmode bits 1, 2: the K1e and K2e
+// Hartree parts; Conv_H[conj drho] = conj Conv_H[drho] for the real, even
+// kernel) + fxc (drho_b and/or conj drho_b) (xmode bits 1, 2).
+// vloc == nullptr: no local term; hmode = xmode = 0: no phi_v W_b term.
 template <typename T>
 __global__ void k_init_out(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ phi, const T* __restrict__ vloc,
                            const cplx<T>* __restrict__ wconv, const T* __restrict__ fxc, const cplx<T>* __restrict__ drho,
-                           cplx<T>* __restrict__ out, int nocc, int nb, long long n3) {
+                           cplx<T>* __restrict__ out, int nocc, int nb, long long n3, int hmode, int xmode) {
   const long long total = (long long)nb * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / n3, r = i - b * n3;
     cplx<T> W = {T(0), T(0)};
-    if (wconv) W = wconv[i];
-    if (fxc) W = cadd(W, cscale(drho[i], fxc[r]));
-    const bool k1e = (wconv != nullptr) || (fxc != nullptr);
+    if (hmode) {
+      const cplx<T> w = wconv[i];
+      if (hmode & 1) W = cadd(W, w);
+      if (hmode & 2) W = cadd(W, cplx<T>{w.x, -w.y});
+    }
+    if (xmode) {
+      const cplx<T> d = drho[i];
+      const T f = fxc[r];
+      if (xmode & 1) W = cadd(W, cscale(d, f));
+      if (xmode & 2) W = cadd(W, cscale(cplx<T>{d.x, -d.y}, f));
+    }
+    const bool k1e = (hmode | xmode) != 0;
     const T vl = vloc ? vloc[r] : T(0);
     for (int v = 0; v < nocc; ++v) {
       const long long o = (b * nocc + v) * n3 + r;

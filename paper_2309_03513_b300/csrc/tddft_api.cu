@@ -598,20 +598,23 @@ static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T
   cplx<T>* out_r = (cplx<T>*)h->b.out_r;
   cplx<T>* drho = (cplx<T>*)h->b.drho;
   cplx<T>* wb = (cplx<T>*)h->b.wb;
-  const bool k1e_h = (mask & TDDFT_TERM_K1E_H) && !h->sf();
-  const bool k1e_xc = (mask & TDDFT_TERM_K1E_XC) && h->b.fxc;
+  if (h->sf() && (mask & (TDDFT_TERM_K2E_H | TDDFT_TERM_K2E_XC | TDDFT_TERM_K2D)))
+    return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
+  // Hartree and xc parts of K1e (W) and K2e (conj W); spin-flip has no Hartree part
+  const int hmode = (((mask & TDDFT_TERM_K1E_H) && !h->sf()) ? 1 : 0) | ((mask & TDDFT_TERM_K2E_H) ? 2 : 0);
+  const int xmode = h->b.fxc ? (((mask & TDDFT_TERM_K1E_XC) ? 1 : 0) | ((mask & TDDFT_TERM_K2E_XC) ? 2 : 0)) : 0;
   const bool vloc = (mask & TDDFT_TERM_D_VLOC) && h->b.vloc;
   for (int b0 = 0; b0 < nb; b0 += h->nb_chunk) {
     const int nbc = std::min(h->nb_chunk, nb - b0);
     const int nf = nbc * nocc;
     const cplx<T>* Ab = A + (long long)b0 * nocc * npw;
     STATUS_TRY(pw_to_real<T>(h, Ab, nf, a_r, st));
-    if (k1e_h || k1e_xc)
+    if (hmode || xmode)
       { k_delta_rho<T><<<grid_for((long long)nbc * n3, 256), 256, 0, st>>>(phis, a_r, drho, nocc, nbc, n3); note_launch(); }
-    if (k1e_h) STATUS_TRY(convolve_fields<T>(h, drho, nbc, (const T*)h->b.kh, T(1), wb, st));
+    if (hmode) STATUS_TRY(convolve_fields<T>(h, drho, nbc, (const T*)h->b.kh, T(1), wb, st));
     { k_init_out<T><<<grid_for((long long)nbc * n3, 256), 256, 0, st>>>(
-        a_r, phis, vloc ? (const T*)h->b.vloc : nullptr, k1e_h ? wb : nullptr, k1e_xc ? (const T*)h->b.fxc : nullptr,
-        drho, out_r, nocc, nbc, n3); note_launch(); }
+        a_r, phis, vloc ? (const T*)h->b.vloc : nullptr, wb, (const T*)h->b.fxc, drho, out_r, nocc, nbc, n3, hmode,
+        xmode); note_launch(); }
     STATUS_TRY(check_launch("init_out"));
     if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0 && !h->ace_on) {
       // out[t] += -alpha sum_w phi_w Conv_x[conj(phi_w) a_t],  t = (b, v)
@@ -619,6 +622,13 @@ static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T
       STATUS_TRY(pair_accumulate<T>(h, phit, a_r, phit, out_r, pg, (const T*)h->b.kx, (T)(-h->d.alpha), st));
     }
     if ((mask & TDDFT_TERM_K1D) && h->d.alpha != 0.0) STATUS_TRY(k1d_term<T>(h, nbc, st));
+    if ((mask & TDDFT_TERM_K2D) && h->d.alpha != 0.0) {
+      // out[b,v] += -alpha sum_v' phi_v' Conv_x[conj(a_{b,v'}) phi_v]  (Eq. 7): per b, targets v, sources v'
+      for (int b = 0; b < nbc; ++b) {
+        PairGrid pg{nocc, nocc, b * nocc, 1, 0, 0, 0, 1, 0, 1, 0, b * nocc, 1};
+        STATUS_TRY(pair_accumulate<T>(h, a_r, phis, phis, out_r, pg, (const T*)h->b.kx, (T)(-h->d.alpha), st));
+      }
+    }
     STATUS_TRY(real_to_pw<T>(h, out_r, nf, LA + (long long)b0 * nocc * npw,
                              (mask & TDDFT_TERM_D_KIN) ? Ab : nullptr, st));
   }
@@ -1287,6 +1297,9 @@ tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, v
   if (d.spin_mode == TDDFT_SPIN_CONSERVING && d.nocc_tgt != d.nocc_src)
     return fail(TDDFT_EINVAL, "spin-conserving systems need nocc_tgt == nocc_src");
   if (d.nocc_tgt < 1) return fail(TDDFT_EINVAL, "nocc_tgt must be >= 1");
+  if (d.term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
+  if (d.spin_mode == TDDFT_SPIN_FLIP && (d.term_mask & ~TDDFT_TERMS_ALL))
+    return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
   if (!in->phi_src || !in->eps_src) return fail(TDDFT_EINVAL, "orbitals and eigenvalues are required");
   if (d.spin_mode == TDDFT_SPIN_FLIP && !in->phi_tgt) return fail(TDDFT_EINVAL, "spin-flip needs phi_tgt");
   std::vector<Miller> sph;
@@ -1323,7 +1336,9 @@ tddft_status tddft_query(tddft_handle h, tddft_info* info) {
 
 tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
   if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (term_mask & ~TDDFT_TERMS_ALL) return fail(TDDFT_EINVAL, "unknown term bits");
+  if (term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
+  if (h->sf() && (term_mask & ~TDDFT_TERMS_ALL))
+    return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
   h->d.term_mask = term_mask;  // a cached graph is re-captured when the mask differs
   return TDDFT_OK;
 }
@@ -1512,6 +1527,217 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
   if (h->d.precision == TDDFT_PREC_FP64)
     return adjoint_impl<double>(h, nb, (const cplx<double>*)X, w, omega, (cplx<double>*)grad_phi, grad_vloc, st);
   return adjoint_impl<float>(h, nb, (const cplx<float>*)X, w, omega, (cplx<float>*)grad_phi, grad_vloc, st);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Z-vector equation (Eq. 19) by conjugate gradients with the inexact Krylov
+// switch (Sec. 3.3)
+// ---------------------------------------------------------------------------
+
+// per state b (rows of length len): Z_b += step_b p_b, r_b -= step_b q_b
+template <typename T>
+__global__ void k_zv_step(cplx<T>* __restrict__ Z, cplx<T>* __restrict__ r, const cplx<T>* __restrict__ p,
+                          const cplx<T>* __restrict__ q, const double* __restrict__ step, long long len,
+                          long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const double a = step[i / len];
+    if (a == 0.0) continue;
+    const cplx<T> pv = p[i], qv = q[i];
+    Z[i] = {(T)(Z[i].x + a * pv.x), (T)(Z[i].y + a * pv.y)};
+    r[i] = {(T)(r[i].x - a * qv.x), (T)(r[i].y - a * qv.y)};
+  }
+}
+
+// per state b that moved (step_b != 0): p_b = s_b + beta_b p_b
+template <typename T>
+__global__ void k_zv_direction(cplx<T>* __restrict__ p, const cplx<T>* __restrict__ sv, const double* __restrict__ beta,
+                               const double* __restrict__ step, long long len, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    if (step[i / len] == 0.0) continue;
+    const double bt = beta[i / len];
+    p[i] = {(T)(sv[i].x + bt * p[i].x), (T)(sv[i].y + bt * p[i].y)};
+  }
+}
+
+// s = r / d, d = |G|^2/2 - eps_v with |d| clamped to >= 0.1 Ha (sign kept); rows [nb][nocc][npw]
+template <typename T>
+__global__ void k_zv_precondition(const cplx<T>* __restrict__ r, const T* __restrict__ g2h, const T* __restrict__ eps,
+                                  int nocc, int npw, long long total, cplx<T>* __restrict__ sv) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / npw, g = i - row * npw;
+    double d = (double)g2h[g] - (double)eps[row % nocc];
+    if (fabs(d) < 0.1) d = d < 0.0 ? -0.1 : 0.1;
+    sv[i] = {(T)(r[i].x / d), (T)(r[i].y / d)};
+  }
+}
+
+template <typename T>
+__global__ void k_negate(cplx<T>* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = {-x[i].x, -x[i].y};
+}
+
+// Terms of the exact Z-vector operator for the handle's Tamm-Dancoff mask: the
+// K2 counterpart of every K1 term that is switched on.
+static unsigned zvector_mask(unsigned m) {
+  m &= TDDFT_TERMS_ALL;
+  if (m & TDDFT_TERM_K1E_H) m |= TDDFT_TERM_K2E_H;
+  if (m & TDDFT_TERM_K1E_XC) m |= TDDFT_TERM_K2E_XC;
+  if (m & TDDFT_TERM_K1D) m |= TDDFT_TERM_K2D;
+  return m;
+}
+
+template <typename T>
+static tddft_status zvector_rhs_impl(tddft_system* h, int nb, const cplx<T>* X, cplx<T>* U, cudaStream_t st) {
+  const long long len = (long long)h->d.nocc_src * h->npw;
+  const double one = 1.0;
+  for (int b = 0; b < nb; ++b) {
+    STATUS_TRY(adjoint_impl<T>(h, 1, X + b * len, &one, h->b.wdev, U + b * len, nullptr, st));
+    STATUS_TRY(project_rows<T>(h, (const cplx<T>*)h->b.phi_src_pw, h->d.nocc_src, U + b * len, h->d.nocc_src, st));
+    { k_negate<T><<<grid_for(len, 256), 256, 0, st>>>(U + b * len, len); note_launch(); }
+  }
+  return check_launch("zvector rhs");
+}
+
+template <typename T>
+static tddft_status zvector_impl(tddft_system* h, int nb, const cplx<T>* U, cplx<T>* Z, const tddft_zvector_opts& o,
+                                 int* iters_out, int* exact_out, double* res_out, cudaStream_t st) {
+  const long long len = (long long)h->d.nocc_src * h->npw, total = nb * len;
+  const size_t bytes = (size_t)total * sizeof(cplx<T>);
+  const unsigned m_exact = zvector_mask(h->d.term_mask), m_approx = m_exact & ~TDDFT_TERM_K2D;
+  TempAllocs tmp;
+  cplx<T> *r, *p, *q, *sv, *gin, *gout;
+  double* dsc;  // [3][nb]: dots, steps, betas
+  STATUS_TRY(tmp.get((void**)&r, bytes));
+  STATUS_TRY(tmp.get((void**)&p, bytes));
+  STATUS_TRY(tmp.get((void**)&q, bytes));
+  STATUS_TRY(tmp.get((void**)&gin, bytes));
+  STATUS_TRY(tmp.get((void**)&gout, bytes));
+  if (o.precondition) STATUS_TRY(tmp.get((void**)&sv, bytes));
+  else sv = r;
+  STATUS_TRY(tmp.get((void**)&dsc, 3 * (size_t)nb * sizeof(double)));
+  double* d_dot = dsc;
+  double* d_step = dsc + nb;
+  double* d_beta = dsc + 2 * nb;
+  auto precond = [&]() -> tddft_status {
+    if (!o.precondition) return TDDFT_OK;
+    { k_zv_precondition<T><<<grid_for(total, 256), 256, 0, st>>>(r, (const T*)h->b.g2h, (const T*)h->b.eps,
+                                                                 h->d.nocc_src, h->npw, total, sv); note_launch(); }
+    return project_rows<T>(h, (const cplx<T>*)h->b.phi_tgt_pw, h->d.nocc_tgt, sv, nb * h->d.nocc_src, st);
+  };
+  // Re<x_b|y_b> for every b, to the host
+  auto dots = [&](const cplx<T>* x, const cplx<T>* y, std::vector<double>& out) -> tddft_status {
+    { k_bilinear<T><<<nb, 256, 0, st>>>(x, y, len, d_dot); note_launch(); }
+    STATUS_TRY(check_launch("zvector dots"));
+    out.resize(nb);
+    CUDA_TRY(cudaMemcpyAsync(out.data(), d_dot, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDDFT_OK;
+  };
+  // q_b = L p_b for the states in `set` with the given terms (contiguous runs in place, others gathered)
+  auto apply_set = [&](const std::vector<int>& set, unsigned mask) -> tddft_status {
+    if (set.empty()) return TDDFT_OK;
+    bool run = true;
+    for (size_t j = 1; j < set.size(); ++j) run = run && set[j] == set[j - 1] + 1;
+    if (run) return apply_impl<T>(h, (int)set.size(), p + set[0] * len, q + set[0] * len, mask, st);
+    for (size_t j = 0; j < set.size(); ++j)
+      CUDA_TRY(cudaMemcpyAsync(gin + j * len, p + set[j] * len, len * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st));
+    STATUS_TRY(apply_impl<T>(h, (int)set.size(), gin, gout, mask, st));
+    for (size_t j = 0; j < set.size(); ++j)
+      CUDA_TRY(cudaMemcpyAsync(q + set[j] * len, gout + j * len, len * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st));
+    return TDDFT_OK;
+  };
+
+  CUDA_TRY(cudaMemsetAsync(Z, 0, bytes, st));
+  CUDA_TRY(cudaMemcpyAsync(r, U, bytes, cudaMemcpyDeviceToDevice, st));
+  STATUS_TRY(precond());
+  CUDA_TRY(cudaMemcpyAsync(p, sv, bytes, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> rs, rr, pq, rs_new;
+  STATUS_TRY(dots(r, sv, rs));
+  STATUS_TRY(dots(r, r, rr));
+  std::vector<int> iters(nb, 0), n_exact(nb, 0);
+  std::vector<double> step(nb), beta(nb);
+  for (int it = 0; it < o.max_iter; ++it) {
+    std::vector<int> ex, ap;
+    for (int b = 0; b < nb; ++b) {
+      const double rn = std::sqrt(std::max(rr[b], 0.0));
+      if (!(rn >= o.tol)) continue;  // converged
+      (rn >= o.lambda_thr ? ex : ap).push_back(b);
+    }
+    if (ex.empty() && ap.empty()) break;
+    STATUS_TRY(apply_set(ex, m_exact));
+    STATUS_TRY(apply_set(ap, m_approx));
+    STATUS_TRY(dots(p, q, pq));
+    std::fill(step.begin(), step.end(), 0.0);
+    for (const std::vector<int>* set : {&ex, &ap})
+      for (int b : *set) {
+        if (!(pq[b] > 0.0))
+          return fail(TDDFT_ENUMERIC, "the Z-vector operator is not positive definite on the search direction of state " +
+                                          std::to_string(b));
+        step[b] = rs[b] / pq[b];
+        iters[b] += 1;
+        n_exact[b] += set == &ex ? 1 : 0;
+      }
+    CUDA_TRY(cudaMemcpyAsync(d_step, step.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    { k_zv_step<T><<<grid_for(total, 256), 256, 0, st>>>(Z, r, p, q, d_step, len, total); note_launch(); }
+    STATUS_TRY(precond());
+    STATUS_TRY(dots(r, sv, rs_new));
+    STATUS_TRY(dots(r, r, rr));
+    for (int b = 0; b < nb; ++b) {
+      beta[b] = (step[b] != 0.0 && rs[b] > 0.0) ? rs_new[b] / rs[b] : 0.0;
+      if (step[b] != 0.0) rs[b] = rs_new[b];
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_beta, beta.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    { k_zv_direction<T><<<grid_for(total, 256), 256, 0, st>>>(p, sv, d_beta, d_step, len, total); note_launch(); }
+    STATUS_TRY(check_launch("zvector update"));
+  }
+  STATUS_TRY(check_device_flag(h, st));
+  bool all = true;
+  for (int b = 0; b < nb; ++b) {
+    const double rn = std::sqrt(std::max(rr[b], 0.0));
+    if (iters_out) iters_out[b] = iters[b];
+    if (exact_out) exact_out[b] = n_exact[b];
+    if (res_out) res_out[b] = rn;
+    all = all && rn < o.tol;
+  }
+  if (!all) return fail(TDDFT_ENOTCONV, "the Z-vector CG did not reach the tolerance within max_iter");
+  return TDDFT_OK;
+}
+
+extern "C" {
+
+tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
+  if (h->ace_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact exchange; disable ACE first");
+  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+  if (!X || !U) return fail(TDDFT_EINVAL, "null buffer");
+  if (X == U) return fail(TDDFT_EINVAL, "X and U must not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return zvector_rhs_impl<double>(h, nb, (const cplx<double>*)X, (cplx<double>*)U, st);
+  return zvector_rhs_impl<float>(h, nb, (const cplx<float>*)X, (cplx<float>*)U, st);
+}
+
+tddft_status tddft_zvector_solve(tddft_handle h, int nb, const void* U, void* Z, const tddft_zvector_opts* opts,
+                                 int* iterations, int* exact_iterations, double* residual, void* stream) {
+  if (!h || !opts) return fail(TDDFT_EINVAL, "null argument");
+  if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
+  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+  if (!U || !Z) return fail(TDDFT_EINVAL, "null buffer");
+  if (U == Z) return fail(TDDFT_EINVAL, "U and Z must not alias");
+  if (!(opts->tol > 0.0) || !(opts->lambda_thr >= 0.0) || opts->max_iter < 0 || opts->precondition < 0 ||
+      opts->precondition > 1)
+    return fail(TDDFT_EINVAL, "need tol > 0, lambda_thr >= 0, max_iter >= 0, precondition 0 or 1");
+  if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "the Z-vector solve needs the projector term");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return zvector_impl<double>(h, nb, (const cplx<double>*)U, (cplx<double>*)Z, *opts, iterations, exact_iterations,
+                                residual, st);
+  return zvector_impl<float>(h, nb, (const cplx<float>*)U, (cplx<float>*)Z, *opts, iterations, exact_iterations,
+                             residual, st);
 }
 
 }  // extern "C"
@@ -1725,6 +1951,8 @@ tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const
   if (max_basis < 2 * nroots || max_basis < nguess) return fail(TDDFT_EINVAL, "max_basis must be >= 2*nroots and >= nguess");
   if (h->d.nb_max < nroots) return fail(TDDFT_EINVAL, "the handle's nb_max must be >= nroots");
   if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "Davidson needs the projector term");
+  if (h->d.term_mask & ~TDDFT_TERMS_ALL)
+    return fail(TDDFT_EINVAL, "Davidson diagonalises the Tamm-Dancoff operator: no K2 terms");
   cudaStream_t st = (cudaStream_t)stream;
   tddft_davidson* d = new tddft_davidson();
   d->h = h;

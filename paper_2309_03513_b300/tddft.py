@@ -23,6 +23,10 @@ TERM_K1E_XC = 16
 TERM_K1D = 32
 TERM_PROJ = 64
 TERMS_ALL = 127
+TERM_K2E_H = 128
+TERM_K2E_XC = 256
+TERM_K2D = 512
+TERMS_ZVEC = 1023
 
 SPIN_CONSERVING = 0
 SPIN_FLIP = 1
@@ -35,7 +39,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUM
 EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
     "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi",
-    "tddft_ace_build", "tddft_ace_enable", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_ace_build", "tddft_ace_enable", "tddft_zvector_solve", "tddft_zvector_rhs", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -65,6 +69,11 @@ class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int)]
+
+
+class ZvectorOpts(ctypes.Structure):
+    _fields_ = [("lambda_thr", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("precondition", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -97,6 +106,8 @@ def load() -> ctypes.CDLL:
         "tddft_apply_liouville_multi": ([ci, vp, vp, vp, vp, vp], st),
         "tddft_ace_build": ([vp, ci, vp, vp], st),
         "tddft_ace_enable": ([vp, ci], st),
+        "tddft_zvector_solve": ([vp, ci, vp, vp, vp, vp, vp, vp, vp], st),
+        "tddft_zvector_rhs": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -324,6 +335,33 @@ class LiouvilleSystem:
                                                     gphi.data_ptr(), None if gv is None else gv.data_ptr(),
                                                     _stream_ptr(stream)), "tddft_apply_liouville_adjoint")
         return omega, gphi, gv
+
+    def zvector_rhs(self, X, stream=None):
+        """U_s = -P^c u_s for each state of X (tddft_zvector_rhs); same shape and dtype as X."""
+        torch = self._check_batch(X)
+        U = torch.empty_like(X)
+        _check(load().tddft_zvector_rhs(self._h, X.shape[0], X.data_ptr(), U.data_ptr(), _stream_ptr(stream)),
+               "tddft_zvector_rhs")
+        return U
+
+    def zvector_solve(self, U, lambda_thr=0.0, tol=1e-8, max_iter=200, precondition=False, stream=None,
+                      require_convergence=True):
+        """Z with (D + K1e - K1d + K2e - K2d) Z_s = U_s by CG (tddft_zvector_solve).
+
+        Returns (Z, iterations [nb], exact_iterations [nb], residual norms [nb]). With
+        require_convergence=False a TDDFT_ENOTCONV result is returned instead of raised."""
+        torch = self._check_batch(U)
+        nb = U.shape[0]
+        Z = torch.empty_like(U)
+        it = np.zeros(nb, dtype=np.int32)
+        ex = np.zeros(nb, dtype=np.int32)
+        res = np.zeros(nb, dtype=np.float64)
+        o = ZvectorOpts(float(lambda_thr), float(tol), int(max_iter), 1 if precondition else 0)
+        st = load().tddft_zvector_solve(self._h, nb, U.data_ptr(), Z.data_ptr(), ctypes.byref(o), it.ctypes.data,
+                                        ex.ctypes.data, res.ctypes.data, _stream_ptr(stream))
+        if not (st == 6 and not require_convergence):
+            _check(st, "tddft_zvector_solve")
+        return Z, it, ex, res
 
     def close(self):
         if getattr(self, "_h", None):
