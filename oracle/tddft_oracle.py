@@ -19,6 +19,10 @@ What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
   Sec. S1), with X, eps, f_xc and the Coulomb kernels held fixed;
 * a dense matrix of L on tiny systems and a plain block-Davidson solver
   (Sec. 4 names Davidson's method for diagonalising L);
+* the truncation of K1d over localised orbitals (Sec. 3.2, Eq. 31): with
+  phi_v = sum_n U_vn phi~_n, K1d is evaluated as
+  alpha sum_m U_vm sum_n a~_n tau~_mn with tau~_mn = 0 wherever the overlap
+  function S_mn of the localised orbitals is below S_thr;
 * the K2e and K2d terms (Eqs. 5 and 7) of the full operator of the Z-vector
   equation (Eq. 19) and its conjugate-gradient solution with the inexact
   Krylov switch of Sec. 3.3 (exact operator while the residual norm is at
@@ -165,6 +169,16 @@ class Grid:
 # The system and the operator
 # --------------------------------------------------------------------------
 
+def pair_overlap(phi_r: np.ndarray) -> np.ndarray:
+    """Overlap function of Sec. 3.2 between orbitals given in real space [n, N, N, N]:
+    S_mn = int |phi_m|^2 |phi_n|^2 / sqrt(int |phi_m|^4 int |phi_n|^4) (grid sums;
+    the integration weight cancels)."""
+    d = (np.abs(phi_r) ** 2).reshape(phi_r.shape[0], -1)
+    num = d @ d.T
+    nrm = np.sqrt(np.diag(num))
+    return num / np.outer(nrm, nrm)
+
+
 class System:
     """Inputs of one spin-conserving (SC) or spin-flip (SF, source up -> target down) system.
 
@@ -199,6 +213,11 @@ class System:
         self._phi_tgt_r = None
         self.use_ace = False   # D_EXX through V_X^ACE (after ace_build) instead of the exact V_X
         self.ace_xi = None
+        self.loc_U = None      # K1d through Eq. 31 with truncated pairs (after set_localization)
+        self.loc_keep = None
+        self.loc_S = None
+        self._loc_phi_r = None
+        self._loc_tau = {}
 
     @property
     def nocc_src(self):
@@ -266,6 +285,34 @@ class System:
         xi = self.ace_xi
         return -np.einsum("kg,...k->...g", xi, np.einsum("kg,...g->...k", xi.conj(), psi))
 
+    # -- pair truncation over localised orbitals (Sec. 3.2) --
+    def set_localization(self, U: np.ndarray | None, s_thr: float = 0.0) -> np.ndarray | None:
+        """Evaluate K1d by Eq. 31 with phi_v = sum_n U_vn phi~_n (U unitary,
+        [nocc_src, nocc_src]) and tau~_mn = 0 where S_mn < s_thr; U = None goes back
+        to Eq. 6. Returns the overlap function S [nocc_src, nocc_src]."""
+        if U is None:
+            self.loc_U = self.loc_keep = self.loc_S = self._loc_phi_r = None
+            self._loc_tau = {}
+            return None
+        U = np.asarray(U, dtype=np.complex128)
+        if np.abs(U.conj().T @ U - np.eye(U.shape[0])).max() > 1e-10:
+            raise ValueError("U must be unitary")
+        phi_loc = np.einsum("vn,vg->ng", U.conj(), self.phi_src)  # phi~_n = sum_v U_vn^* phi_v
+        self._loc_phi_r = self.grid.pw_to_real(phi_loc)
+        self.loc_S = pair_overlap(self._loc_phi_r)
+        self.loc_keep = self.loc_S >= s_thr
+        self.loc_U = U
+        self._loc_tau = {}
+        return self.loc_S
+
+    def _tau_loc(self, m: int, n: int) -> np.ndarray:
+        """tau~_mn = Conv_x[phi~_n^* phi~_m] (cached)."""
+        key = (m, n)
+        if key not in self._loc_tau:
+            pr = self._loc_phi_r
+            self._loc_tau[key] = self.grid.conv(pr[n].conj() * pr[m], self.kx)
+        return self._loc_tau[key]
+
     # -- pieces of the operator --
     def delta_rho(self, a_r: np.ndarray) -> np.ndarray:
         """Delta rho(r) = sum_v phi_v^*(r) a_v(r) (Eq. 2 diagonal; Sec. 2.3 for SF)."""
@@ -289,7 +336,7 @@ class System:
             W += self.fxc * drho.conj()
         return W
 
-    def unprojected_row(self, a_r, Xb, W, v, terms, tau_row=None) -> np.ndarray:
+    def unprojected_row(self, a_r, Xb, W, v, terms, tau_row=None, a_loc_r=None) -> np.ndarray:
         """The bracket of row v before P^c, in plane waves:
         (1/2|G|^2 - eps_v) a_v + [V_loc a_v + alpha V_X a_v + phi_v W
         - alpha sum_v' a_v' Conv_x[phi_v'^* phi_v]] -> PW.
@@ -305,7 +352,19 @@ class System:
                 out_r -= self.alpha * phit[w] * g.conv(phit[w].conj() * a_r[v], self.kx)
         if terms & (K1E_H | K1E_XC | K2E_H | K2E_XC):
             out_r += self.phi_src_r()[v] * W
-        if terms & K1D:
+        if (terms & K1D) and self.loc_U is not None:
+            # Eq. 31: alpha sum_m U_vm sum_n a~_n tau~_mn, truncated pairs left out
+            acc = np.zeros_like(out_r)
+            for m in range(self.nocc_src):
+                if self.loc_U[v, m] == 0:
+                    continue
+                inner = np.zeros_like(out_r)
+                for n in range(self.nocc_src):
+                    if self.loc_keep[m, n]:
+                        inner += a_loc_r[n] * self._tau_loc(m, n)
+                acc += self.loc_U[v, m] * inner
+            out_r -= self.alpha * acc
+        elif terms & K1D:
             phis = self.phi_src_r()
             for vp in range(self.nocc_src):
                 tau = g.conv(phis[vp].conj() * phis[v], self.kx)  # tau_{v v'} (Sec. 3.2)
@@ -341,8 +400,11 @@ class System:
             a_r = self.grid.pw_to_real(X[b])
             W = (self.k1e_potential(self.delta_rho(a_r), terms)
                  if terms & (K1E_H | K1E_XC | K2E_H | K2E_XC) else None)
+            a_loc_r = None
+            if (terms & K1D) and self.loc_U is not None:
+                a_loc_r = np.einsum("vn,vzyx->nzyx", self.loc_U.conj(), a_r)  # a~_n = sum_v' U_v'n^* a_v'
             for i, v in items:
-                row = self.unprojected_row(a_r, X[b], W, v, terms)
+                row = self.unprojected_row(a_r, X[b], W, v, terms, a_loc_r=a_loc_r)
                 out[i] = self.project(row) if terms & PROJ else row
         if rows is None:
             return out.reshape(nb, self.nocc_src, self.grid.npw)

@@ -18,6 +18,13 @@ not available here):
 * Smooth real fields (local potential, xc kernels): the real part of a sum of
   plane waves exp(2 pi i m.j/N) with |m|^2 <= 4 and complex normal weights,
   scaled to a stated maximum modulus.
+* Localised orbitals (stand-ins for maximally localised Wannier functions,
+  for the pair truncation of Sec. 3.2): Gaussians exp(-|r-R_n|^2/(2 sigma^2))
+  written on the sphere as exp(-sigma^2 |G|^2/2 - i G.R_n), centred on a
+  jittered simple-cubic lattice, made orthonormal by Loewdin's symmetric
+  orthonormalisation (S^{-1/2}, which keeps them localised); the "canonical"
+  orbitals are phi_v = sum_n U_vn phi~_n with a random unitary U (QR of a
+  complex normal matrix), so they are delocalised like Kohn-Sham orbitals.
 
 Array conventions shared by both sides:
 * plane-wave coefficient arrays are [..., npw] complex128 in the order of the
@@ -51,6 +58,8 @@ class Workload:
     vloc: np.ndarray | None  # [N, N, N] real, target spin
     fxc: np.ndarray | None  # [N, N, N] real (f_xc, or f_xc^SF for spin-flip)
     X: np.ndarray  # [nb, nocc_src, npw]
+    loc_U: np.ndarray | None = None  # [nocc_src, nocc_src] unitary: phi_src = loc_U @ phi_loc
+    phi_loc: np.ndarray | None = None  # [nocc_src, npw] localised orbitals
 
     @property
     def npw(self) -> int:
@@ -111,6 +120,25 @@ def complement_rows(rng: np.random.Generator, phi_tgt: np.ndarray, k: int) -> np
     return np.ascontiguousarray(q[:, nocc_tgt:].T)
 
 
+def localized_orbitals(rng: np.random.Generator, miller: np.ndarray, a: float, nocc: int, sigma: float,
+                       jitter: float = 0.1) -> np.ndarray:
+    """nocc orthonormal localised orbitals [nocc, npw] on the sphere given by its Miller
+    indices [npw, 3] (sphere order of the side under test): Gaussians of width sigma
+    centred on a jittered simple-cubic lattice (random subset of ceil(nocc^(1/3))^3
+    sites, each coordinate moved by up to jitter * spacing), Loewdin-orthonormalised."""
+    m = int(np.ceil(nocc ** (1.0 / 3.0) - 1e-9))
+    spacing = a / m
+    sites = np.array([(i, j, k) for i in range(m) for j in range(m) for k in range(m)], dtype=np.float64)
+    pick = rng.choice(len(sites), size=nocc, replace=False)
+    R = (sites[pick] + rng.uniform(-jitter, jitter, size=(nocc, 3))) * spacing
+    G = (2.0 * np.pi / a) * np.asarray(miller, dtype=np.float64)  # [npw, 3]
+    C = np.exp(-0.5 * sigma * sigma * np.sum(G * G, axis=1))[None, :] * np.exp(-1j * (R @ G.T))
+    S = C.conj() @ C.T  # overlap <c_m|c_n> = sum_G c_m^* c_n
+    w, V = np.linalg.eigh(S)
+    S_inv_half = (V * (1.0 / np.sqrt(w))) @ V.conj().T
+    return np.ascontiguousarray(S_inv_half.T @ C)
+
+
 def make_workload(
     *,
     n: int,
@@ -126,6 +154,8 @@ def make_workload(
     rc: float = 5.0,
     with_vloc: bool = True,
     with_fxc: bool = True,
+    localized_sigma: float | None = None,
+    miller: np.ndarray | None = None,
 ) -> Workload:
     """Draw one synthetic system.
 
@@ -133,7 +163,9 @@ def make_workload(
     obtains it from the side it is testing and both sides must agree.
     Seeds: orbitals and eigenvalues from `seed`, V_loc from seed + 1000,
     f_xc from seed + 2000 (f_xc^SF from seed + 3000), trial vectors from
-    seed + 4000.
+    seed + 4000. With localized_sigma (and the sphere's Miller indices) the
+    source-spin orbitals are U phi~ with localised phi~ (seed + 5000) and a
+    random unitary U (seed + 6000); loc_U and phi_loc are returned with them.
     """
     rng = np.random.default_rng(seed)
     if spin_flip:
@@ -145,6 +177,16 @@ def make_workload(
         nocc_tgt = nocc_src
         phi_src = random_orthonormal_rows(rng, nocc_src, npw)
         phi_tgt = phi_src
+    loc_U = phi_loc = None
+    if localized_sigma is not None:
+        if miller is None:
+            raise ValueError("localised orbitals need the sphere's Miller indices")
+        phi_loc = localized_orbitals(np.random.default_rng(seed + 5000), miller, a, nocc_src, localized_sigma)
+        r6 = np.random.default_rng(seed + 6000)
+        loc_U, _ = np.linalg.qr(r6.standard_normal((nocc_src, nocc_src)) + 1j * r6.standard_normal((nocc_src, nocc_src)))
+        phi_src = np.ascontiguousarray(loc_U @ phi_loc)
+        if not spin_flip:
+            phi_tgt = phi_src
     eps = np.sort(rng.uniform(-0.5, 0.0, size=nocc_src))
     vloc = smooth_field(np.random.default_rng(seed + 1000), n, 0.1) if with_vloc else None
     fxc = None
@@ -155,7 +197,7 @@ def make_workload(
     return Workload(
         n=n, a=a, ecut=ecut, alpha=alpha, spin_flip=spin_flip, nocc_src=nocc_src,
         nocc_tgt=nocc_tgt, nb=nb, seed=seed, kx_g0=2.0 * np.pi * rc * rc,
-        phi_src=phi_src, phi_tgt=phi_tgt, eps_src=eps, vloc=vloc, fxc=fxc, X=X,
+        phi_src=phi_src, phi_tgt=phi_tgt, eps_src=eps, vloc=vloc, fxc=fxc, X=X, loc_U=loc_U, phi_loc=phi_loc,
     )
 
 

@@ -542,3 +542,71 @@ def test_inexact_krylov_error_shrinks_with_the_threshold():
     assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
     assert all(n2 >= n1 for n1, n2 in zip(nexs, nexs[1:])), nexs
     assert errs[-1] < 1e-4 and errs[0] > 1e-6, errs
+
+
+# --------------------------------------------------------------------------
+# pair truncation over localised orbitals (Sec. 3.2, Eq. 31)
+# --------------------------------------------------------------------------
+
+def test_pair_overlap_of_gaussians_closed_form():
+    """For Gaussians exp(-|r-R|^2/(2 s^2)), S_mn = exp(-d^2/(2 s^2)) (d = |R_m - R_n|);
+    grid sums of well-resolved Gaussians in a large cell reproduce it."""
+    n, a, s = 48, 12.0, 1.1
+    j = np.arange(n) * a / n
+    z, y, x = np.meshgrid(j, j, j, indexing="ij")
+    cen = [(6.0, 6.0, 6.0), (7.3, 6.4, 5.1), (4.0, 8.5, 6.6)]
+    phi = np.stack([np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / (2 * s * s)) for c in cen])
+    S = O.pair_overlap(phi.astype(np.complex128))
+    for m in range(3):
+        for k in range(3):
+            d2 = sum((cen[m][i] - cen[k][i]) ** 2 for i in range(3))
+            assert abs(S[m, k] - math.exp(-d2 / (2 * s * s))) < 1e-9
+
+
+def _localized(n=24, a=10.0, ecut=10.0, nocc=8, nb=2, seed=3, sigma=1.2):
+    g = O.Grid(n, a, ecut)
+    wl = synth.make_workload(n=n, a=a, ecut=ecut, npw=g.npw, nocc_src=nocc, nb=nb, seed=seed,
+                             localized_sigma=sigma, miller=g.miller)
+    return wl, O.system_from_workload(wl)
+
+
+def test_truncation_at_zero_threshold_is_the_exact_k1d():
+    """Eq. 31 with every pair kept equals Eq. 6 (K1d alone and the whole operator)."""
+    wl, S = _localized()
+    exact_k1d = S.apply(wl.X, O.K1D)
+    exact_all = S.apply(wl.X)
+    Sm = S.set_localization(wl.loc_U, 0.0)
+    assert np.allclose(np.diag(Sm), 1.0) and np.allclose(Sm, Sm.T) and Sm.min() >= 0
+    assert np.allclose(S.apply(wl.X, O.K1D), exact_k1d, atol=1e-12 * np.abs(exact_k1d).max())
+    assert np.allclose(S.apply(wl.X), exact_all, atol=1e-12 * np.abs(exact_all).max())
+    # phi~ = U^dagger phi recovers the localised orbitals the canonical ones were built from
+    g = O.Grid(wl.n, wl.a, wl.ecut)
+    assert np.allclose(Sm, O.pair_overlap(g.pw_to_real(wl.phi_loc)), rtol=0, atol=1e-12)
+
+
+def test_truncation_of_every_pair_removes_k1d():
+    wl, S = _localized(nb=1)
+    S.set_localization(wl.loc_U, 2.0)  # S_mn <= 1 < 2 for every pair
+    assert not S.loc_keep.any()
+    assert np.abs(S.apply(wl.X, O.K1D | O.PROJ)).max() == 0.0
+
+
+def test_truncation_keeps_hermiticity_and_error_shrinks_with_threshold():
+    """L with truncated K1d stays Hermitian (the kept set is symmetric), the number of
+    kept pairs grows and the K1d error shrinks as S_thr is lowered (Sec. 3.2)."""
+    wl, S = _localized(nb=2, seed=4)
+    exact = S.apply(wl.X, O.K1D | O.PROJ)
+    errs, kept = [], []
+    for thr in (1e-1, 1e-3, 1e-4, 1e-6):
+        S.set_localization(wl.loc_U, thr)
+        kept.append(int(S.loc_keep.sum()))
+        got = S.apply(wl.X, O.K1D | O.PROJ)
+        errs.append(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+        if thr == 1e-3:
+            L = S.apply(wl.X)
+            lhs = np.vdot(wl.X[0], L[1])
+            rhs = np.conj(np.vdot(wl.X[1], L[0]))
+            assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    assert kept == sorted(kept) and kept[0] < kept[-1], kept
+    assert all(e2 <= e1 * (1 + 1e-9) for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[0] > 1e-6 and errs[-1] < errs[0] * 0.05, errs
