@@ -285,6 +285,8 @@ def run_native(args):
         extras["ace"] = bench_ace(torch, T, dev, stream, wl, X, LA)
     if "zvector" in args.extra:
         extras["zvector"] = bench_zvector(torch, T, dev, stream, wl, X)
+    if "pairtrunc" in args.extra:
+        extras["pairtrunc"] = bench_pairtrunc(torch, T, dev, stream)
 
     # plain FP64 GPU path on the same batch
     fp64 = None
@@ -463,6 +465,52 @@ def bench_zvector(torch, T, dev, stream, wl, X, max_iter=40):
             "note": "preconditioned CG; per state the exact operator while ||r|| >= lambda_thr"}
 
 
+def bench_pairtrunc(torch, T, dev, stream, s_thr=1e-3):
+    """K1d with pair truncation over localised orbitals (Sec. 3.2): the diamond64
+    grid and batch with 128 localised orbitals (Gaussians of width 1 bohr,
+    Loewdin-orthonormalised, rotated by a random unitary), FP32. K1d time per
+    batch exact (given frame) and truncated at S_thr = 1e-3, computed over the
+    pair list of kept pairs and over 16 x 16 blocks with the dropped pairs
+    masked, the whole operator, and the deviation of the truncated L from the
+    exact one on this batch."""
+    from paper_2309_03513_b300 import synth
+    w = WORKLOAD
+    n, a, ecut = w["n"], w["a"], w["ecut"]
+    wl = synth.make_workload(n=n, a=a, ecut=ecut, npw=T.sphere_size(n, a, ecut), nocc_src=w["nocc"], nb=w["nb"],
+                             seed=11, localized_sigma=1.0, miller=T.sphere_miller(n, a, ecut))
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    X = torch.from_numpy(wl.X).to(dev, torch.complex64)
+    LA = torch.empty_like(X)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(mask):
+        s.set_terms(mask)
+        s.apply(X, out=LA, stream=stream)
+        e0.record(stream)
+        s.apply(X, out=LA, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    out = {"s_thr": s_thr, "nocc": w["nocc"], "sigma_bohr": 1.0}
+    out["k1d_ms_exact"] = timed(T.TERM_K1D)
+    out["L_ms_exact"] = timed(T.TERMS_ALL)
+    exact = LA.clone()
+    S, kept = s.set_localization(wl.loc_U, s_thr, stream=stream)
+    out["kept_pairs"] = kept
+    out["kept_fraction"] = kept / float(w["nocc"] ** 2)
+    s.set_tuning(k1d_sparse=0, k1d_block=16)
+    out["k1d_ms_truncated_blocks16"] = timed(T.TERM_K1D)
+    s.set_tuning(k1d_sparse=1)
+    out["k1d_ms_truncated_pair_list"] = timed(T.TERM_K1D)
+    out["k1d_speedup_pair_list"] = out["k1d_ms_exact"] / out["k1d_ms_truncated_pair_list"]
+    out["L_ms_truncated"] = timed(T.TERMS_ALL)
+    out["rel_deviation_from_exact_L"] = float(torch.linalg.vector_norm(LA - exact) / torch.linalg.vector_norm(exact))
+    s.close()
+    return out
+
+
 def bench_sf216(torch, T, dev, stream, steps=1):
     """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path."""
     from paper_2309_03513_b300 import synth
@@ -497,7 +545,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")
     ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
-                                             "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch)")
+                                             "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch), "
+                                             "pairtrunc (K1d pair truncation, localised orbitals)")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()

@@ -160,6 +160,11 @@ typedef struct tddft_tuning {
                        split-precision TF32 products (hi*hi + hi*lo + lo*hi, FP32
                        accumulation in tensor memory); 0 SIMT FP32. FP64 handles
                        always use SIMT FP64. -1 keeps the value in set_tuning */
+  int k1d_sparse;   /* K1d in the localised frame with truncated pairs
+                       (tddft_set_localization): 1 only the kept pairs, from a pair
+                       list; 0 blocks of k1d_block x k1d_block pairs, blocks without a
+                       kept pair skipped; 2 automatic (pair list when fewer than half
+                       of the pairs are kept). -1 keeps the value in set_tuning */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);
@@ -227,6 +232,27 @@ tddft_status tddft_zvector_solve(tddft_handle h, int nb, const void* U, void* Z,
  * ground-state density, which are inputs here). U: device, same layout,
  * written. Spin-conserving handles with ACE off (else TDDFT_ENOTSUP). */
 tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, void* stream);
+
+/* Localised frame and pair truncation of K1d (Sec. 3.2, Eq. 31).
+ * U: HOST complex128 [nocc_src][nocc_src], unitary (max |U^H U - I| <= 1e-10,
+ * else TDDFT_EINVAL), relating the handle's given source orbitals to localised
+ * ones: phi_v = sum_n U_vn phi~_n (e.g. the rotation to maximally localised
+ * Wannier functions, computed elsewhere). The handle then computes in the
+ * localised frame: every term of L except the eigenvalue part of D is
+ * covariant under the rotation, so L A = U [L~ (U^dagger A) - eps~ U^dagger A]
+ * with eps~ = U^dagger diag(eps) U, and in L~ the K1d integrals
+ * tau~_mn = Conv_x[phi~_n^* phi~_m] of pairs whose overlap function
+ * S_mn = int |phi~_m|^2 |phi~_n|^2 / sqrt(int |phi~_m|^4 int |phi~_n|^4)
+ * is below s_thr are taken as zero (whole blocks of such pairs are not
+ * computed). s_thr = 0 keeps every pair (the exact operator, in the other frame).
+ * Trial vectors and results stay in the given (canonical) frame.
+ * S: optional HOST [nocc_src][nocc_src] output of S_mn (evaluated in FP64 from
+ * the handle's real-space orbitals); kept_pairs: optional HOST count of ordered
+ * pairs (m, n) kept. U = NULL goes back to the given orbitals. The adjoint and
+ * tddft_zvector_rhs return TDDFT_ENOTSUP while the frame is on. Synchronises
+ * the stream. */
+tddft_status tddft_set_localization(tddft_handle h, const double* U, double s_thr, double* S, int* kept_pairs,
+                                    void* stream);
 
 /* Adaptively compressed exchange (ACE, Sec. 3.1, Eqs. 29-30) for the exchange
  * term inside D: V_X^ACE = -sum_k |xi_k><xi_k| with xi = W L^{-dagger},

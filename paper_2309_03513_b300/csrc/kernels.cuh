@@ -18,6 +18,8 @@ struct PairMap {
   int r0, rk, rt;
   int p0, pk, pt;
   int o0, ot;
+  // optional explicit (q, r) field indices per item for the forward pass (pair lists)
+  const int2* list = nullptr;
 };
 
 template <typename T>
@@ -44,9 +46,16 @@ __global__ void __launch_bounds__(plane_threads<N>())
   const int tid = threadIdx.x, z = blockIdx.x, item = blockIdx.y;
   const int t = item / pm.kdim, k = item - t * pm.kdim;
   for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
-  const cplx<T>* R = plane_ptr(rb, pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt, z, N3, N2);
+  long long qi = pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt;
+  long long ri = pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt;
+  if (pm.list) {
+    const int2 pr = pm.list[item];
+    qi = pr.x;
+    ri = pr.y;
+  }
+  const cplx<T>* R = plane_ptr(rb, ri, z, N3, N2);
   if constexpr (MODE == XY_PRODUCT) {
-    const cplx<T>* Q = plane_ptr(qb, pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt, z, N3, N2);
+    const cplx<T>* Q = plane_ptr(qb, qi, z, N3, N2);
 #pragma unroll 4
     for (int e = tid; e < N2; e += NT) {
       const int y = e / N, x = e - y * N;
@@ -333,7 +342,7 @@ __global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long f = i / npw, g = i - f * npw;
     cplx<T> v = cscale(cube[f * n3 + pos[g]], s);
-    if (A) v = cadd(v, cscale(A[i], g2h[g] - eps[(f0 + f) % nocc]));
+    if (A) v = cadd(v, cscale(A[i], eps ? g2h[g] - eps[(f0 + f) % nocc] : g2h[g]));
     out[i] = v;
   }
 }
@@ -343,6 +352,8 @@ __global__ void k_gather(const cplx<T>* __restrict__ cube, const int* __restrict
 //   out[b, i0+vi] += s * sum_vj a[b, j0+vj] tau[vi][vj]
 //   and, when I != J, out[b, j0+vj] += s * sum_vi a[b, i0+vi] conj(tau[vi][vj])
 //   (tau_{v'v} = conj(tau_{vv'}) because the kernel is real and even).
+// keep (optional, [nocc][nocc], symmetric): pairs with keep = 0 are truncated
+// (their tau is taken as zero on both sides).
 // A CTA of 256 threads takes PTS consecutive grid points: the tau values of
 // those points are staged once in shared memory with coalesced loads, then
 // thread (q, l) computes orbital q of each side for the points l + 16 j, for
@@ -351,7 +362,7 @@ constexpr int K1D_THREADS = 256;
 template <typename T, int TB, int PTS>
 __global__ void __launch_bounds__(K1D_THREADS)
     k_k1d_contract(const cplx<T>* __restrict__ tau, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out, int i0,
-                   int ti, int j0, int tj, int nocc, int nb, T s, long long n3) {
+                   int ti, int j0, int tj, int nocc, int nb, T s, long long n3, const unsigned char* __restrict__ keep) {
   static_assert(K1D_THREADS == TB * 16 && PTS % 16 == 0, "thread layout");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* st = reinterpret_cast<cplx<T>*>(smem_raw);  // [TB*TB][PTS]
@@ -361,7 +372,8 @@ __global__ void __launch_bounds__(K1D_THREADS)
   for (int e = threadIdx.x; e < TB * TB * PTS; e += K1D_THREADS) {
     const int slot = e / PTS, p = e - slot * PTS;
     const int vi = slot / TB, vj = slot - vi * TB;
-    st[e] = (vi < ti && vj < tj && p < npts) ? tau[(long long)(vi * tj + vj) * n3 + r0 + p] : cplx<T>{T(0), T(0)};
+    const bool kept = vi < ti && vj < tj && p < npts && (!keep || keep[(long long)(i0 + vi) * nocc + j0 + vj]);
+    st[e] = kept ? tau[(long long)(vi * tj + vj) * n3 + r0 + p] : cplx<T>{T(0), T(0)};
   }
   __syncthreads();
   const int q = threadIdx.x / 16, l = threadIdx.x - q * 16;
@@ -394,6 +406,62 @@ __global__ void __launch_bounds__(K1D_THREADS)
           acc = cadd(acc, cmul(av[j][k], tv));
         }
         if (p < npts) ob[p] = cadd(ov[j], cscale(acc, s));
+      }
+    }
+  }
+}
+
+// K1d contraction over a list of kept pairs (pair truncation, Sec. 3.2).
+// tau[slot] (slot < np) holds Conv_x[conj(phi_n) phi_m] of the batch's pairs.
+// Output rows: row i adds to orbital row_out[i], over its entries
+// e in [row_ptr[i], row_ptr[i+1]): ent[e] = (n << 1 | c, slot):
+//   out[b, row_out[i]] += s * sum_e a[b, n] * (c ? conj(tau[slot]) : tau[slot]).
+// Rows are distinct orbitals, so each (b, orbital, point) is written by one
+// thread. A CTA takes PTS points: the tau values of all np slots at those points
+// are staged in shared memory once and reused for every b.
+template <typename T, int PTS>
+__global__ void __launch_bounds__(K1D_THREADS)
+    k_k1d_sparse(const cplx<T>* __restrict__ tau, int np, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out,
+                 const int* __restrict__ row_ptr, const int* __restrict__ row_out, int nrows,
+                 const int2* __restrict__ ent, int nocc, int nb, T s, long long n3) {
+  static_assert(PTS % 16 == 0, "thread layout");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* st = reinterpret_cast<cplx<T>*>(smem_raw);  // [np][PTS]
+  const long long r0 = (long long)blockIdx.x * PTS;
+  const int npts = (int)min((long long)PTS, n3 - r0);
+  for (int e = threadIdx.x; e < np * PTS; e += K1D_THREADS) {
+    const int slot = e / PTS, p = e - slot * PTS;
+    st[e] = p < npts ? tau[(long long)slot * n3 + r0 + p] : cplx<T>{T(0), T(0)};
+  }
+  __syncthreads();
+  const int q = threadIdx.x / 16, l = threadIdx.x - q * 16;
+  constexpr int PPT = PTS / 16;
+  for (int i = q; i < nrows; i += K1D_THREADS / 16) {
+    const int e0 = row_ptr[i], e1 = row_ptr[i + 1], dst = row_out[i];
+    for (int b = 0; b < nb; ++b) {
+      const cplx<T>* ab = a + (long long)b * nocc * n3 + r0;
+      cplx<T>* ob = out + ((long long)b * nocc + dst) * n3 + r0;
+      cplx<T> acc[PPT];
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) acc[j] = {T(0), T(0)};
+#pragma unroll 4
+      for (int e = e0; e < e1; ++e) {
+        const int2 en = ent[e];
+        const int n = en.x >> 1;
+        const bool cj = en.x & 1;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const int p = l + 16 * j;
+          if (p < npts) {
+            const cplx<T> tv = st[en.y * PTS + p];
+            acc[j] = cadd(acc[j], cmul(ab[(long long)n * n3 + p], cj ? cconj(tv) : tv));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const int p = l + 16 * j;
+        if (p < npts) ob[p] = cadd(ob[p], cscale(acc[j], s));
       }
     }
   }

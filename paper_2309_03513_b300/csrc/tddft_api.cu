@@ -269,6 +269,7 @@ struct Buffers {
   void* phi_src_pw = nullptr;  // [nocc_src][npw]
   void* phi_tgt_pw = nullptr;  // [nocc_tgt][npw] (aliases phi_src_pw for SC)
   cplx<double>* phi_tgt_pw64 = nullptr;  // FP64 copy for Davidson
+  cplx<double>* phi_src_pw64 = nullptr;  // FP64 copy of the given (canonical) source orbitals
   void* phi_src_r = nullptr;   // [nocc_src][n^3]
   void* phi_tgt_r = nullptr;   // [nocc_tgt][n^3] (aliases for SC)
   void* vloc = nullptr;        // [n^3] real or null
@@ -305,6 +306,30 @@ struct tddft_system {
   void* ace_xi = nullptr;    // [n_ace][npw] working precision
   void* ace_c = nullptr;     // [n_ace][nb_max * nocc_src]
   void* ace_part = nullptr;  // split-K partials [2 * nsplit][n_ace][nb_max * nocc_src]
+  // localised frame (tddft_set_localization): the handle's source orbitals are
+  // phi~ = U^dagger phi, trial vectors are rotated in and results rotated out
+  bool loc_on = false;
+  int loc_kept = 0;
+  void* loc_Uc = nullptr;    // [nocc][nocc]: C[v][n] = conj(U_vn)   (A~ = U^dagger A)
+  void* loc_Ut = nullptr;    // [nocc][nocc]: C[n][v] = U_vn         (L A = U L~ A~)
+  void* loc_E = nullptr;     // [nocc][nocc]: C[n'][n] = eps~_nn' = sum_v conj(U_vn) eps_v U_vn'
+  void* loc_a = nullptr;     // [nb_max][nocc][npw] A~
+  void* loc_b = nullptr;     // [nb_max][nocc][npw] L~ A~
+  unsigned char* loc_keep = nullptr;        // device [nocc][nocc]
+  std::vector<unsigned char> loc_keep_host;
+  // kept unique pairs as batches of a pair list (k1d_sparse path)
+  struct PairBatch {
+    int pair0, np;   // slots [pair0, pair0 + np) of loc_list
+    int rp0, nrows;  // row pointers loc_rowptr[rp0 .. rp0 + nrows], outputs loc_rowout[rp0 .. rp0 + nrows)
+  };
+  std::vector<PairBatch> loc_batches;
+  int2* loc_list = nullptr;    // (q = n, r = m) per kept unique pair (m <= n)
+  int* loc_rowptr = nullptr;
+  int* loc_rowout = nullptr;
+  int2* loc_ent = nullptr;     // (n << 1 | conj, slot)
+  bool loc_sparse_auto = false;
+  int k1d_sparse = 2;          // 0 blocks, 1 pair list, 2 automatic
+  std::vector<double> eps64;  // the given eigenvalues
   int ncols_act = 0;     // number of such columns (0 = no list: the grid aliases pair densities)
   int nsplit = 1;
   size_t bytes = 0;
@@ -397,7 +422,7 @@ static tddft_status real_to_pw(tddft_system* h, const cplx<T>* src, int nf, cplx
     o.z(Z_FWD, ib, cnt, nullptr, T(1), tw, st);
     { k_gather<T><<<grid_for((long long)cnt * h->npw, 256), 256, 0, st>>>(
         ib, h->b.pos, h->npw, cnt, s, A ? A + (long long)f0 * h->npw : nullptr, (const T*)h->b.g2h,
-        (const T*)h->b.eps, h->d.nocc_src, f0, dst + (long long)f0 * h->npw, h->n3); note_launch(); }
+        h->loc_on ? nullptr : (const T*)h->b.eps, h->d.nocc_src, f0, dst + (long long)f0 * h->npw, h->n3); note_launch(); }
   }
   return check_launch("real_to_pw");
 }
@@ -555,6 +580,11 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
 
 // K1d: out[b][v] -= alpha sum_v' a[b][v'] Conv_x[conj(phi_v') phi_v], tau computed once per
 // unordered block pair (I <= J) and shared by every b of the chunk.
+// pair-list K1d: points per CTA and the largest batch whose tau values fit in shared memory
+constexpr int K1D_SPARSE_PTS = 32;
+template <typename T>
+constexpr int k1d_sparse_np_max() { return sizeof(T) == 4 ? 384 : 192; }
+
 template <typename T>
 static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   PlaneOps<T>& o = ops_of<T>(h);
@@ -565,10 +595,36 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   int TB = std::min(h->k1d_block, nocc);
   while (TB * TB > h->ibuf_fields) --TB;
   const T s = (T)(-h->d.alpha);
+  if (h->loc_on && (h->k1d_sparse == 1 || (h->k1d_sparse == 2 && h->loc_sparse_auto))) {
+    // only the kept pairs: tau of each batch of the pair list, then the row-wise contraction
+    for (const auto& pb : h->loc_batches) {
+      PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+      pm.list = h->loc_list + pb.pair0;
+      o.xy_fwd(XY_PRODUCT, phi, phi, pm, pb.np, ib, tw, st);
+      o.z(Z_CONV, ib, pb.np, (const T*)h->b.kx, T(1), tw, st, pair_columns(h));
+      PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+      o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, pb.np, T(1), tw, st);
+      const size_t smem = (size_t)pb.np * K1D_SPARSE_PTS * sizeof(cplx<T>);
+      const unsigned blocks = (unsigned)((h->n3 + K1D_SPARSE_PTS - 1) / K1D_SPARSE_PTS);
+      { k_k1d_sparse<T, K1D_SPARSE_PTS><<<blocks, K1D_THREADS, smem, st>>>(
+          ib, pb.np, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, h->loc_rowptr + pb.rp0, h->loc_rowout + pb.rp0,
+          pb.nrows, h->loc_ent, nocc, nbc, s, h->n3); note_launch(); }
+    }
+    return check_launch("k1d_term (pair list)");
+  }
+  // truncated pairs of the localised frame: blocks without a kept pair are skipped
+  const unsigned char* keep = h->loc_on ? h->loc_keep : nullptr;
+  auto block_kept = [&](int i0, int ti, int j0, int tj) {
+    for (int i = i0; i < i0 + ti; ++i)
+      for (int j = j0; j < j0 + tj; ++j)
+        if (h->loc_keep_host[(size_t)i * nocc + j]) return true;
+    return false;
+  };
   for (int i0 = 0; i0 < nocc; i0 += TB) {
     const int ti = std::min(TB, nocc - i0);
     for (int j0 = i0; j0 < nocc; j0 += TB) {
       const int tj = std::min(TB, nocc - j0);
+      if (keep && !block_kept(i0, ti, j0, tj)) continue;
       // item = vi * tj + vj : Q = phi[j0 + vj], R = phi[i0 + vi]
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
       o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
@@ -580,16 +636,18 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
         const size_t smem = (size_t)KB * KB * PTS * sizeof(cplx<T>);
         const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
         { k_k1d_contract<T, KB, PTS><<<blocks, K1D_THREADS, smem, st>>>(
-            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3); note_launch(); }
+            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3, keep); note_launch(); }
       }
     }
   }
   return check_launch("k1d_term");
 }
 
-// (L A) for nb trial vectors; terms of `mask` (PROJ bit included or not).
+// (L A) for nb trial vectors in the handle's orbital frame; terms of `mask`
+// (PROJ bit included or not). In the localised frame the eigenvalue part of D
+// is left out here (it is a matrix there, added by apply_impl).
 template <typename T>
-static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T>* LA, unsigned mask, cudaStream_t st) {
+static tddft_status apply_core(tddft_system* h, int nb, const cplx<T>* A, cplx<T>* LA, unsigned mask, cudaStream_t st) {
   const int nocc = h->d.nocc_src, npw = h->npw;
   const long long n3 = h->n3;
   const cplx<T>* phis = (const cplx<T>*)h->b.phi_src_r;
@@ -644,6 +702,33 @@ static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T
   return TDDFT_OK;
 }
 
+// (L A) for nb trial vectors (terms of `mask`). In the localised frame
+// (Sec. 3.2, Eq. 31) every term except the eigenvalue part of D is covariant
+// under the rotation phi_v = sum_n U_vn phi~_n, so L A = U [L~ A~ - eps~ A~]
+// with A~ = U^dagger A, L~ the operator on phi~ with K1d's truncated pairs
+// left out and eps~ = U^dagger diag(eps) U; P^c is the same in both frames.
+template <typename T>
+static tddft_status apply_impl(tddft_system* h, int nb, const cplx<T>* A, cplx<T>* LA, unsigned mask, cudaStream_t st) {
+  if (!h->loc_on) return apply_core<T>(h, nb, A, LA, mask, st);
+  const int nocc = h->d.nocc_src;
+  const long long len = (long long)nocc * h->npw;
+  cplx<T>* At = (cplx<T>*)h->loc_a;
+  cplx<T>* Lt = (cplx<T>*)h->loc_b;
+  CUDA_TRY(cudaMemsetAsync(At, 0, (size_t)nb * len * sizeof(cplx<T>), st));
+  for (int b = 0; b < nb; ++b)
+    STATUS_TRY(gemm_update<T>(h, A + b * len, nocc, (const cplx<T>*)h->loc_Uc, At + b * len, nocc, T(1), st));
+  STATUS_TRY(apply_core<T>(h, nb, At, Lt, mask & ~TDDFT_TERM_PROJ, st));
+  if (mask & TDDFT_TERM_D_KIN)
+    for (int b = 0; b < nb; ++b)
+      STATUS_TRY(gemm_update<T>(h, At + b * len, nocc, (const cplx<T>*)h->loc_E, Lt + b * len, nocc, T(-1), st));
+  if (mask & TDDFT_TERM_PROJ)
+    STATUS_TRY(project_rows<T>(h, (const cplx<T>*)h->b.phi_tgt_pw, h->d.nocc_tgt, Lt, nb * nocc, st));
+  CUDA_TRY(cudaMemsetAsync(LA, 0, (size_t)nb * len * sizeof(cplx<T>), st));
+  for (int b = 0; b < nb; ++b)
+    STATUS_TRY(gemm_update<T>(h, Lt + b * len, nocc, (const cplx<T>*)h->loc_Ut, LA + b * len, nocc, T(1), st));
+  return TDDFT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
@@ -665,6 +750,8 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   CUDA_TRY(o.prepare());
   CUDA_TRY(cudaFuncSetAttribute(k_k1d_contract<T, 16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(16 * 16 * 32 * sizeof(cplx<T>))));
+  CUDA_TRY(cudaFuncSetAttribute(k_k1d_sparse<T, K1D_SPARSE_PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(k1d_sparse_np_max<T>() * K1D_SPARSE_PTS * sizeof(cplx<T>))));
   CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<OvA, OvB, OvEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
   CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<UpA, UpB, UpEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
   STATUS_TRY(dalloc(h, (void**)&h->b.dev_err, sizeof(int)));
@@ -742,6 +829,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   CUDA_TRY(cudaMemcpyAsync(B.pos, pos.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.g2h, g2h.data(), npw * rz, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.eps, eps.data(), d.nocc_src * rz, cudaMemcpyHostToDevice, st));
+  h->eps64.assign(in->eps_src, in->eps_src + d.nocc_src);
 
   // orbitals: FP64 upload, orthonormality check, cast to the working precision
   const int nsets = h->sf() ? 2 : 1;
@@ -749,6 +837,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   STATUS_TRY(dalloc(h, (void**)&B.phi_tgt_pw64, (size_t)ntgt * npw * sizeof(cplx<double>)));
   cplx<double>* phi_src64 = nullptr;
   STATUS_TRY(dalloc(h, (void**)&phi_src64, (size_t)d.nocc_src * npw * sizeof(cplx<double>)));
+  B.phi_src_pw64 = phi_src64;
   CUDA_TRY(cudaMemcpyAsync(phi_src64, in->phi_src, (size_t)d.nocc_src * npw * 16, cudaMemcpyHostToDevice, st));
   if (h->sf())
     CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, in->phi_tgt, (size_t)ntgt * npw * 16, cudaMemcpyHostToDevice, st));
@@ -997,6 +1086,218 @@ static tddft_status ace_build_impl(tddft_system* h, int n_extra, const double* e
   CUDA_TRY(cudaStreamSynchronize(st));
   h->n_ace = na;
   h->ace_on = true;
+  return TDDFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// localised frame and pair truncation (Sec. 3.2, Eq. 31)
+// ---------------------------------------------------------------------------
+
+namespace {
+void drop_graphs(tddft_system* h);  // forgets captured graphs that contain h's launches
+}  // namespace
+
+// part[z][m][n] = sum over the z-th slice of points of d_m(r) d_n(r), d = |phi(r)|^2,
+// FP64 accumulation of the products. 16 x 16 (m, n) tile per CTA, points staged
+// in shared memory 64 at a time.
+constexpr int DG_TILE = 16, DG_PTS = 64;
+template <typename T>
+__global__ void __launch_bounds__(DG_TILE * DG_TILE)
+    k_density_gram(const cplx<T>* __restrict__ phi, int nocc, long long n3, long long per_slice,
+                   double* __restrict__ part) {
+  __shared__ double dm[DG_TILE][DG_PTS + 1], dn[DG_TILE][DG_PTS + 1];
+  const int m0 = blockIdx.y * DG_TILE, n0 = blockIdx.x * DG_TILE;
+  const int tm = threadIdx.x / DG_TILE, tn = threadIdx.x % DG_TILE;
+  const long long r_begin = (long long)blockIdx.z * per_slice;
+  const long long r_end = min(n3, r_begin + per_slice);
+  double acc = 0.0;
+  for (long long r0 = r_begin; r0 < r_end; r0 += DG_PTS) {
+    for (int e = threadIdx.x; e < DG_TILE * DG_PTS; e += DG_TILE * DG_TILE) {
+      const int o = e / DG_PTS, p = e % DG_PTS;
+      const long long r = r0 + p;
+      double vm = 0.0, vn = 0.0;
+      if (r < r_end) {
+        if (m0 + o < nocc) {
+          const cplx<T> c = phi[(long long)(m0 + o) * n3 + r];
+          vm = (double)c.x * c.x + (double)c.y * c.y;
+        }
+        if (n0 + o < nocc) {
+          const cplx<T> c = phi[(long long)(n0 + o) * n3 + r];
+          vn = (double)c.x * c.x + (double)c.y * c.y;
+        }
+      }
+      dm[o][p] = vm;
+      dn[o][p] = vn;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int p = 0; p < DG_PTS; ++p) acc += dm[tm][p] * dn[tn][p];
+    __syncthreads();
+  }
+  if (m0 + tm < nocc && n0 + tn < nocc) part[((long long)blockIdx.z * nocc + m0 + tm) * nocc + n0 + tn] = acc;
+}
+
+// phi_src (PW, handle precision) and its real-space copy from FP64 rows
+template <typename T>
+static tddft_status load_source_orbitals(tddft_system* h, const cplx<double>* phi64, cudaStream_t st) {
+  const long long cnt = (long long)h->d.nocc_src * h->npw;
+  { k_cast<T><<<grid_for(cnt, 256), 256, 0, st>>>(phi64, (cplx<T>*)h->b.phi_src_pw, cnt); note_launch(); }
+  STATUS_TRY(check_launch("orbital cast"));
+  return pw_to_real<T>(h, (const cplx<T>*)h->b.phi_src_pw, h->d.nocc_src, (cplx<T>*)h->b.phi_src_r, st);
+}
+
+// Kept unique pairs (m <= n, by m then n) in batches of at most
+// min(ibuf_fields, k1d_sparse_np_max) slots, each with its rows: orbital m gets
+// (n, slot) and, for m != n, orbital n gets (m, slot) with tau conjugated.
+template <typename T>
+static tddft_status build_pair_batches(tddft_system* h, cudaStream_t st) {
+  const int nocc = h->d.nocc_src;
+  const int npmax = std::max(1, std::min(h->ibuf_fields, k1d_sparse_np_max<T>()));
+  std::vector<int2> list;
+  for (int m = 0; m < nocc; ++m)
+    for (int n = m; n < nocc; ++n)
+      if (h->loc_keep_host[(size_t)m * nocc + n]) list.push_back(make_int2(n, m));
+  const size_t unique_total = (size_t)nocc * (nocc + 1) / 2;
+  h->loc_sparse_auto = 2 * list.size() < unique_total;
+  std::vector<int> rowptr, rowout;
+  std::vector<int2> ent;
+  h->loc_batches.clear();
+  for (size_t p0 = 0; p0 < list.size(); p0 += npmax) {
+    const int np = (int)std::min<size_t>(npmax, list.size() - p0);
+    std::vector<std::vector<int2>> rows(nocc);
+    for (int j = 0; j < np; ++j) {
+      const int n = list[p0 + j].x, m = list[p0 + j].y;
+      rows[m].push_back(make_int2(n << 1, j));
+      if (m != n) rows[n].push_back(make_int2((m << 1) | 1, j));
+    }
+    tddft_system::PairBatch pb{(int)p0, np, (int)rowptr.size(), 0};
+    for (int o = 0; o < nocc; ++o) {
+      if (rows[o].empty()) continue;
+      rowptr.push_back((int)ent.size());
+      rowout.push_back(o);
+      ent.insert(ent.end(), rows[o].begin(), rows[o].end());
+      ++pb.nrows;
+    }
+    rowptr.push_back((int)ent.size());
+    rowout.push_back(-1);  // keeps rowout aligned with rowptr; never read
+    h->loc_batches.push_back(pb);
+  }
+  for (void** q : {(void**)&h->loc_list, (void**)&h->loc_rowptr, (void**)&h->loc_rowout, (void**)&h->loc_ent}) {
+    if (*q) {
+      cudaFree(*q);
+      h->allocations.erase(std::remove(h->allocations.begin(), h->allocations.end(), *q), h->allocations.end());
+      *q = nullptr;
+    }
+  }
+  if (list.empty()) return TDDFT_OK;
+  STATUS_TRY(dalloc(h, (void**)&h->loc_list, list.size() * sizeof(int2)));
+  STATUS_TRY(dalloc(h, (void**)&h->loc_rowptr, rowptr.size() * sizeof(int)));
+  STATUS_TRY(dalloc(h, (void**)&h->loc_rowout, rowout.size() * sizeof(int)));
+  STATUS_TRY(dalloc(h, (void**)&h->loc_ent, ent.size() * sizeof(int2)));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_list, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_rowout, rowout.data(), rowout.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_ent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  return TDDFT_OK;
+}
+
+template <typename T>
+static tddft_status localization_impl(tddft_system* h, const double* Uh, double s_thr, double* S_out, int* kept,
+                                      cudaStream_t st) {
+  using C = std::complex<double>;
+  const int nocc = h->d.nocc_src, npw = h->npw;
+  const C* U = reinterpret_cast<const C*>(Uh);
+  drop_graphs(h);
+  if (!U) {  // back to the given orbitals
+    h->loc_on = false;
+    STATUS_TRY(load_source_orbitals<T>(h, h->b.phi_src_pw64, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (kept) *kept = nocc * nocc;
+    return TDDFT_OK;
+  }
+  double dev = 0.0;
+  for (int i = 0; i < nocc; ++i)
+    for (int j = 0; j < nocc; ++j) {
+      C g = 0.0;
+      for (int v = 0; v < nocc; ++v) g += std::conj(U[(size_t)v * nocc + i]) * U[(size_t)v * nocc + j];
+      dev = std::max(dev, std::abs(g - (i == j ? 1.0 : 0.0)));
+    }
+  if (!(dev <= 1e-10)) return fail(TDDFT_EINVAL, "U is not unitary: max |U^H U - I| = " + std::to_string(dev));
+  if (!h->loc_a) {
+    const size_t rows = (size_t)h->d.nb_max * nocc * npw * sizeof(cplx<T>);
+    STATUS_TRY(dalloc(h, &h->loc_a, rows));
+    STATUS_TRY(dalloc(h, &h->loc_b, rows));
+    STATUS_TRY(dalloc(h, &h->loc_Uc, (size_t)nocc * nocc * sizeof(cplx<T>)));
+    STATUS_TRY(dalloc(h, &h->loc_Ut, (size_t)nocc * nocc * sizeof(cplx<T>)));
+    STATUS_TRY(dalloc(h, &h->loc_E, (size_t)nocc * nocc * sizeof(cplx<T>)));
+    STATUS_TRY(dalloc(h, (void**)&h->loc_keep, (size_t)nocc * nocc));
+  }
+  h->loc_on = false;
+  // phi~_n = sum_v conj(U_vn) phi_v in FP64, then the handle's orbitals
+  TempAllocs tmp;
+  cplx<double>* phil = nullptr;
+  cplx<double>* c64 = nullptr;
+  STATUS_TRY(tmp.get((void**)&phil, (size_t)nocc * npw * sizeof(cplx<double>)));
+  STATUS_TRY(tmp.get((void**)&c64, (size_t)nocc * nocc * sizeof(cplx<double>)));
+  std::vector<cplx<double>> cu((size_t)nocc * nocc);
+  std::vector<cplx<T>> cuT(cu.size()), ctT(cu.size()), ceT(cu.size());
+  const std::vector<double>& eps = h->eps64;
+  for (int v = 0; v < nocc; ++v)
+    for (int n = 0; n < nocc; ++n) {
+      const C u = U[(size_t)v * nocc + n];
+      cu[(size_t)v * nocc + n] = {std::conj(u).real(), std::conj(u).imag()};
+      cuT[(size_t)v * nocc + n] = {(T)u.real(), (T)(-u.imag())};
+      ctT[(size_t)n * nocc + v] = {(T)u.real(), (T)u.imag()};
+    }
+  for (int n = 0; n < nocc; ++n)
+    for (int np = 0; np < nocc; ++np) {
+      C e = 0.0;
+      for (int v = 0; v < nocc; ++v) e += std::conj(U[(size_t)v * nocc + n]) * eps[v] * U[(size_t)v * nocc + np];
+      ceT[(size_t)np * nocc + n] = {(T)e.real(), (T)e.imag()};
+    }
+  CUDA_TRY(cudaMemcpyAsync(c64, cu.data(), cu.size() * sizeof(cplx<double>), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(phil, 0, (size_t)nocc * npw * sizeof(cplx<double>), st));
+  { dim3 g2((npw + 63) / 64, (nocc + 31) / 32);
+    k_update<double><<<g2, 256, 0, st>>>(h->b.phi_src_pw64, nocc, c64, nocc, npw, 1.0, phil); note_launch(); }
+  STATUS_TRY(check_launch("localised orbitals"));
+  STATUS_TRY(load_source_orbitals<T>(h, phil, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_Uc, cuT.data(), cuT.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_Ut, ctT.data(), ctT.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(h->loc_E, ceT.data(), ceT.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+  // overlap function S_mn of the localised orbitals (densities of the handle's real-space orbitals)
+  const long long n3 = h->n3;
+  const int slices = (int)std::max(1LL, std::min(64LL, n3 / 4096));
+  const long long per = (n3 + slices - 1) / slices;
+  double* part = nullptr;
+  STATUS_TRY(tmp.get((void**)&part, (size_t)slices * nocc * nocc * sizeof(double)));
+  { dim3 g((nocc + DG_TILE - 1) / DG_TILE, (nocc + DG_TILE - 1) / DG_TILE, slices);
+    k_density_gram<T><<<g, DG_TILE * DG_TILE, 0, st>>>((const cplx<T>*)h->b.phi_src_r, nocc, n3, per, part); note_launch(); }
+  STATUS_TRY(check_launch("density gram"));
+  std::vector<double> ph((size_t)slices * nocc * nocc);
+  CUDA_TRY(cudaMemcpyAsync(ph.data(), part, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> Q((size_t)nocc * nocc, 0.0);
+  for (int z = 0; z < slices; ++z)
+    for (size_t i = 0; i < Q.size(); ++i) Q[i] += ph[(size_t)z * Q.size() + i];
+  h->loc_keep_host.assign((size_t)nocc * nocc, 0);
+  int cnt = 0;
+  for (int m = 0; m < nocc; ++m)
+    for (int n = 0; n < nocc; ++n) {
+      // symmetric by construction: (Q_mn + Q_nm) / 2 against the diagonal
+      const double q = 0.5 * (Q[(size_t)m * nocc + n] + Q[(size_t)n * nocc + m]);
+      const double S = q / std::sqrt(Q[(size_t)m * nocc + m] * Q[(size_t)n * nocc + n]);
+      if (S_out) S_out[(size_t)m * nocc + n] = S;
+      const unsigned char k = S >= s_thr ? 1 : 0;
+      h->loc_keep_host[(size_t)m * nocc + n] = k;
+      cnt += k;
+    }
+  CUDA_TRY(cudaMemcpyAsync(h->loc_keep, h->loc_keep_host.data(), h->loc_keep_host.size(), cudaMemcpyHostToDevice, st));
+  STATUS_TRY(build_pair_batches<T>(h, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  h->loc_kept = cnt;
+  if (kept) *kept = cnt;
+  h->loc_on = true;
   return TDDFT_OK;
 }
 
@@ -1362,6 +1663,10 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     if (t->projector > 1) return fail(TDDFT_EINVAL, "projector must be 0 or 1");
     h->projector_tc = t->projector;
   }
+  if (t->k1d_sparse >= 0) {
+    if (t->k1d_sparse > 2) return fail(TDDFT_EINVAL, "k1d_sparse must be 0, 1 or 2");
+    h->k1d_sparse = t->k1d_sparse;
+  }
   if (t->z_kernel >= 0) {
     if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
     const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
@@ -1385,6 +1690,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->prune = h->prune ? 1 : 0;
   t->z_kernel = kc.z;
   t->projector = h->projector_tc;
+  t->k1d_sparse = h->k1d_sparse;
   return TDDFT_OK;
 }
 
@@ -1451,6 +1757,15 @@ tddft_status tddft_ace_build(tddft_handle h, int n_extra, const double* extra, v
   drop_graphs(h);  // a captured graph would keep the old exchange path
   if (h->d.precision == TDDFT_PREC_FP64) return ace_build_impl<double>(h, n_extra, extra, st);
   return ace_build_impl<float>(h, n_extra, extra, st);
+}
+
+tddft_status tddft_set_localization(tddft_handle h, const double* U, double s_thr, double* S, int* kept_pairs,
+                                    void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (U && !(s_thr >= 0.0)) return fail(TDDFT_EINVAL, "s_thr must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64) return localization_impl<double>(h, U, s_thr, S, kept_pairs, st);
+  return localization_impl<float>(h, U, s_thr, S, kept_pairs, st);
 }
 
 tddft_status tddft_ace_enable(tddft_handle h, int enable) {
@@ -1521,6 +1836,7 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
   if (!h) return fail(TDDFT_EINVAL, "null handle");
   if (h->sf()) return fail(TDDFT_ENOTSUP, "the adjoint is implemented for spin-conserving systems");
   if (h->ace_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact exchange; disable ACE first");
+  if (h->loc_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact K1d; disable the localised frame first");
   if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
   if (!X || !w || !omega || !grad_phi) return fail(TDDFT_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1712,6 +2028,7 @@ tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, v
   if (!h) return fail(TDDFT_EINVAL, "null handle");
   if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
   if (h->ace_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact exchange; disable ACE first");
+  if (h->loc_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact K1d; disable the localised frame first");
   if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
   if (!X || !U) return fail(TDDFT_EINVAL, "null buffer");
   if (X == U) return fail(TDDFT_EINVAL, "X and U must not alias");

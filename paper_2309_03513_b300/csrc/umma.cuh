@@ -75,8 +75,8 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
 template <class LA, class LB, class EP>
 __global__ void __launch_bounds__(128)
     k_umma_gemm(LA la, LB lb, EP ep, int kchunks, int chunks_per_split, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* a_hi = smem_raw;
+  extern __shared__ __align__(1024) unsigned char umma_smem[];
+  unsigned char* a_hi = umma_smem;
   unsigned char* a_lo = a_hi + UMMA_TILE_BYTES;
   unsigned char* b_hi = a_lo + UMMA_TILE_BYTES;
   unsigned char* b_lo = b_hi + UMMA_TILE_BYTES;

@@ -39,7 +39,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUM
 EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
     "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi",
-    "tddft_ace_build", "tddft_ace_enable", "tddft_zvector_solve", "tddft_zvector_rhs", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_ace_build", "tddft_ace_enable", "tddft_zvector_solve", "tddft_zvector_rhs",
+    "tddft_set_localization", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -68,7 +69,8 @@ class Inputs(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
-                ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int)]
+                ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int),
+                ("k1d_sparse", ctypes.c_int)]
 
 
 class ZvectorOpts(ctypes.Structure):
@@ -108,6 +110,7 @@ def load() -> ctypes.CDLL:
         "tddft_ace_enable": ([vp, ci], st),
         "tddft_zvector_solve": ([vp, ci, vp, vp, vp, vp, vp, vp, vp], st),
         "tddft_zvector_rhs": ([vp, ci, vp, vp, vp], st),
+        "tddft_set_localization": ([vp, vp, ctypes.c_double, vp, vp, vp], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -256,9 +259,9 @@ class LiouvilleSystem:
         _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
-                   graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1):
+                   graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1):
         t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
-                   int(z_kernel), int(projector))
+                   int(z_kernel), int(projector), int(k1d_sparse))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 
     def check(self):
@@ -335,6 +338,21 @@ class LiouvilleSystem:
                                                     gphi.data_ptr(), None if gv is None else gv.data_ptr(),
                                                     _stream_ptr(stream)), "tddft_apply_liouville_adjoint")
         return omega, gphi, gv
+
+    def set_localization(self, U=None, s_thr=0.0, stream=None):
+        """Compute in the frame of localised orbitals phi~ (phi = U phi~) with K1d pairs of
+        overlap S_mn < s_thr truncated (tddft_set_localization); U=None switches it off.
+        Returns (S [nocc, nocc] float64 or None, kept pair count)."""
+        kept = ctypes.c_int()
+        if U is None:
+            _check(load().tddft_set_localization(self._h, None, 0.0, None, ctypes.byref(kept), _stream_ptr(stream)),
+                   "tddft_set_localization")
+            return None, kept.value
+        Uc = np.ascontiguousarray(U, dtype=np.complex128)
+        S = np.zeros((self.nocc_src, self.nocc_src), dtype=np.float64)
+        _check(load().tddft_set_localization(self._h, Uc.ctypes.data, float(s_thr), S.ctypes.data, ctypes.byref(kept),
+                                             _stream_ptr(stream)), "tddft_set_localization")
+        return S, kept.value
 
     def zvector_rhs(self, X, stream=None):
         """U_s = -P^c u_s for each state of X (tddft_zvector_rhs); same shape and dtype as X."""

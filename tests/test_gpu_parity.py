@@ -135,7 +135,7 @@ def test_tuning_fields_round_trip(torch):
     s = T.system_from_workload(wl, precision=T.PREC_FP32)
     for kw in (dict(targets=4), dict(sources=2), dict(k1d_block=8), dict(accumulate=0), dict(accumulate=1),
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
-               dict(projector=0), dict(projector=1)):
+               dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2)):
         before = s.get_tuning()
         s.set_tuning(**kw)
         after = s.get_tuning()
