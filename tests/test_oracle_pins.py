@@ -97,8 +97,11 @@ def test_convolution_against_brute_force_gaussian_images():
     r = j * (a / n)
     K = 3
     Rs = np.array(list(itertools.product(range(-K, K + 1), repeat=3)), dtype=float) * a
-    d = r[:, None, None, :] - r[None, :, None, :] + Rs[None, None, :, :]
-    kern = np.exp(-mu * np.sum(d * d, axis=-1)).sum(axis=2)  # [j, j']
+    diff = r[:, None, :] - r[None, :, :]
+    kern = np.zeros((n ** 3, n ** 3))  # [j, j'], summed image by image
+    for R in Rs:
+        d = diff + R
+        kern += np.exp(-mu * np.sum(d * d, axis=-1))
     want = (a ** 3 / n ** 3) * kern @ rho.reshape(-1)  # rho flattened (jz,jy,jx) = rows of j reversed
     assert np.allclose(got.reshape(-1), want, rtol=0, atol=1e-11 * np.abs(want).max())
 
