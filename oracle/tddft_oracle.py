@@ -14,9 +14,12 @@ What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
 * the spin-flip operator of Eq. 21 (D^SF, K1e^SF with the local f_xc^SF and no
   Hartree part, K1d^SF over source-spin pairs; Sec. 2.3);
 * the bilinear form omega = <X|L X> (the excitation energy of Sec. 2.2) and
-  its gradient with respect to the occupied orbitals and the local potential
-  (the u_v ingredient of the Z-vector equation, Eq. 19, defined in Eq. 20 and the Supporting Information
-  Sec. S1), with X, eps, f_xc and the Coulomb kernels held fixed;
+  its gradient with respect to the occupied orbitals (both spins for
+  spin-flip) and the local potential (the u_v ingredient of the Z-vector
+  equation, Eq. 19, defined in Eq. 20 and the Supporting Information Sec. S1),
+  with X, eps, f_xc and the Coulomb kernels held fixed;
+* the density responses Delta rho^(x) and Delta rho^(Z) of the force
+  expression (Sec. 2.2; Delta rho^(x) of Sec. 2.3 for spin-flip);
 * a dense matrix of L on tiny systems and a plain block-Davidson solver
   (Sec. 4 names Davidson's method for diagonalising L);
 * the truncation of K1d over localised orbitals (Sec. 3.2, Eq. 31): with
@@ -423,24 +426,26 @@ class System:
         return np.einsum("bvg,bvg->b", P.conj(), Y).real
 
     def omega_grad(self, X: np.ndarray, w: np.ndarray):
-        """omega_b and the gradients of sum_b w_b omega_b (spin-conserving only).
+        """omega_b and the gradients of sum_b w_b omega_b.
 
-        Returns (omega [nb], grad_phi [nocc, npw], grad_vloc [N,N,N]).
-        grad_phi is the Wirtinger derivative d/d c_u^*(G) with X, eps,
-        V_loc, f_xc and the kernels fixed and P^c taken on the given orbitals.
+        Returns (omega [nb], grad_phi, grad_vloc [N,N,N]). grad_phi is the
+        Wirtinger derivative d/d c_u^*(G) with X, eps, V_loc, f_xc and the
+        kernels fixed and P^c taken on the given orbitals: [nocc, npw] for the
+        spin-conserving operator; for spin-flip [nocc_src + nocc_tgt, npw], the
+        source-spin orbitals first, then the target-spin ones.
         In real space (grid integrals, weight Omega/N_r) it is, per b:
-          -alpha sum_v p_v Conv_x[p_v^* phi_u]        (from alpha V_X in D)
-          + p_u conj(W)                                (from K1e, W as in Eq. 4)
-          -alpha sum_v phi_v Conv_x[p_v^* p_u]         (from K1d)
-        mapped to plane waves, plus the plane-wave terms of the projector
+          -alpha sum_v p_v Conv_x[p_v^* phi_u]        (alpha V_X in D; target orbital u)
+          + p_u conj(W)                                (K1e, W as in Eq. 4; source orbital u)
+          -alpha sum_v phi_v Conv_x[p_v^* p_u]         (K1d; source orbitals)
+        mapped to plane waves, plus the plane-wave terms of the projector (target u)
           -sum_v [<x_v|phi_u> y_v + <y_v|phi_u> x_v],  y = M p, p = P^c x.
         These are the counterparts of terms 2, 4, 7 and 5, 8 of u_v in the
-        Supporting Information (Sec. S1), without the terms that come from
-        H^KS, eps and V_xc depending on the ground-state density, which are
-        inputs here.  grad_vloc(r_j) = (Omega/N_r) sum_b w_b sum_v |p_{b,v}(r_j)|^2.
+        Supporting Information (Sec. S1; the spin-flip u_v there has the same
+        structure with W = f_xc^SF Delta rho^SF), without the terms that come
+        from H^KS, eps and V_xc depending on the ground-state density, which
+        are inputs here. grad_vloc(r_j) = (Omega/N_r) sum_b w_b sum_v |p_{b,v}(r_j)|^2
+        (V_loc of the target spin).
         """
-        if self.spin_flip:
-            raise NotImplementedError("the spin-flip gradient is not part of this oracle")
         g = self.grid
         X = np.asarray(X, dtype=np.complex128)
         w = np.asarray(w, dtype=np.float64)
@@ -448,32 +453,73 @@ class System:
         Pm = self.project(X)
         Y = self.apply(Pm, ALL_TERMS & ~PROJ)
         omega = np.einsum("bvg,bvg->b", Pm.conj(), Y).real
-        phi_r = self.phi_src_r()
-        nocc = self.nocc_src
-        grad_r = np.zeros((nocc,) + (g.n,) * 3, dtype=np.complex128)
+        phis_r = self.phi_src_r()
+        phit_r = self.phi_tgt_r()
+        ns, nt = self.nocc_src, self.nocc_tgt
+        gs_r = np.zeros((ns,) + (g.n,) * 3, dtype=np.complex128)
+        gt_r = gs_r if not self.spin_flip else np.zeros((nt,) + (g.n,) * 3, dtype=np.complex128)
         grad_v = np.zeros((g.n,) * 3)
         for b in range(nb):
             if w[b] == 0.0:
                 continue
             p_r = g.pw_to_real(Pm[b])
             W = self.k1e_potential(self.delta_rho(p_r), ALL_TERMS)
-            for u in range(nocc):
+            for u in range(nt):
                 acc = np.zeros((g.n,) * 3, dtype=np.complex128)
-                for v in range(nocc):
-                    acc -= self.alpha * p_r[v] * g.conv(p_r[v].conj() * phi_r[u], self.kx)
-                    acc -= self.alpha * phi_r[v] * g.conv(p_r[v].conj() * p_r[u], self.kx)
+                for v in range(ns):
+                    acc -= self.alpha * p_r[v] * g.conv(p_r[v].conj() * phit_r[u], self.kx)
+                gt_r[u] += w[b] * acc
+            for u in range(ns):
+                acc = np.zeros((g.n,) * 3, dtype=np.complex128)
+                for v in range(ns):
+                    acc -= self.alpha * phis_r[v] * g.conv(p_r[v].conj() * p_r[u], self.kx)
                 acc += p_r[u] * W.conj()
-                grad_r[u] += w[b] * acc
+                gs_r[u] += w[b] * acc
             grad_v += w[b] * (g.omega / g.nr) * np.sum(np.abs(p_r) ** 2, axis=0)
-        grad = g.real_to_pw(grad_r)
-        phi = self.phi_src
+        grad_s = g.real_to_pw(gs_r)
+        grad_t = grad_s if not self.spin_flip else g.real_to_pw(gt_r)
+        phi = self.phi_tgt
         for b in range(nb):
             if w[b] == 0.0:
                 continue
             xs = np.einsum("vg,ug->vu", X[b].conj(), phi)  # <x_v|phi_u>
             ys = np.einsum("vg,ug->vu", Y[b].conj(), phi)  # <y_v|phi_u>
-            grad -= w[b] * (np.einsum("vu,vg->ug", xs, Y[b]) + np.einsum("vu,vg->ug", ys, X[b]))
-        return omega, grad, grad_v
+            grad_t -= w[b] * (np.einsum("vu,vg->ug", xs, Y[b]) + np.einsum("vu,vg->ug", ys, X[b]))
+        if self.spin_flip:
+            return omega, np.concatenate([grad_s, grad_t]), grad_v
+        return omega, grad_s, grad_v
+
+    def relaxed_densities(self, X: np.ndarray, w: np.ndarray, Z: np.ndarray | None = None) -> np.ndarray:
+        """sum_b w_b of the density responses that enter the forces (Sec. 2.2, Sec. 2.3).
+
+        Delta rho^(x)(r) = sum_v |a_v(r)|^2 - sum_vv' phi_v^*(r) phi_v'(r) <a_v|a_v'>,
+        Delta rho^(Z)(r) = sum_v [Z_v^*(r) phi_v(r) + phi_v^*(r) Z_v(r)].
+        Spin-conserving: [1, N, N, N] (x part plus Z part when Z is given).
+        Spin-flip (source spin s -> target spin t, the trial orbitals a_v live
+        in the t channel): [2, N, N, N] with channel 0 = t: sum_v |a_v|^2 and
+        channel 1 = s: -sum_vv' phi_vs^* phi_v's <a_v|a_v'> (no Z part).
+        """
+        g = self.grid
+        X = np.asarray(X, dtype=np.complex128)
+        w = np.asarray(w, dtype=np.float64)
+        if self.spin_flip and Z is not None:
+            raise NotImplementedError("the Z-vector part is defined here for the spin-conserving operator")
+        phis_r = self.phi_src_r()
+        out = np.zeros((2 if self.spin_flip else 1,) + (g.n,) * 3)
+        for b in range(X.shape[0]):
+            a_r = g.pw_to_real(X[b])
+            Sab = np.einsum("vg,ug->vu", X[b].conj(), X[b])  # <a_v|a_v'>
+            first = np.sum(np.abs(a_r) ** 2, axis=0)
+            second = np.einsum("vzyx,uzyx,vu->zyx", phis_r.conj(), phis_r, Sab).real
+            if self.spin_flip:
+                out[0] += w[b] * first
+                out[1] -= w[b] * second
+            else:
+                out[0] += w[b] * (first - second)
+                if Z is not None:
+                    z_r = g.pw_to_real(np.asarray(Z[b], dtype=np.complex128))
+                    out[0] += w[b] * 2.0 * np.einsum("vzyx,vzyx->zyx", phis_r.conj(), z_r).real
+        return out
 
     # -- dense operator on tiny systems --
     def complement_basis(self) -> np.ndarray:

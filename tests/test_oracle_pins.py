@@ -613,3 +613,87 @@ def test_truncation_keeps_hermiticity_and_error_shrinks_with_threshold():
     assert kept == sorted(kept) and kept[0] < kept[-1], kept
     assert all(e2 <= e1 * (1 + 1e-9) for e1, e2 in zip(errs, errs[1:])), errs
     assert errs[0] > 1e-6 and errs[-1] < errs[0] * 0.05, errs
+
+
+# --------------------------------------------------------------------------
+# spin-flip gradient and the density responses of the force expression
+# --------------------------------------------------------------------------
+
+def test_spin_flip_gradient_against_finite_differences():
+    """Source-spin rows (K1e^SF, K1d^SF) and target-spin rows (V_X in D, P^c) of the
+    spin-flip gradient against central differences of omega (FP64, h = 1e-4)."""
+    wl, S = _tiny(spin_flip=True, n=12, a=7.0, ecut=3.0, nocc=3, nocc_tgt=2, nb=2, seed=10)
+    w = np.array([0.9, -0.6])
+    om, gphi, gv = S.omega_grad(wl.X, w)
+    assert gphi.shape == (5, S.grid.npw)
+    assert np.allclose(om, S.omega(wl.X), rtol=1e-13)
+
+    def total(src=None, tgt=None):
+        S2 = O.System(wl.n, wl.a, wl.ecut, wl.phi_src if src is None else src, wl.eps_src, alpha=wl.alpha,
+                      kx_g0=wl.kx_g0, spin_flip=True, phi_tgt=wl.phi_tgt if tgt is None else tgt, vloc=wl.vloc,
+                      fxc=wl.fxc)
+        return float(np.dot(w, S2.omega(wl.X)))
+
+    h = 1e-4
+    rng = np.random.default_rng(11)
+    for which, base, off in (("src", wl.phi_src, 0), ("tgt", wl.phi_tgt, 3)):
+        for _ in range(4):
+            u = int(rng.integers(base.shape[0]))
+            k = int(rng.integers(S.grid.npw))
+            d = []
+            for step in (1.0, 1j):
+                p1 = base.copy()
+                p1[u, k] += h * step
+                p2 = base.copy()
+                p2[u, k] -= h * step
+                d.append((total(**{which: p1}) - total(**{which: p2})) / (2 * h))
+            fd = d[0] + 1j * d[1]
+            assert abs(fd - 2 * gphi[off + u, k]) < 1e-7 * max(1.0, abs(fd)), (which, u, k, fd, 2 * gphi[off + u, k])
+
+
+def test_density_response_integrates_to_zero():
+    """int Delta rho^(x) = sum_v ||a_v||^2 - sum_vv' <phi_v|phi_v'> <a_v|a_v'> = 0 for
+    orthonormal orbitals (the excitation moves charge, it does not create it), per spin
+    channel pair for spin-flip; int Delta rho^(Z) = 2 Re sum_v <phi_v|Z_v> = 0 for Z in P^c."""
+    for sf in (False, True):
+        wl, S = _tiny(spin_flip=sf, nb=2)
+        d = S.relaxed_densities(wl.X, np.array([1.0, 0.5]))
+        tot = d.sum(axis=0).sum() * wl.a ** 3 / wl.n ** 3
+        assert abs(tot) < 1e-12
+        assert np.abs(d).max() > 1e-4
+        if sf:  # the target channel gains sum_b w_b ||a_b||^2 = 1.5, the source channel loses it
+            assert abs(d[0].sum() * wl.a ** 3 / wl.n ** 3 - 1.5) < 1e-12
+    wl, S = _tiny(nb=2)
+    Z = S.project(wl.X[::-1].copy())
+    dz = S.relaxed_densities(wl.X, np.array([1.0, 0.5]), Z) - S.relaxed_densities(wl.X, np.array([1.0, 0.5]))
+    assert abs(dz.sum()) * wl.a ** 3 / wl.n ** 3 < 1e-12 and np.abs(dz).max() > 1e-6
+
+
+def test_density_response_free_electron_closed_form():
+    """Orbitals = single plane waves G_v, a_v = sum_K x_vK e^{iK.r}/sqrt(Omega):
+    sum_v |a_v|^2 - sum_vv' e^{i(G_v'-G_v).r} <a_v|a_v'> / Omega, evaluated point by point."""
+    n, a, ecut = 8, 6.0, 3.2
+    g = O.Grid(n, a, ecut)
+    mill = [tuple(int(t) for t in v) for v in g.miller]
+    pos = {m: i for i, m in enumerate(mill)}
+    occ = [(0, 0, 0), (1, 0, 0), (0, -1, 1)]
+    phi = np.zeros((3, g.npw), dtype=np.complex128)
+    for v, m in enumerate(occ):
+        phi[v, pos[m]] = 1.0
+    S = O.System(n, a, ecut, phi, np.array([-0.4, -0.2, -0.1]), alpha=0.3, kx_g0=10.0)
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((1, 3, g.npw)) + 1j * rng.standard_normal((1, 3, g.npw))
+    for m in occ:
+        X[:, :, pos[m]] = 0.0
+    got = S.relaxed_densities(X, np.ones(1))[0]
+    omega = a ** 3
+    jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ph = {m: np.exp(2j * np.pi * (m[0] * jx + m[1] * jy + m[2] * jz) / n) for m in mill}
+    want = np.zeros((n,) * 3)
+    for v in range(3):
+        av = sum(X[0, v, pos[m]] * ph[m] for m in mill) / np.sqrt(omega)
+        want += np.abs(av) ** 2
+        for vp in range(3):
+            svv = np.vdot(X[0, v], X[0, vp])
+            want -= (np.conj(ph[occ[v]]) * ph[occ[vp]] * svv).real / omega
+    assert np.allclose(got, want, atol=1e-12 * np.abs(want).max())
