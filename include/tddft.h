@@ -197,6 +197,19 @@ tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_ho
 tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
                                          void* const* LA, void* stream);
 
+/* Density responses of the force expression (Secs. 2.2 and 2.3), summed
+ * over states with weights w (HOST [nb]):
+ *   Delta rho^(x)(r) = sum_v |a_v(r)|^2 - sum_vv' phi_v^*(r) phi_v'(r) <a_v|a_v'>
+ *   Delta rho^(Z)(r) = sum_v [Z_v^*(r) phi_v(r) + phi_v^*(r) Z_v(r)]
+ * X (and Z, optional): device [nb][nocc_src][npw], handle precision.
+ * drho: device double, written. Spin-conserving: [n^3] = Delta rho^(x) (+
+ * Delta rho^(Z) when Z is given). Spin-flip (no Z): [2][n^3], channel 0 the
+ * target spin (sum_v |a_v|^2), channel 1 the source spin
+ * (-sum_vv' phi_v^* phi_v' <a_v|a_v'>). TDDFT_ENOTSUP for Z on a spin-flip
+ * handle or while the localised frame is on. One host sync per state. */
+tddft_status tddft_relaxed_density(tddft_handle h, int nb, const void* X, const void* Z, const double* w, double* drho,
+                                   void* stream);
+
 /* Z-vector equation (Eq. 19): (D + K1e - K1d + K2e - K2d) Z_s = U_s, solved
  * for each state s by conjugate gradients (Sec. 3.3). Spin-conserving handles
  * with the projector term (else TDDFT_ENOTSUP / TDDFT_EINVAL).
@@ -273,16 +286,20 @@ tddft_status tddft_ace_enable(tddft_handle h, int enable);
 
 /* Bilinear form omega_b = <P^c X_b | M | P^c X_b> (M = L without the outer
  * P^c; equal to <X_b|L X_b> for X_b orthogonal to the orbitals) and the
- * gradient of E = sum_b w_b omega_b (spin-conserving handles only).
- * X: device [nb][nocc][npw] (handle precision). w: HOST [nb].
+ * gradient of E = sum_b w_b omega_b.
+ * X: device [nb][nocc_src][npw] (handle precision). w: HOST [nb].
  * omega: device double [nb].
- * grad_phi: device [nocc][npw] (handle precision), the Wirtinger derivative
- *   dE/dc_u^*(G) with X, eps, V_loc, f_xc and the kernels held fixed and P^c
- *   taken on the handle's orbitals (the part of u_v of the Supporting
- *   Information, Sec. S1, that does not come from the ground-state density).
- * grad_vloc: device double [n^3], dE/dV_loc(r_j); may be NULL.
+ * grad_phi: device, handle precision, the Wirtinger derivative dE/dc_u^*(G)
+ *   with X, eps, V_loc, f_xc and the kernels held fixed and P^c taken on the
+ *   handle's orbitals (the part of u_v of the Supporting Information, Sec. S1,
+ *   that does not come from the ground-state density). Spin-conserving:
+ *   [nocc][npw]. Spin-flip: [nocc_src + nocc_tgt][npw], the source-spin
+ *   orbitals first (terms of K1e^SF and K1d^SF), then the target-spin ones
+ *   (terms of V_X in D and of P^c).
+ * grad_vloc: device double [n^3], dE/dV_loc(r_j) (target spin); may be NULL.
  * Pair convolutions are recomputed, not stored. Written, not accumulated.
- * TDDFT_ENOTSUP while ACE is switched on (the gradient is of the exact exchange). */
+ * TDDFT_ENOTSUP while ACE or the localised frame is switched on (the
+ * gradient is of the exact operator). */
 tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
                                            void* grad_phi, double* grad_vloc, void* stream);
 

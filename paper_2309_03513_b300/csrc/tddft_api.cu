@@ -1307,24 +1307,30 @@ static tddft_status localization_impl(tddft_system* h, const double* Uh, double 
 template <typename T>
 static tddft_status adjoint_impl(tddft_system* h, int nb, const cplx<T>* X, const double* w, double* omega,
                                  cplx<T>* grad_phi, double* grad_vloc, cudaStream_t st) {
-  const int nocc = h->d.nocc_src, npw = h->npw;
+  const int nocc = h->d.nocc_src, ntgt = h->d.nocc_tgt, npw = h->npw;
+  const bool sf = h->sf();
   const long long n3 = h->n3, rows = (long long)nb * nocc;
   Buffers& B = h->b;
-  if (!B.grad_r) STATUS_TRY(dalloc(h, &B.grad_r, (size_t)nocc * n3 * sizeof(cplx<T>)));
+  const int gfields = nocc + (sf ? ntgt : 0);
+  if (!B.grad_r) STATUS_TRY(dalloc(h, &B.grad_r, (size_t)gfields * n3 * sizeof(cplx<T>)));
   cplx<T>* P = (cplx<T>*)B.io_a;   // P^c X
   cplx<T>* Y = (cplx<T>*)B.io_b;   // M P^c X
-  cplx<T>* G = (cplx<T>*)B.grad_r;
-  const cplx<T>* phi = (const cplx<T>*)B.phi_src_pw;
+  // source-spin rows (K1e, K1d) and target-spin rows (V_X in D, P^c); the same rows when spin-conserving
+  cplx<T>* Gs = (cplx<T>*)B.grad_r;
+  cplx<T>* Gt = sf ? Gs + (long long)nocc * n3 : Gs;
+  cplx<T>* grad_t = sf ? grad_phi + (long long)nocc * npw : grad_phi;
+  const cplx<T>* phi = (const cplx<T>*)B.phi_tgt_pw;  // projector orbitals
   const cplx<T>* phi_r = (const cplx<T>*)B.phi_src_r;
+  const cplx<T>* phit_r = (const cplx<T>*)B.phi_tgt_r;
   CUDA_TRY(cudaMemcpyAsync(P, X, (size_t)rows * npw * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st));
-  STATUS_TRY(project_rows<T>(h, phi, nocc, P, (int)rows, st));
+  STATUS_TRY(project_rows<T>(h, phi, ntgt, P, (int)rows, st));
   const unsigned mask = TDDFT_TERMS_ALL & ~TDDFT_TERM_PROJ;
   STATUS_TRY(apply_impl<T>(h, nb, P, Y, mask, st));
   { k_bilinear<T><<<nb, 256, 0, st>>>(P, Y, (long long)nocc * npw, omega); note_launch(); }
   STATUS_TRY(check_launch("bilinear"));
 
   // real-space part of the gradient, one trial vector at a time
-  CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)nocc * n3 * sizeof(cplx<T>), st));
+  CUDA_TRY(cudaMemsetAsync(Gs, 0, (size_t)gfields * n3 * sizeof(cplx<T>), st));
   if (grad_vloc) CUDA_TRY(cudaMemsetAsync(grad_vloc, 0, (size_t)n3 * sizeof(double), st));
   cplx<T>* p_r = (cplx<T>*)B.a_r;
   cplx<T>* drho = (cplx<T>*)B.drho;
@@ -1335,23 +1341,24 @@ static tddft_status adjoint_impl(tddft_system* h, int nb, const cplx<T>* X, cons
     STATUS_TRY(pw_to_real<T>(h, P + (long long)b * nocc * npw, nocc, p_r, st));
     const T wa = (T)(-h->d.alpha * w[b]);
     if (h->d.alpha != 0.0) {
-      // -alpha w sum_v p_v Conv_x[conj(p_v) phi_u]:  target u, source v
-      PairGrid ga{nocc, nocc, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
-      STATUS_TRY(pair_accumulate<T>(h, p_r, phi_r, p_r, G, ga, (const T*)B.kx, wa, st));
-      // -alpha w sum_v phi_v Conv_x[conj(p_v) p_u]
+      // -alpha w sum_v p_v Conv_x[conj(p_v) phi_u]:  target-spin orbital u, source v
+      PairGrid ga{ntgt, nocc, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
+      STATUS_TRY(pair_accumulate<T>(h, p_r, phit_r, p_r, Gt, ga, (const T*)B.kx, wa, st));
+      // -alpha w sum_v phi_v Conv_x[conj(p_v) p_u]:  source-spin orbital u
       PairGrid gb{nocc, nocc, 0, 1, 0, 0, 0, 1, 0, 1, 0, 0, 1};
-      STATUS_TRY(pair_accumulate<T>(h, p_r, p_r, phi_r, G, gb, (const T*)B.kx, wa, st));
+      STATUS_TRY(pair_accumulate<T>(h, p_r, p_r, phi_r, Gs, gb, (const T*)B.kx, wa, st));
     }
-    // K1e: w p_u conj(W), W = Conv_H[drho] + f_xc drho
+    // K1e: w p_u conj(W), W = Conv_H[drho] + f_xc drho (spin-flip: f_xc^SF drho only)
     { k_delta_rho<T><<<grid_for(n3, 256), 256, 0, st>>>(phi_r, p_r, drho, nocc, 1, n3); note_launch(); }
-    STATUS_TRY(convolve_fields<T>(h, drho, 1, (const T*)B.kh, T(1), wb, st));
+    if (sf) CUDA_TRY(cudaMemsetAsync(wb, 0, (size_t)n3 * sizeof(cplx<T>), st));
+    else STATUS_TRY(convolve_fields<T>(h, drho, 1, (const T*)B.kh, T(1), wb, st));
     { k_add_fxc<T><<<grid_for(n3, 256), 256, 0, st>>>(wb, (const T*)B.fxc, drho, n3); note_launch(); }
-    { k_grad_k1e<T><<<grid_for((long long)nocc * n3, 256), 256, 0, st>>>(p_r, wb, G, nocc, (T)w[b], n3); note_launch(); }
+    { k_grad_k1e<T><<<grid_for((long long)nocc * n3, 256), 256, 0, st>>>(p_r, wb, Gs, nocc, (T)w[b], n3); note_launch(); }
     STATUS_TRY(check_launch("adjoint k1e"));
     if (grad_vloc)
       { k_grad_vloc<T><<<grid_for(n3, 256), 256, 0, st>>>(p_r, nocc, w[b] * vol / (double)n3, grad_vloc, n3); note_launch(); }
   }
-  STATUS_TRY(real_to_pw<T>(h, G, nocc, grad_phi, nullptr, st));
+  STATUS_TRY(real_to_pw<T>(h, Gs, gfields, grad_phi, nullptr, st));
 
   // projector terms: -sum_k w_b(k) [ <x_k|phi_u> y_k + <y_k|phi_u> x_k ]
   CUDA_TRY(cudaMemcpyAsync(B.wdev, w, (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1363,12 +1370,12 @@ static tddft_status adjoint_impl(tddft_system* h, int nb, const cplx<T>* X, cons
   for (int pass = 0; pass < 2; ++pass) {
     const cplx<T>* V = pass == 0 ? X : Y;        // overlap partner
     const cplx<T>* Wv = pass == 0 ? Y : X;       // vectors that get the coefficients
-    dim3 g1((nocc + 31) / 32, (unsigned)((rows + 31) / 32), nsplit);
-    { k_overlap<T><<<g1, 256, 0, st>>>(phi, nocc, V, (int)rows, npw, kchunk, Cp); note_launch(); }
-    { k_reduce_split<T><<<grid_for((long long)nocc * rows, 256), 256, 0, st>>>(Cp, nsplit, (long long)nocc * rows, C); note_launch(); }
-    { k_proj_grad_coef<T><<<grid_for((long long)nocc * rows, 256), 256, 0, st>>>(C, nocc, (int)rows, nocc, B.wdev, Ct); note_launch(); }
-    dim3 g2((npw + 63) / 64, (nocc + 31) / 32);
-    { k_update<T><<<g2, 256, 0, st>>>(Wv, (int)rows, Ct, nocc, npw, T(1), grad_phi); note_launch(); }
+    dim3 g1((ntgt + 31) / 32, (unsigned)((rows + 31) / 32), nsplit);
+    { k_overlap<T><<<g1, 256, 0, st>>>(phi, ntgt, V, (int)rows, npw, kchunk, Cp); note_launch(); }
+    { k_reduce_split<T><<<grid_for((long long)ntgt * rows, 256), 256, 0, st>>>(Cp, nsplit, (long long)ntgt * rows, C); note_launch(); }
+    { k_proj_grad_coef<T><<<grid_for((long long)ntgt * rows, 256), 256, 0, st>>>(C, ntgt, (int)rows, nocc, B.wdev, Ct); note_launch(); }
+    dim3 g2((npw + 63) / 64, (ntgt + 31) / 32);
+    { k_update<T><<<g2, 256, 0, st>>>(Wv, (int)rows, Ct, ntgt, npw, T(1), grad_t); note_launch(); }
   }
   return check_launch("adjoint projector terms");
 }
@@ -1834,7 +1841,6 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
 tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
                                            void* grad_phi, double* grad_vloc, void* stream) {
   if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (h->sf()) return fail(TDDFT_ENOTSUP, "the adjoint is implemented for spin-conserving systems");
   if (h->ace_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact exchange; disable ACE first");
   if (h->loc_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact K1d; disable the localised frame first");
   if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
@@ -1846,6 +1852,77 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// density responses of the force expression (Sec. 2.2, Sec. 2.3)
+// ---------------------------------------------------------------------------
+
+// out[r] += s * sum_v Re(conj(f_v(r)) g_v(r))
+template <typename T>
+__global__ void k_density_accum(const cplx<T>* __restrict__ f, const cplx<T>* __restrict__ g, int nocc, double s,
+                                double* __restrict__ out, long long n3) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n3; r += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      const cplx<T> a = f[(long long)v * n3 + r], b = g[(long long)v * n3 + r];
+      acc += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+    }
+    out[r] += s * acc;
+  }
+}
+
+template <typename T>
+static tddft_status relaxed_density_impl(tddft_system* h, int nb, const cplx<T>* X, const cplx<T>* Z, const double* w,
+                                         double* drho, cudaStream_t st) {
+  const int nocc = h->d.nocc_src, npw = h->npw;
+  const long long n3 = h->n3, len = (long long)nocc * npw;
+  const bool sf = h->sf();
+  CUDA_TRY(cudaMemsetAsync(drho, 0, (size_t)(sf ? 2 : 1) * n3 * sizeof(double), st));
+  cplx<T>* a_r = (cplx<T>*)h->b.a_r;
+  cplx<T>* f_r = (cplx<T>*)h->b.out_r;
+  cplx<T>* psi = (cplx<T>*)h->b.io_a;
+  const cplx<T>* phi_r = (const cplx<T>*)h->b.phi_src_r;
+  std::vector<cplx<T>> S((size_t)nocc * nocc), St(S.size());
+  cplx<T>* C = (cplx<T>*)h->b.cmat;
+  for (int b = 0; b < nb; ++b) {
+    if (w[b] == 0.0) continue;
+    const cplx<T>* Xb = X + b * len;
+    // sum_v |a_v|^2: the target-spin channel (channel 0)
+    STATUS_TRY(pw_to_real<T>(h, Xb, nocc, a_r, st));
+    { k_density_accum<T><<<grid_for(n3, 256), 256, 0, st>>>(a_r, a_r, nocc, w[b], drho, n3); note_launch(); }
+    // -sum_vv' conj(phi_v) phi_v' <a_v|a_v'>: psi_v = sum_v' <a_v|a_v'> phi_v' in plane waves
+    STATUS_TRY(gemm_overlap<T>(h, Xb, nocc, Xb, nocc, (cplx<T>*)h->b.cpart, C, st));  // C[u][r] = <a_u|a_r>
+    CUDA_TRY(cudaMemcpyAsync(S.data(), C, S.size() * sizeof(cplx<T>), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int v = 0; v < nocc; ++v)
+      for (int vp = 0; vp < nocc; ++vp) St[(size_t)vp * nocc + v] = S[(size_t)v * nocc + vp];  // [v'][v] = <a_v|a_v'>
+    CUDA_TRY(cudaMemcpyAsync(C, St.data(), St.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(psi, 0, (size_t)len * sizeof(cplx<T>), st));
+    STATUS_TRY(gemm_update<T>(h, (const cplx<T>*)h->b.phi_src_pw, nocc, C, psi, nocc, T(1), st));
+    STATUS_TRY(pw_to_real<T>(h, psi, nocc, f_r, st));
+    { k_density_accum<T><<<grid_for(n3, 256), 256, 0, st>>>(phi_r, f_r, nocc, -w[b], sf ? drho + n3 : drho, n3);
+      note_launch(); }
+    if (Z) {  // 2 Re sum_v conj(phi_v) Z_v
+      STATUS_TRY(pw_to_real<T>(h, Z + b * len, nocc, f_r, st));
+      { k_density_accum<T><<<grid_for(n3, 256), 256, 0, st>>>(phi_r, f_r, nocc, 2.0 * w[b], drho, n3); note_launch(); }
+    }
+    STATUS_TRY(check_launch("relaxed density"));
+  }
+  return TDDFT_OK;
+}
+
+extern "C" tddft_status tddft_relaxed_density(tddft_handle h, int nb, const void* X, const void* Z, const double* w,
+                                              double* drho, void* stream) {
+  if (!h) return fail(TDDFT_EINVAL, "null handle");
+  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+  if (!X || !w || !drho) return fail(TDDFT_EINVAL, "null buffer");
+  if (Z && h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector part is implemented for spin-conserving systems");
+  if (h->loc_on) return fail(TDDFT_ENOTSUP, "disable the localised frame first (the density uses the given orbitals)");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->d.precision == TDDFT_PREC_FP64)
+    return relaxed_density_impl<double>(h, nb, (const cplx<double>*)X, (const cplx<double>*)Z, w, drho, st);
+  return relaxed_density_impl<float>(h, nb, (const cplx<float>*)X, (const cplx<float>*)Z, w, drho, st);
+}
 
 // ---------------------------------------------------------------------------
 // Z-vector equation (Eq. 19) by conjugate gradients with the inexact Krylov

@@ -40,7 +40,7 @@ EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
     "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi",
     "tddft_ace_build", "tddft_ace_enable", "tddft_zvector_solve", "tddft_zvector_rhs",
-    "tddft_set_localization", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_set_localization", "tddft_relaxed_density", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc",
@@ -111,6 +111,7 @@ def load() -> ctypes.CDLL:
         "tddft_zvector_solve": ([vp, ci, vp, vp, vp, vp, vp, vp, vp], st),
         "tddft_zvector_rhs": ([vp, ci, vp, vp, vp], st),
         "tddft_set_localization": ([vp, vp, ctypes.c_double, vp, vp, vp], st),
+        "tddft_relaxed_density": ([vp, ci, vp, vp, vp, vp, vp], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_adjoint": ([vp, ci, vp, vp, vp, vp, vp, vp], st),
@@ -324,7 +325,8 @@ class LiouvilleSystem:
     def adjoint(self, X, w, stream=None, with_vloc=True):
         """omega_b and the gradients of sum_b w_b omega_b (tddft_apply_liouville_adjoint).
 
-        Returns (omega [nb] float64, grad_phi [nocc, npw] (Wirtinger d/dc^*), grad_vloc [n,n,n] or None).
+        Returns (omega [nb] float64, grad_phi (Wirtinger d/dc^*: [nocc, npw], or for spin-flip
+        [nocc_src + nocc_tgt, npw] with the source-spin rows first), grad_vloc [n,n,n] or None).
         """
         torch = self._check_batch(X)
         nb = X.shape[0]
@@ -332,7 +334,8 @@ class LiouvilleSystem:
         if w.shape != (nb,):
             raise ValueError("w must have one weight per trial vector")
         omega = torch.empty(nb, dtype=torch.float64, device=X.device)
-        gphi = torch.empty((self.nocc_src, self.npw), dtype=self.complex_dtype, device=X.device)
+        rows = self.nocc_src + (self.nocc_tgt if self.spin_flip else 0)
+        gphi = torch.empty((rows, self.npw), dtype=self.complex_dtype, device=X.device)
         gv = torch.empty((self.n,) * 3, dtype=torch.float64, device=X.device) if with_vloc else None
         _check(load().tddft_apply_liouville_adjoint(self._h, nb, X.data_ptr(), w.ctypes.data, omega.data_ptr(),
                                                     gphi.data_ptr(), None if gv is None else gv.data_ptr(),
@@ -353,6 +356,23 @@ class LiouvilleSystem:
         _check(load().tddft_set_localization(self._h, Uc.ctypes.data, float(s_thr), S.ctypes.data, ctypes.byref(kept),
                                              _stream_ptr(stream)), "tddft_set_localization")
         return S, kept.value
+
+    def relaxed_density(self, X, w, Z=None, stream=None):
+        """sum_b w_b (Delta rho^(x)[X_b] + Delta rho^(Z)[Z_b]) (tddft_relaxed_density):
+        [n,n,n] float64, or [2,n,n,n] for spin-flip (target channel first)."""
+        torch = self._check_batch(X)
+        nb = X.shape[0]
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (nb,):
+            raise ValueError("w must have one weight per trial vector")
+        if Z is not None and tuple(Z.shape) != tuple(X.shape):
+            raise ValueError("Z must have the shape of X")
+        shape = ((2,) if self.spin_flip else ()) + (self.n,) * 3
+        out = torch.empty(shape, dtype=torch.float64, device=X.device)
+        _check(load().tddft_relaxed_density(self._h, nb, X.data_ptr(), None if Z is None else Z.data_ptr(),
+                                            w.ctypes.data, out.data_ptr(), _stream_ptr(stream)),
+               "tddft_relaxed_density")
+        return out
 
     def zvector_rhs(self, X, stream=None):
         """U_s = -P^c u_s for each state of X (tddft_zvector_rhs); same shape and dtype as X."""

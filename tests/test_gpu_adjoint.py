@@ -60,14 +60,54 @@ def test_adjoint_weights_are_linear(torch):
     assert torch.allclose(v3, 2 * v1 - 3 * v2, atol=1e-12 * float(v3.abs().max()))
 
 
-def test_spin_flip_adjoint_is_reported_unsupported(torch):
-    wl = synth.make_workload(n=12, a=7.0, ecut=4.0, npw=T.sphere_size(12, 7.0, 4.0), nocc_src=3, nb=1, seed=1,
-                             spin_flip=True, nocc_tgt=2)
-    s = T.system_from_workload(wl, precision=T.PREC_FP64)
+@pytest.mark.parametrize("prec,tol", [(T.PREC_FP64, 1e-10), (T.PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("shape", [(12, 7.0, 4.0, 3, 2, 2, 1), (24, 10.0, 10.0, 8, 6, 3, 2)])
+def test_spin_flip_adjoint_matches_oracle(torch, prec, tol, shape):
+    """Spin-flip gradient: source-spin rows (K1e^SF, K1d^SF) then target-spin rows (V_X in D, P^c)."""
+    n, a, ecut, ns, nt, nb, seed = shape
+    wl = synth.make_workload(n=n, a=a, ecut=ecut, npw=T.sphere_size(n, a, ecut), nocc_src=ns, nb=nb, seed=seed,
+                             spin_flip=True, nocc_tgt=nt)
+    w = np.linspace(1.2, -0.4, nb)
+    om_o, g_o, gv_o = O.system_from_workload(wl).omega_grad(wl.X, w)
+    s = T.system_from_workload(wl, precision=prec)
+    om, g, gv = s.adjoint(torch.from_numpy(wl.X).to("cuda", s.complex_dtype), w)
+    torch.cuda.synchronize()
+    s.close()
+    om, g, gv = om.cpu().numpy(), g.cpu().numpy().astype(np.complex128), gv.cpu().numpy()
+    assert g.shape == (ns + nt, wl.phi_src.shape[1])
+    assert np.abs(om - om_o).max() < tol * np.abs(om_o).max()
+    assert _rel(g[:ns], g_o[:ns]) < tol
+    assert _rel(g[ns:], g_o[ns:]) < tol
+    assert _rel(gv, gv_o) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(T.PREC_FP64, 1e-11), (T.PREC_FP32, 1e-5)])
+def test_relaxed_density_matches_oracle(torch, prec, tol):
+    """Delta rho^(x) (+ Delta rho^(Z)) spin-conserving, and both channels of the spin-flip Delta rho^(x)."""
+    wl = _wl(24, 10.0, 10.0, 8, 3, 12)
+    S = O.system_from_workload(wl)
+    w = np.array([1.0, -0.5, 0.25])
+    Z = S.project(wl.X[::-1].copy())
+    s = T.system_from_workload(wl, precision=prec)
+    X = torch.from_numpy(wl.X).to("cuda", s.complex_dtype)
+    Zd = torch.from_numpy(Z).to("cuda", s.complex_dtype)
+    got = s.relaxed_density(X, w).cpu().numpy()
+    got_z = s.relaxed_density(X, w, Zd).cpu().numpy()
+    s.close()
+    assert _rel(got, S.relaxed_densities(wl.X, w)[0]) < tol
+    assert _rel(got_z, S.relaxed_densities(wl.X, w, Z)[0]) < tol
+    wl = synth.make_workload(n=24, a=10.0, ecut=10.0, npw=T.sphere_size(24, 10.0, 10.0), nocc_src=8, nb=2, seed=13,
+                             spin_flip=True, nocc_tgt=6)
+    want = O.system_from_workload(wl).relaxed_densities(wl.X, np.array([0.7, 1.1]))
+    s = T.system_from_workload(wl, precision=prec)
+    X = torch.from_numpy(wl.X).to("cuda", s.complex_dtype)
+    got = s.relaxed_density(X, np.array([0.7, 1.1])).cpu().numpy()
     with pytest.raises(T.TddftError) as e:
-        s.adjoint(torch.from_numpy(wl.X).cuda(), np.ones(1))
+        s.relaxed_density(X, np.array([0.7, 1.1]), X)
     assert e.value.status == 7
     s.close()
+    assert got.shape == want.shape
+    assert _rel(got[0], want[0]) < tol and _rel(got[1], want[1]) < tol
 
 
 def test_autograd_function(torch):
