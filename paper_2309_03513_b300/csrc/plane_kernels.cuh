@@ -1,0 +1,271 @@
+// Plane kernels of the pair convolutions: the forward xy pass, the z pass
+// and the inverse xy pass (templated on the real type T and the grid size N).
+//
+// Field layout: a real-space field is N^3 complex values indexed [z][y][x]
+// (x fastest). A reciprocal-space field produced by the forward kernels is
+// the same array with each axis in the digit-reversed order of its radix plan.
+#pragma once
+#include "fft.cuh"
+
+namespace tddft {
+
+// Affine description of a batch of pair convolutions. Item i = t * kdim + k
+// (t = target slot, k = source slot) convolves conj(Q) * R and, in the
+// accumulate mode, adds scale * P * Conv[conj(Q) R] to output field o.
+struct PairMap {
+  int kdim;
+  int q0, qk, qt;
+  int r0, rk, rt;
+  int p0, pk, pt;
+  int o0, ot;
+  // optional explicit (q, r) field indices per item for the forward pass (pair lists)
+  const int2* list = nullptr;
+};
+
+template <typename T>
+__device__ __forceinline__ const cplx<T>* plane_ptr(const cplx<T>* base, long long field, int z, long long n3, int n2) {
+  return base + field * n3 + (long long)z * n2;
+}
+
+// ---------------------------------------------------------------------------
+// Forward xy pass. MODE_PRODUCT: plane = conj(Q) * R; MODE_LOAD: plane = R.
+// Grid (N, items). Output item i goes to ibuf field i (digit-reversed in x, y).
+// ---------------------------------------------------------------------------
+constexpr int XY_LOAD = 0;
+constexpr int XY_PRODUCT = 1;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_xy_fwd(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
+             cplx<T>* __restrict__ ibuf, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + tw_table_len<N>();
+  const int tid = threadIdx.x, z = blockIdx.x, item = blockIdx.y;
+  const int t = item / pm.kdim, k = item - t * pm.kdim;
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
+  long long qi = pm.q0 + (long long)k * pm.qk + (long long)t * pm.qt;
+  long long ri = pm.r0 + (long long)k * pm.rk + (long long)t * pm.rt;
+  if (pm.list) {
+    const int2 pr = pm.list[item];
+    qi = pr.x;
+    ri = pr.y;
+  }
+  const cplx<T>* R = plane_ptr(rb, ri, z, N3, N2);
+  if constexpr (MODE == XY_PRODUCT) {
+    const cplx<T>* Q = plane_ptr(qb, qi, z, N3, N2);
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = cmulc(Q[e], R[e]);
+    }
+  } else {
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = R[e];
+    }
+  }
+  __syncthreads();
+  const int line = tid % N, g = tid / N;
+  fft_lines<T, N, FWD, true>(s, tw, line, g);
+  fft_lines<T, N, FWD, false>(s, tw, line, g);
+  cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * N2;
+  for (int e = tid; e < N2; e += NT) {
+    const int y = e / N, x = e - y * N;
+    O[e] = s[y * PITCH + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z pass over the xz-plane at fixed y of every item.
+// Z_CONV: forward z, multiply by kernel * kscale, inverse z.  Z_FWD / Z_INV: one direction.
+// kernel is real, [N^3] in digit-reversed (position) order.
+// ---------------------------------------------------------------------------
+constexpr int Z_CONV = 0;
+constexpr int Z_FWD = 1;
+constexpr int Z_INV = 2;
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_z(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + tw_table_len<N>();
+  const int tid = threadIdx.x, y = blockIdx.x, item = blockIdx.y;
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
+  cplx<T>* B = ibuf + (long long)item * N3 + (long long)y * N;
+  for (int e = tid; e < N2; e += NT) {
+    const int z = e / N, x = e - z * N;
+    s[z * PITCH + x] = B[(long long)z * N2 + x];
+  }
+  __syncthreads();
+  const int line = tid % N, g = tid / N;
+  if constexpr (MODE != Z_INV) fft_lines<T, N, FWD, false>(s, tw, line, g);
+  if constexpr (MODE == Z_CONV) {
+    const T* K = kern + (long long)y * N;
+    for (int e = tid; e < N2; e += NT) {
+      const int z = e / N, x = e - z * N;
+      s[z * PITCH + x] = cscale(s[z * PITCH + x], K[(long long)z * N2 + x] * kscale);
+    }
+    __syncthreads();
+  }
+  if constexpr (MODE != Z_FWD) fft_lines<T, N, INV, false>(s, tw, line, g);
+  for (int e = tid; e < N2; e += NT) {
+    const int z = e / N, x = e - z * N;
+    B[(long long)z * N2 + x] = s[z * PITCH + x];
+  }
+}
+
+// Register-resident z pass: one thread per (x, y) column holds the whole
+// column of N values, so the transform needs neither shared memory nor a
+// barrier; loads and stores of a warp cover 32 consecutive columns of one
+// z-plane (coalesced). Used where the column fits the register file.
+template <typename T, int N>
+__host__ __device__ constexpr bool z_in_registers() {
+  return sizeof(T) == 4 && N >= 8 && N <= 80;
+}
+constexpr int ZREG_THREADS = 128;
+
+// cols (optional): the N^2 column positions with the nact columns that can be
+// non-zero first (ascending), then the others (ascending). Threads of the
+// first kind transform their column; threads of the second kind only write
+// zeros, which is what the transform of an all-zero column gives exactly.
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ZREG_THREADS)
+    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, const int* __restrict__ cols,
+            int nact) {
+  constexpr int N2 = N * N;
+  constexpr long long N3 = (long long)N * N * N;
+  const int i = blockIdx.x * ZREG_THREADS + threadIdx.x;
+  if (i >= N2) return;
+  const int c = cols ? cols[i] : i;
+  cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + c;
+  if (cols && i >= nact) {
+#pragma unroll 8
+    for (int z = 0; z < N; ++z) B[(long long)z * N2] = cplx<T>{T(0), T(0)};
+    return;
+  }
+  cplx<T> v[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = B[(long long)z * N2];
+  TwConst<T, N> tw;
+  if constexpr (MODE != Z_INV) fft_reg<T, N, FWD>(v, tw);
+  if constexpr (MODE == Z_CONV) {
+    const T* K = kern + c;
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = cscale(v[z], K[(long long)z * N2] * kscale);
+  }
+  if constexpr (MODE != Z_FWD) fft_reg<T, N, INV>(v, tw);
+#pragma unroll
+  for (int z = 0; z < N; ++z) B[(long long)z * N2] = v[z];
+}
+
+// ---------------------------------------------------------------------------
+// Inverse xy pass.
+// INV_WRITE: out field (o0 + t*ot) plane z = scale * IFFT_xy(ibuf item t).
+// INV_ACCUM: out field (o0 + t*ot) plane z += scale * sum_k P_(t,k) * IFFT_xy(ibuf item t*kdim+k).
+//            Grid (N, targets); each CTA loops over the sources of its target.
+// INV_ATOMIC: the same sum with one CTA per item (grid (N, targets*kdim)),
+//            added to the output with atomics (summation order not fixed). In INV_WRITE mode ob may be ibuf itself (in place: each
+// CTA reads its whole plane before it writes it back).
+// ---------------------------------------------------------------------------
+constexpr int INV_WRITE = 0;
+constexpr int INV_ACCUM = 1;
+constexpr int INV_ATOMIC = 2;  // one CTA per pair item, atomic accumulation into the target
+
+template <typename T>
+__device__ __forceinline__ void atomic_cadd(cplx<T>* p, cplx<T> v);
+template <>
+__device__ __forceinline__ void atomic_cadd<float>(cplx<float>* p, cplx<float> v) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
+}
+template <>
+__device__ __forceinline__ void atomic_cadd<double>(cplx<double>* p, cplx<double> v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(plane_threads<N>())
+    k_xy_inv(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm,
+             T scale, const cplx<T>* __restrict__ twg) {
+  constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
+  constexpr int EPT = (N2 + NT - 1) / NT;
+  constexpr long long N3 = (long long)N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* s = tw + tw_table_len<N>();
+  const int tid = threadIdx.x, z = blockIdx.x, t = blockIdx.y;
+  for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
+  const int line = tid % N, g = tid / N;
+  cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z * N2;
+  if constexpr (MODE == INV_WRITE) {
+    const cplx<T>* I = ibuf + (long long)t * N3 + (long long)z * N2;
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = I[e];
+    }
+    __syncthreads();
+    fft_lines<T, N, INV, false>(s, tw, line, g);
+    fft_lines<T, N, INV, true>(s, tw, line, g);
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      O[e] = cscale(s[y * PITCH + x], scale);
+    }
+  } else if constexpr (MODE == INV_ATOMIC) {
+    const int item = t;
+    const int tt = item / pm.kdim, k = item - tt * pm.kdim;
+    const cplx<T>* I = ibuf + (long long)item * N3 + (long long)z * N2;
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = I[e];
+    }
+    __syncthreads();
+    fft_lines<T, N, INV, false>(s, tw, line, g);
+    fft_lines<T, N, INV, true>(s, tw, line, g);
+    const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)tt * pm.pt, z, N3, N2);
+    cplx<T>* Oa = ob + (long long)(pm.o0 + (long long)tt * pm.ot) * N3 + (long long)z * N2;
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      atomic_cadd(Oa + e, cscale(cmul(P[e], s[y * PITCH + x]), scale));
+    }
+  } else {
+    cplx<T> acc[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) acc[i] = {T(0), T(0)};
+    for (int k = 0; k < pm.kdim; ++k) {
+      const long long item = (long long)t * pm.kdim + k;
+      const cplx<T>* I = ibuf + item * N3 + (long long)z * N2;
+      for (int e = tid; e < N2; e += NT) {
+        const int y = e / N, x = e - y * N;
+        s[y * PITCH + x] = I[e];
+      }
+      __syncthreads();
+      fft_lines<T, N, INV, false>(s, tw, line, g);
+      fft_lines<T, N, INV, true>(s, tw, line, g);
+      const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)t * pm.pt, z, N3, N2);
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + i * NT;
+        if (e < N2) {
+          const int y = e / N, x = e - y * N;
+          acc[i] = cadd(acc[i], cmul(P[e], s[y * PITCH + x]));
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * NT;
+      if (e < N2) O[e] = cadd(O[e], cscale(acc[i], scale));
+    }
+  }
+}
+
+}  // namespace tddft

@@ -38,7 +38,9 @@ def _rel_err(got, want):
 
 def _run(torch, wl, prec, mask=T.TERMS_ALL, X=None, tiling=None):
     sys_ = T.system_from_workload(wl, precision=prec, term_mask=mask)
-    if tiling:
+    if isinstance(tiling, dict):
+        sys_.set_tuning(**tiling)
+    elif tiling:
         sys_.set_tuning(*tiling)
     X = wl.X if X is None else X
     Xd = torch.from_numpy(X).to("cuda", sys_.complex_dtype)
@@ -67,16 +69,20 @@ def test_each_term_fp64(torch, term):
     assert _rel_err(got, want).max() < 1e-11
 
 
-@pytest.mark.parametrize("n,a,ecut,nocc,nb", [(8, 6.0, 3.2, 3, 2), (16, 8.0, 6.0, 5, 2), (32, 9.0, 12.0, 6, 2),
+@pytest.mark.parametrize("n,a,ecut,nocc,nb", [(8, 6.0, 3.2, 3, 2), (12, 7.0, 4.0, 3, 1), (16, 8.0, 6.0, 5, 2),
+                                               (24, 10.0, 10.0, 3, 1), (32, 9.0, 12.0, 6, 2),
                                                (36, 9.0, 14.0, 5, 1), (48, 10.0, 20.0, 4, 1),
                                                (64, 11.0, 25.0, 3, 1), (72, 13.48, 25.0, 3, 1),
                                                (80, 15.0, 25.0, 2, 1), (96, 17.97, 25.0, 2, 1),
-                                               (108, 20.2, 25.0, 2, 1)])
+                                               (108, 20.2, 25.0, 2, 1), (128, 23.96, 25.0, 1, 1)])
 def test_every_grid_plan(torch, n, a, ecut, nocc, nb):
-    """One system per supported radix plan (8, 4x3, 16, 8x4, 4x9, 16x3, 8x8, 8x9, 16x5, 12x8, 12x9)."""
+    """One system per supported radix plan (8, 4x3, 16, 8x3, 8x4, 4x9, 16x3, 8x8, 8x9,
+    16x5, 12x8, 12x9, 8x16; 128^3 in FP32 only)."""
     wl = _workload(n, a, ecut, nocc, nb, seed=n)
     want = O.system_from_workload(wl).apply(wl.X)
     for prec in (T.PREC_FP64, T.PREC_FP32):
+        if n == 128 and prec == T.PREC_FP64:
+            continue  # the FP64 128^3 plane does not fit in shared memory
         got = _run(torch, wl, prec)
         assert _rel_err(got, want).max() < TOL[prec], (n, prec)
 
@@ -110,7 +116,8 @@ def test_kernel_variants_fp32(torch, n, a, ecut):
     for prune in (0, 1):
         for z in (0, 1):
             for acc in (0, 1):
-                got = _run(torch, wl, T.PREC_FP32, tiling=(3, 4, 5, acc, -1, prune, z))
+                got = _run(torch, wl, T.PREC_FP32, tiling=dict(targets=3, sources=4, k1d_block=5, accumulate=acc,
+                                                              prune=prune, z_kernel=z))
                 assert _rel_err(got, want).max() < 1e-5, (prune, z, acc)
     got = _run(torch, wl, T.PREC_FP64, tiling=(3, 4, 5, 1, -1, 1, 0))
     assert _rel_err(got, want).max() < 1e-11
