@@ -148,12 +148,16 @@ typedef struct tddft_tuning {
   int graph;        /* 1: tddft_apply_liouville captures its launches into a CUDA
                        graph on first use for a given (nb, A, LA, term mask) and
                        replays it on the caller's stream; 0: plain launches */
-  int prune;        /* 1: the z pass of pair convolutions transforms only the (k_x, k_y)
-                       columns inside the disc of radius 2 G_max and writes zeros to the
-                       others, which are exactly zero for products of two sphere
+  int prune;        /* 1 (default): pair convolutions of the exchange terms and the
+                       Hartree convolution keep, after the xy transform, only the
+                       (k_x, k_y) columns inside the disc of radius 2 G_max, stored
+                       densely: the others are exactly zero for products of two sphere
                        functions when the grid does not alias them (checked at set-up;
-                       otherwise every column is transformed); 0: off. Register-
-                       resident z pass only. -1 keeps the value in set_tuning */
+                       otherwise full planes are used). The z pass and the
+                       intermediate's memory traffic shrink by the share of columns
+                       outside the disc (44% on an alias-free 72^3 grid at 25 Ha).
+                       Register-resident z pass only. 0: full planes. -1 keeps the
+                       value in set_tuning */
   int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
                        (FP32, n <= 80). -1 keeps the value in set_tuning */
   int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with

@@ -27,9 +27,41 @@ __device__ __forceinline__ const cplx<T>* plane_ptr(const cplx<T>* base, long lo
   return base + field * n3 + (long long)z * n2;
 }
 
+// Compact intermediate of pair densities (ccols != nullptr): a pair density
+// ρ = conj(q) r of two fields band-limited to |G| < G_max is band-limited to
+// 2 G_max, so after the xy transform only the nact columns (x, y) inside that
+// disk can be non-zero, for every z. Plane z of an item then holds just those
+// columns, densely: element c of the plane is column ccols[c] (= y * N + x in
+// the digit-reversed positions), at item base + z * nact + c. The other columns
+// are zero and are neither stored, transformed along z nor read back.
+// Plane z of an item (full or compact) into the shared-memory plane s (row pitch PITCH).
+template <typename T, int N, int NT, int PITCH>
+__device__ __forceinline__ void stage_in_plane(cplx<T>* s, const cplx<T>* item, int z, const int* __restrict__ ccols,
+                                               int nact, int tid) {
+  constexpr int N2 = N * N;
+  if (ccols) {
+    for (int e = tid; e < N * PITCH; e += NT) s[e] = cplx<T>{T(0), T(0)};
+    __syncthreads();
+    const cplx<T>* I = item + (long long)z * nact;
+#pragma unroll 4
+    for (int c = tid; c < nact; c += NT) {
+      const int q = ccols[c], y = q / N;
+      s[y * PITCH + q - y * N] = I[c];
+    }
+  } else {
+    const cplx<T>* I = item + (long long)z * N2;
+#pragma unroll 4
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      s[y * PITCH + x] = I[e];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward xy pass. MODE_PRODUCT: plane = conj(Q) * R; MODE_LOAD: plane = R.
-// Grid (N, items). Output item i goes to ibuf field i (digit-reversed in x, y).
+// Grid (N, items). Output item i goes to ibuf field i (digit-reversed in x, y;
+// compact when ccols is given).
 // ---------------------------------------------------------------------------
 constexpr int XY_LOAD = 0;
 constexpr int XY_PRODUCT = 1;
@@ -37,7 +69,7 @@ constexpr int XY_PRODUCT = 1;
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(plane_threads<N>())
     k_xy_fwd(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
-             cplx<T>* __restrict__ ibuf, const cplx<T>* __restrict__ twg) {
+             cplx<T>* __restrict__ ibuf, const cplx<T>* __restrict__ twg, const int* __restrict__ ccols, int nact) {
   constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
   constexpr long long N3 = (long long)N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -71,10 +103,19 @@ __global__ void __launch_bounds__(plane_threads<N>())
   const int line = tid % N, g = tid / N;
   fft_lines<T, N, FWD, true>(s, tw, line, g);
   fft_lines<T, N, FWD, false>(s, tw, line, g);
-  cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * N2;
-  for (int e = tid; e < N2; e += NT) {
-    const int y = e / N, x = e - y * N;
-    O[e] = s[y * PITCH + x];
+  if (ccols) {
+    cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * nact;
+#pragma unroll 4
+    for (int c = tid; c < nact; c += NT) {
+      const int q = ccols[c], y = q / N;
+      O[c] = s[y * PITCH + q - y * N];
+    }
+  } else {
+    cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * N2;
+    for (int e = tid; e < N2; e += NT) {
+      const int y = e / N, x = e - y * N;
+      O[e] = s[y * PITCH + x];
+    }
   }
 }
 
@@ -130,38 +171,30 @@ __host__ __device__ constexpr bool z_in_registers() {
 }
 constexpr int ZREG_THREADS = 128;
 
-// cols (optional): the N^2 column positions with the nact columns that can be
-// non-zero first (ascending), then the others (ascending). Threads of the
-// first kind transform their column; threads of the second kind only write
-// zeros, which is what the transform of an all-zero column gives exactly.
-template <typename T, int N, int MODE>
+// COMPACT: compact items (see stage_in_plane): thread i < nact takes compact
+// column i, and kern is the compact kernel table [z][nact].
+template <typename T, int N, int MODE, bool COMPACT = false>
 __global__ void __launch_bounds__(ZREG_THREADS)
-    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, const int* __restrict__ cols,
-            int nact) {
+    k_z_reg(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern, T kscale, int nact) {
   constexpr int N2 = N * N;
   constexpr long long N3 = (long long)N * N * N;
   const int i = blockIdx.x * ZREG_THREADS + threadIdx.x;
-  if (i >= N2) return;
-  const int c = cols ? cols[i] : i;
-  cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + c;
-  if (cols && i >= nact) {
-#pragma unroll 8
-    for (int z = 0; z < N; ++z) B[(long long)z * N2] = cplx<T>{T(0), T(0)};
-    return;
-  }
+  const int stride = COMPACT ? nact : N2;
+  if (i >= stride) return;
+  cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + i;
   cplx<T> v[N];
 #pragma unroll
-  for (int z = 0; z < N; ++z) v[z] = B[(long long)z * N2];
+  for (int z = 0; z < N; ++z) v[z] = B[(long long)z * stride];
   TwConst<T, N> tw;
   if constexpr (MODE != Z_INV) fft_reg<T, N, FWD>(v, tw);
   if constexpr (MODE == Z_CONV) {
-    const T* K = kern + c;
+    const T* K = kern + i;
 #pragma unroll
-    for (int z = 0; z < N; ++z) v[z] = cscale(v[z], K[(long long)z * N2] * kscale);
+    for (int z = 0; z < N; ++z) v[z] = cscale(v[z], K[(long long)z * stride] * kscale);
   }
   if constexpr (MODE != Z_FWD) fft_reg<T, N, INV>(v, tw);
 #pragma unroll
-  for (int z = 0; z < N; ++z) B[(long long)z * N2] = v[z];
+  for (int z = 0; z < N; ++z) B[(long long)z * stride] = v[z];
 }
 
 // ---------------------------------------------------------------------------
@@ -171,7 +204,7 @@ __global__ void __launch_bounds__(ZREG_THREADS)
 //            Grid (N, targets); each CTA loops over the sources of its target.
 // INV_ATOMIC: the same sum with one CTA per item (grid (N, targets*kdim)),
 //            added to the output with atomics (summation order not fixed). In INV_WRITE mode ob may be ibuf itself (in place: each
-// CTA reads its whole plane before it writes it back).
+// CTA reads its whole plane before it writes it back), unless the items are compact (ccols).
 // ---------------------------------------------------------------------------
 constexpr int INV_WRITE = 0;
 constexpr int INV_ACCUM = 1;
@@ -192,7 +225,7 @@ __device__ __forceinline__ void atomic_cadd<double>(cplx<double>* p, cplx<double
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(plane_threads<N>())
     k_xy_inv(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm,
-             T scale, const cplx<T>* __restrict__ twg) {
+             T scale, const cplx<T>* __restrict__ twg, const int* __restrict__ ccols, int nact) {
   constexpr int NT = plane_threads<N>(), PITCH = plane_pitch<N>(), N2 = N * N;
   constexpr int EPT = (N2 + NT - 1) / NT;
   constexpr long long N3 = (long long)N * N * N;
@@ -204,11 +237,7 @@ __global__ void __launch_bounds__(plane_threads<N>())
   const int line = tid % N, g = tid / N;
   cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z * N2;
   if constexpr (MODE == INV_WRITE) {
-    const cplx<T>* I = ibuf + (long long)t * N3 + (long long)z * N2;
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      s[y * PITCH + x] = I[e];
-    }
+    stage_in_plane<T, N, NT, PITCH>(s, ibuf + (long long)t * N3, z, ccols, nact, tid);
     __syncthreads();
     fft_lines<T, N, INV, false>(s, tw, line, g);
     fft_lines<T, N, INV, true>(s, tw, line, g);
@@ -219,12 +248,7 @@ __global__ void __launch_bounds__(plane_threads<N>())
   } else if constexpr (MODE == INV_ATOMIC) {
     const int item = t;
     const int tt = item / pm.kdim, k = item - tt * pm.kdim;
-    const cplx<T>* I = ibuf + (long long)item * N3 + (long long)z * N2;
-#pragma unroll 4
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      s[y * PITCH + x] = I[e];
-    }
+    stage_in_plane<T, N, NT, PITCH>(s, ibuf + (long long)item * N3, z, ccols, nact, tid);
     __syncthreads();
     fft_lines<T, N, INV, false>(s, tw, line, g);
     fft_lines<T, N, INV, true>(s, tw, line, g);
@@ -241,11 +265,7 @@ __global__ void __launch_bounds__(plane_threads<N>())
     for (int i = 0; i < EPT; ++i) acc[i] = {T(0), T(0)};
     for (int k = 0; k < pm.kdim; ++k) {
       const long long item = (long long)t * pm.kdim + k;
-      const cplx<T>* I = ibuf + item * N3 + (long long)z * N2;
-      for (int e = tid; e < N2; e += NT) {
-        const int y = e / N, x = e - y * N;
-        s[y * PITCH + x] = I[e];
-      }
+      stage_in_plane<T, N, NT, PITCH>(s, ibuf + item * N3, z, ccols, nact, tid);
       __syncthreads();
       fft_lines<T, N, INV, false>(s, tw, line, g);
       fft_lines<T, N, INV, true>(s, tw, line, g);

@@ -22,7 +22,10 @@ struct KernelChoice {
   int z = 1;
 };
 
-// Columns of the z pass that can be non-zero (see k_z_reg); nullptr = all.
+// Compact pair-density columns (see stage_in_plane in plane_kernels.cuh):
+// the nact column positions that can be non-zero; nullptr = full planes. The
+// three passes of a convolution get the same list; it is only given when the
+// register-resident z pass runs (the staged z pass takes full planes).
 struct ColumnList {
   const int* cols = nullptr;
   int nact = 0;
@@ -35,22 +38,22 @@ struct PlaneOps {
   KernelChoice kc;
   cudaError_t (*prepare)() = nullptr;
   void (*f_xy_fwd)(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
-                   const cplx<T>* tw, cudaStream_t st) = nullptr;
+                   const cplx<T>* tw, ColumnList cl, cudaStream_t st) = nullptr;
   void (*f_z)(KernelChoice kc, int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw,
               ColumnList cl, cudaStream_t st) = nullptr;
   void (*f_xy_inv)(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
-                   const cplx<T>* tw, cudaStream_t st) = nullptr;
+                   const cplx<T>* tw, ColumnList cl, cudaStream_t st) = nullptr;
   void xy_fwd(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
-              const cplx<T>* tw, cudaStream_t st) const {
-    f_xy_fwd(mode, qb, rb, pm, items, ibuf, tw, st);
+              const cplx<T>* tw, cudaStream_t st, ColumnList cl = ColumnList{}) const {
+    f_xy_fwd(mode, qb, rb, pm, items, ibuf, tw, cl, st);
   }
   void z(int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw, cudaStream_t st,
          ColumnList cl = ColumnList{}) const {
     f_z(kc, mode, ibuf, items, kern, kscale, tw, cl, st);
   }
   void xy_inv(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
-              const cplx<T>* tw, cudaStream_t st) const {
-    f_xy_inv(mode, ibuf, ob, pb, pm, targets, scale, tw, st);
+              const cplx<T>* tw, cudaStream_t st, ColumnList cl = ColumnList{}) const {
+    f_xy_inv(mode, ibuf, ob, pb, pm, targets, scale, tw, cl, st);
   }
 };
 
@@ -101,17 +104,18 @@ struct PlaneLaunch {
   }
 
   static void xy_fwd(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
-                     const cplx<T>* tw, cudaStream_t st) {
+                     const cplx<T>* tw, ColumnList cl, cudaStream_t st) {
     if (items <= 0) return;
     dim3 grid(N, items);
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
+    const double fout = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;  // share of the plane written
     prof_begin(KC_XY_FWD, st);
     if (mode == XY_PRODUCT)
-      k_xy_fwd<T, N, XY_PRODUCT><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
+      k_xy_fwd<T, N, XY_PRODUCT><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw, cl.cols, cl.nact);
     else
-      k_xy_fwd<T, N, XY_LOAD><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw);
+      k_xy_fwd<T, N, XY_LOAD><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw, cl.cols, cl.nact);
     note_launch();
-    prof_end(KC_XY_FWD, st, (mode == XY_PRODUCT ? 3.0 : 2.0) * F * items);
+    prof_end(KC_XY_FWD, st, ((mode == XY_PRODUCT ? 2.0 : 1.0) + fout) * F * items);
   }
 
   static void zl(KernelChoice kc, int mode, cplx<T>* ibuf, int items, const T* kern, T kscale, const cplx<T>* tw,
@@ -119,18 +123,22 @@ struct PlaneLaunch {
     if (items <= 0) return;
     dim3 grid(N, items);
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
+    const double fcol = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;
     prof_begin(KC_Z, st);
     bool done = false;
     if constexpr (z_in_registers<T, N>()) {
       if (kc.z == 1) {
         done = true;
-        dim3 g((N * N + ZREG_THREADS - 1) / ZREG_THREADS, items);
-        if (mode == Z_CONV)
-          k_z_reg<T, N, Z_CONV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, cl.cols, cl.nact);
+        const int ncol = cl.cols ? cl.nact : N * N;
+        dim3 g((ncol + ZREG_THREADS - 1) / ZREG_THREADS, items);
+        if (mode == Z_CONV && cl.cols)
+          k_z_reg<T, N, Z_CONV, true><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, cl.nact);
+        else if (mode == Z_CONV)
+          k_z_reg<T, N, Z_CONV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, 0);
         else if (mode == Z_FWD)
-          k_z_reg<T, N, Z_FWD><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, nullptr, 0);
+          k_z_reg<T, N, Z_FWD><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, 0);
         else
-          k_z_reg<T, N, Z_INV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, nullptr, 0);
+          k_z_reg<T, N, Z_INV><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, 0);
       }
     }
     if (!done) {
@@ -142,22 +150,25 @@ struct PlaneLaunch {
         k_z<T, N, Z_INV><<<grid, NT, SMEM, st>>>(ibuf, kern, kscale, tw);
     }
     note_launch();
-    prof_end(KC_Z, st, 2.0 * F * items + (mode == Z_CONV ? F / 2.0 : 0.0));
+    prof_end(KC_Z, st, fcol * (2.0 * F * items + (mode == Z_CONV ? F / 2.0 : 0.0)));
   }
 
   static void xy_inv(int mode, const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* pb, PairMap pm, int targets, T scale,
-                     const cplx<T>* tw, cudaStream_t st) {
+                     const cplx<T>* tw, ColumnList cl, cudaStream_t st) {
     if (targets <= 0) return;
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
+    const double fin = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;  // share of the plane read
     prof_begin(KC_XY_INV, st);
     if (mode == INV_ACCUM)
-      k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+      k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw, cl.cols, cl.nact);
     else if (mode == INV_ATOMIC)
-      k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+      k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw, cl.cols,
+                                                                            cl.nact);
     else
-      k_xy_inv<T, N, INV_WRITE><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw);
+      k_xy_inv<T, N, INV_WRITE><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw, cl.cols, cl.nact);
     note_launch();
-    prof_end(KC_XY_INV, st, mode == INV_WRITE ? 2.0 * F * targets : (2.0 * pm.kdim + 2.0) * F * targets);
+    prof_end(KC_XY_INV, st,
+             mode == INV_WRITE ? (fin + 1.0) * F * targets : ((fin + 1.0) * pm.kdim + 2.0) * F * targets);
   }
 
   static PlaneOps<T> ops() {

@@ -287,7 +287,9 @@ struct Buffers {
   void* grad_r = nullptr;      // [nocc_src][n^3] (adjoint)
   double* wdev = nullptr;      // [nb_max]
   int* dev_err = nullptr;      // set by a device wait that ran out of polls
-  int* zcols = nullptr;        // [n*n] z-pass column positions, the ncols_act possibly non-zero ones first
+  int* zcols = nullptr;        // [n*n] column positions, the ncols_act that a pair density can occupy first
+  void* kx_c = nullptr;        // [n][ncols_act] exchange kernel on those columns (compact pair densities)
+  void* kh_c = nullptr;        // [n][ncols_act] Hartree kernel on those columns
 };
 
 struct tddft_system {
@@ -299,7 +301,7 @@ struct tddft_system {
   int tile_targets = 16, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
-  bool prune = false;    // z pass of pair convolutions only on the columns a pair density can occupy
+  bool prune = true;     // pair convolutions keep only the columns a pair density can occupy (compact)
   // adaptively compressed exchange for the exchange term inside D (tddft_ace_build)
   bool ace_on = false;
   int n_ace = 0;
@@ -352,15 +354,30 @@ struct tddft_system {
   size_t rsz() const { return d.precision == TDDFT_PREC_FP64 ? 8 : 4; }
 };
 
-// Column list of the z pass of pair convolutions (all columns when pruning is off
-// or the grid would alias a pair density).
-static ColumnList pair_columns(const tddft_system* h) {
+template <typename T>
+static PlaneOps<T>& ops_of(tddft_system* h);
+
+// Compact pair-density columns for the three passes of a pair convolution
+// (plane_kernels.cuh): given when pruning is on, the grid does not alias pair
+// densities and the register-resident z pass runs; otherwise full planes.
+template <typename T>
+static ColumnList pair_columns(tddft_system* h) {
   ColumnList cl;
-  if (h->prune && h->b.zcols) {
+  const PlaneOps<T>& o = ops_of<T>(h);
+  if (h->prune && h->b.zcols && o.reg_ok && o.kc.z == 1) {
     cl.cols = h->b.zcols;
     cl.nact = h->ncols_act;
   }
   return cl;
+}
+
+// the convolution kernel in the layout of the column list (compact table when compact)
+template <typename T>
+static const T* pair_kernel(const tddft_system* h, const T* kern, const ColumnList& cl) {
+  if (!cl.cols) return kern;
+  if (kern == (const T*)h->b.kx) return (const T*)h->b.kx_c;
+  if (kern == (const T*)h->b.kh) return (const T*)h->b.kh_c;
+  return kern;
 }
 
 static tddft_status dalloc(tddft_system* h, void** p, size_t bytes) {
@@ -521,10 +538,12 @@ static tddft_status convolve_fields(tddft_system* h, const cplx<T>* src, int nf,
   for (int f0 = 0; f0 < nf; f0 += h->ibuf_fields) {
     const int cnt = std::min(h->ibuf_fields, nf - f0);
     PairMap pin{1, 0, 0, 0, f0, 0, 1, 0, 0, 0, 0, 0};
-    o.xy_fwd(XY_LOAD, nullptr, src, pin, cnt, ib, tw, st);
-    o.z(Z_CONV, ib, cnt, kern, kscale, tw, st, pair_columns(h));  // the fields are pair densities
+    // the fields are pair-density sums (Delta rho): compact when pruning; dst may equal src, never ib
+    const ColumnList cl = pair_columns<T>(h);
+    o.xy_fwd(XY_LOAD, nullptr, src, pin, cnt, ib, tw, st, cl);
+    o.z(Z_CONV, ib, cnt, pair_kernel<T>(h, kern, cl), kscale, tw, st, cl);
     PairMap pout{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, f0, 1};
-    o.xy_inv(INV_WRITE, ib, dst, nullptr, pout, cnt, T(1), tw, st);
+    o.xy_inv(INV_WRITE, ib, dst, nullptr, pout, cnt, T(1), tw, st, cl);
   }
   return check_launch("convolve_fields");
 }
@@ -547,6 +566,7 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
   PlaneOps<T>& o = ops_of<T>(h);
   const cplx<T>* tw = (const cplx<T>*)h->b.tw;
   cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+  const ColumnList cl = pair_columns<T>(h);  // pair densities: compact intermediates when pruning
   int TT = std::max(1, std::min(h->tile_targets, pg.ntargets));
   int KS = std::max(1, std::min(h->tile_sources, pg.nsources));
   while (TT * KS > h->ibuf_fields) {
@@ -570,9 +590,9 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
       pm.pt = pg.p_ts;
       pm.o0 = pg.o_base + t0 * pg.o_ts;
       pm.ot = pg.o_ts;
-      o.xy_fwd(XY_PRODUCT, qb, rb, pm, tt * kk, ib, tw, st);
-      o.z(Z_CONV, ib, tt * kk, kern, T(1), tw, st, pair_columns(h));
-      o.xy_inv(h->accumulate, ib, ob, pb, pm, tt, scale, tw, st);
+      o.xy_fwd(XY_PRODUCT, qb, rb, pm, tt * kk, ib, tw, st, cl);
+      o.z(Z_CONV, ib, tt * kk, pair_kernel<T>(h, kern, cl), T(1), tw, st, cl);
+      o.xy_inv(h->accumulate, ib, ob, pb, pm, tt, scale, tw, st, cl);
     }
   }
   return check_launch("pair_accumulate");
@@ -601,7 +621,7 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       pm.list = h->loc_list + pb.pair0;
       o.xy_fwd(XY_PRODUCT, phi, phi, pm, pb.np, ib, tw, st);
-      o.z(Z_CONV, ib, pb.np, (const T*)h->b.kx, T(1), tw, st, pair_columns(h));
+      o.z(Z_CONV, ib, pb.np, (const T*)h->b.kx, T(1), tw, st);  // full planes: the inverse runs in place
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, pb.np, T(1), tw, st);
       const size_t smem = (size_t)pb.np * K1D_SPARSE_PTS * sizeof(cplx<T>);
@@ -628,7 +648,7 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       // item = vi * tj + vj : Q = phi[j0 + vj], R = phi[i0 + vi]
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
       o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
-      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st, pair_columns(h));
+      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);  // full planes: the inverse runs in place
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
       o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
       {
@@ -819,9 +839,23 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   STATUS_TRY(dalloc(h, (void**)&B.pos, npw * sizeof(int)));
   STATUS_TRY(dalloc(h, &B.g2h, npw * rz));
   STATUS_TRY(dalloc(h, &B.eps, d.nocc_src * rz));
+  std::vector<T> kx_c, kh_c;
   if (!zcols.empty()) {
     STATUS_TRY(dalloc(h, (void**)&B.zcols, zcols.size() * sizeof(int)));
     CUDA_TRY(cudaMemcpyAsync(B.zcols, zcols.data(), zcols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // kernels on the compact columns: [z][c] = kappa at (z, zcols[c])
+    const int na = h->ncols_act;
+    kx_c.resize((size_t)n * na);
+    kh_c.resize((size_t)n * na);
+    for (int z = 0; z < n; ++z)
+      for (int c = 0; c < na; ++c) {
+        kx_c[(size_t)z * na + c] = kx[(size_t)z * n * n + zcols[c]];
+        kh_c[(size_t)z * na + c] = kh[(size_t)z * n * n + zcols[c]];
+      }
+    STATUS_TRY(dalloc(h, &B.kx_c, kx_c.size() * rz));
+    STATUS_TRY(dalloc(h, &B.kh_c, kh_c.size() * rz));
+    CUDA_TRY(cudaMemcpyAsync(B.kx_c, kx_c.data(), kx_c.size() * rz, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(B.kh_c, kh_c.data(), kh_c.size() * rz, cudaMemcpyHostToDevice, st));
   }
   CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * ez, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kx, kx.data(), n3 * rz, cudaMemcpyHostToDevice, st));
