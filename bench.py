@@ -35,8 +35,8 @@ WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 
 # sources it was taken on; reported as null when the sources have changed.
 NCU_TRAFFIC = {
     # profiles/plane_kernels_traffic_diamond64.md: one 128-pair launch of each class
-    "fa0566d1518a": {"xy_fwd_pair_product": 437.4e6, "z_kernel_multiply": 704.4e6,
-                     "xy_inv_remultiply_accumulate": 523.3e6},
+    "c7c2c2dc6de0": {"xy_fwd_pair_product": 255.3e6, "z_kernel_multiply": 394.6e6,
+                     "xy_inv_remultiply_accumulate": 334.3e6},
 }
 
 
