@@ -294,14 +294,36 @@ __host__ __device__ constexpr int plane_pitch() {
 
 // One DIF stage (forward) or its inverse over all N lines of a plane in smem.
 // Line l is a row (elements l*PITCH + i) when ROWS, a column (i*PITCH + l) otherwise.
-template <typename T, int N, int S, int DIR, bool ROWS>
-__device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, int g) {
+// The butterfly inputs come from ld(i) and the outputs go to st(i, v) (element i of
+// the line): by default the plane in shared memory; the first or last stage of a
+// pass can read from or write to global memory instead.
+template <typename T, int N, int ROWS>
+struct PlaneLd {
+  const cplx<T>* s;
+  int line;
+  __device__ __forceinline__ cplx<T> operator()(int i) const {
+    constexpr int PITCH = plane_pitch<N>();
+    return ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
+  }
+};
+template <typename T, int N, int ROWS>
+struct PlaneSt {
+  cplx<T>* s;
+  int line;
+  __device__ __forceinline__ void operator()(int i, cplx<T> v) const {
+    constexpr int PITCH = plane_pitch<N>();
+    if (ROWS) s[line * PITCH + i] = v;
+    else s[i * PITCH + line] = v;
+  }
+};
+
+template <typename T, int N, int S, int DIR, bool ROWS, typename LD, typename ST>
+__device__ __forceinline__ void stage_io(const cplx<T>* tw, int g, const LD& ld, const ST& st) {
   constexpr int R = Plan<N>::r[S];
   constexpr int L = plan_block<N, S>();
   constexpr int M = L / R;
   constexpr int G = lines_group<N>();
   constexpr int NB = N / R;         // butterflies per line
-  constexpr int PITCH = plane_pitch<N>();
   const cplx<T>* stw = tw + N + stage_tw_off<N, S>();  // [k2 * M + n1]
 #pragma unroll 1
   for (int j = g; j < NB; j += G) {
@@ -310,36 +332,29 @@ __device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, i
     cplx<T> v[R];
     if constexpr (DIR == FWD) {
 #pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) {
-        const int i = base + M * n2;
-        v[n2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
-      }
+      for (int n2 = 0; n2 < R; ++n2) v[n2] = ld(base + M * n2);
       dft<R, FWD>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2)
         if (n1) v[k2] = twmul<FWD>(v[k2], stw[k2 * M + n1]);
 #pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) {
-        const int i = base + M * k2;
-        if (ROWS) s[line * PITCH + i] = v[k2];
-        else s[i * PITCH + line] = v[k2];
-      }
+      for (int k2 = 0; k2 < R; ++k2) st(base + M * k2, v[k2]);
     } else {
 #pragma unroll
       for (int k2 = 0; k2 < R; ++k2) {
-        const int i = base + M * k2;
-        v[k2] = ROWS ? s[line * PITCH + i] : s[i * PITCH + line];
+        v[k2] = ld(base + M * k2);
         if (k2 && n1) v[k2] = twmul<INV>(v[k2], stw[k2 * M + n1]);
       }
       dft<R, INV>(v, TwPtr<T>{tw}, N / R);
 #pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) {
-        const int i = base + M * n2;
-        if (ROWS) s[line * PITCH + i] = v[n2];
-        else s[i * PITCH + line] = v[n2];
-      }
+      for (int n2 = 0; n2 < R; ++n2) st(base + M * n2, v[n2]);
     }
   }
+}
+
+template <typename T, int N, int S, int DIR, bool ROWS>
+__device__ __forceinline__ void stage(cplx<T>* s, const cplx<T>* tw, int line, int g) {
+  stage_io<T, N, S, DIR, ROWS>(tw, g, PlaneLd<T, N, ROWS>{s, line}, PlaneSt<T, N, ROWS>{s, line});
 }
 
 // Full 1D transform of all lines of the plane (syncs between stages and at the end).
@@ -351,6 +366,30 @@ __device__ __forceinline__ void fft_lines(cplx<T>* s, const cplx<T>* tw, int lin
     stage<T, N, st, DIR, ROWS>(s, tw, line, g);
     __syncthreads();
     fft_lines<T, N, DIR, ROWS, S + 1>(s, tw, line, g);
+  }
+}
+
+// The same with the first stage reading its inputs through ld (instead of the plane).
+template <typename T, int N, int DIR, bool ROWS, typename LD>
+__device__ __forceinline__ void fft_lines_from(cplx<T>* s, const cplx<T>* tw, int line, int g, const LD& ld) {
+  constexpr int NS = Plan<N>::S;
+  constexpr int st0 = (DIR == FWD) ? 0 : NS - 1;
+  stage_io<T, N, st0, DIR, ROWS>(tw, g, ld, PlaneSt<T, N, ROWS>{s, line});
+  __syncthreads();
+  if constexpr (NS > 1) fft_lines<T, N, DIR, ROWS, 1>(s, tw, line, g);
+}
+
+// The same with the last stage writing its outputs through st (no barrier after it).
+template <typename T, int N, int DIR, bool ROWS, typename ST, int S = 0>
+__device__ __forceinline__ void fft_lines_to(cplx<T>* s, const cplx<T>* tw, int line, int g, const ST& st) {
+  constexpr int NS = Plan<N>::S;
+  constexpr int stg = (DIR == FWD) ? S : (NS - 1 - S);
+  if constexpr (S + 1 < NS) {
+    stage<T, N, stg, DIR, ROWS>(s, tw, line, g);
+    __syncthreads();
+    fft_lines_to<T, N, DIR, ROWS, ST, S + 1>(s, tw, line, g, st);
+  } else {
+    stage_io<T, N, stg, DIR, ROWS>(tw, g, PlaneLd<T, N, ROWS>{s, line}, st);
   }
 }
 

@@ -66,6 +66,19 @@ __device__ __forceinline__ void stage_in_plane(cplx<T>* s, const cplx<T>* item, 
 constexpr int XY_LOAD = 0;
 constexpr int XY_PRODUCT = 1;
 
+// element i (= y) of column `line` of the plane conj(Q) * R (or R) in global memory
+template <typename T, int N, bool PRODUCT>
+struct PairLd {
+  const cplx<T>* Q;
+  const cplx<T>* R;
+  int line;
+  __device__ __forceinline__ cplx<T> operator()(int i) const {
+    const int e = i * N + line;
+    if constexpr (PRODUCT) return cmulc(Q[e], R[e]);
+    else return R[e];
+  }
+};
+
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(plane_threads<N>())
     k_xy_fwd(const cplx<T>* __restrict__ qb, const cplx<T>* __restrict__ rb, PairMap pm,
@@ -86,23 +99,13 @@ __global__ void __launch_bounds__(plane_threads<N>())
     ri = pr.y;
   }
   const cplx<T>* R = plane_ptr(rb, ri, z, N3, N2);
-  if constexpr (MODE == XY_PRODUCT) {
-    const cplx<T>* Q = plane_ptr(qb, qi, z, N3, N2);
-#pragma unroll 4
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      s[y * PITCH + x] = cmulc(Q[e], R[e]);
-    }
-  } else {
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      s[y * PITCH + x] = R[e];
-    }
-  }
-  __syncthreads();
+  const cplx<T>* Q = MODE == XY_PRODUCT ? plane_ptr(qb, qi, z, N3, N2) : nullptr;
+  __syncthreads();  // twiddle tables
+  // columns first, their first stage straight from global memory (consecutive threads take
+  // consecutive x), then the rows
   const int line = tid % N, g = tid / N;
+  fft_lines_from<T, N, FWD, false>(s, tw, line, g, PairLd<T, N, MODE == XY_PRODUCT>{Q, R, line});
   fft_lines<T, N, FWD, true>(s, tw, line, g);
-  fft_lines<T, N, FWD, false>(s, tw, line, g);
   if (ccols) {
     cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * nact;
 #pragma unroll 4
@@ -222,6 +225,26 @@ __device__ __forceinline__ void atomic_cadd<double>(cplx<double>* p, cplx<double
   atomicAdd(&p->y, v.y);
 }
 
+// Last stage of the inverse (columns, element i = y of column `line`) into global memory.
+template <typename T, int N>
+struct AtomicSt {  // O += scale * P * v with atomics
+  const cplx<T>* P;
+  cplx<T>* O;
+  T scale;
+  int line;
+  __device__ __forceinline__ void operator()(int i, cplx<T> v) const {
+    const int e = i * N + line;
+    atomic_cadd(O + e, cscale(cmul(P[e], v), scale));
+  }
+};
+template <typename T, int N>
+struct WriteSt {  // O = scale * v
+  cplx<T>* O;
+  T scale;
+  int line;
+  __device__ __forceinline__ void operator()(int i, cplx<T> v) const { O[i * N + line] = cscale(v, scale); }
+};
+
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(plane_threads<N>())
     k_xy_inv(const cplx<T>* ibuf, cplx<T>* ob, const cplx<T>* __restrict__ pb, PairMap pm,
@@ -236,29 +259,23 @@ __global__ void __launch_bounds__(plane_threads<N>())
   for (int i = tid; i < tw_table_len<N>(); i += NT) tw[i] = twg[i];
   const int line = tid % N, g = tid / N;
   cplx<T>* O = ob + (long long)(pm.o0 + (long long)t * pm.ot) * N3 + (long long)z * N2;
+  // rows first, then the columns, whose last stage writes to global memory directly
+  // (consecutive threads take consecutive x); every read of the input plane comes
+  // before the first barrier, so INV_WRITE may overwrite its own input (full planes)
   if constexpr (MODE == INV_WRITE) {
     stage_in_plane<T, N, NT, PITCH>(s, ibuf + (long long)t * N3, z, ccols, nact, tid);
     __syncthreads();
-    fft_lines<T, N, INV, false>(s, tw, line, g);
     fft_lines<T, N, INV, true>(s, tw, line, g);
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      O[e] = cscale(s[y * PITCH + x], scale);
-    }
+    fft_lines_to<T, N, INV, false>(s, tw, line, g, WriteSt<T, N>{O, scale, line});
   } else if constexpr (MODE == INV_ATOMIC) {
     const int item = t;
     const int tt = item / pm.kdim, k = item - tt * pm.kdim;
     stage_in_plane<T, N, NT, PITCH>(s, ibuf + (long long)item * N3, z, ccols, nact, tid);
     __syncthreads();
-    fft_lines<T, N, INV, false>(s, tw, line, g);
-    fft_lines<T, N, INV, true>(s, tw, line, g);
     const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)tt * pm.pt, z, N3, N2);
     cplx<T>* Oa = ob + (long long)(pm.o0 + (long long)tt * pm.ot) * N3 + (long long)z * N2;
-#pragma unroll 4
-    for (int e = tid; e < N2; e += NT) {
-      const int y = e / N, x = e - y * N;
-      atomic_cadd(Oa + e, cscale(cmul(P[e], s[y * PITCH + x]), scale));
-    }
+    fft_lines<T, N, INV, true>(s, tw, line, g);
+    fft_lines_to<T, N, INV, false>(s, tw, line, g, AtomicSt<T, N>{P, Oa, scale, line});
   } else {
     cplx<T> acc[EPT];
 #pragma unroll
