@@ -159,7 +159,10 @@ typedef struct tddft_tuning {
                        Register-resident z pass only. 0: full planes. -1 keeps the
                        value in set_tuning */
   int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
-                       (FP32, n <= 80). -1 keeps the value in set_tuning */
+                       (FP32, n <= 80); 2 (default where it exists: FP32, n = 16, 24,
+                       32, 48, 64, 72) as 1, with the compact pair-density
+                       convolutions on two threads per column. -1 keeps the value in
+                       set_tuning */
   int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with
                        split-precision TF32 products (hi*hi + hi*lo + lo*hi, FP32
                        accumulation in tensor memory); 0 SIMT FP32. FP64 handles

@@ -22,6 +22,14 @@ struct PairMap {
   const int2* list = nullptr;
 };
 
+// A copy of p that the compiler cannot relate to p: walking it again for the stores of a
+// column keeps one address live instead of one per element (runtime column strides).
+template <typename T>
+__device__ __forceinline__ T* opaque_ptr(T* p) {
+  asm volatile("" : "+l"(p));
+  return p;
+}
+
 template <typename T>
 __device__ __forceinline__ const cplx<T>* plane_ptr(const cplx<T>* base, long long field, int z, long long n3, int n2) {
   return base + field * n3 + (long long)z * n2;
@@ -198,6 +206,66 @@ __global__ void __launch_bounds__(ZREG_THREADS)
   if constexpr (MODE != Z_FWD) fft_reg<T, N, INV>(v, tw);
 #pragma unroll
   for (int z = 0; z < N; ++z) B[(long long)z * stride] = v[z];
+}
+
+// Register-resident z pass of compact pair densities with two threads per
+// column (half the registers of k_z_reg, so more warps per SM hide the memory
+// latency). Lanes 2c and 2c + 1 hold the points n and n + N/2 of column c; the
+// first radix-2 decimation-in-frequency butterfly is exchanged with __shfl_xor,
+// then each lane transforms its N/2 points in registers: lane h ends with the
+// frequencies 2 k' + h in the digit-reversed order of the N/2 plan, which is the
+// order of the kernel table kern2 [(h N/2 + j)][nact]. The inverse runs the same
+// steps backwards (decimation-in-time butterfly, conjugate twiddles).
+template <typename T, int N>
+__host__ __device__ constexpr bool z_pair_ok() {
+  return z_in_registers<T, N>() && N % 2 == 0 && tw_offset(N / 2) >= 0;
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> shfl_xor_c(cplx<T> v, int mask) {
+  return {__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask)};
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ZREG_THREADS)
+    k_z_pair(cplx<T>* __restrict__ ibuf, const T* __restrict__ kern2, T kscale, int nact) {
+  constexpr int H = N / 2;
+  constexpr long long N3 = (long long)N * N * N;
+  const int gt = blockIdx.x * ZREG_THREADS + threadIdx.x;
+  const int h = gt & 1;
+  int c = gt >> 1;
+  const bool valid = c < nact;
+  if (!valid) c = nact - 1;  // both lanes of every pair take part in the exchanges; no store
+  cplx<T>* B = ibuf + (long long)blockIdx.y * N3 + c + (long long)h * H * nact;
+  cplx<T> v[H];
+  {
+    const cplx<T>* p = B;
+#pragma unroll
+    for (int n = 0; n < H; ++n, p += nact) v[n] = *p;
+  }
+  TwConst<T, N> twn;
+#pragma unroll
+  for (int n = 0; n < H; ++n) {  // lane 0: x_n + x_(n+H); lane 1: (x_n - x_(n+H)) W_N^n
+    const cplx<T> p = shfl_xor_c(v[n], 1);
+    v[n] = h ? cmul(csub(p, v[n]), twn(n)) : cadd(v[n], p);
+  }
+  TwConst<T, H> twh;
+  fft_reg<T, H, FWD>(v, twh);
+  const T* K = opaque_ptr(kern2 + c + (long long)h * H * nact);
+#pragma unroll
+  for (int j = 0; j < H; ++j, K += nact) v[j] = cscale(v[j], *K * kscale);
+  fft_reg<T, H, INV>(v, twh);
+#pragma unroll
+  for (int n = 0; n < H; ++n) {  // lane 0: A_n + conj(W_N^n) B_n; lane 1: A_n - conj(W_N^n) B_n
+    const cplx<T> p = shfl_xor_c(v[n], 1);
+    const cplx<T> w = twn(n);
+    v[n] = h ? csub(p, cmulc(w, v[n])) : cadd(v[n], cmulc(w, p));
+  }
+  if (valid) {
+    cplx<T>* q = opaque_ptr(B);
+#pragma unroll
+    for (int n = 0; n < H; ++n, q += nact) *q = v[n];
+  }
 }
 
 // ---------------------------------------------------------------------------

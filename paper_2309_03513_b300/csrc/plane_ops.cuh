@@ -17,7 +17,8 @@ void note_launch();
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double bytes);
 
-// z = 0: shared-memory staged z pass; 1: register-resident columns (FP32, n <= 80).
+// z = 0: shared-memory staged z pass; 1: register-resident columns (FP32, n <= 80);
+// 2: as 1, with the compact pair-density convolutions on two threads per column.
 struct KernelChoice {
   int z = 1;
 };
@@ -34,7 +35,8 @@ struct ColumnList {
 template <typename T>
 struct PlaneOps {
   int n = 0;
-  bool reg_ok = false;  // the register-resident z pass exists for this (T, N)
+  bool reg_ok = false;   // the register-resident z pass exists for this (T, N)
+  bool pair_ok = false;  // the two-threads-per-column z pass exists for this (T, N)
   KernelChoice kc;
   cudaError_t (*prepare)() = nullptr;
   void (*f_xy_fwd)(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
@@ -100,6 +102,19 @@ struct PlaneLaunch {
       e = cudaMemcpyToSymbol(c_tw_f32, t.data(), N * sizeof(cplx<T>), tw_offset(N) * sizeof(cplx<T>));
     else
       e = cudaMemcpyToSymbol(c_tw_f64, t.data(), N * sizeof(cplx<T>), tw_offset(N) * sizeof(cplx<T>));
+    if (e != cudaSuccess) return e;
+    if constexpr (z_pair_ok<T, N>()) {  // the half-length table of the paired z pass
+      constexpr int H = N / 2;
+      std::vector<cplx<T>> th(H);
+      for (int k = 0; k < H; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)H;
+        th[k] = {(T)std::cos(ang), (T)std::sin(ang)};
+      }
+      if constexpr (sizeof(T) == 4)
+        e = cudaMemcpyToSymbol(c_tw_f32, th.data(), H * sizeof(cplx<T>), tw_offset(H) * sizeof(cplx<T>));
+      else
+        e = cudaMemcpyToSymbol(c_tw_f64, th.data(), H * sizeof(cplx<T>), tw_offset(H) * sizeof(cplx<T>));
+    }
     return e;
   }
 
@@ -126,8 +141,15 @@ struct PlaneLaunch {
     const double fcol = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;
     prof_begin(KC_Z, st);
     bool done = false;
+    if constexpr (z_pair_ok<T, N>()) {
+      if (kc.z == 2 && cl.cols && mode == Z_CONV) {
+        done = true;
+        dim3 g((2 * cl.nact + ZREG_THREADS - 1) / ZREG_THREADS, items);
+        k_z_pair<T, N><<<g, ZREG_THREADS, 0, st>>>(ibuf, kern, kscale, cl.nact);
+      }
+    }
     if constexpr (z_in_registers<T, N>()) {
-      if (kc.z == 1) {
+      if (!done && kc.z >= 1) {
         done = true;
         const int ncol = cl.cols ? cl.nact : N * N;
         dim3 g((ncol + ZREG_THREADS - 1) / ZREG_THREADS, items);
@@ -175,7 +197,8 @@ struct PlaneLaunch {
     PlaneOps<T> o;
     o.n = N;
     o.reg_ok = z_in_registers<T, N>();
-    o.kc.z = o.reg_ok ? 1 : 0;
+    o.pair_ok = z_pair_ok<T, N>();
+    o.kc.z = o.pair_ok ? 2 : (o.reg_ok ? 1 : 0);
     o.prepare = &prepare;
     o.f_xy_fwd = &xy_fwd;
     o.f_z = &zl;

@@ -290,6 +290,8 @@ struct Buffers {
   int* zcols = nullptr;        // [n*n] column positions, the ncols_act that a pair density can occupy first
   void* kx_c = nullptr;        // [n][ncols_act] exchange kernel on those columns (compact pair densities)
   void* kh_c = nullptr;        // [n][ncols_act] Hartree kernel on those columns
+  void* kx_p = nullptr;        // [n][ncols_act] exchange kernel in the order of the paired z pass
+  void* kh_p = nullptr;        // [n][ncols_act] Hartree kernel in that order
 };
 
 struct tddft_system {
@@ -364,7 +366,7 @@ template <typename T>
 static ColumnList pair_columns(tddft_system* h) {
   ColumnList cl;
   const PlaneOps<T>& o = ops_of<T>(h);
-  if (h->prune && h->b.zcols && o.reg_ok && o.kc.z == 1) {
+  if (h->prune && h->b.zcols && o.reg_ok && o.kc.z >= 1) {
     cl.cols = h->b.zcols;
     cl.nact = h->ncols_act;
   }
@@ -373,10 +375,12 @@ static ColumnList pair_columns(tddft_system* h) {
 
 // the convolution kernel in the layout of the column list (compact table when compact)
 template <typename T>
-static const T* pair_kernel(const tddft_system* h, const T* kern, const ColumnList& cl) {
+static const T* pair_kernel(tddft_system* h, const T* kern, const ColumnList& cl) {
   if (!cl.cols) return kern;
-  if (kern == (const T*)h->b.kx) return (const T*)h->b.kx_c;
-  if (kern == (const T*)h->b.kh) return (const T*)h->b.kh_c;
+  const PlaneOps<T>& o = ops_of<T>(h);
+  const bool paired = o.pair_ok && o.kc.z == 2 && h->b.kx_p;
+  if (kern == (const T*)h->b.kx) return (const T*)(paired ? h->b.kx_p : h->b.kx_c);
+  if (kern == (const T*)h->b.kh) return (const T*)(paired ? h->b.kh_p : h->b.kh_c);
   return kern;
 }
 
@@ -839,7 +843,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   STATUS_TRY(dalloc(h, (void**)&B.pos, npw * sizeof(int)));
   STATUS_TRY(dalloc(h, &B.g2h, npw * rz));
   STATUS_TRY(dalloc(h, &B.eps, d.nocc_src * rz));
-  std::vector<T> kx_c, kh_c;
+  std::vector<T> kx_c, kh_c, kx_p, kh_p;
   if (!zcols.empty()) {
     STATUS_TRY(dalloc(h, (void**)&B.zcols, zcols.size() * sizeof(int)));
     CUDA_TRY(cudaMemcpyAsync(B.zcols, zcols.data(), zcols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -856,6 +860,28 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
     STATUS_TRY(dalloc(h, &B.kh_c, kh_c.size() * rz));
     CUDA_TRY(cudaMemcpyAsync(B.kx_c, kx_c.data(), kx_c.size() * rz, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(B.kh_c, kh_c.data(), kh_c.size() * rz, cudaMemcpyHostToDevice, st));
+    if (o.pair_ok) {
+      // paired z pass: lane h, register j holds k_z = 2 k' + h, with k' the natural index
+      // of position j of the N/2 plan's digit-reversed order
+      const int hn = n / 2;
+      const std::vector<int> rad_h = plan_radices(hn);
+      std::vector<int> irev_h(hn);
+      for (int k = 0; k < hn; ++k) irev_h[dif_position(k, rad_h, hn)] = k;
+      kx_p.resize((size_t)n * na);
+      kh_p.resize((size_t)n * na);
+      for (int hh = 0; hh < 2; ++hh)
+        for (int j = 0; j < hn; ++j) {
+          const int pz = rev[2 * irev_h[j] + hh];
+          for (int c = 0; c < na; ++c) {
+            kx_p[(size_t)(hh * hn + j) * na + c] = kx_c[(size_t)pz * na + c];
+            kh_p[(size_t)(hh * hn + j) * na + c] = kh_c[(size_t)pz * na + c];
+          }
+        }
+      STATUS_TRY(dalloc(h, &B.kx_p, kx_p.size() * rz));
+      STATUS_TRY(dalloc(h, &B.kh_p, kh_p.size() * rz));
+      CUDA_TRY(cudaMemcpyAsync(B.kx_p, kx_p.data(), kx_p.size() * rz, cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(B.kh_p, kh_p.data(), kh_p.size() * rz, cudaMemcpyHostToDevice, st));
+    }
   }
   CUDA_TRY(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * ez, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.kx, kx.data(), n3 * rz, cudaMemcpyHostToDevice, st));
@@ -1709,9 +1735,11 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->k1d_sparse = t->k1d_sparse;
   }
   if (t->z_kernel >= 0) {
-    if (t->z_kernel > 1) return fail(TDDFT_EINVAL, "z_kernel must be 0 or 1");
+    if (t->z_kernel > 2) return fail(TDDFT_EINVAL, "z_kernel must be 0, 1 or 2");
     const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
+    const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
     if (t->z_kernel && !reg) return fail(TDDFT_EINVAL, "register-resident passes need FP32 and n <= 80");
+    if (t->z_kernel == 2 && !pair) return fail(TDDFT_EINVAL, "the paired z pass needs a supported n / 2");
     h->ops32.kc.z = t->z_kernel;
     h->ops64.kc.z = t->z_kernel;
   }

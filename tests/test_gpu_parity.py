@@ -108,13 +108,13 @@ def test_ragged_tiles_give_the_same_result(torch):
 
 @pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0), (32, 9.0, 12.0)])
 def test_kernel_variants_fp32(torch, n, a, ecut):
-    """Every plane-pass variant (column pruning on / off, staged / register-resident
-    z pass, loop / atomic accumulation) gives the oracle's L. The 24^3 grid aliases
+    """Every plane-pass variant (compact pair densities on / off, staged / register-resident /
+    paired register z pass, loop / atomic accumulation) gives the oracle's L. The 24^3 grid aliases
     pair densities (pruning stays off there); 72^3 and 32^3 do not."""
     wl = _workload(n, a, ecut, 6, 2, seed=15)
     want = O.system_from_workload(wl).apply(wl.X)
     for prune in (0, 1):
-        for z in (0, 1):
+        for z in (0, 1, 2):
             for acc in (0, 1):
                 got = _run(torch, wl, T.PREC_FP32, tiling=dict(targets=3, sources=4, k1d_block=5, accumulate=acc,
                                                               prune=prune, z_kernel=z))
@@ -142,6 +142,7 @@ def test_tuning_fields_round_trip(torch):
     s = T.system_from_workload(wl, precision=T.PREC_FP32)
     for kw in (dict(targets=4), dict(sources=2), dict(k1d_block=8), dict(accumulate=0), dict(accumulate=1),
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
+               dict(z_kernel=2),
                dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2)):
         before = s.get_tuning()
         s.set_tuning(**kw)
