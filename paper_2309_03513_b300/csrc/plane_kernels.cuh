@@ -43,18 +43,18 @@ __device__ __forceinline__ const cplx<T>* plane_ptr(const cplx<T>* base, long lo
 // the digit-reversed positions), at item base + z * nact + c. The other columns
 // are zero and are neither stored, transformed along z nor read back.
 // Plane z of an item (full or compact) into the shared-memory plane s (row pitch PITCH).
+// Compact: ccols lists all N^2 positions, the nact stored columns first, so every
+// position of the plane is written once (data or zero).
 template <typename T, int N, int NT, int PITCH>
 __device__ __forceinline__ void stage_in_plane(cplx<T>* s, const cplx<T>* item, int z, const int* __restrict__ ccols,
                                                int nact, int tid) {
   constexpr int N2 = N * N;
   if (ccols) {
-    for (int e = tid; e < N * PITCH; e += NT) s[e] = cplx<T>{T(0), T(0)};
-    __syncthreads();
     const cplx<T>* I = item + (long long)z * nact;
 #pragma unroll 4
-    for (int c = tid; c < nact; c += NT) {
+    for (int c = tid; c < N2; c += NT) {
       const int q = ccols[c], y = q / N;
-      s[y * PITCH + q - y * N] = I[c];
+      s[y * PITCH + q - y * N] = c < nact ? I[c] : cplx<T>{T(0), T(0)};
     }
   } else {
     const cplx<T>* I = item + (long long)z * N2;

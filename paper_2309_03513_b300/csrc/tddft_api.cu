@@ -300,7 +300,7 @@ struct tddft_system {
   long long n3 = 0;
   int nb_chunk = 0;
   int ibuf_fields = 0;
-  int tile_targets = 16, tile_sources = 8, k1d_block = 16;
+  int tile_targets = 32, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
   bool prune = true;     // pair convolutions keep only the columns a pair density can occupy (compact)
@@ -1852,8 +1852,8 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
   struct Cand {
     int tt, ks, acc, kb;
   };
-  const Cand cands[] = {{16, 8, 1, 16}, {8, 8, 1, 16}, {32, 4, 1, 16}, {16, 4, 1, 16}, {4, 16, 1, 16},
-                        {16, 8, 0, 16},  {8, 8, 1, 8}};
+  const Cand cands[] = {{32, 8, 1, 16}, {16, 8, 1, 16}, {8, 8, 1, 16}, {32, 4, 1, 16}, {64, 4, 1, 16},
+                        {16, 16, 1, 16}, {32, 8, 0, 16}, {8, 8, 1, 8}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
