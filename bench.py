@@ -34,9 +34,9 @@ WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
 # sources it was taken on; reported as null when the sources have changed.
 NCU_TRAFFIC = {
-    # profiles/plane_kernels_traffic_diamond64.md: one 128-pair launch of each class
-    "3d7eda415d81": {"xy_fwd_pair_product": 253.8e6, "z_kernel_multiply": 368.2e6,
-                     "xy_inv_remultiply_accumulate": 333.1e6},
+    # profiles/plane_kernels_traffic_diamond64.md: one 256-pair launch of each class
+    "eaaf4f527de1": {"xy_fwd_pair_product": 538.4e6, "z_kernel_multiply": 792.8e6,
+                     "xy_inv_remultiply_accumulate": 661.7e6},
 }
 
 
