@@ -831,6 +831,22 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
         if (mx * mx + my * my <= r2) zcols.push_back(py * n + px);
         else rest.push_back(py * n + px);
       }
+    // Within each part, interleave the 16 shared-memory bank classes of the positions
+    // (8-byte words y * (n + 1) + x in the plane kernels): the compact planes are staged
+    // with 16 consecutive list entries per half-warp, which then hit distinct banks.
+    auto interleave_banks = [n](std::vector<int>& v) {
+      std::vector<std::vector<int>> cls(16);
+      for (int q : v) cls[((q / n) * (n + 1) + q % n) % 16].push_back(q);
+      std::vector<int> out;
+      out.reserve(v.size());
+      std::vector<size_t> at(16, 0);
+      while (out.size() < v.size())
+        for (int k = 0; k < 16; ++k)
+          if (at[k] < cls[k].size()) out.push_back(cls[k][at[k]++]);
+      v.swap(out);
+    };
+    interleave_banks(zcols);
+    interleave_banks(rest);
     h->ncols_act = (int)zcols.size();
     zcols.insert(zcols.end(), rest.begin(), rest.end());
   }
