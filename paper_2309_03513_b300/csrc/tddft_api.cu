@@ -2313,9 +2313,10 @@ __global__ void k_normalize(cplx<double>* __restrict__ x, const double* __restri
 }
 
 // t = r / d with d = |G|^2/2 - eps_v - theta, |d| clamped to >= 0.1 Ha (sign kept)
-__global__ void k_precondition(const cplx<double>* __restrict__ r, const double* __restrict__ g2h,
+// (t may equal r: element-wise, in place)
+__global__ void k_precondition(const cplx<double>* r, const double* __restrict__ g2h,
                                const double* __restrict__ eps, double theta, int npw, long long len,
-                               cplx<double>* __restrict__ t) {
+                               cplx<double>* t) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
     const long long v = i / npw, g = i - v * npw;
     double d = g2h[g] - eps[v] - theta;
