@@ -697,3 +697,92 @@ def test_density_response_free_electron_closed_form():
             svv = np.vdot(X[0, v], X[0, vp])
             want -= (np.conj(ph[occ[v]]) * ph[occ[vp]] * svv).real / omega
     assert np.allclose(got, want, atol=1e-12 * np.abs(want).max())
+
+
+# --------------------------------------------------------------------------
+# TDA = CIS: L on the unoccupied space against matrix elements assembled
+# from brute-force two-electron integrals (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+def _grid_points(n):
+    """Integer grid coordinates [N_r, 3] = (j_x, j_y, j_z), rows in [z][y][x] order."""
+    jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return np.stack([jx.ravel(), jy.ravel(), jz.ravel()], axis=1)
+
+
+def _orbitals_on_grid(c, miller, n, a):
+    """psi(r_j) = Omega^{-1/2} sum_G c(G) exp(2 pi i m.j / N) by explicit sums; c is [..., npw]."""
+    ph = (_grid_points(n) @ miller.T) % n  # exact integer phase index
+    E = np.exp(2j * math.pi * ph / n) / math.sqrt(a ** 3)  # [N_r, npw]
+    return np.asarray(c) @ E.T
+
+
+def _kernel_matrix(n, a, g0):
+    """Kmat[j, k] = N_r^{-1} sum_m kappa(G_m) exp(2 pi i m.(j - k)/N) over the FFT cube, with
+    kappa = 4 pi / |G|^2 and kappa(0) = g0: the periodic Coulomb kernel between two grid points."""
+    h = n // 2
+    J = _grid_points(n)
+    M = J - h  # every m in [-N/2, N/2)^3 exactly once
+    g2 = (2 * math.pi / a) ** 2 * np.sum(M * M, axis=1).astype(np.float64)
+    kap = np.where(g2 > 0, 4 * math.pi / np.where(g2 > 0, g2, 1.0), g0)
+    # kappa(m) = kappa(-m mod N) on the cube, so the sine parts cancel and K is real
+    Kd = np.cos(2 * math.pi * ((J @ M.T) % n) / n) @ kap / n ** 3
+    D = (J[:, None, :] - J[None, :, :]) % n
+    return Kd[(D[..., 2] * n + D[..., 1]) * n + D[..., 0]]
+
+
+@pytest.mark.parametrize("sf", [False, True])
+def test_tda_equals_cis_with_brute_force_integrals(sf):
+    """Matrix of L in the basis e_i (x) psi_a (occupied i of the source spin, psi_a an orthonormal
+    basis of the target spin's unoccupied plane-wave space) against the CIS matrix
+        A_{ia,jb} = delta_ij [<a|T + V_loc + alpha V_X|b> - eps_i delta_ab]
+                    + (a i|j b)_H + <a i|f_xc|j b> - alpha (a b|j i)_x,
+    <a|V_X|b> = -sum_w (a w|w b)_x, with every two-electron integral
+    (p q|r s) = (Omega/N_r) sum_{j,k} p*(r_j) q(r_j) K(r_j - r_k) r*(r_k) s(r_k)
+    summed pointwise over the grid with the real-space kernel K; no Hartree term in the spin-flip
+    case (Eq. 21)."""
+    n, a, ecut = 8, 6.0, 2.5
+    wl, S = _tiny(spin_flip=sf, n=n, a=a, ecut=ecut, nocc=3 if sf else 2, nocc_tgt=2, nb=1, seed=31)
+    H, Qc = S.dense_matrix()
+    miller = S.grid.miller
+    nr, vol = n ** 3, a ** 3
+    w_r = vol / nr
+    psi = _orbitals_on_grid(Qc.T, miller, n, a)          # [nc, N_r] unoccupied basis
+    phs = _orbitals_on_grid(wl.phi_src, miller, n, a)    # [no, N_r] source occupied
+    pht = _orbitals_on_grid(wl.phi_tgt, miller, n, a)    # [nt, N_r] target occupied
+    nc, no = psi.shape[0], phs.shape[0]
+    Kx = _kernel_matrix(n, a, wl.kx_g0)
+    Kh = _kernel_matrix(n, a, 0.0)
+    vloc = wl.vloc.ravel()
+    fxc = wl.fxc.ravel()
+
+    def eri(P, Q, K):
+        """(P|Q) for pair densities P [.., N_r] (= p* q) and Q [.., N_r] (= r* s)."""
+        P2, Q2 = P.reshape(-1, nr), Q.reshape(-1, nr)
+        return w_r * (P2 @ K @ Q2.T).reshape(P.shape[:-1] + Q.shape[:-1])
+
+    g2 = (2 * math.pi / a) ** 2 * np.sum(miller.astype(np.float64) ** 2, axis=1)
+    T = Qc.conj().T @ (0.5 * g2[:, None] * Qc)
+    V = w_r * (psi.conj() * vloc) @ psi.T
+    aw = psi.conj()[:, None, :] * pht[None, :, :]        # [a, w] = psi_a* phi_w
+    wb = pht.conj()[:, None, :] * psi[None, :, :]        # [w, b] = phi_w* psi_b
+    VX = -np.einsum("awwb->ab", eri(aw, wb, Kx))
+    ai = psi.conj()[:, None, :] * phs[None, :, :]        # [a, i]
+    jb = phs.conj()[:, None, :] * psi[None, :, :]        # [j, b]
+    ab = psi.conj()[:, None, :] * psi[None, :, :]        # [a, b]
+    ji = phs.conj()[:, None, :] * phs[None, :, :]        # [j, i]
+
+    A = np.zeros((no, nc, no, nc), dtype=np.complex128)
+    for i in range(no):
+        A[i, :, i, :] += T + V + wl.alpha * VX - wl.eps_src[i] * np.eye(nc)
+    if not sf:
+        A += eri(ai, jb, Kh).transpose(1, 0, 2, 3)       # (a i|j b)_H -> [i, a, j, b]
+    F = w_r * (ai.reshape(-1, nr) * fxc) @ jb.reshape(-1, nr).T
+    A += F.reshape(nc, no, no, nc).transpose(1, 0, 2, 3)
+    A -= wl.alpha * eri(ab, ji, Kx).transpose(3, 0, 2, 1)  # (a b|j i)_x [a, b, j, i] -> [i, a, j, b]
+    A = A.reshape(no * nc, no * nc)
+
+    assert np.abs(H - A).max() < 1e-11 * np.abs(A).max(), np.abs(H - A).max()
+    # the three two-electron blocks are each far above that tolerance
+    for blk in (wl.alpha * VX, wl.alpha * eri(ab, ji, Kx), F):
+        assert np.abs(blk).max() > 1e-4 * np.abs(A).max()
