@@ -143,6 +143,38 @@ def test_coulomb_energy_of_gaussian_charges():
     assert abs(E_self - t2.sum() / a ** 3) < 1e-12 * abs(E_self)
 
 
+def test_coulomb_energy_of_a_neutral_gaussian_pair_against_the_isolated_closed_form():
+    """Periodic grid energy (1/2) <rho|Conv_H[rho]> of a +1/-1 pair of Gaussians (width s, separation d)
+    against the isolated Coulomb energy 1/(s sqrt(pi)) - erf(d/(2s))/d. With kappa(0) = 0 the periodic
+    energy is the isolated one minus the dipole term 2 pi d^2 / (3 Omega) of a cubic lattice; what is
+    left falls as the fifth power of the cell side (quadrupole-order image terms)."""
+    s = 1.0
+    Ra = np.array([8.1, 9.3, 10.2])
+    Rb = Ra + np.array([1.8, 1.6, 1.78])
+    d = float(np.linalg.norm(Rb - Ra))
+    E_iso = 1.0 / (s * math.sqrt(math.pi)) - math.erf(d / (2 * s)) / d
+    resid = {}
+    for n, a in ((48, 20.0), (64, 26.0)):
+        g = O.Grid(n, a, 5.0)
+        jz, jy, jx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        r = np.stack([jx, jy, jz], axis=-1) * (a / n)
+
+        def gauss(R):
+            out = np.zeros((n,) * 3)
+            for t in itertools.product((-1, 0, 1), repeat=3):
+                dd = r - R - np.array(t) * a
+                out += np.exp(-np.sum(dd * dd, axis=-1) / (2 * s * s))
+            return out / (2 * math.pi * s * s) ** 1.5
+
+        rho = gauss(Ra) - gauss(Rb)
+        E = 0.5 * g.inner(rho, g.conv(rho, g.coulomb(0.0))).real
+        dip = 2 * math.pi * d * d / (3 * a ** 3)
+        resid[a] = E - (E_iso - dip)
+        assert abs(resid[a]) < 0.03 * dip, (a, E, E_iso, dip)
+    ratio = resid[20.0] / resid[26.0]
+    assert abs(ratio / (26.0 / 20.0) ** 5 - 1.0) < 0.05, ratio
+
+
 # --------------------------------------------------------------------------
 # whole operator: free-electron closed form
 # --------------------------------------------------------------------------
