@@ -397,6 +397,25 @@ static tddft_status dalloc(tddft_system* h, void** p, size_t bytes) {
   return TDDFT_OK;
 }
 
+namespace {
+// temporaries of one call, released on every exit path
+struct TempAllocs {
+  std::vector<void*> p;
+  tddft_status get(void** out, size_t bytes) {
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    p.push_back(*out);
+    return TDDFT_OK;
+  }
+  ~TempAllocs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+}  // namespace
+
 template <typename T>
 static PlaneOps<T>& ops_of(tddft_system* h);
 template <>
@@ -963,10 +982,9 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   STATUS_TRY(check_launch("orbital cast"));
 
   // local fields
+  TempAllocs tmp;
   double* tmp64 = nullptr;
-  if (in->vloc || in->fxc) {
-    CUDA_TRY(cudaMalloc((void**)&tmp64, n3 * sizeof(double)));
-  }
+  if (in->vloc || in->fxc) STATUS_TRY(tmp.get((void**)&tmp64, n3 * sizeof(double)));
   if (in->vloc) {
     STATUS_TRY(dalloc(h, &B.vloc, n3 * rz));
     CUDA_TRY(cudaMemcpyAsync(tmp64, in->vloc, n3 * 8, cudaMemcpyHostToDevice, st));
@@ -979,7 +997,6 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
     { k_real_cast<T><<<grid_for(n3, 256), 256, 0, st>>>(tmp64, (T*)B.fxc, n3); note_launch(); }
     CUDA_TRY(cudaStreamSynchronize(st));
   }
-  if (tmp64) CUDA_TRY(cudaFree(tmp64));
 
   // workspace: chunk of trial vectors and the pair-batch buffer, bounded to leave
   // room on the device (cfg-independent: at most ~60% of free memory)
@@ -1050,24 +1067,6 @@ static std::vector<std::complex<double>> lower_inverse(int n, const std::vector<
   return X;
 }
 
-namespace {
-// temporaries of one ACE build, released on every exit path
-struct TempAllocs {
-  std::vector<void*> p;
-  tddft_status get(void** out, size_t bytes) {
-    cudaError_t e = cudaMalloc(out, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-    }
-    p.push_back(*out);
-    return TDDFT_OK;
-  }
-  ~TempAllocs() {
-    for (void* q : p) cudaFree(q);
-  }
-};
-}  // namespace
 
 template <typename T>
 static tddft_status ace_build_impl(tddft_system* h, int n_extra, const double* extra, cudaStream_t st) {
