@@ -172,6 +172,18 @@ typedef struct tddft_tuning {
                        list; 0 blocks of k1d_block x k1d_block pairs, blocks without a
                        kept pair skipped; 2 automatic (pair list when fewer than half
                        of the pairs are kept). -1 keeps the value in set_tuning */
+  int k1d_cache;    /* 1: K1d reads tau_vv' = Conv_x[phi_v'^* phi_v] (Eq. 6) of every
+                       unordered pair from device memory instead of convolving the
+                       pairs in every application. The tau depend on the occupied
+                       orbitals only; setting 1 builds them once (synchronises; the
+                       rows of the diagonal 16 x 16 blocks are stored in both orders:
+                       about nocc (nocc + 16) / 2 fields of n^3 points, 27.5 GB for 128
+                       orbitals on 72^3 in FP32) and fails with TDDFT_ENOMEM when they
+                       do not fit, or with TDDFT_ENOTSUP while the localised frame is on
+                       (the truncated K1d of that frame recomputes its pairs; the stored
+                       tau serve again once it is switched off). The result equals that
+                       of the recomputing path up to rounding. 0 (default): recompute;
+                       releases the stored tau. -1 keeps the value in set_tuning */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

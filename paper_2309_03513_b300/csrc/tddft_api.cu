@@ -333,6 +333,11 @@ struct tddft_system {
   int2* loc_ent = nullptr;     // (n << 1 | conj, slot)
   bool loc_sparse_auto = false;
   int k1d_sparse = 2;          // 0 blocks, 1 pair list, 2 automatic
+  // K1d from stored tau (tuning.k1d_cache): tau_vv' of every unordered block pair of the source
+  // orbitals, device-resident; built from the orbitals of the given frame
+  bool k1d_cache = false;
+  void* tau_cache = nullptr;
+  size_t tau_cache_bytes = 0;
   std::vector<double> eps64;  // the given eigenvalues
   int ncols_act = 0;     // number of such columns (0 = no list: the grid aliases pair densities)
   int nsplit = 1;
@@ -628,6 +633,44 @@ constexpr int K1D_SPARSE_PTS = 32;
 template <typename T>
 constexpr int k1d_sparse_np_max() { return sizeof(T) == 4 ? 384 : 192; }
 
+// Stored tau: Conv_x[conj(phi_v') phi_v] of every unordered block pair (I <= J) of
+// K1D_CACHE_BLOCK source orbitals, block pair after block pair (I, then J), each block pair
+// in the field order k_k1d_contract reads (vi * tj + vj). The tau depend on the occupied
+// orbitals only, so one build serves every application.
+constexpr int K1D_CACHE_BLOCK = 16;
+
+static size_t tau_cache_fields(int nocc) {
+  size_t f = 0;
+  for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {
+    const int ti = std::min(K1D_CACHE_BLOCK, nocc - i0);
+    for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) f += (size_t)ti * std::min(K1D_CACHE_BLOCK, nocc - j0);
+  }
+  return f;
+}
+
+template <typename T>
+static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
+  PlaneOps<T>& o = ops_of<T>(h);
+  const cplx<T>* tw = (const cplx<T>*)h->b.tw;
+  const cplx<T>* phi = (const cplx<T>*)h->b.phi_src_r;
+  const int nocc = h->d.nocc_src;
+  cplx<T>* blk = (cplx<T>*)h->tau_cache;
+  for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {
+    const int ti = std::min(K1D_CACHE_BLOCK, nocc - i0);
+    for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) {
+      const int tj = std::min(K1D_CACHE_BLOCK, nocc - j0);
+      // the pair convolutions of k1d_term, written straight into the block pair's slot
+      PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
+      o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, blk, tw, st);
+      o.z(Z_CONV, blk, ti * tj, (const T*)h->b.kx, T(1), tw, st);
+      PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+      o.xy_inv(INV_WRITE, blk, blk, nullptr, pw, ti * tj, T(1), tw, st);
+      blk += (long long)ti * tj * h->n3;
+    }
+  }
+  return check_launch("tau cache build");
+}
+
 template <typename T>
 static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   PlaneOps<T>& o = ops_of<T>(h);
@@ -654,6 +697,23 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
           pb.nrows, h->loc_ent, nocc, nbc, s, h->n3); note_launch(); }
     }
     return check_launch("k1d_term (pair list)");
+  }
+  if (h->k1d_cache && h->tau_cache && !h->loc_on) {
+    // stored tau: the contraction alone, block pair after block pair in the build order
+    const cplx<T>* blk = (const cplx<T>*)h->tau_cache;
+    for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {
+      const int ti = std::min(K1D_CACHE_BLOCK, nocc - i0);
+      for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) {
+        const int tj = std::min(K1D_CACHE_BLOCK, nocc - j0);
+        constexpr int KB = K1D_CACHE_BLOCK, PTS = 32;
+        const size_t smem = (size_t)KB * KB * PTS * sizeof(cplx<T>);
+        const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
+        { k_k1d_contract<T, KB, PTS><<<blocks, K1D_THREADS, smem, st>>>(
+            blk, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3, nullptr); note_launch(); }
+        blk += (long long)ti * tj * h->n3;
+      }
+    }
+    return check_launch("k1d_term (stored tau)");
   }
   // truncated pairs of the localised frame: blocks without a kept pair are skipped
   const unsigned char* keep = h->loc_on ? h->loc_keep : nullptr;
@@ -1664,6 +1724,7 @@ tddft_status tddft_destroy(tddft_handle h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocations) cudaFree(p);
+  if (h->tau_cache) cudaFree(h->tau_cache);
   delete h;
   return TDDFT_OK;
 }
@@ -1726,6 +1787,57 @@ tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
   return TDDFT_OK;
 }
 
+// tuning.k1d_cache: build the stored tau (synchronises) or release them
+static tddft_status set_tau_cache(tddft_system* h, bool on) {
+  if (!on) {
+    if (h->tau_cache) {
+      CUDA_TRY(cudaFree(h->tau_cache));
+      h->bytes -= h->tau_cache_bytes;
+    }
+    h->tau_cache = nullptr;
+    h->tau_cache_bytes = 0;
+    h->k1d_cache = false;
+    return TDDFT_OK;
+  }
+  if (h->tau_cache) {
+    h->k1d_cache = true;
+    return TDDFT_OK;
+  }
+  // the source orbitals must be the given ones (the localised frame replaces them while it is on)
+  if (h->loc_on) return fail(TDDFT_ENOTSUP, "stored tau are built in the given frame: switch localisation off first");
+  const size_t bytes = tau_cache_fields(h->d.nocc_src) * (size_t)h->n3 * h->esz();
+  cudaError_t e = cudaMalloc(&h->tau_cache, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->tau_cache = nullptr;
+    return fail(TDDFT_ENOMEM, "stored tau need " + std::to_string(bytes) + " bytes of device memory: " +
+                                  cudaGetErrorString(e));
+  }
+  h->tau_cache_bytes = bytes;
+  h->bytes += bytes;
+  tddft_status s = ensure_capture_stream(h);
+  if (s == TDDFT_OK) {
+    // work queued on other streams (orbital loads) completes first; the build runs on the handle's stream
+    cudaError_t e2 = cudaDeviceSynchronize();
+    if (e2 != cudaSuccess) s = fail(TDDFT_ECUDA, std::string("before the tau build: ") + cudaGetErrorString(e2));
+  }
+  if (s == TDDFT_OK)
+    s = h->d.precision == TDDFT_PREC_FP64 ? build_tau_cache<double>(h, h->cap) : build_tau_cache<float>(h, h->cap);
+  if (s == TDDFT_OK) {
+    cudaError_t e3 = cudaStreamSynchronize(h->cap);
+    if (e3 != cudaSuccess) s = fail(TDDFT_ECUDA, std::string("tau build: ") + cudaGetErrorString(e3));
+  }
+  if (s != TDDFT_OK) {
+    cudaFree(h->tau_cache);
+    h->bytes -= bytes;
+    h->tau_cache = nullptr;
+    h->tau_cache_bytes = 0;
+    return s;
+  }
+  h->k1d_cache = true;
+  return TDDFT_OK;
+}
+
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
   if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
   if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 16)
@@ -1758,8 +1870,13 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->ops32.kc.z = t->z_kernel;
     h->ops64.kc.z = t->z_kernel;
   }
+  tddft_status cs = TDDFT_OK;
+  if (t->k1d_cache >= 0) {
+    if (t->k1d_cache > 1) cs = fail(TDDFT_EINVAL, "k1d_cache must be 0 or 1");
+    else cs = set_tau_cache(h, t->k1d_cache == 1);
+  }
   drop_graphs(h);  // the schedule changed: the next graph call captures again
-  return TDDFT_OK;
+  return cs;
 }
 
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
@@ -1775,6 +1892,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->z_kernel = kc.z;
   t->projector = h->projector_tc;
   t->k1d_sparse = h->k1d_sparse;
+  t->k1d_cache = h->k1d_cache ? 1 : 0;
   return TDDFT_OK;
 }
 

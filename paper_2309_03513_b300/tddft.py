@@ -70,7 +70,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int),
-                ("k1d_sparse", ctypes.c_int)]
+                ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int)]
 
 
 class ZvectorOpts(ctypes.Structure):
@@ -260,10 +260,18 @@ class LiouvilleSystem:
         _check(load().tddft_set_terms(self._h, int(mask)), "tddft_set_terms")
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
-                   graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1):
+                   graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1,
+                   k1d_cache: int = -1):
         t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
-                   int(z_kernel), int(projector), int(k1d_sparse))
+                   int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
+
+    def query(self) -> dict:
+        """Sizes of the handle, with the device memory it owns now (tddft_query; synchronises)."""
+        info = Info()
+        _check(load().tddft_query(self._h, ctypes.byref(info)), "tddft_query")
+        return {"npw": info.npw, "n": info.n, "nb_chunk": info.nb_chunk, "precision": info.precision,
+                "device_bytes": info.device_bytes}
 
     def check(self):
         """Synchronise and raise if a bounded device wait of the library ran out (tddft_query)."""

@@ -143,7 +143,8 @@ def test_tuning_fields_round_trip(torch):
     for kw in (dict(targets=4), dict(sources=2), dict(k1d_block=8), dict(accumulate=0), dict(accumulate=1),
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
                dict(z_kernel=2),
-               dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2)):
+               dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
+               dict(k1d_cache=1), dict(k1d_cache=0)):
         before = s.get_tuning()
         s.set_tuning(**kw)
         after = s.get_tuning()
@@ -152,6 +153,39 @@ def test_tuning_fields_round_trip(torch):
         assert {x: after[x] for x in after if x != k} == {x: before[x] for x in before if x != k}, (kw, before, after)
     with pytest.raises(T.TddftError):
         s.set_tuning(projector=2)
+    with pytest.raises(T.TddftError):
+        s.set_tuning(k1d_cache=2)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
+def test_stored_tau_give_the_recomputed_k1d(torch, prec):
+    """K1d from the stored tau_vv' (tuning.k1d_cache) against the oracle and against the recomputing
+    path, on 20 orbitals (a full 16-orbital block and a ragged 4-orbital one), with plain launches and
+    under graph replay; the stored tau take the expected device memory and are released again."""
+    wl = _workload(24, 10.0, 10.0, 20, 3, seed=18)
+    want = O.system_from_workload(wl).apply(wl.X)
+    want_k1d = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
+    s = T.system_from_workload(wl, precision=prec)
+    Xd = torch.from_numpy(wl.X).to("cuda", s.complex_dtype)
+    plain = s.apply(Xd).cpu().numpy().astype(np.complex128)
+    before = s.query()["device_bytes"]
+    s.set_tuning(k1d_cache=1)
+    fields = 16 * 16 + 16 * 4 + 4 * 4  # block pairs (0,0), (0,16), (16,16)
+    assert s.query()["device_bytes"] - before == fields * 24 ** 3 * (16 if prec == T.PREC_FP64 else 8)
+    got = s.apply(Xd).cpu().numpy().astype(np.complex128)
+    assert _rel_err(got, want).max() < TOL[prec]
+    assert _rel_err(got, plain).max() < (1e-13 if prec == T.PREC_FP64 else 1e-6)
+    s.set_terms(T.TERM_K1D)
+    assert _rel_err(s.apply(Xd).cpu().numpy().astype(np.complex128), want_k1d).max() < TOL[prec]
+    s.set_terms(T.TERMS_ALL)
+    s.set_tuning(graph=1)
+    for _ in range(2):
+        got_g = s.apply(Xd).cpu().numpy().astype(np.complex128)
+        assert _rel_err(got_g, want).max() < TOL[prec]
+    s.set_tuning(graph=0, k1d_cache=0)
+    assert s.query()["device_bytes"] == before
+    assert s.get_tuning()["k1d_cache"] == 0
     s.close()
 
 
@@ -208,6 +242,10 @@ def test_diamond64_sampled_rows_fp32(torch):
     want = O.system_from_workload(wl).apply(wl.X, rows=rows)
     g = np.stack([got[b, v] for b, v in rows])
     assert _rel_err(g, want).max() < 1e-5
+    # the same batch with K1d from the stored tau (27.5 GB)
+    cached = _run(torch, wl, T.PREC_FP32, tiling=dict(k1d_cache=1))
+    assert _rel_err(np.stack([cached[b, v] for b, v in rows]), want).max() < 1e-5
+    assert _rel_err(cached, got).max() < 1e-6
     # every row lies in the unoccupied space
     ov = np.einsum("ug,bvg->buv", wl.phi_src.conj(), got)
     assert np.abs(ov).max() < 1e-5 * np.abs(got).max()
