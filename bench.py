@@ -32,11 +32,12 @@ WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 
 
 # DRAM traffic per launch of the dominant kernel class from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
-# sources it was taken on; reported as null when the sources have changed.
+# sources it was taken on and the grid of the pair convolutions; reported as null
+# when either differs.
 NCU_TRAFFIC = {
-    # profiles/plane_kernels_traffic_diamond64.md: one 256-pair launch of each class
-    "eaaf4f527de1": {"xy_fwd_pair_product": 538.4e6, "z_kernel_multiply": 792.8e6,
-                     "xy_inv_remultiply_accumulate": 661.7e6},
+    # profiles/plane_kernels_traffic_diamond64.md: one 256-pair launch of each class on 72^3
+    "eaaf4f527de1/72": {"xy_fwd_pair_product": 538.4e6, "z_kernel_multiply": 792.8e6,
+                        "xy_inv_remultiply_accumulate": 661.7e6},
 }
 
 
@@ -215,6 +216,8 @@ def run_native(args):
     stream = torch.cuda.current_stream(dev)
     sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
     npw = sys_.npw
+    # pair convolutions on the smallest grid on which they are exact (the same operator as on n^3)
+    n_exchange = sys_.query()["n_exchange"]
     X = torch.from_numpy(wl.X).to(dev, torch.complex64)
     LA = torch.empty_like(X)
 
@@ -319,13 +322,14 @@ def run_native(args):
     d = cls[dom]
     achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else None
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(src_hash, {}).get(dom)
+    traffic = NCU_TRAFFIC.get(f"{src_hash}/{n_exchange}", {}).get(dom)
     shares = {k: round(v["ms"] / max(1e-9, sum(c["ms"] for c in cls.values())), 4) for k, v in cls.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "npw": npw, "nocc": nocc, "nb": nb,
+                   "exchange_grid": n_exchange,
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (trial vectors and outputs in real space: 2 x 3.1 GB per step)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],

@@ -101,6 +101,7 @@ typedef struct tddft_info {
   int nb_chunk;            /* trial vectors processed per internal pass */
   int precision;
   size_t device_bytes;     /* device memory owned by the handle */
+  int n_exchange;          /* grid points per axis of the pair-convolution terms (tuning.exchange_grid) */
 } tddft_info;
 
 typedef struct tddft_system* tddft_handle;
@@ -184,6 +185,15 @@ typedef struct tddft_tuning {
                        tau serve again once it is switched off). The result equals that
                        of the recomputing path up to rounding. 0 (default): recompute;
                        releases the stored tau. -1 keeps the value in set_tuning */
+  int exchange_grid; /* 1 (default): the pair-convolution terms (D_EXX, K1d, K2d) run on the
+                       smallest supported grid N_x < n with N_x > 4 max|m_i| over the
+                       sphere, when there is one (64^3 for a 72^3 grid at a = 13.48 bohr,
+                       25 Ha). On any grid with N > 4 max|m_i| a pair density never folds
+                       onto itself and its products with the orbitals fold only onto
+                       plane waves outside the sphere, so these terms are the same as on
+                       the n grid up to rounding; the local terms (V_loc, K1e, the
+                       diagonal) stay on the n grid. tddft_info.n_exchange reports the grid
+                       in use. 0: every term on the n grid. -1 keeps the value */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

@@ -338,6 +338,12 @@ struct tddft_system {
   bool k1d_cache = false;
   void* tau_cache = nullptr;
   size_t tau_cache_bytes = 0;
+  bool k1d_cache_req = false;  // tuning.k1d_cache as set (the stored tau live where K1d runs)
+  // Exchange terms (D_EXX, K1d, K2d) on a smaller grid on which they are exact (tuning.exchange_grid):
+  // an internal system on that grid and its plane-wave results [nb_max][nocc_src][npw]
+  tddft_system* xsub = nullptr;
+  bool use_xsub = true;
+  void* x_pw = nullptr;
   std::vector<double> eps64;  // the given eigenvalues
   int ncols_act = 0;     // number of such columns (0 = no list: the grid aliases pair densities)
   int nsplit = 1;
@@ -746,6 +752,13 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   return check_launch("k1d_term");
 }
 
+// y += x (element-wise)
+template <typename T>
+__global__ void k_accumulate(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = cadd(y[i], x[i]);
+}
+
 // (L A) for nb trial vectors in the handle's orbital frame; terms of `mask`
 // (PROJ bit included or not). In the localised frame the eigenvalue part of D
 // is left out here (it is a matrix there, added by apply_impl).
@@ -765,6 +778,13 @@ static tddft_status apply_core(tddft_system* h, int nb, const cplx<T>* A, cplx<T
   const int hmode = (((mask & TDDFT_TERM_K1E_H) && !h->sf()) ? 1 : 0) | ((mask & TDDFT_TERM_K2E_H) ? 2 : 0);
   const int xmode = h->b.fxc ? (((mask & TDDFT_TERM_K1E_XC) ? 1 : 0) | ((mask & TDDFT_TERM_K2E_XC) ? 2 : 0)) : 0;
   const bool vloc = (mask & TDDFT_TERM_D_VLOC) && h->b.vloc;
+  // the pair-convolution terms on the exchange grid: same plane-wave result, fewer points
+  unsigned xmask = 0;
+  if (h->xsub && h->use_xsub && !h->loc_on && h->d.alpha != 0.0) {
+    xmask = mask & (TDDFT_TERM_K1D | TDDFT_TERM_K2D | (h->ace_on ? 0u : TDDFT_TERM_D_EXX));
+    if (xmask) STATUS_TRY(apply_core<T>(h->xsub, nb, A, (cplx<T>*)h->x_pw, xmask, st));
+    mask &= ~xmask;
+  }
   for (int b0 = 0; b0 < nb; b0 += h->nb_chunk) {
     const int nbc = std::min(h->nb_chunk, nb - b0);
     const int nf = nbc * nocc;
@@ -792,6 +812,11 @@ static tddft_status apply_core(tddft_system* h, int nb, const cplx<T>* A, cplx<T
     }
     STATUS_TRY(real_to_pw<T>(h, out_r, nf, LA + (long long)b0 * nocc * npw,
                              (mask & TDDFT_TERM_D_KIN) ? Ab : nullptr, st));
+  }
+  if (xmask) {
+    const long long len = (long long)nb * nocc * npw;
+    { k_accumulate<T><<<grid_for(len, 256), 256, 0, st>>>(LA, (const cplx<T>*)h->x_pw, len); note_launch(); }
+    STATUS_TRY(check_launch("exchange-grid terms"));
   }
   if ((mask & TDDFT_TERM_D_EXX) && h->d.alpha != 0.0 && h->ace_on) {
     // alpha V_X^ACE a = -alpha sum_k xi_k <xi_k|a>, in plane waves
@@ -840,6 +865,22 @@ static bool supported_n(int n, int prec) {
   for (int s : sizes)
     if (s == n) return !(prec == TDDFT_PREC_FP64 && n == 128);
   return false;
+}
+
+// Smallest supported grid on which the exchange terms equal those computed on the n grid.
+// With M = max |m_i| over the sphere, a pair density occupies |m_i| <= 2M and its
+// convolution times an orbital |m_i| <= 3M. On a grid of N > 4M points per axis no two
+// pair-density components fold onto one another, the kernel is sampled at the same G,
+// and a product component can only fold onto |m_i| >= N - 3M > M, outside the sphere:
+// the plane-wave result on the sphere is the alias-free one, the same on every such grid.
+// Returns n when no smaller grid qualifies (in particular when n itself folds).
+static int exchange_grid_for(int n, int prec, const std::vector<Miller>& sph) {
+  int M = 0;
+  for (const Miller& m : sph) M = std::max(M, std::max(std::abs(m.x), std::max(std::abs(m.y), std::abs(m.z))));
+  static const int sizes[] = {8, 12, 16, 24, 32, 36, 48, 64, 72, 80, 96, 108, 128};
+  for (int g : sizes)
+    if (g < n && g > 4 * M && supported_n(g, prec)) return g;
+  return n;
 }
 
 template <typename T>
@@ -1725,6 +1766,7 @@ tddft_status tddft_destroy(tddft_handle h) {
   if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocations) cudaFree(p);
   if (h->tau_cache) cudaFree(h->tau_cache);
+  if (h->xsub) tddft_destroy(h->xsub);
   delete h;
   return TDDFT_OK;
 }
@@ -1763,6 +1805,28 @@ tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, v
     g_last_error = msg;
     return s;
   }
+  const int nx = exchange_grid_for(d.n, d.precision, sph);
+  if (nx < d.n) {
+    // the exchange terms on the nx grid: an internal system with the same orbitals and no
+    // local fields; without room for it the n grid serves (same result, more points)
+    tddft_desc dx = d;
+    dx.n = nx;
+    tddft_inputs ix = *in;
+    ix.vloc = nullptr;
+    ix.fxc = nullptr;
+    const std::string saved = g_last_error;
+    tddft_handle hx = nullptr;
+    if (tddft_init_system(&dx, &ix, stream, &hx) == TDDFT_OK) {
+      void* xpw = nullptr;
+      if (dalloc(h, &xpw, (size_t)d.nb_max * d.nocc_src * h->npw * h->esz()) == TDDFT_OK) {
+        h->xsub = hx;
+        h->x_pw = xpw;
+      } else {
+        tddft_destroy(hx);
+      }
+    }
+    g_last_error = saved;
+  }
   *out = h;
   return TDDFT_OK;
 }
@@ -1775,6 +1839,12 @@ tddft_status tddft_query(tddft_handle h, tddft_info* info) {
   info->nb_chunk = h->nb_chunk;
   info->precision = h->d.precision;
   info->device_bytes = h->bytes;
+  info->n_exchange = h->n;
+  if (h->xsub) {
+    STATUS_TRY(check_device_flag(h->xsub, nullptr));
+    info->device_bytes += h->xsub->bytes;
+    if (h->use_xsub) info->n_exchange = h->xsub->n;
+  }
   return TDDFT_OK;
 }
 
@@ -1838,6 +1908,22 @@ static tddft_status set_tau_cache(tddft_system* h, bool on) {
   return TDDFT_OK;
 }
 
+// the stored tau where K1d runs (the exchange-grid system when it is in use), none elsewhere
+static tddft_status sync_tau_cache(tddft_system* h) {
+  tddft_system* run = (h->xsub && h->use_xsub) ? h->xsub : h;
+  tddft_system* idle = run == h ? h->xsub : h;
+  if (idle) STATUS_TRY(set_tau_cache(idle, false));
+  const tddft_status s = set_tau_cache(run, h->k1d_cache_req);
+  if (s != TDDFT_OK) h->k1d_cache_req = false;
+  return s;
+}
+
+static bool z_kernel_ok(const tddft_system* h, int z) {
+  const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
+  const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
+  return z == 0 || (reg && (z == 1 || pair));
+}
+
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
   if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
   if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 16)
@@ -1871,9 +1957,20 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->ops64.kc.z = t->z_kernel;
   }
   tddft_status cs = TDDFT_OK;
-  if (t->k1d_cache >= 0) {
-    if (t->k1d_cache > 1) cs = fail(TDDFT_EINVAL, "k1d_cache must be 0 or 1");
-    else cs = set_tau_cache(h, t->k1d_cache == 1);
+  if (t->exchange_grid > 1) cs = fail(TDDFT_EINVAL, "exchange_grid must be 0 or 1");
+  if (t->k1d_cache > 1) cs = fail(TDDFT_EINVAL, "k1d_cache must be 0 or 1");
+  if (cs == TDDFT_OK && h->xsub) {
+    // the same schedule for the exchange-grid system (its z pass where that grid has it)
+    tddft_tuning tx = *t;
+    tx.k1d_cache = -1;
+    tx.exchange_grid = -1;
+    if (tx.z_kernel >= 0 && !z_kernel_ok(h->xsub, tx.z_kernel)) tx.z_kernel = -1;
+    cs = tddft_set_tuning(h->xsub, &tx);
+  }
+  if (cs == TDDFT_OK && (t->exchange_grid >= 0 || t->k1d_cache >= 0)) {
+    if (t->exchange_grid >= 0) h->use_xsub = t->exchange_grid == 1;
+    if (t->k1d_cache >= 0) h->k1d_cache_req = t->k1d_cache == 1;
+    cs = sync_tau_cache(h);
   }
   drop_graphs(h);  // the schedule changed: the next graph call captures again
   return cs;
@@ -1892,7 +1989,8 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->z_kernel = kc.z;
   t->projector = h->projector_tc;
   t->k1d_sparse = h->k1d_sparse;
-  t->k1d_cache = h->k1d_cache ? 1 : 0;
+  t->k1d_cache = h->k1d_cache_req ? 1 : 0;
+  t->exchange_grid = h->use_xsub ? 1 : 0;
   return TDDFT_OK;
 }
 
@@ -1995,11 +2093,17 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
   float best_ms = 1e30f;
   Cand bc = cands[0];
   tddft_status s = TDDFT_OK;
+  auto set_tiles = [h](const Cand& c) {
+    for (tddft_system* x : {h, h->xsub}) {
+      if (!x) continue;
+      x->tile_targets = c.tt;
+      x->tile_sources = c.ks;
+      x->accumulate = c.acc ? INV_ATOMIC : INV_ACCUM;
+      x->k1d_block = c.kb;
+    }
+  };
   for (const Cand& c : cands) {
-    h->tile_targets = c.tt;
-    h->tile_sources = c.ks;
-    h->accumulate = c.acc ? INV_ATOMIC : INV_ACCUM;
-    h->k1d_block = c.kb;
+    set_tiles(c);
     s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);  // warm
     if (s != TDDFT_OK) break;
     cudaEventRecord(e0, st);
@@ -2020,10 +2124,7 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->use_graph = graph;
-  h->tile_targets = bc.tt;
-  h->tile_sources = bc.ks;
-  h->accumulate = bc.acc ? INV_ATOMIC : INV_ACCUM;
-  h->k1d_block = bc.kb;
+  set_tiles(bc);
   if (h->gexec) {
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;

@@ -70,7 +70,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int),
-                ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int)]
+                ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int), ("exchange_grid", ctypes.c_int)]
 
 
 class ZvectorOpts(ctypes.Structure):
@@ -80,7 +80,7 @@ class ZvectorOpts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("npw", ctypes.c_int), ("n", ctypes.c_int), ("nb_chunk", ctypes.c_int),
-                ("precision", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+                ("precision", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("n_exchange", ctypes.c_int)]
 
 
 _lib = None
@@ -240,7 +240,7 @@ class LiouvilleSystem:
             self.close()
             raise ValueError(f"orbital arrays have {self.npw} coefficients, the sphere has {info.npw}")
         self.info = {"npw": info.npw, "n": info.n, "nb_chunk": info.nb_chunk, "precision": info.precision,
-                     "device_bytes": info.device_bytes}
+                     "device_bytes": info.device_bytes, "n_exchange": info.n_exchange}
 
     # -- helpers --
     @property
@@ -261,9 +261,9 @@ class LiouvilleSystem:
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
                    graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1,
-                   k1d_cache: int = -1):
+                   k1d_cache: int = -1, exchange_grid: int = -1):
         t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
-                   int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache))
+                   int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache), int(exchange_grid))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 
     def query(self) -> dict:
@@ -271,7 +271,7 @@ class LiouvilleSystem:
         info = Info()
         _check(load().tddft_query(self._h, ctypes.byref(info)), "tddft_query")
         return {"npw": info.npw, "n": info.n, "nb_chunk": info.nb_chunk, "precision": info.precision,
-                "device_bytes": info.device_bytes}
+                "device_bytes": info.device_bytes, "n_exchange": info.n_exchange}
 
     def check(self):
         """Synchronise and raise if a bounded device wait of the library ran out (tddft_query)."""

@@ -85,6 +85,60 @@ def test_every_grid_plan(torch, n, a, ecut, nocc, nb):
             continue  # the FP64 128^3 plane does not fit in shared memory
         got = _run(torch, wl, prec)
         assert _rel_err(got, want).max() < TOL[prec], (n, prec)
+        # the pair convolutions on the n grid itself too, where a smaller exchange grid exists
+        s = T.system_from_workload(wl, precision=prec)
+        nx = s.query()["n_exchange"]
+        s.close()
+        assert nx == EXCHANGE_GRID.get(n, n), (n, nx)
+        if nx != n:
+            got = _run(torch, wl, prec, tiling=dict(exchange_grid=0))
+            assert _rel_err(got, want).max() < TOL[prec], (n, prec, "n grid")
+
+
+# smallest supported N_x < n with N_x > 4 max|m_i| for the cells of test_every_grid_plan
+EXCHANGE_GRID = {36: 32, 72: 64, 80: 72, 108: 96, 128: 108}
+
+
+def test_exchange_grid_is_the_same_operator(torch):
+    """72^3 cell at 25 Ha (max |m_i| = 15): the pair-convolution terms on 64^3 against the same terms
+    on 72^3 and the oracle (on 72^3), for the Tamm-Dancoff operator, the Z-vector operator (K2 terms),
+    K1d alone with stored tau, and with the compressed exchange inside D."""
+    wl = _workload(72, 13.48, 25.0, 6, 2, seed=19)
+    S = O.system_from_workload(wl)
+    for prec in (T.PREC_FP64, T.PREC_FP32):
+        tight = 1e-12 if prec == T.PREC_FP64 else 2e-6
+        s = T.system_from_workload(wl, precision=prec)
+        assert s.query()["n_exchange"] == 64
+        Xd = torch.from_numpy(wl.X).to("cuda", s.complex_dtype)
+
+        def both(mask):
+            s.set_terms(mask)
+            s.set_tuning(exchange_grid=1)
+            small = s.apply(Xd).cpu().numpy().astype(np.complex128)
+            s.set_tuning(exchange_grid=0)
+            assert s.query()["n_exchange"] == 72
+            full = s.apply(Xd).cpu().numpy().astype(np.complex128)
+            s.set_tuning(exchange_grid=1)
+            return small, full
+
+        small, full = both(T.TERMS_ALL)
+        assert _rel_err(small, S.apply(wl.X)).max() < TOL[prec]
+        assert _rel_err(small, full).max() < tight
+        small, full = both(T.TERM_K1D | T.TERM_D_EXX)
+        assert _rel_err(small, S.apply(wl.X, T.TERM_K1D | T.TERM_D_EXX)).max() < TOL[prec]
+        small, full = both(T.TERMS_ZVEC)
+        assert _rel_err(small, S.apply(wl.X, T.TERMS_ZVEC)).max() < TOL[prec]
+        assert _rel_err(small, full).max() < tight
+        # stored tau live on the grid K1d runs on
+        before = s.query()["device_bytes"]
+        s.set_tuning(k1d_cache=1)
+        assert s.query()["device_bytes"] - before == 36 * 64 ** 3 * (16 if prec == T.PREC_FP64 else 8)
+        small, full = both(T.TERM_K1D)
+        assert _rel_err(small, S.apply(wl.X, T.TERM_K1D)).max() < TOL[prec]
+        assert _rel_err(small, full).max() < tight
+        s.set_tuning(k1d_cache=0)
+        assert s.query()["device_bytes"] == before
+        s.close()
 
 
 @pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
@@ -144,7 +198,7 @@ def test_tuning_fields_round_trip(torch):
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
                dict(z_kernel=2),
                dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
-               dict(k1d_cache=1), dict(k1d_cache=0)):
+               dict(k1d_cache=1), dict(k1d_cache=0), dict(exchange_grid=0), dict(exchange_grid=1)):
         before = s.get_tuning()
         s.set_tuning(**kw)
         after = s.get_tuning()
@@ -155,6 +209,8 @@ def test_tuning_fields_round_trip(torch):
         s.set_tuning(projector=2)
     with pytest.raises(T.TddftError):
         s.set_tuning(k1d_cache=2)
+    with pytest.raises(T.TddftError):
+        s.set_tuning(exchange_grid=2)
     s.close()
 
 

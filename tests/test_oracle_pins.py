@@ -818,3 +818,31 @@ def test_tda_equals_cis_with_brute_force_integrals(sf):
     # the three two-electron blocks are each far above that tolerance
     for blk in (wl.alpha * VX, wl.alpha * eri(ab, ji, Kx), F):
         assert np.abs(blk).max() > 1e-4 * np.abs(A).max()
+
+
+# --------------------------------------------------------------------------
+# grid independence of the pair-convolution terms
+# --------------------------------------------------------------------------
+
+def test_exchange_terms_are_the_same_on_every_grid_with_n_above_four_m():
+    """With M = max |m_i| over the sphere, the terms built from pair convolutions (V_X inside D, K1d,
+    K2d) give the same plane-wave result on every grid of N > 4M points per axis: a pair density has
+    |m_i| <= 2M, its products with orbitals |m_i| <= 3M, so nothing folds onto the sphere. On a grid
+    of N = 4M a pair-density component folds onto another and the result changes."""
+    a, ecut = 9.0, 14.0
+    M = int(np.abs(O.miller_sphere(36, a, ecut)).max())
+    assert M == 7
+    wl = synth.make_workload(n=36, a=a, ecut=ecut, npw=O.Grid(36, a, ecut).npw, nocc_src=3, nb=2, seed=61,
+                             with_vloc=False, with_fxc=False)
+    mask = O.D_EXX | O.K1D | O.K2D
+
+    def on_grid(n):
+        S = O.System(n, a, ecut, wl.phi_src, wl.eps_src, alpha=wl.alpha, kx_g0=wl.kx_g0)
+        assert S.grid.npw == wl.phi_src.shape[1] and np.array_equal(S.grid.miller, O.miller_sphere(36, a, ecut))
+        return S.apply(wl.X, mask)
+
+    ref = on_grid(36)
+    scale = np.abs(ref).max()
+    for n in (30, 32):
+        assert np.abs(on_grid(n) - ref).max() < 1e-12 * scale, n
+    assert np.abs(on_grid(28) - ref).max() > 1e-6 * scale
