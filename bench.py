@@ -217,6 +217,7 @@ def run_native(args):
     sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
     npw = sys_.npw
     # pair convolutions on the smallest grid on which they are exact (the same operator as on n^3)
+    sys_.set_tuning(exchange_grid=args.exchange_grid)
     n_exchange = sys_.query()["n_exchange"]
     X = torch.from_numpy(wl.X).to(dev, torch.complex64)
     LA = torch.empty_like(X)
@@ -593,6 +594,8 @@ def main():
                                              "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch), "
                                              "pairtrunc (K1d pair truncation, localised orbitals), "
                                              "taucache (K1d from stored tau of every pair)")
+    ap.add_argument("--exchange-grid", type=int, default=1, choices=[0, 1],
+                    help="1: pair convolutions on the smallest exact grid (64^3 here; the default); 0: on the 72^3 grid")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()
