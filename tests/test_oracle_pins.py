@@ -846,3 +846,51 @@ def test_exchange_terms_are_the_same_on_every_grid_with_n_above_four_m():
     for n in (30, 32):
         assert np.abs(on_grid(n) - ref).max() < 1e-12 * scale, n
     assert np.abs(on_grid(28) - ref).max() > 1e-6 * scale
+
+
+def test_zvector_operator_b_block_with_brute_force_integrals():
+    """The operator of the Z-vector equation (Eq. 19) acts as Z -> A Z + B conj(Z) on the unoccupied
+    space: A is the CIS matrix above and, from the K2 terms (Eqs. 5, 7),
+        B_{ia,jb} = (a i|b j)_H + <a i|f_xc|b j> - alpha (a j|b i)_x,
+    with <a i|f|b j> = (Omega/N_r) sum_r psi_a* phi_i f psi_b* phi_j. A and B are separated by applying
+    the oracle to e_{jb} and i e_{jb}; the integrals are summed point by point with the real-space kernel."""
+    n, a, ecut = 8, 6.0, 2.5
+    wl, S = _tiny(n=n, a=a, ecut=ecut, nocc=2, nb=1, seed=32)
+    Qc = S.complement_basis()
+    miller = S.grid.miller
+    nr, vol = n ** 3, a ** 3
+    w_r = vol / nr
+    psi = _orbitals_on_grid(Qc.T, miller, n, a)
+    phs = _orbitals_on_grid(wl.phi_src, miller, n, a)
+    nc, no = psi.shape[0], phs.shape[0]
+    Kx = _kernel_matrix(n, a, wl.kx_g0)
+    Kh = _kernel_matrix(n, a, 0.0)
+    fxc = wl.fxc.ravel()
+
+    def eri(P, Q, K):
+        P2, Q2 = P.reshape(-1, nr), Q.reshape(-1, nr)
+        return w_r * (P2 @ K @ Q2.T).reshape(P.shape[:-1] + Q.shape[:-1])
+
+    ai = psi.conj()[:, None, :] * phs[None, :, :]          # [a, i] = psi_a* phi_i
+    bj = psi.conj()[:, None, :] * phs[None, :, :]          # [b, j] = psi_b* phi_j
+    aj = ai                                                 # [a, j]
+    bi = bj                                                 # [b, i]
+    B = eri(ai, bj, Kh).transpose(1, 0, 3, 2)              # (a i|b j)_H [a, i, b, j] -> [i, a, j, b]
+    B += (w_r * (ai.reshape(-1, nr) * fxc) @ bj.reshape(-1, nr).T).reshape(nc, no, nc, no).transpose(1, 0, 3, 2)
+    B -= wl.alpha * eri(aj, bi, Kx).transpose(3, 0, 1, 2)  # (a j|b i)_x [a, j, b, i] -> [i, a, j, b]
+    B = B.reshape(no * nc, no * nc)
+
+    dim = no * nc
+    cols = np.zeros((dim, no, S.grid.npw), dtype=np.complex128)
+    for j in range(no):
+        for b in range(nc):
+            cols[j * nc + b, j] = Qc[:, b]
+    L1 = S.apply(cols, O.ZVEC_TERMS)
+    Li = S.apply(1j * cols, O.ZVEC_TERMS)
+    to_basis = lambda Y: np.einsum("gk,cvg->vkc", Qc.conj(), Y).reshape(dim, dim)
+    A_o = (to_basis(L1) - 1j * to_basis(Li)) / 2
+    B_o = (to_basis(L1) + 1j * to_basis(Li)) / 2
+    H, _ = S.dense_matrix()
+    assert np.abs(A_o - H).max() < 1e-11 * np.abs(H).max()
+    assert np.abs(B_o - B).max() < 1e-11 * np.abs(B).max(), np.abs(B_o - B).max()
+    assert np.abs(B).max() > 1e-3 * np.abs(H).max()
