@@ -1818,7 +1818,8 @@ tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, v
     tddft_handle hx = nullptr;
     if (tddft_init_system(&dx, &ix, stream, &hx) == TDDFT_OK) {
       void* xpw = nullptr;
-      if (dalloc(h, &xpw, (size_t)d.nb_max * d.nocc_src * h->npw * h->esz()) == TDDFT_OK) {
+      // the same sphere in the same order (it fits: N_x > 4M), so plane-wave rows are shared
+      if (hx->npw == h->npw && dalloc(h, &xpw, (size_t)d.nb_max * d.nocc_src * h->npw * h->esz()) == TDDFT_OK) {
         h->xsub = hx;
         h->x_pw = xpw;
       } else {
