@@ -195,7 +195,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas", "step": "one row (b, v) of L.A"},
+        "config": {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "npw": int(wl.phi_src.shape[1]), "nocc": nocc,
+                   "nb": WORKLOAD["nb"], "exchange_grid": WORKLOAD["n"], "parallelism": "replicas",
+                   "step": "one row (b, v) of L.A"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one row (b, v) of the batch per step: all pair convolutions of that row, "
                                    "with the Hartree/xc density of its trial vector; rows/s / Nocc"},
