@@ -114,6 +114,13 @@ tddft_status tddft_sphere_size(int n, double a, double ecut, int* npw);
  * (m_x, m_y, m_z) of point i. The caller provides npw*3 ints. Host only. */
 tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller);
 
+/* Grid (points per axis) on which tddft_init_system runs the pair-convolution terms
+ * when tuning.exchange_grid is on: the smallest supported N_x < n with N_x > 4 M,
+ * M = max |m_i| over the sphere S (on such a grid those terms equal the n-grid ones up
+ * to rounding, see tddft_tuning.exchange_grid), else n. Host only. EINVAL for an
+ * unsupported (n, precision) or when S does not fit the grid. */
+tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange);
+
 /* Build a system: copy the inputs to the device, build the sphere map and
  * kernel tables, transform the orbitals to real space and allocate the
  * workspace for nb_max trial vectors. The orbitals are checked orthonormal

@@ -1729,6 +1729,16 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller) {
   return TDDFT_OK;
 }
 
+tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange) {
+  if (!n_exchange) return fail(TDDFT_EINVAL, "null output");
+  if (precision != TDDFT_PREC_FP64 && precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
+  if (!supported_n(n, precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
+  std::vector<Miller> s;
+  STATUS_TRY(build_sphere(n, a, ecut, s));
+  *n_exchange = exchange_grid_for(n, precision, s);
+  return TDDFT_OK;
+}
+
 tddft_status tddft_profile_enable(int enable) {
   g_prof.on = enable != 0;
   g_prof.used = 0;

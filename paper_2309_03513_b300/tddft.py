@@ -43,7 +43,7 @@ EXPORTS = [
     "tddft_set_localization", "tddft_relaxed_density", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
-    "tddft_exchange_pair_noalloc",
+    "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
 ]
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
@@ -125,6 +125,7 @@ def load() -> ctypes.CDLL:
         "tddft_profile_enable": ([ci], st),
         "tddft_profile_read": ([vp, vp, vp, vp], st),
         "tddft_exchange_pair_noalloc": ([ci, cd, cd, cd, cd, vp, vp, vp, vp], st),
+        "tddft_exchange_grid": ([ci, cd, cd, ci, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -142,6 +143,14 @@ def _check(status: int, where: str):
 
 def _ptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data
+
+
+def exchange_grid(n: int, a: float, ecut: float, precision: int = PREC_FP32) -> int:
+    """Grid of the pair-convolution terms for a system on n^3 (tddft_exchange_grid; host only)."""
+    out = ctypes.c_int()
+    _check(load().tddft_exchange_grid(int(n), float(a), float(ecut), int(precision), ctypes.byref(out)),
+           "tddft_exchange_grid")
+    return out.value
 
 
 def sphere_size(n: int, a: float, ecut: float) -> int:
