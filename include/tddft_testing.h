@@ -1,0 +1,35 @@
+/*
+ * Host-only entry points to the library's small dense FP64 routines, for testing them on
+ * the CPU. They are the routines that the Davidson step uses for its Rayleigh-Ritz problem
+ * (Hermitian eigenproblem) and that the ACE build uses for -M = L L^dagger and L^{-1}
+ * (Sec. 3.1); they are not part of the operator's interface.
+ *
+ * Matrices are row-major n x n arrays of interleaved complex128 (2n^2 doubles), owned by
+ * the caller. No call touches the GPU.
+ */
+#ifndef TDDFT_TESTING_H
+#define TDDFT_TESTING_H
+
+#include "tddft.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Eigenvalues (ascending, w[n]) and eigenvectors (columns of V) of the Hermitian matrix A,
+ * by cyclic complex Jacobi rotations. EINVAL for n < 1 or a null pointer; ENUMERIC when the
+ * sweeps do not converge (w and V then hold the last iterate). */
+tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V);
+
+/* In place: the lower Cholesky factor L of a Hermitian positive definite A (A = L L^dagger,
+ * real positive diagonal, zeros above it). ENUMERIC when a pivot is not positive. */
+tddft_status tddft_testing_cholesky(int n, double* A);
+
+/* X = L^{-1} for a lower-triangular L with non-zero diagonal. */
+tddft_status tddft_testing_lower_inverse(int n, const double* L, double* X);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDDFT_TESTING_H */

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/tddft.h"
+#include "../../include/tddft_testing.h"
 #include "gemm.cuh"
 #include "plane_ops.cuh"
 #include "umma.cuh"
@@ -2904,3 +2905,40 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
                                                          (cplx<float>*)out_pw, n3); note_launch(); }
   return check_launch("tddft_exchange_pair_noalloc");
 }
+
+// ---------------------------------------------------------------------------
+// host-only test entry points of the small dense routines
+// ---------------------------------------------------------------------------
+extern "C" {
+
+tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V) {
+  if (n < 1 || !A || !w || !V) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
+  const std::complex<double>* a = reinterpret_cast<const std::complex<double>*>(A);
+  std::vector<std::complex<double>> M(a, a + (size_t)n * n), vecs;
+  std::vector<double> vals;
+  const bool ok = herm_eig(n, M, vals, vecs);
+  std::copy(vals.begin(), vals.end(), w);
+  std::copy(vecs.begin(), vecs.end(), reinterpret_cast<std::complex<double>*>(V));
+  return ok ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+}
+
+tddft_status tddft_testing_cholesky(int n, double* A) {
+  if (n < 1 || !A) return fail(TDDFT_EINVAL, "n >= 1 and a non-null array required");
+  std::complex<double>* a = reinterpret_cast<std::complex<double>*>(A);
+  std::vector<std::complex<double>> M(a, a + (size_t)n * n);
+  if (!cholesky_lower(n, M)) return fail(TDDFT_ENUMERIC, "matrix is not positive definite");
+  std::copy(M.begin(), M.end(), a);
+  return TDDFT_OK;
+}
+
+tddft_status tddft_testing_lower_inverse(int n, const double* L, double* X) {
+  if (n < 1 || !L || !X) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
+  const std::complex<double>* l = reinterpret_cast<const std::complex<double>*>(L);
+  for (int i = 0; i < n; ++i)
+    if (l[(size_t)i * n + i] == 0.0) return fail(TDDFT_EINVAL, "zero on the diagonal");
+  const std::vector<std::complex<double>> inv = lower_inverse(n, std::vector<std::complex<double>>(l, l + (size_t)n * n));
+  std::copy(inv.begin(), inv.end(), reinterpret_cast<std::complex<double>*>(X));
+  return TDDFT_OK;
+}
+
+}  // extern "C"

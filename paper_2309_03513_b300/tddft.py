@@ -44,6 +44,8 @@ EXPORTS = [
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
+    # include/tddft_testing.h
+    "tddft_testing_herm_eig", "tddft_testing_cholesky", "tddft_testing_lower_inverse",
 ]
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
@@ -126,6 +128,9 @@ def load() -> ctypes.CDLL:
         "tddft_profile_read": ([vp, vp, vp, vp], st),
         "tddft_exchange_pair_noalloc": ([ci, cd, cd, cd, cd, vp, vp, vp, vp], st),
         "tddft_exchange_grid": ([ci, cd, cd, ci, vp], st),
+        "tddft_testing_herm_eig": ([ci, vp, vp, vp], st),
+        "tddft_testing_cholesky": ([ci, vp], st),
+        "tddft_testing_lower_inverse": ([ci, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
