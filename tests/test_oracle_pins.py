@@ -894,3 +894,31 @@ def test_zvector_operator_b_block_with_brute_force_integrals():
     assert np.abs(A_o - H).max() < 1e-11 * np.abs(H).max()
     assert np.abs(B_o - B).max() < 1e-11 * np.abs(B).max(), np.abs(B_o - B).max()
     assert np.abs(B).max() > 1e-3 * np.abs(H).max()
+
+
+# --------------------------------------------------------------------------
+# regression fixture of the oracle itself
+# --------------------------------------------------------------------------
+
+def test_oracle_reproduces_its_tiny_digest():
+    """The oracle on the tiny 24^3 configuration against tests/golden/tiny_24_digest.json, written by
+    tests/golden/make_tiny_digest.py from the oracle alone: a change of the oracle's arithmetic shows
+    up here (regenerate the file only with a change that a passage of the paper justifies)."""
+    import importlib.util
+    import json
+    import os
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_tiny_digest", os.path.join(here, "make_tiny_digest.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "tiny_24_digest.json")) as fh:
+        want = json.load(fh)
+    got = mod.digest()
+    assert got["npw"] == want["npw"] == 1503
+    assert np.allclose(got["omega"], want["omega"], rtol=1e-10, atol=0)
+    assert np.allclose(got["row_norms"], want["row_norms"], rtol=1e-10, atol=0)
+    scale = max(want["row_norms"])
+    for g, w in zip(got["samples"], want["samples"]):
+        assert g[:3] == w[:3]
+        assert abs(complex(g[3], g[4]) - complex(w[3], w[4])) < 1e-10 * scale
