@@ -125,6 +125,9 @@ tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, in
  * kernel tables, transform the orbitals to real space and allocate the
  * workspace for nb_max trial vectors. The orbitals are checked orthonormal
  * in FP64 (max |Phi^dagger Phi - I| <= 1e-10) -> else TDDFT_EINVAL.
+ * When tddft_exchange_grid gives a smaller grid, the handle also builds the
+ * same system on that grid for the pair-convolution terms (tuning.exchange_grid);
+ * if there is no room for it, every term runs on the n grid (same result).
  * The handle owns all device memory until tddft_destroy. Synchronises the
  * stream before returning. */
 tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, void* stream,
