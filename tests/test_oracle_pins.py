@@ -386,8 +386,9 @@ def test_vloc_gradient_closed_form():
 # dense operator and Davidson
 # --------------------------------------------------------------------------
 
-def test_davidson_matches_dense_diagonalisation():
-    wl, S = _tiny(n=8, a=6.0, ecut=2.5, nocc=2, nb=4, seed=10)
+@pytest.mark.parametrize("sf", [False, True])
+def test_davidson_matches_dense_diagonalisation(sf):
+    wl, S = _tiny(spin_flip=sf, n=8, a=6.0, ecut=2.5, nocc=2 if not sf else 3, nocc_tgt=2, nb=4, seed=10)
     H, Qc = S.dense_matrix()
     assert np.abs(H - H.conj().T).max() < 1e-12 * np.abs(H).max()
     ev = np.linalg.eigvalsh(H)
