@@ -540,6 +540,37 @@ def _real_coords(Qc, Z):
     return np.concatenate([c.real, c.imag])
 
 
+def test_zvector_rhs_against_finite_differences_of_omega():
+    """U_s = -P^c u_s with u_s = d omega_s / d phi^* (Eqs. 19, 20), pinned without
+    the oracle's gradient code: U lies in the unoccupied space (Phi^dagger U = 0),
+    and for every direction delta of the orbitals inside that space,
+    Re<U|delta> = -(1/2) d omega / dh along phi + h delta, by central differences
+    of omega itself (FP64, h = 1e-4). With delta and i delta this fixes the whole
+    complex inner product, so a flipped sign, a missing or misplaced projector or a
+    conjugated gradient fails."""
+    wl, S = _tiny(n=12, a=7.0, ecut=3.0, nocc=3, nb=2, seed=31)
+    U = S.zvector_rhs(wl.X)
+    assert U.shape == wl.X.shape
+    assert np.abs(wl.phi_tgt.conj() @ U.reshape(-1, U.shape[-1]).T).max() < 1e-12 * np.abs(U).max()
+    rng = np.random.default_rng(32)
+
+    def omega_at(phi, s):
+        S2 = O.System(wl.n, wl.a, wl.ecut, phi, wl.eps_src, alpha=wl.alpha, kx_g0=wl.kx_g0, vloc=wl.vloc,
+                      fxc=wl.fxc)
+        return float(S2.omega(wl.X[s:s + 1])[0])
+
+    h = 1e-4
+    for s in range(2):
+        for _ in range(2):
+            d = rng.normal(size=wl.phi_src.shape) + 1j * rng.normal(size=wl.phi_src.shape)
+            d = S.project(d[None])[0]  # a direction inside the unoccupied space
+            for ph in (1.0, 1j):
+                delta = ph * d
+                fd = (omega_at(wl.phi_src + h * delta, s) - omega_at(wl.phi_src - h * delta, s)) / (2 * h)
+                lhs = np.vdot(U[s], delta).real
+                assert abs(lhs + 0.5 * fd) < 1e-7 * max(1.0, abs(fd)), (s, ph, lhs, fd)
+
+
 @pytest.mark.parametrize("precondition", [False, True])
 def test_zvector_cg_matches_dense_solve(precondition):
     """CG with the exact operator throughout (lambda_thr = 0) against numpy's dense
