@@ -35,7 +35,7 @@ WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 
 # sources it was taken on and the grid of the pair convolutions; reported as null
 # when either differs.
 NCU_TRAFFIC = {
-    # profiles/plane_kernels_traffic_diamond64.md: one 256-pair launch of each class on 72^3
+    # one 256-pair launch of each class on 72^3 (pair convolutions on the caller's grid)
     "eaaf4f527de1/72": {"xy_fwd_pair_product": 538.4e6, "z_kernel_multiply": 792.8e6,
                         "xy_inv_remultiply_accumulate": 661.7e6},
 }
@@ -117,17 +117,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(rank: int):
+def make_workload(rank: int, npw: int):
+    """The bench batch; npw is the sphere size, counted by the caller's own side
+    (the library for the native arm, the oracle for the reference arm)."""
     from paper_2309_03513_b300 import synth
-    from paper_2309_03513_b300 import tddft as T
     w = WORKLOAD
-    npw = T.sphere_size(w["n"], w["a"], w["ecut"])
     return synth.make_workload(n=w["n"], a=w["a"], ecut=w["ecut"], npw=npw, nocc_src=w["nocc"], nb=w["nb"],
                                seed=w["seed"] + rank, alpha=w["alpha"])
 
 
 def oracle_sample(wl, rows):
-    """Time the FP64 oracle on a few rows (b, v) of the batch; returns (seconds, cores)."""
+    """Time the FP64 oracle on a few rows (b, v) of the batch; returns (seconds, threads)."""
     from oracle import tddft_oracle as O
     S = O.system_from_workload(wl)
     S.phi_src_r()  # orbitals to real space once, as the oracle's set-up
@@ -175,35 +175,62 @@ def job_throughput(ws: int, units_per_rank: float, local_seconds: float) -> tupl
     return ws * units_per_rank / t, t
 
 
+def bench_config(ws: int) -> dict:
+    """The workload keys both arms print (identical, so the two lines describe the same job)."""
+    w = WORKLOAD
+    return {"workload": WORKLOAD_NAME, "n": w["n"], "npw": 14771, "nocc": w["nocc"], "nb": w["nb"],
+            "parallelism": "replicas" if ws > 1 else "single process",
+            "l2": "inputs larger than L2 (trial vectors and outputs in real space: 2 x 3.1 GB per step)"}
+
+
 def run_reference(args):
+    """The FP64 oracle on the host cores, one row (b, v) of the bench batch per step.
+    The sphere is counted by the oracle itself: this arm never loads the CUDA library."""
+    from oracle import tddft_oracle as O
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = make_workload(0)
-    nocc = WORKLOAD["nocc"]
+    w = WORKLOAD
+    wl = make_workload(0, O.miller_sphere(w["n"], w["a"], w["ecut"]).shape[0])
+    nocc = w["nocc"]
     times = []
     cores = 1
     for i in range(args.warmup + args.steps):
-        row = [(i % WORKLOAD["nb"], (7 * i) % nocc)]
+        row = [(i % w["nb"], (7 * i) % nocc)]
         dt, cores = oracle_sample(wl, row)
         if i >= args.warmup:
             times.append(dt)
     total = sum(times)
     value = (len(times) / nocc) / total  # rows -> applications
+    cfg = bench_config(ws)
+    cfg["npw"] = int(wl.phi_src.shape[1])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "npw": int(wl.phi_src.shape[1]), "nocc": nocc,
-                   "nb": WORKLOAD["nb"], "exchange_grid": WORKLOAD["n"], "parallelism": "replicas",
-                   "step": "one row (b, v) of L.A"},
+        "config": cfg,
+        "step": "one row (b, v) of L.A, all pair convolutions of that row",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one row (b, v) of the batch per step: all pair convolutions of that row, "
                                    "with the Hartree/xc density of its trial vector; rows/s / Nocc"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def row_errors(got_rows, want_rows, x_rows) -> dict:
+    """Errors of sampled rows (b, v) of L.A against the FP64 oracle: relative
+    Frobenius error per row, and the error of those rows' contribution to
+    omega_b = <X_b|L X_b> (sum over the sampled v of Re<x_v|(L x)_v>, Ha)."""
+    got = np.asarray(got_rows, dtype=np.complex128)
+    want = np.asarray(want_rows, dtype=np.complex128)
+    x = np.asarray(x_rows, dtype=np.complex128)
+    rel = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    om_got = float(np.sum(np.einsum("vg,vg->v", x.conj(), got).real))
+    om_want = float(np.sum(np.einsum("vg,vg->v", x.conj(), want).real))
+    return {"rows_rel_err": [float(e) for e in rel], "rows_rel_err_max": float(rel.max()),
+            "omega_rows_Ha": om_want, "omega_rows_abs_err_Ha": abs(om_got - om_want)}
 
 
 def run_native(args):
@@ -213,8 +240,9 @@ def run_native(args):
 
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local if ws > 1 else 0)
-    wl = make_workload(rank)
-    nb, nocc = WORKLOAD["nb"], WORKLOAD["nocc"]
+    w = WORKLOAD
+    wl = make_workload(rank, T.sphere_size(w["n"], w["a"], w["ecut"]))
+    nb, nocc = w["nb"], w["nocc"]
     stream = torch.cuda.current_stream(dev)
     sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
     npw = sys_.npw
@@ -228,10 +256,9 @@ def run_native(args):
         sys_.apply(X, out=LA, stream=stream)
     torch.cuda.synchronize(dev)
 
-    # timed region
+    # timed region: the bare operator (no profiler events)
     sampler = ClockSampler(local if ws > 1 else 0)
     sampler.start()
-    T.profile_enable(True)
     launches0 = T.launch_count()
     barrier(ws)
     torch.cuda.synchronize(dev)
@@ -245,11 +272,22 @@ def run_native(args):
     barrier(ws)
     ms = e0.elapsed_time(e1)
     launches = T.launch_count() - launches0
-    prof = T.profile_read()
-    T.profile_enable(False)
     clocks = sampler.stop()
     value, sec_max = job_throughput(ws, args.steps * nb, ms / 1e3)
     ms_max = sec_max * 1e3
+    nrows = max(1, args.cpu_rows)
+    la_rows = LA[0, :nrows].cpu().numpy()
+    x_rows = X[0, :nrows].cpu().numpy()
+
+    # per-class device time of the plane kernels: a separate pass with the library's
+    # profiler (CUDA events around every plane-kernel launch, on the launching stream)
+    prof_steps = max(1, min(args.steps, 3))
+    T.profile_enable(True)
+    for _ in range(prof_steps):
+        sys_.apply(X, out=LA, stream=stream)
+    torch.cuda.synchronize(dev)
+    prof = T.profile_read()
+    T.profile_enable(False)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     Xh_t = torch.from_numpy(wl.X.astype(np.complex64)).pin_memory()
@@ -298,6 +336,7 @@ def run_native(args):
 
     # plain FP64 GPU path on the same batch
     fp64 = None
+    la64_rows = None
     if args.fp64_steps > 0:
         del LA
         s64 = T.system_from_workload(wl, precision=T.PREC_FP64, stream=stream)
@@ -315,6 +354,7 @@ def run_native(args):
         fms = max_over_ranks(ws, f0.elapsed_time(f1))
         fp64 = {"value": ws * args.fp64_steps * nb / (fms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": fms / args.fp64_steps}
+        la64_rows = LA64[0, :nrows].cpu().numpy()
         s64.close()
 
     if rank != 0:
@@ -327,20 +367,21 @@ def run_native(args):
     src_hash = kernel_source_hash()
     traffic = NCU_TRAFFIC.get(f"{src_hash}/{n_exchange}", {}).get(dom)
     shares = {k: round(v["ms"] / max(1e-9, sum(c["ms"] for c in cls.values())), 4) for k, v in cls.items()}
+    cfg = bench_config(ws)
+    cfg["npw"] = npw
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "npw": npw, "nocc": nocc, "nb": nb,
-                   "exchange_grid": n_exchange,
-                   "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (trial vectors and outputs in real space: 2 x 3.1 GB per step)"},
+        "config": cfg,
+        "schedule": {"exchange_grid": n_exchange, "step": "one tddft_apply_liouville on the whole batch"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                      "traffic": traffic, "peak_source": peaks["source"],
                      "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                      "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
-                     "class_time_share": shares, "kernel_sources": src_hash},
+                     "class_time_share": shares, "kernel_sources": src_hash,
+                     "timing": f"separate pass of {prof_steps} step(s) with per-launch CUDA events"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -351,12 +392,23 @@ def run_native(args):
         "speedup_vs_fp64_path": (value / fp64["value"]) if fp64 else None,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        rows = [(0, v) for v in range(args.cpu_rows)]
-        dt, cores = oracle_sample(wl, rows)
-        line["cpu_baseline"] = {"value": (len(rows) / nocc) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+        from oracle import tddft_oracle as O
+        rows = [(0, v) for v in range(nrows)]
+        S = O.system_from_workload(wl)
+        S.phi_src_r()  # orbitals to real space once, as the oracle's set-up
+        t0 = time.perf_counter()
+        want = S.apply(wl.X, rows=rows)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": (len(rows) / nocc) / dt, "unit": UNIT, "cores": O.fft_workers(),
+                                "kind": "oracle",
                                 "sample": f"{len(rows)} rows (b=0, v=0..{len(rows)-1}) of the same batch: all pair "
                                           f"convolutions of those rows plus the Hartree/xc density of b=0; "
                                           f"rows/s / Nocc; {dt:.1f} s"}
+        errs = {"fp32_path": row_errors(la_rows, want, x_rows),
+                "tolerance": {"rows_rel_err": 1e-5, "omega_abs_err_Ha": 1e-6}}
+        if la64_rows is not None:
+            errs["fp64_path"] = row_errors(la64_rows, want, wl.X[0, :nrows])
+        line["errors_vs_oracle"] = errs
     print(json.dumps(line), flush=True)
     sys_.close()
 
@@ -588,7 +640,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")

@@ -121,9 +121,14 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller);
  * unsupported (n, precision) or when S does not fit the grid. */
 tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange);
 
-/* Build a system: copy the inputs to the device, build the sphere map and
- * kernel tables, transform the orbitals to real space and allocate the
- * workspace for nb_max trial vectors. The orbitals are checked orthonormal
+/* Build a system: the inputs of the operator of Eq. 9 (spin-flip: Eq. 21) --
+ * the occupied orbitals phi_v and eigenvalues eps_v of Eq. 3 (both spins for
+ * spin-flip, Sec. 2.3), the local part of H^KS (Eq. 3), the local kernel f_xc of
+ * Eq. 4 (f_xc^SF for spin-flip), the exact-exchange fraction alpha of the hybrid
+ * functional (Sec. 2.1) and the Coulomb kernel of the exchange terms (Eqs. 3, 6
+ * and Sec. 3.1) at G = 0. It copies the inputs to the device, builds the sphere
+ * map and kernel tables, transforms the orbitals to real space and allocates
+ * the workspace for nb_max trial vectors. The orbitals are checked orthonormal
  * in FP64 (max |Phi^dagger Phi - I| <= 1e-10) -> else TDDFT_EINVAL.
  * When tddft_exchange_grid gives a smaller grid, the handle also builds the
  * same system on that grid for the pair-convolution terms (tuning.exchange_grid);
@@ -347,17 +352,24 @@ tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X
 typedef struct tddft_davidson* tddft_dav_handle;
 
 /* Start a solve for nroots roots from nguess >= nroots guess vectors
- * X0 (HOST complex128 [nguess][nocc_src][npw]); max_basis >= 2*nroots bounds
- * the basis before a restart. Applies L to the guess (stream-ordered). */
+ * X0 (HOST complex128 [nguess][nocc_src][npw]); 2*nroots <= max_basis <= 1024
+ * bounds the basis before a restart (EINVAL outside). Applies L to the guess
+ * and synchronises the stream. */
 tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const double* X0, int max_basis,
                                    void* stream, tddft_dav_handle* out);
 
-/* One Davidson iteration: Rayleigh-Ritz on the current basis, residuals,
- * preconditioned corrections, FP64 orthogonalisation against the target
- * orbitals and the basis, and L applied to the new vectors. Writes the
- * current Ritz values (HOST double [nroots]) and the number of roots with
- * residual norm < tol. One host synchronisation. TDDFT_ENUMERIC if the
- * subspace eigensolver fails. */
+/* One Davidson iteration (Sec. 4 names Davidson's method for L; the block
+ * scheme is this library's): Rayleigh-Ritz on the current basis (H = V^H L V
+ * and its Hermitian eigenproblem, both FP64 on the device), Ritz vectors,
+ * residuals and their norms, then preconditioned corrections r_i/(|G|^2/2 -
+ * eps_v - theta_i) (|denominator| clamped >= 0.1 Ha, eps_v the FP64 values
+ * given at set-up), FP64 orthogonalisation against the target orbitals and the
+ * basis, and L applied to the new vectors. Writes the current Ritz values
+ * (HOST double [nroots]), optionally the residual norms (HOST double [nroots]),
+ * and the number of roots with residual norm < tol. One host synchronisation
+ * per call (the Ritz values, residual norms and status flags come back in one
+ * copy). TDDFT_ENUMERIC if the subspace eigensolver does not converge;
+ * TDDFT_ETIMEOUT if a bounded device wait of the projector ran out. */
 tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converged, double* ritz_values,
                                  double* residual_norms, void* stream);
 
@@ -394,12 +406,19 @@ tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, 
  * The call allocates nothing: its working memory is one file-scope device
  * array of 3.5 MiB that every GPU which loads the library keeps until the
  * process exits, which limits n to <= 48 (larger n -> TDDFT_EINVAL with a
- * message naming the limit). The first call on a device looks up the
- * array's device address (set-up, once per device); make that first call
- * before any stream capture. Every call uses the same array and leaves its
- * contents behind; calls whose work overlaps on the GPU (different streams,
- * or several host threads) race on it and must be serialised by the caller.
- * Stream-ordered; the host tables are copied with cudaMemcpyAsync. */
+ * message naming the limit). Set-up: the first call on a device looks up the
+ * array's device address, and the first call with a given n on a device sets
+ * the launch attributes and constant twiddles of that grid (synchronous);
+ * make such first calls before any stream capture. The array also holds the
+ * tables of one geometry (twiddles, Coulomb kernel, sphere map): a call whose
+ * (n, a, ecut, kx_g0) differs from the geometry the array holds rebuilds them
+ * on the host and copies them in with cudaMemcpyAsync on `stream` (the host
+ * buffers are pageable and released on return); a call with the same geometry
+ * launches kernels only. Every call uses the same array and leaves its
+ * contents behind (the fields it needs at zero are cleared by the call itself);
+ * calls whose work overlaps on the GPU (different streams, or several host
+ * threads) race on it and must be serialised by the caller. Stream-ordered
+ * on `stream`. */
 tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut, double alpha, double kx_g0,
                                          const void* phi_pw, const void* a_pw, void* out_pw, void* stream);
 

@@ -1,11 +1,11 @@
 /*
- * Host-only entry points to the library's small dense FP64 routines, for testing them on
- * the CPU. They are the routines that the Davidson step uses for its Rayleigh-Ritz problem
- * (Hermitian eigenproblem) and that the ACE build uses for -M = L L^dagger and L^{-1}
- * (Sec. 3.1); they are not part of the operator's interface.
+ * Test entry points to the library's small dense FP64 routines. They are the routines that
+ * the Davidson step uses for its Rayleigh-Ritz problem (Hermitian eigenproblem, solved on
+ * the device) and that the ACE build uses for -M = L L^dagger and L^{-1} (Sec. 3.1); they
+ * are not part of the operator's interface.
  *
  * Matrices are row-major n x n arrays of interleaved complex128 (2n^2 doubles), owned by
- * the caller. No call touches the GPU.
+ * the caller, in host memory. Only tddft_testing_herm_eig_device touches the GPU.
  */
 #ifndef TDDFT_TESTING_H
 #define TDDFT_TESTING_H
@@ -20,6 +20,13 @@ extern "C" {
  * by cyclic complex Jacobi rotations. EINVAL for n < 1 or a null pointer; ENUMERIC when the
  * sweeps do not converge (w and V then hold the last iterate). */
 tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V);
+
+/* The device solver of the Davidson step's Rayleigh-Ritz matrix (one-CTA cyclic Jacobi in the
+ * round-robin order, FP64) on the current device: the nr lowest eigenvalues (ascending, w[nr])
+ * and their eigenvectors (V [n][nr] row-major, column j for w[j]) of the Hermitian part of A.
+ * Allocates and frees its own device buffers and synchronises. EINVAL unless 1 <= nr <= n <=
+ * 1024; ENUMERIC when the sweeps do not converge. */
+tddft_status tddft_testing_herm_eig_device(int n, int nr, const double* A, double* w, double* V);
 
 /* In place: the lower Cholesky factor L of a Hermitian positive definite A (A = L L^dagger,
  * real positive diagonal, zeros above it). ENUMERIC when a pivot is not positive. */

@@ -2510,13 +2510,6 @@ static bool herm_eig(int n, std::vector<std::complex<double>> A, std::vector<dou
   return ok;
 }
 
-// y[i] = a[i] - theta * x[i]
-__global__ void k_residual(const cplx<double>* __restrict__ a, const cplx<double>* __restrict__ x, double theta,
-                           cplx<double>* __restrict__ y, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = {a[i].x - theta * x[i].x, a[i].y - theta * x[i].y};
-}
-
 // nrm[b] = ||x_b||_2 (one block per row of length len)
 __global__ void k_row_norms(const cplx<double>* __restrict__ x, long long len, double* __restrict__ nrm) {
   __shared__ double red[256];
@@ -2555,6 +2548,155 @@ __global__ void k_precondition(const cplx<double>* r, const double* __restrict__
   }
 }
 
+// theta-shifted residuals of nr Ritz pairs: y_i = a_i - theta_i x_i (theta on the device)
+__global__ void k_residuals(const cplx<double>* __restrict__ a, const cplx<double>* __restrict__ x,
+                            const double* __restrict__ theta, cplx<double>* __restrict__ y, long long len, int nr) {
+  const long long n = len * nr;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double t = theta[i / len];
+    y[i] = {a[i].x - t * x[i].x, a[i].y - t * x[i].y};
+  }
+}
+
+// FP64 Hermitian eigensolver of the Rayleigh-Ritz matrix on the device: cyclic
+// complex Jacobi rotations in the round-robin (tournament) order, so that the M/2
+// rotations of a round act on disjoint index pairs and are applied together; one
+// CTA. A [m][m] row-major is overwritten (its Hermitian part is taken first),
+// V [m][m] is workspace. Writes theta[0..nr) ascending, S [m][nr] row-major (column
+// j = eigenvector of theta[j]) and flag[0] = 1 when the off-diagonal norm fell
+// below 1e-15 of the Frobenius norm within 100 sweeps (else 0; outputs then hold
+// the last iterate).
+constexpr int JACOBI_THREADS = 256;
+constexpr int JACOBI_MAX_N = 1024;
+__global__ void __launch_bounds__(JACOBI_THREADS)
+    k_herm_jacobi(cplx<double>* A, cplx<double>* V, int m, int nr, double* theta, cplx<double>* S, double* flag) {
+  __shared__ double rc[JACOBI_MAX_N / 2], rs[JACOBI_MAX_N / 2];
+  __shared__ cplx<double> rph[JACOBI_MAX_N / 2];
+  __shared__ int rp[JACOBI_MAX_N / 2], rq[JACOBI_MAX_N / 2];
+  __shared__ double red[JACOBI_THREADS];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int M = m + (m & 1), np = M / 2;
+  auto block_sum = [&](double v) {
+    red[tid] = v;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+  };
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e - i * m;
+    V[e] = {i == j ? 1.0 : 0.0, 0.0};
+    if (i < j) {
+      const cplx<double> a = A[e], b = A[(long long)j * m + i];
+      const cplx<double> h = {0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+      A[e] = h;
+      A[(long long)j * m + i] = {h.x, -h.y};
+    } else if (i == j) {
+      A[e].y = 0.0;
+    }
+  }
+  __syncthreads();
+  double f = 0.0;
+  for (int e = tid; e < m * m; e += nt) f += A[e].x * A[e].x + A[e].y * A[e].y;
+  const double fro = block_sum(f);
+  bool conv = false;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double o = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e - i * m;
+      if (i < j) o += A[e].x * A[e].x + A[e].y * A[e].y;
+    }
+    if (block_sum(o) <= 1e-30 * fmax(fro, 1e-300)) {
+      conv = true;
+      break;
+    }
+    for (int r = 0; r < M - 1; ++r) {
+      for (int k = tid; k < np; k += nt) {
+        int p = k == 0 ? M - 1 : (r + k) % (M - 1);
+        int q = k == 0 ? r : (r - k + (M - 1)) % (M - 1);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, sn = 0.0;
+        cplx<double> ph = {1.0, 0.0};
+        if (q < m) {
+          const cplx<double> apq = A[(long long)p * m + q];
+          const double rr = sqrt(apq.x * apq.x + apq.y * apq.y);
+          if (rr >= 1e-300) {
+            ph = {apq.x / rr, apq.y / rr};
+            const double tau = (A[(long long)q * m + q].x - A[(long long)p * m + p].x) / (2.0 * rr);
+            const double t = tau == 0.0 ? 1.0 : (tau > 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        rc[k] = c;
+        rs[k] = sn;
+        rph[k] = ph;
+        rp[k] = p;
+        rq[k] = q;
+      }
+      __syncthreads();
+      // U = diag(1, conj(ph)) [[c, sn], [-sn, c]] on (p, q):  A <- A U,  V <- V U
+      for (int e = tid; e < np * m; e += nt) {
+        const int k = e / m, i = e - k * m;
+        const int p = rp[k], q = rq[k];
+        if (q >= m || rs[k] == 0.0) continue;
+        const double c = rc[k], sn = rs[k];
+        const cplx<double> cph = {rph[k].x, -rph[k].y};
+        const cplx<double> uqp = cscale(cph, -sn), uqq = cscale(cph, c);
+        cplx<double>* ai = A + (long long)i * m;
+        const cplx<double> aip = ai[p], aiq = ai[q];
+        ai[p] = cadd(cscale(aip, c), cmul(aiq, uqp));
+        ai[q] = cadd(cscale(aip, sn), cmul(aiq, uqq));
+        cplx<double>* vi = V + (long long)i * m;
+        const cplx<double> vip = vi[p], viq = vi[q];
+        vi[p] = cadd(cscale(vip, c), cmul(viq, uqp));
+        vi[q] = cadd(cscale(vip, sn), cmul(viq, uqq));
+      }
+      __syncthreads();
+      // A <- U^H A
+      for (int e = tid; e < np * m; e += nt) {
+        const int k = e / m, j = e - k * m;
+        const int p = rp[k], q = rq[k];
+        if (q >= m || rs[k] == 0.0) continue;
+        const double c = rc[k], sn = rs[k];
+        const cplx<double> cph = {rph[k].x, -rph[k].y};
+        const cplx<double> uqp = cscale(cph, -sn), uqq = cscale(cph, c);
+        const cplx<double> apj = A[(long long)p * m + j], aqj = A[(long long)q * m + j];
+        A[(long long)p * m + j] = cadd(cscale(apj, c), cmulc(uqp, aqj));
+        A[(long long)q * m + j] = cadd(cscale(apj, sn), cmulc(uqq, aqj));
+      }
+      __syncthreads();
+    }
+  }
+  // ascending order: rank of each diagonal entry (ties by index)
+  for (int i = tid; i < m; i += nt) {
+    const double di = A[(long long)i * m + i].x;
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[(long long)j * m + j].x;
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    if (rank < nr) {
+      theta[rank] = di;
+      for (int k = 0; k < m; ++k) S[(long long)k * nr + rank] = V[(long long)k * m + i];
+    }
+  }
+  if (tid == 0) flag[0] = conv ? 1.0 : 0.0;
+}
+
+// info[slot] = the handle's device-wait error flag (0 when the handle has none)
+__global__ void k_copy_flag(const int* __restrict__ err, double* __restrict__ info) {
+  info[0] = err ? (double)err[0] : 0.0;
+}
+
 struct tddft_davidson {
   tddft_system* h = nullptr;
   int nroots = 0, max_basis = 0, m = 0;
@@ -2572,6 +2714,9 @@ struct tddft_davidson {
   double* g2h = nullptr;          // [npw]
   double* eps = nullptr;          // [nocc_src]
   double* nrm = nullptr;          // [max_basis]
+  cplx<double>* evec = nullptr;   // [max_basis][max_basis] eigenvector workspace of the Rayleigh-Ritz solve
+  cplx<double>* ritz = nullptr;   // [max_basis][nroots] lowest Ritz coefficient vectors
+  double* info = nullptr;         // [2 nroots + 2]: Ritz values, residual norms, eigensolver flag, wait flag
   int nsplit = 1;
   std::vector<double> theta;
   ~tddft_davidson() {
@@ -2652,6 +2797,8 @@ tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const
   *out = nullptr;
   if (nroots < 1 || nguess < nroots) return fail(TDDFT_EINVAL, "need 1 <= nroots <= nguess");
   if (max_basis < 2 * nroots || max_basis < nguess) return fail(TDDFT_EINVAL, "max_basis must be >= 2*nroots and >= nguess");
+  if (max_basis > JACOBI_MAX_N)
+    return fail(TDDFT_EINVAL, "max_basis above the Rayleigh-Ritz solver's limit of " + std::to_string(JACOBI_MAX_N));
   if (h->d.nb_max < nroots) return fail(TDDFT_EINVAL, "the handle's nb_max must be >= nroots");
   if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "Davidson needs the projector term");
   if (h->d.term_mask & ~TDDFT_TERMS_ALL)
@@ -2680,6 +2827,9 @@ tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const
   A((void**)&d->g2h, sizeof(double) * h->npw);
   A((void**)&d->eps, sizeof(double) * h->d.nocc_src);
   A((void**)&d->nrm, sizeof(double) * max_basis);
+  A((void**)&d->evec, sizeof(cplx<double>) * max_basis * max_basis);
+  A((void**)&d->ritz, sizeof(cplx<double>) * max_basis * nroots);
+  A((void**)&d->info, sizeof(double) * (2 * nroots + 2));
   if (s != TDDFT_OK) {
     delete d;
     return s;
@@ -2694,15 +2844,9 @@ tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const
   const double tpiba = 2.0 * M_PI / h->d.a, tpiba2 = tpiba * tpiba;
   std::vector<double> g2h(h->npw);
   for (int i = 0; i < h->npw; ++i) g2h[i] = 0.5 * (tpiba2 * (double)sph[i].m2);
-  // the handle keeps eps in the working precision; Davidson keeps its own FP64 copy
-  std::vector<double> eps(h->d.nocc_src);
-  if (h->d.precision == TDDFT_PREC_FP64) {
-    cudaMemcpy(eps.data(), h->b.eps, eps.size() * sizeof(double), cudaMemcpyDeviceToHost);
-  } else {
-    std::vector<float> e32(h->d.nocc_src);
-    cudaMemcpy(e32.data(), h->b.eps, e32.size() * sizeof(float), cudaMemcpyDeviceToHost);
-    for (size_t i = 0; i < e32.size(); ++i) eps[i] = e32[i];
-  }
+  // the preconditioner's eigenvalues in FP64: the values given at set-up (the handle's
+  // device copy is in the working precision)
+  const std::vector<double>& eps = h->eps64;
   cudaMemcpyAsync(d->g2h, g2h.data(), g2h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d->eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d->R, X0, vb * nguess, cudaMemcpyHostToDevice, st);
@@ -2725,52 +2869,43 @@ tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converge
   if (!d || !n_converged || !ritz_values) return fail(TDDFT_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = d->m, nr = d->nroots;
-  // Rayleigh-Ritz: H = V^H L V (FP64), diagonalised on the host
+  // Rayleigh-Ritz on the device: H = V^H L V (FP64), its lowest nr eigenpairs by Jacobi rotations
   dav_overlap(d, d->V, m, d->LV, m, st);
-  std::vector<std::complex<double>> H((size_t)m * m);
-  CUDA_TRY(cudaMemcpyAsync(H.data(), d->small, H.size() * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  for (int i = 0; i < m; ++i)
-    for (int j = i; j < m; ++j) {
-      const std::complex<double> a = 0.5 * (H[(size_t)i * m + j] + std::conj(H[(size_t)j * m + i]));
-      H[(size_t)i * m + j] = a;
-      H[(size_t)j * m + i] = std::conj(a);
-    }
-  std::vector<double> w;
-  std::vector<std::complex<double>> S;
-  if (!herm_eig(m, H, w, S)) return fail(TDDFT_ENUMERIC, "subspace eigensolver did not converge");
-  d->theta.assign(w.begin(), w.begin() + nr);
-  // S restricted to the lowest nr columns, [m][nr] row-major, to the device
-  std::vector<std::complex<double>> Sx((size_t)m * nr);
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < nr; ++j) Sx[(size_t)i * nr + j] = S[(size_t)i * m + j];
-  CUDA_TRY(cudaMemcpyAsync(d->small, Sx.data(), Sx.size() * sizeof(cplx<double>), cudaMemcpyHostToDevice, st));
+  { k_herm_jacobi<<<1, JACOBI_THREADS, 0, st>>>(d->small, d->evec, m, nr, d->info, d->ritz, d->info + 2 * nr);
+    note_launch(); }
+  // Ritz vectors X = V S, W = L V S, residuals R = W - theta X and their norms
   const size_t vb = (size_t)d->len * sizeof(cplx<double>);
   CUDA_TRY(cudaMemsetAsync(d->X, 0, vb * nr, st));
   CUDA_TRY(cudaMemsetAsync(d->W, 0, vb * nr, st));
-  dav_combine(d, d->V, m, d->small, nr, 1.0, d->X, st);
-  dav_combine(d, d->LV, m, d->small, nr, 1.0, d->W, st);
-  for (int i = 0; i < nr; ++i)
-    { k_residual<<<grid_for(d->len, 256), 256, 0, st>>>(d->W + (long long)i * d->len, d->X + (long long)i * d->len,
-                                                       d->theta[i], d->R + (long long)i * d->len, d->len); note_launch(); }
-  { k_row_norms<<<nr, 256, 0, st>>>(d->R, d->len, d->nrm); note_launch(); }
-  std::vector<double> rn(nr);
-  CUDA_TRY(cudaMemcpyAsync(rn.data(), d->nrm, nr * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
+  dav_combine(d, d->V, m, d->ritz, nr, 1.0, d->X, st);
+  dav_combine(d, d->LV, m, d->ritz, nr, 1.0, d->W, st);
+  { k_residuals<<<grid_for(d->len * nr, 256), 256, 0, st>>>(d->W, d->X, d->info, d->R, d->len, nr); note_launch(); }
+  { k_row_norms<<<nr, 256, 0, st>>>(d->R, d->len, d->info + nr); note_launch(); }
+  { k_copy_flag<<<1, 1, 0, st>>>(d->h->b.dev_err, d->info + 2 * nr + 1); note_launch(); }
   STATUS_TRY(check_launch("davidson step"));
+  // the one host synchronisation: Ritz values, residual norms and both flags in one copy
+  std::vector<double> info(2 * nr + 2);
+  CUDA_TRY(cudaMemcpyAsync(info.data(), d->info, info.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (info[2 * nr + 1] != 0.0) {
+    CUDA_TRY(cudaMemsetAsync(d->h->b.dev_err, 0, sizeof(int), st));
+    return fail(TDDFT_ETIMEOUT, "a bounded device wait (tensor-core projector) ran out; results of the call are invalid");
+  }
+  if (info[2 * nr] != 1.0) return fail(TDDFT_ENUMERIC, "subspace eigensolver did not converge");
+  d->theta.assign(info.begin(), info.begin() + nr);
   int nconv = 0;
-  STATUS_TRY(check_device_flag(d->h, st));
-  for (int i = 0; i < nr; ++i) nconv += rn[i] < tol;
   for (int i = 0; i < nr; ++i) {
+    const double rn = info[nr + i];
+    nconv += rn < tol;
     ritz_values[i] = d->theta[i];
-    if (residual_norms) residual_norms[i] = rn[i];
+    if (residual_norms) residual_norms[i] = rn;
   }
   *n_converged = nconv;
   if (nconv == nr) return TDDFT_OK;
   // corrections for the unconverged roots
   std::vector<int> todo;
   for (int i = 0; i < nr; ++i)
-    if (!(rn[i] < tol)) todo.push_back(i);
+    if (!(info[nr + i] < tol)) todo.push_back(i);
   for (int i : todo)
     { k_precondition<<<grid_for(d->len, 256), 256, 0, st>>>(d->R + (long long)i * d->len, d->g2h, d->eps, d->theta[i],
                                                            d->h->npw, d->len, d->R + (long long)i * d->len); note_launch(); }
@@ -2822,7 +2957,17 @@ constexpr size_t NA_G = NA_A + NOALLOC_N3 * sizeof(cplx<float>);
 constexpr size_t NOALLOC_BYTES = NA_G + NOALLOC_N3 * sizeof(cplx<float>);  // 3.5 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 constexpr int NOALLOC_MAX_DEVICES = 64;
-unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+// per device: the scratch array's device address, the grid sizes whose launchers are
+// prepared, and the geometry whose tables the array holds now
+struct NoallocDevice {
+  unsigned char* ptr = nullptr;
+  std::vector<int> prepared;
+  bool tables = false;
+  int n = 0;
+  double a = 0.0, ecut = 0.0, kx_g0 = 0.0;
+  int npw = 0;
+};
+NoallocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
 }  // namespace
 
 extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut, double alpha, double kx_g0,
@@ -2833,22 +2978,24 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
     return fail(TDDFT_EINVAL, "grid size " + std::to_string(n) + " exceeds the allocation-free limit of " +
                                   std::to_string(NOALLOC_MAX_N));
   if (!supported_n(n, TDDFT_PREC_FP32)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
-  std::vector<Miller> sph;
-  STATUS_TRY(build_sphere(n, a, ecut, sph));
-  const int npw = (int)sph.size();
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(TDDFT_EINVAL, "device index out of range");
-  if (!g_noalloc_ptr[dev]) {
+  NoallocDevice& D = g_noalloc_dev[dev];
+  if (!D.ptr) {
     // set-up, once per device: the device address of the scratch array
     void* p = nullptr;
     CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = (unsigned char*)p;
+    D.ptr = (unsigned char*)p;
   }
-  unsigned char* base = g_noalloc_ptr[dev];
+  unsigned char* base = D.ptr;
   PlaneOps<float> o = plane_ops_for<float>(n);
   if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
-  CUDA_TRY(o.prepare());
+  if (std::find(D.prepared.begin(), D.prepared.end(), n) == D.prepared.end()) {
+    // set-up, once per device and grid size: launch attributes and constant twiddles
+    CUDA_TRY(o.prepare());
+    D.prepared.push_back(n);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const long long n3 = (long long)n * n * n;
   cplx<float>* tw = (cplx<float>*)(base + NA_TW);
@@ -2858,26 +3005,43 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
   cplx<float>* a_r = (cplx<float>*)(base + NA_A);
   cplx<float>* gbuf = (cplx<float>*)(base + NA_G);
 
-  // tables of this grid (the same host arithmetic as a handle's set-up)
-  std::vector<int> radices = plan_radices(n), rev(n);
-  for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
-  std::vector<cplx<float>> twh = host_twiddles<float>(n, radices);
-  const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
-  auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
-  std::vector<float> kh(n3);
-  for (int kz = 0; kz < n; ++kz)
-    for (int ky = 0; ky < n; ++ky)
-      for (int kxx = 0; kxx < n; ++kxx) {
-        const long long m2 = (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
-        const double vx = m2 == 0 ? kx_g0 : 4.0 * M_PI / (tpiba2 * (double)m2);
-        kh[((long long)rev[kz] * n + rev[ky]) * n + rev[kxx]] = (float)(vx / (double)n3);
-      }
-  std::vector<int> posh(npw);
-  for (int i = 0; i < npw; ++i)
-    posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
-  CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!(D.tables && D.n == n && D.a == a && D.ecut == ecut && D.kx_g0 == kx_g0)) {
+    // tables of this geometry (the same host arithmetic as a handle's set-up), uploaded
+    // only when the geometry differs from the one the array holds
+    std::vector<Miller> sph;
+    STATUS_TRY(build_sphere(n, a, ecut, sph));
+    const int npw_new = (int)sph.size();
+    std::vector<int> radices = plan_radices(n), rev(n);
+    for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
+    std::vector<cplx<float>> twh = host_twiddles<float>(n, radices);
+    if (twh.size() * sizeof(cplx<float>) > NA_KERN - NA_TW)
+      return fail(TDDFT_EINVAL, "twiddle table of grid " + std::to_string(n) + " exceeds its scratch region");
+    const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
+    auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
+    std::vector<float> kh(n3);
+    for (int kz = 0; kz < n; ++kz)
+      for (int ky = 0; ky < n; ++ky)
+        for (int kxx = 0; kxx < n; ++kxx) {
+          const long long m2 =
+              (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
+          const double vx = m2 == 0 ? kx_g0 : 4.0 * M_PI / (tpiba2 * (double)m2);
+          kh[((long long)rev[kz] * n + rev[ky]) * n + rev[kxx]] = (float)(vx / (double)n3);
+        }
+    std::vector<int> posh(npw_new);
+    for (int i = 0; i < npw_new; ++i)
+      posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
+    D.tables = false;
+    CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw_new * sizeof(int), cudaMemcpyHostToDevice, st));
+    D.tables = true;
+    D.n = n;
+    D.a = a;
+    D.ecut = ecut;
+    D.kx_g0 = kx_g0;
+    D.npw = npw_new;
+  }
+  const int npw = D.npw;
 
   // both orbitals to real space (cube cleared first: it keeps the previous call's contents)
   const float s_in = (float)(1.0 / std::sqrt(a * a * a));
@@ -2920,6 +3084,28 @@ tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V
   std::copy(vals.begin(), vals.end(), w);
   std::copy(vecs.begin(), vecs.end(), reinterpret_cast<std::complex<double>*>(V));
   return ok ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+}
+
+tddft_status tddft_testing_herm_eig_device(int n, int nr, const double* A, double* w, double* V) {
+  if (n < 1 || nr < 1 || nr > n || !A || !w || !V) return fail(TDDFT_EINVAL, "1 <= nr <= n and non-null arrays required");
+  if (n > JACOBI_MAX_N) return fail(TDDFT_EINVAL, "n above the device solver's limit of " + std::to_string(JACOBI_MAX_N));
+  TempAllocs tmp;
+  void *dA = nullptr, *dV = nullptr, *dS = nullptr, *dw = nullptr;
+  const size_t nn = (size_t)n * n * sizeof(cplx<double>);
+  STATUS_TRY(tmp.get(&dA, nn));
+  STATUS_TRY(tmp.get(&dV, nn));
+  STATUS_TRY(tmp.get(&dS, (size_t)n * nr * sizeof(cplx<double>)));
+  STATUS_TRY(tmp.get(&dw, (size_t)(nr + 1) * sizeof(double)));
+  CUDA_TRY(cudaMemcpy(dA, A, nn, cudaMemcpyHostToDevice));
+  k_herm_jacobi<<<1, JACOBI_THREADS>>>((cplx<double>*)dA, (cplx<double>*)dV, n, nr, (double*)dw, (cplx<double>*)dS,
+                                       (double*)dw + nr);
+  note_launch();
+  STATUS_TRY(check_launch("device Jacobi"));
+  std::vector<double> wf(nr + 1);
+  CUDA_TRY(cudaMemcpy(wf.data(), dw, wf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(V, dS, (size_t)n * nr * sizeof(cplx<double>), cudaMemcpyDeviceToHost));
+  std::copy(wf.begin(), wf.begin() + nr, w);
+  return wf[nr] == 1.0 ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
 }
 
 tddft_status tddft_testing_cholesky(int n, double* A) {

@@ -46,6 +46,7 @@ EXPORTS = [
     "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
     # include/tddft_testing.h
     "tddft_testing_herm_eig", "tddft_testing_cholesky", "tddft_testing_lower_inverse",
+    "tddft_testing_herm_eig_device",
 ]
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
@@ -131,6 +132,7 @@ def load() -> ctypes.CDLL:
         "tddft_testing_herm_eig": ([ci, vp, vp, vp], st),
         "tddft_testing_cholesky": ([ci, vp], st),
         "tddft_testing_lower_inverse": ([ci, vp, vp], st),
+        "tddft_testing_herm_eig_device": ([ci, ci, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

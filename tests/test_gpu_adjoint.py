@@ -1,9 +1,11 @@
 """Adjoint of omega = <X|L X> on the GPU against the FP64 oracle gradient.
 
 The oracle's gradient is itself pinned to central finite differences in
-tests/test_oracle_pins.py. Tolerances: FP64 1e-10 relative, FP32 1e-4 relative
-(Frobenius norm over all coefficients).
+tests/test_oracle_pins.py. Tolerances: gradients FP64 1e-10 relative, FP32 1e-4
+relative (Frobenius norm over all coefficients); omega (the excitation energy of
+Eq. 9 for a normalised X) FP64 1e-10 relative, FP32 1e-6 Ha absolute.
 """
+
 import numpy as np
 import pytest
 
@@ -30,6 +32,13 @@ def _rel(got, want):
     return np.linalg.norm(got - want) / np.linalg.norm(want)
 
 
+def _omega_err_ok(om, om_o, prec):
+    err = np.abs(np.asarray(om) - np.asarray(om_o)).max()
+    if prec == T.PREC_FP32:
+        return err < 1e-6, err
+    return err < 1e-10 * np.abs(om_o).max(), err
+
+
 @pytest.mark.parametrize("prec,tol", [(T.PREC_FP64, 1e-10), (T.PREC_FP32, 1e-4)])
 @pytest.mark.parametrize("shape", [(12, 7.0, 3.0, 3, 2, 8), (24, 10.0, 10.0, 8, 3, 9)])
 def test_adjoint_matches_oracle(torch, prec, tol, shape):
@@ -43,7 +52,8 @@ def test_adjoint_matches_oracle(torch, prec, tol, shape):
     torch.cuda.synchronize()
     s.close()
     om, g, gv = om.cpu().numpy(), g.cpu().numpy().astype(np.complex128), gv.cpu().numpy()
-    assert np.abs(om - om_o).max() < tol * np.abs(om_o).max()
+    ok, err = _omega_err_ok(om, om_o, prec)
+    assert ok, (err, om_o)
     assert _rel(g, g_o) < tol
     assert _rel(gv, gv_o) < tol
 
@@ -75,7 +85,8 @@ def test_spin_flip_adjoint_matches_oracle(torch, prec, tol, shape):
     s.close()
     om, g, gv = om.cpu().numpy(), g.cpu().numpy().astype(np.complex128), gv.cpu().numpy()
     assert g.shape == (ns + nt, wl.phi_src.shape[1])
-    assert np.abs(om - om_o).max() < tol * np.abs(om_o).max()
+    ok, err = _omega_err_ok(om, om_o, prec)
+    assert ok, (err, om_o)
     assert _rel(g[:ns], g_o[:ns]) < tol
     assert _rel(g[ns:], g_o[ns:]) < tol
     assert _rel(gv, gv_o) < tol
@@ -150,7 +161,9 @@ def test_diamond64_adjoint_properties(torch):
     s32.close()
     assert _rel(g32.cpu().numpy().astype(np.complex128), g64) < 1e-4
     assert _rel(gv32.cpu().numpy(), gv_closed) < 1e-5
-    assert np.abs(om32.cpu().numpy() - om64.cpu().numpy()).max() < 1e-5 * np.abs(om64.cpu().numpy()).max()
+    # omega in FP32 within 1e-6 Ha of the FP64 path (which matches the oracle to 1e-11 relative)
+    om_err = np.abs(om32.cpu().numpy() - om64.cpu().numpy()).max()
+    assert om_err < 1e-6, (om_err, om64.cpu().numpy())
 
     # direction d orthogonal to every orbital and every trial orbital, normalised
     rng = np.random.default_rng(5)

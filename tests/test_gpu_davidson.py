@@ -94,3 +94,28 @@ def test_davidson_larger_system_iterates(torch):
     G = np.einsum("rvg,svg->rs", V.conj(), V)
     assert np.abs(G - np.eye(2)).max() < 1e-10
     assert np.abs(np.einsum("ug,rvg->ruv", wl.phi_src.conj(), V)).max() < 1e-12
+
+
+@pytest.mark.parametrize("m,nr", [(1, 1), (2, 2), (7, 3), (33, 5), (96, 8)])
+def test_device_rayleigh_ritz_solver_against_lapack(torch, m, nr):
+    """The Davidson step's device eigensolver (round-robin Jacobi, FP64) against numpy's
+    LAPACK eigh: the lowest nr eigenvalues and eigenvectors, also on a spectrum with
+    repeated eigenvalues."""
+    rng = np.random.default_rng(m)
+    B = rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m))
+    cases = [B + B.conj().T]
+    if m >= 7:
+        Q, _ = np.linalg.qr(B)
+        d = np.repeat(np.arange(m // 2 + 1, dtype=float), 2)[:m]
+        cases.append(Q @ np.diag(d) @ Q.conj().T)
+    for H in cases:
+        A = np.ascontiguousarray(H, dtype=np.complex128)
+        w = np.zeros(nr)
+        V = np.zeros((m, nr), dtype=np.complex128)
+        st = T.load().tddft_testing_herm_eig_device(m, nr, A.ctypes.data, w.ctypes.data, V.ctypes.data)
+        assert st == 0, T.load().tddft_last_error()
+        we = np.linalg.eigvalsh(H)
+        scale = max(1.0, np.abs(we).max())
+        assert np.abs(w - we[:nr]).max() < 1e-12 * scale
+        assert np.abs(H @ V - V * w).max() < 1e-11 * scale
+        assert np.abs(V.conj().T @ V - np.eye(nr)).max() < 1e-12
