@@ -247,7 +247,7 @@ def run_native(args):
     sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
     npw = sys_.npw
     # pair convolutions on the smallest grid on which they are exact (the same operator as on n^3)
-    sys_.set_tuning(exchange_grid=args.exchange_grid)
+    sys_.set_tuning(exchange_grid=args.exchange_grid, xy_kernel=args.xy_kernel)
     n_exchange = sys_.query()["n_exchange"]
     X = torch.from_numpy(wl.X).to(dev, torch.complex64)
     LA = torch.empty_like(X)
@@ -278,6 +278,10 @@ def run_native(args):
     nrows = max(1, args.cpu_rows)
     la_rows = LA[0, :nrows].cpu().numpy()
     x_rows = X[0, :nrows].cpu().numpy()
+
+    # measured arithmetic peaks of this GPU (ALU / tensor-core roofline denominators)
+    alu_peaks = {"fp32_fma_tflops": T.measure_peak(0)["tflops"], "tf32_tensor_tflops": T.measure_peak(1)["tflops"],
+                 "how": "tddft_testing_peak: FMA chains on every SM; tcgen05.mma kind::tf32 128x256x8 back to back"}
 
     # per-class device time of the plane kernels: a separate pass with the library's
     # profiler (CUDA events around every plane-kernel launch, on the launching stream)
@@ -374,7 +378,8 @@ def run_native(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": cfg,
-        "schedule": {"exchange_grid": n_exchange, "step": "one tddft_apply_liouville on the whole batch"},
+        "schedule": {"exchange_grid": n_exchange, "xy_kernel": args.xy_kernel,
+                     "step": "one tddft_apply_liouville on the whole batch"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                      "traffic": traffic, "peak_source": peaks["source"],
@@ -384,6 +389,7 @@ def run_native(args):
                      "timing": f"separate pass of {prof_steps} step(s) with per-launch CUDA events"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
+        "measured_alu_peaks": alu_peaks,
         "clocks": clocks,
         "terms_ms_per_step": term_ms or None,
         "k1d_only_apps_per_s": (nb / (term_ms["K1d"] / 1e3)) if term_ms else None,
@@ -650,6 +656,9 @@ def main():
                                              "taucache (K1d from stored tau of every pair)")
     ap.add_argument("--exchange-grid", type=int, default=1, choices=[0, 1],
                     help="1: pair convolutions on the smallest exact grid (64^3 here; the default); 0: on the 72^3 grid")
+    ap.add_argument("--xy-kernel", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="register-line xy passes where they exist: 1 one thread per line (the default), 2 two "
+                         "lanes per line, 3 forward one thread, inverse two lanes; 0: shared-memory radix stages")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()

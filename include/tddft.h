@@ -176,8 +176,9 @@ typedef struct tddft_tuning {
                        value in set_tuning */
   int z_kernel;     /* z pass: 0 shared-memory radix stages; 1 register-resident columns
                        (FP32, n <= 80); 2 (default where it exists: FP32, n = 16, 24,
-                       32, 48, 64, 72) as 1, with the compact pair-density
-                       convolutions on two threads per column. -1 keeps the value in
+                       32, 48, 64, 72, 96) as 1, with the compact pair-density
+                       convolutions on two threads per column (at n = 96 only those; its
+                       other z passes are the shared-memory ones). -1 keeps the value in
                        set_tuning */
   int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with
                        split-precision TF32 products (hi*hi + hi*lo + lo*hi, FP32
@@ -209,6 +210,15 @@ typedef struct tddft_tuning {
                        the n grid up to rounding; the local terms (V_loc, K1e, the
                        diagonal) stay on the n grid. tddft_info.n_exchange reports the grid
                        in use. 0: every term on the n grid. -1 keeps the value */
+  int xy_kernel;    /* xy passes of the compact pair-density convolutions, where the
+                       register-line kernels exist (FP32, n = 32, 48, 64; the shared-memory
+                       radix stages elsewhere). Register-line passes transpose the plane once
+                       through shared memory and hold each line either in one thread (the
+                       whole line transform in registers) or in two lanes (radix-2 butterfly
+                       by warp shuffle, the rest in registers). 1 (default): one thread per
+                       line in both passes; 2: two lanes per line in both; 3: forward pass
+                       one thread per line, inverse pass two lanes per line; 0: the
+                       shared-memory radix stages. -1 keeps the value */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

@@ -28,6 +28,15 @@ tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V
  * 1024; ENUMERIC when the sweeps do not converge. */
 tddft_status tddft_testing_herm_eig_device(int n, int nr, const double* A, double* w, double* V);
 
+/* Measured arithmetic peak of the current device, for roofline denominators: which = 0 FP32
+ * FMA throughput of the CUDA cores (16 independent FMA chains per thread, 8 CTAs of 256
+ * threads per SM); which = 1 TF32 tensor-core throughput (tcgen05.mma kind::tf32, M = 128,
+ * N = 256, K = 8, one issuing thread per SM, operands in shared memory, accumulator in tensor
+ * memory). Writes TFLOP/s (2 flops per multiply-add) of the fastest of three timed launches
+ * after a warm-up, and optionally that launch's ms. Synchronises; EINVAL for another which;
+ * ETIMEOUT if a bounded wait of the tensor-core kernel ran out. */
+tddft_status tddft_testing_peak(int which, double* tflops, double* ms);
+
 /* In place: the lower Cholesky factor L of a Hermitian positive definite A (A = L L^dagger,
  * real positive diagonal, zeros above it). ENUMERIC when a pivot is not positive. */
 tddft_status tddft_testing_cholesky(int n, double* A);

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtddft.so")
-SOURCES = ["tddft_api.cu", "plane_f32.cu", "plane_f64.cu"]
+SOURCES = ["tddft_api.cu", "plane_f32.cu", "plane_f64.cu", "peaks.cu"]
 NVCC_FLAGS = ["-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

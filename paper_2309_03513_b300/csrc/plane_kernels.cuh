@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(ZREG_THREADS)
 // frequencies 2 k' + h in the digit-reversed order of the N/2 plan, which is the
 // order of the kernel table kern2 [(h N/2 + j)][nact]. The inverse runs the same
 // steps backwards (decimation-in-time butterfly, conjugate twiddles).
+// (also at N = 96, where a whole column does not fit one thread's registers but a half does)
 template <typename T, int N>
 __host__ __device__ constexpr bool z_pair_ok() {
-  return z_in_registers<T, N>() && N % 2 == 0 && tw_offset(N / 2) >= 0;
+  return (z_in_registers<T, N>() || (sizeof(T) == 4 && N == 96)) && N % 2 == 0 && tw_offset(N / 2) >= 0;
 }
 
 template <typename T>

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "plane_lines.cuh"
 
 namespace tddft {
 
@@ -18,7 +19,8 @@ void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double bytes);
 
 // z = 0: shared-memory staged z pass; 1: register-resident columns (FP32, n <= 80);
-// 2: as 1, with the compact pair-density convolutions on two threads per column.
+// 2: as 1, with the compact pair-density convolutions on two threads per column (FP32,
+// n <= 80 and n = 96; at 96 the other z passes are the staged ones).
 struct KernelChoice {
   int z = 1;
 };
@@ -30,6 +32,12 @@ struct KernelChoice {
 struct ColumnList {
   const int* cols = nullptr;
   int nact = 0;
+  // compact index of every (x, y) position, transposed ([x][y], -1 outside the disc): when
+  // given (and the register-line kernels exist for N), the xy passes of compact planes run
+  // on the register-line kernels of plane_lines.cuh
+  const int* cmapT = nullptr;
+  int lanes_fwd = 1;  // register-line kernels: lanes per line (1 or 2) of the forward pass
+  int lanes_inv = 2;  // and of the inverse pass
 };
 
 template <typename T>
@@ -37,6 +45,7 @@ struct PlaneOps {
   int n = 0;
   bool reg_ok = false;   // the register-resident z pass exists for this (T, N)
   bool pair_ok = false;  // the two-threads-per-column z pass exists for this (T, N)
+  bool lines_ok = false; // the register-line xy passes exist for this (T, N)
   KernelChoice kc;
   cudaError_t (*prepare)() = nullptr;
   void (*f_xy_fwd)(int mode, const cplx<T>* qb, const cplx<T>* rb, PairMap pm, int items, cplx<T>* ibuf,
@@ -90,6 +99,16 @@ struct PlaneLaunch {
     TDDFT_CARVE((k_xy_inv<T, N, INV_WRITE>))
     TDDFT_CARVE((k_xy_inv<T, N, INV_ACCUM>))
     TDDFT_CARVE((k_xy_inv<T, N, INV_ATOMIC>))
+    if constexpr (xy_lines_ok<T, N>()) {
+      TDDFT_CARVE((k_xy_fwd_lines<T, N, XY_LOAD, 1>))
+      TDDFT_CARVE((k_xy_fwd_lines<T, N, XY_PRODUCT, 1>))
+      TDDFT_CARVE((k_xy_inv_lines<T, N, INV_WRITE, 1>))
+      TDDFT_CARVE((k_xy_inv_lines<T, N, INV_ATOMIC, 1>))
+      TDDFT_CARVE((k_xy_fwd_lines<T, N, XY_LOAD, 2>))
+      TDDFT_CARVE((k_xy_fwd_lines<T, N, XY_PRODUCT, 2>))
+      TDDFT_CARVE((k_xy_inv_lines<T, N, INV_WRITE, 2>))
+      TDDFT_CARVE((k_xy_inv_lines<T, N, INV_ATOMIC, 2>))
+    }
 #undef TDDFT_CARVE
     // constant-memory twiddles W_N^e for the register-resident transforms,
     // computed in FP64 on the host and rounded once
@@ -125,7 +144,27 @@ struct PlaneLaunch {
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
     const double fout = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;  // share of the plane written
     prof_begin(KC_XY_FWD, st);
-    if (mode == XY_PRODUCT)
+    bool done = false;
+    if constexpr (xy_lines_ok<T, N>()) {
+      if (cl.cols && cl.cmapT) {
+        done = true;
+        if (cl.lanes_fwd == 2) {
+          if (mode == XY_PRODUCT)
+            k_xy_fwd_lines<T, N, XY_PRODUCT, 2><<<grid, lines_threads<N, 2>(), 0, st>>>(qb, rb, pm, ibuf, cl.cmapT,
+                                                                                     cl.nact);
+          else
+            k_xy_fwd_lines<T, N, XY_LOAD, 2><<<grid, lines_threads<N, 2>(), 0, st>>>(qb, rb, pm, ibuf, cl.cmapT, cl.nact);
+        } else {
+          if (mode == XY_PRODUCT)
+            k_xy_fwd_lines<T, N, XY_PRODUCT, 1><<<grid, lines_threads<N, 1>(), 0, st>>>(qb, rb, pm, ibuf, cl.cmapT,
+                                                                                     cl.nact);
+          else
+            k_xy_fwd_lines<T, N, XY_LOAD, 1><<<grid, lines_threads<N, 1>(), 0, st>>>(qb, rb, pm, ibuf, cl.cmapT, cl.nact);
+        }
+      }
+    }
+    if (done) {
+    } else if (mode == XY_PRODUCT)
       k_xy_fwd<T, N, XY_PRODUCT><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw, cl.cols, cl.nact);
     else
       k_xy_fwd<T, N, XY_LOAD><<<grid, NT, SMEM, st>>>(qb, rb, pm, ibuf, tw, cl.cols, cl.nact);
@@ -181,7 +220,30 @@ struct PlaneLaunch {
     constexpr double F = (double)N * N * N * sizeof(cplx<T>);
     const double fin = cl.cols ? (double)cl.nact / ((double)N * N) : 1.0;  // share of the plane read
     prof_begin(KC_XY_INV, st);
-    if (mode == INV_ACCUM)
+    bool done = false;
+    if constexpr (xy_lines_ok<T, N>()) {
+      if (cl.cols && cl.cmapT && mode != INV_ACCUM) {
+        done = true;
+        const dim3 g(N, mode == INV_ATOMIC ? targets * pm.kdim : targets);
+        if (cl.lanes_inv == 2) {
+          if (mode == INV_ATOMIC)
+            k_xy_inv_lines<T, N, INV_ATOMIC, 2><<<g, lines_threads<N, 2>(), 0, st>>>(ibuf, ob, pb, pm, scale, cl.cmapT,
+                                                                                   cl.nact);
+          else
+            k_xy_inv_lines<T, N, INV_WRITE, 2><<<g, lines_threads<N, 2>(), 0, st>>>(ibuf, ob, pb, pm, scale, cl.cmapT,
+                                                                                  cl.nact);
+        } else {
+          if (mode == INV_ATOMIC)
+            k_xy_inv_lines<T, N, INV_ATOMIC, 1><<<g, lines_threads<N, 1>(), 0, st>>>(ibuf, ob, pb, pm, scale, cl.cmapT,
+                                                                                   cl.nact);
+          else
+            k_xy_inv_lines<T, N, INV_WRITE, 1><<<g, lines_threads<N, 1>(), 0, st>>>(ibuf, ob, pb, pm, scale, cl.cmapT,
+                                                                                  cl.nact);
+        }
+      }
+    }
+    if (done) {
+    } else if (mode == INV_ACCUM)
       k_xy_inv<T, N, INV_ACCUM><<<dim3(N, targets), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw, cl.cols, cl.nact);
     else if (mode == INV_ATOMIC)
       k_xy_inv<T, N, INV_ATOMIC><<<dim3(N, targets * pm.kdim), NT, SMEM, st>>>(ibuf, ob, pb, pm, scale, tw, cl.cols,
@@ -198,6 +260,7 @@ struct PlaneLaunch {
     o.n = N;
     o.reg_ok = z_in_registers<T, N>();
     o.pair_ok = z_pair_ok<T, N>();
+    o.lines_ok = xy_lines_ok<T, N>();
     o.kc.z = o.pair_ok ? 2 : (o.reg_ok ? 1 : 0);
     o.prepare = &prepare;
     o.f_xy_fwd = &xy_fwd;

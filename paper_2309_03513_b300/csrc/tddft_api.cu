@@ -289,6 +289,7 @@ struct Buffers {
   double* wdev = nullptr;      // [nb_max]
   int* dev_err = nullptr;      // set by a device wait that ran out of polls
   int* zcols = nullptr;        // [n*n] column positions, the ncols_act that a pair density can occupy first
+  int* cmapT = nullptr;        // [n*n] compact index of position (x, y) at [x][y], -1 outside the disc
   void* kx_c = nullptr;        // [n][ncols_act] exchange kernel on those columns (compact pair densities)
   void* kh_c = nullptr;        // [n][ncols_act] Hartree kernel on those columns
   void* kx_p = nullptr;        // [n][ncols_act] exchange kernel in the order of the paired z pass
@@ -301,10 +302,11 @@ struct tddft_system {
   long long n3 = 0;
   int nb_chunk = 0;
   int ibuf_fields = 0;
-  int tile_targets = 32, tile_sources = 8, k1d_block = 16;
+  int tile_targets = 64, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
   bool prune = true;     // pair convolutions keep only the columns a pair density can occupy (compact)
+  int xy_lines = 1;      // compact xy passes on the register-line kernels where they exist (tuning.xy_kernel)
   // adaptively compressed exchange for the exchange term inside D (tddft_ace_build)
   bool ace_on = false;
   int n_ace = 0;
@@ -378,9 +380,16 @@ template <typename T>
 static ColumnList pair_columns(tddft_system* h) {
   ColumnList cl;
   const PlaneOps<T>& o = ops_of<T>(h);
-  if (h->prune && h->b.zcols && o.reg_ok && o.kc.z >= 1) {
+  if (h->prune && h->b.zcols && ((o.reg_ok && o.kc.z >= 1) || (o.pair_ok && o.kc.z == 2))) {
     cl.cols = h->b.zcols;
     cl.nact = h->ncols_act;
+    if (h->xy_lines && o.lines_ok) {
+      // 1: one thread per line in both passes; 2: two lanes per line in both; 3: forward
+      // pass one thread per line, inverse two lanes per line
+      cl.cmapT = h->b.cmapT;
+      cl.lanes_fwd = h->xy_lines == 2 ? 2 : 1;
+      cl.lanes_inv = h->xy_lines == 1 ? 1 : 2;
+    }
   }
   return cl;
 }
@@ -667,11 +676,20 @@ static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
     for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) {
       const int tj = std::min(K1D_CACHE_BLOCK, nocc - j0);
       // the pair convolutions of k1d_term, written straight into the block pair's slot
+      // (through compact intermediates in the pair buffer when the grid allows them)
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
-      o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, blk, tw, st);
-      o.z(Z_CONV, blk, ti * tj, (const T*)h->b.kx, T(1), tw, st);
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
-      o.xy_inv(INV_WRITE, blk, blk, nullptr, pw, ti * tj, T(1), tw, st);
+      const ColumnList cl = pair_columns<T>(h);
+      if (cl.cols && ti * tj <= h->ibuf_fields) {
+        cplx<T>* ib = (cplx<T>*)h->b.ibuf;
+        o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st, cl);
+        o.z(Z_CONV, ib, ti * tj, pair_kernel<T>(h, (const T*)h->b.kx, cl), T(1), tw, st, cl);
+        o.xy_inv(INV_WRITE, ib, blk, nullptr, pw, ti * tj, T(1), tw, st, cl);
+      } else {
+        o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, blk, tw, st);
+        o.z(Z_CONV, blk, ti * tj, (const T*)h->b.kx, T(1), tw, st);
+        o.xy_inv(INV_WRITE, blk, blk, nullptr, pw, ti * tj, T(1), tw, st);
+      }
       blk += (long long)ti * tj * h->n3;
     }
   }
@@ -724,6 +742,10 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   }
   // truncated pairs of the localised frame: blocks without a kept pair are skipped
   const unsigned char* keep = h->loc_on ? h->loc_keep : nullptr;
+  // compact pair-density intermediates when the grid allows them and the pair buffer holds
+  // both the intermediates and the tau fields of a block pair
+  const ColumnList ccl = pair_columns<T>(h);
+  const bool compact = ccl.cols && 2 * TB * TB <= h->ibuf_fields;
   auto block_kept = [&](int i0, int ti, int j0, int tj) {
     for (int i = i0; i < i0 + ti; ++i)
       for (int j = j0; j < j0 + tj; ++j)
@@ -737,16 +759,26 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       if (keep && !block_kept(i0, ti, j0, tj)) continue;
       // item = vi * tj + vj : Q = phi[j0 + vj], R = phi[i0 + vi]
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
-      o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
-      o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);  // full planes: the inverse runs in place
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
-      o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
+      const cplx<T>* tau = ib;
+      if (compact) {
+        // compact intermediates in the first half of the pair buffer, tau in the second
+        cplx<T>* taub = ib + (long long)TB * TB * h->n3;
+        o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st, ccl);
+        o.z(Z_CONV, ib, ti * tj, pair_kernel<T>(h, (const T*)h->b.kx, ccl), T(1), tw, st, ccl);
+        o.xy_inv(INV_WRITE, ib, taub, nullptr, pw, ti * tj, T(1), tw, st, ccl);
+        tau = taub;
+      } else {
+        o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st);
+        o.z(Z_CONV, ib, ti * tj, (const T*)h->b.kx, T(1), tw, st);  // full planes: the inverse runs in place
+        o.xy_inv(INV_WRITE, ib, ib, nullptr, pw, ti * tj, T(1), tw, st);
+      }
       {
         constexpr int KB = 16, PTS = 32;
         const size_t smem = (size_t)KB * KB * PTS * sizeof(cplx<T>);
         const unsigned blocks = (unsigned)((h->n3 + PTS - 1) / PTS);
         { k_k1d_contract<T, KB, PTS><<<blocks, K1D_THREADS, smem, st>>>(
-            ib, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3, keep); note_launch(); }
+            tau, (const cplx<T>*)h->b.a_r, (cplx<T>*)h->b.out_r, i0, ti, j0, tj, nocc, nbc, s, h->n3, keep); note_launch(); }
       }
     }
   }
@@ -952,22 +984,30 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
         if (mx * mx + my * my <= r2) zcols.push_back(py * n + px);
         else rest.push_back(py * n + px);
       }
-    // Within each part, interleave the 16 shared-memory bank classes of the positions
-    // (8-byte words y * (n + 1) + x in the plane kernels): the compact planes are staged
-    // with 16 consecutive list entries per half-warp, which then hit distinct banks.
-    auto interleave_banks = [n](std::vector<int>& v) {
-      std::vector<std::vector<int>> cls(16);
-      for (int q : v) cls[((q / n) * (n + 1) + q % n) % 16].push_back(q);
-      std::vector<int> out;
-      out.reserve(v.size());
-      std::vector<size_t> at(16, 0);
-      while (out.size() < v.size())
-        for (int k = 0; k < 16; ++k)
-          if (at[k] < cls[k].size()) out.push_back(cls[k][at[k]++]);
-      v.swap(out);
-    };
-    interleave_banks(zcols);
-    interleave_banks(rest);
+    if (o.lines_ok) {
+      // register-line xy passes: ordered by x position, then y position, so that the 16
+      // lanes writing rows y..y+15 of one x position store to consecutive entries
+      auto by_x = [n](int p, int q) { return std::make_pair(p % n, p / n) < std::make_pair(q % n, q / n); };
+      std::sort(zcols.begin(), zcols.end(), by_x);
+      std::sort(rest.begin(), rest.end(), by_x);
+    } else {
+      // Within each part, interleave the 16 shared-memory bank classes of the positions
+      // (8-byte words y * (n + 1) + x in the plane kernels): the compact planes are staged
+      // with 16 consecutive list entries per half-warp, which then hit distinct banks.
+      auto interleave_banks = [n](std::vector<int>& v) {
+        std::vector<std::vector<int>> cls(16);
+        for (int q : v) cls[((q / n) * (n + 1) + q % n) % 16].push_back(q);
+        std::vector<int> out;
+        out.reserve(v.size());
+        std::vector<size_t> at(16, 0);
+        while (out.size() < v.size())
+          for (int k = 0; k < 16; ++k)
+            if (at[k] < cls[k].size()) out.push_back(cls[k][at[k]++]);
+        v.swap(out);
+      };
+      interleave_banks(zcols);
+      interleave_banks(rest);
+    }
     h->ncols_act = (int)zcols.size();
     zcols.insert(zcols.end(), rest.begin(), rest.end());
   }
@@ -984,6 +1024,12 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   if (!zcols.empty()) {
     STATUS_TRY(dalloc(h, (void**)&B.zcols, zcols.size() * sizeof(int)));
     CUDA_TRY(cudaMemcpyAsync(B.zcols, zcols.data(), zcols.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (o.lines_ok) {
+      std::vector<int> cmapT((size_t)n * n, -1);
+      for (int c = 0; c < h->ncols_act; ++c) cmapT[(size_t)(zcols[c] % n) * n + zcols[c] / n] = c;
+      STATUS_TRY(dalloc(h, (void**)&B.cmapT, cmapT.size() * sizeof(int)));
+      CUDA_TRY(cudaMemcpy(B.cmapT, cmapT.data(), cmapT.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     // kernels on the compact columns: [z][c] = kappa at (z, zcols[c])
     const int na = h->ncols_act;
     kx_c.resize((size_t)n * na);
@@ -1105,7 +1151,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   size_t freeb = 0, totalb = 0;
   CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
   const size_t field = (size_t)n3 * ez;
-  h->ibuf_fields = std::max(16, std::min(512, (int)((size_t)(1u << 30) / field)));
+  h->ibuf_fields = std::max(16, std::min(1024, (int)((size_t)(2u << 30) / field)));
   const size_t fixed = field * ((size_t)h->ibuf_fields + (size_t)d.nocc_src + (h->sf() ? ntgt : 0));
   const size_t per_b = field * (2 * (size_t)d.nocc_src + 2);
   const size_t budget = (size_t)(0.6 * (double)freeb);
@@ -1933,7 +1979,7 @@ static tddft_status sync_tau_cache(tddft_system* h) {
 static bool z_kernel_ok(const tddft_system* h, int z) {
   const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
   const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
-  return z == 0 || (reg && (z == 1 || pair));
+  return z == 0 || (z == 1 && reg) || (z == 2 && pair);
 }
 
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
@@ -1963,10 +2009,15 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     if (t->z_kernel > 2) return fail(TDDFT_EINVAL, "z_kernel must be 0, 1 or 2");
     const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
     const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
-    if (t->z_kernel && !reg) return fail(TDDFT_EINVAL, "register-resident passes need FP32 and n <= 80");
-    if (t->z_kernel == 2 && !pair) return fail(TDDFT_EINVAL, "the paired z pass needs a supported n / 2");
+    if (t->z_kernel == 1 && !reg) return fail(TDDFT_EINVAL, "the register-resident z pass needs FP32 and n <= 80");
+    if (t->z_kernel == 2 && !pair)
+      return fail(TDDFT_EINVAL, "the paired z pass needs FP32, n <= 80 or n = 96, and a supported n / 2");
     h->ops32.kc.z = t->z_kernel;
     h->ops64.kc.z = t->z_kernel;
+  }
+  if (t->xy_kernel >= 0) {
+    if (t->xy_kernel > 3) return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 3");
+    h->xy_lines = t->xy_kernel;
   }
   tddft_status cs = TDDFT_OK;
   if (t->exchange_grid > 1) cs = fail(TDDFT_EINVAL, "exchange_grid must be 0 or 1");
@@ -2003,6 +2054,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->k1d_sparse = h->k1d_sparse;
   t->k1d_cache = h->k1d_cache_req ? 1 : 0;
   t->exchange_grid = h->use_xsub ? 1 : 0;
+  t->xy_kernel = h->xy_lines;
   return TDDFT_OK;
 }
 
@@ -2095,8 +2147,8 @@ tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, voi
   struct Cand {
     int tt, ks, acc, kb;
   };
-  const Cand cands[] = {{32, 8, 1, 16}, {16, 8, 1, 16}, {8, 8, 1, 16}, {32, 4, 1, 16}, {64, 4, 1, 16},
-                        {16, 16, 1, 16}, {32, 8, 0, 16}, {8, 8, 1, 8}};
+  const Cand cands[] = {{64, 8, 1, 16}, {128, 8, 1, 16}, {32, 8, 1, 16}, {64, 16, 1, 16}, {16, 8, 1, 16},
+                        {32, 4, 1, 16}, {32, 8, 0, 16}, {8, 8, 1, 8}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));

@@ -46,7 +46,7 @@ EXPORTS = [
     "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
     # include/tddft_testing.h
     "tddft_testing_herm_eig", "tddft_testing_cholesky", "tddft_testing_lower_inverse",
-    "tddft_testing_herm_eig_device",
+    "tddft_testing_herm_eig_device", "tddft_testing_peak",
 ]
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
@@ -73,7 +73,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("targets", ctypes.c_int), ("sources", ctypes.c_int), ("k1d_block", ctypes.c_int),
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int),
-                ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int), ("exchange_grid", ctypes.c_int)]
+                ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int), ("exchange_grid", ctypes.c_int),
+                ("xy_kernel", ctypes.c_int)]
 
 
 class ZvectorOpts(ctypes.Structure):
@@ -133,6 +134,7 @@ def load() -> ctypes.CDLL:
         "tddft_testing_cholesky": ([ci, vp], st),
         "tddft_testing_lower_inverse": ([ci, vp, vp], st),
         "tddft_testing_herm_eig_device": ([ci, ci, vp, vp, vp], st),
+        "tddft_testing_peak": ([ci, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +173,15 @@ def sphere_miller(n: int, a: float, ecut: float) -> np.ndarray:
     m = np.zeros((npw, 3), dtype=np.int32)
     _check(load().tddft_sphere_miller(n, a, ecut, m.ctypes.data), "tddft_sphere_miller")
     return m
+
+
+def measure_peak(which: int) -> dict:
+    """Measured arithmetic peak of the current device (tddft_testing_peak): which = 0 FP32 FMA,
+    1 TF32 tcgen05 tensor cores. Returns {"tflops", "ms"}."""
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(load().tddft_testing_peak(int(which), ctypes.byref(tf), ctypes.byref(ms)), "tddft_testing_peak")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def profile_enable(on: bool = True):
@@ -277,9 +288,10 @@ class LiouvilleSystem:
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
                    graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1,
-                   k1d_cache: int = -1, exchange_grid: int = -1):
+                   k1d_cache: int = -1, exchange_grid: int = -1, xy_kernel: int = -1):
         t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
-                   int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache), int(exchange_grid))
+                   int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache), int(exchange_grid),
+                   int(xy_kernel))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 
     def query(self) -> dict:

@@ -160,19 +160,28 @@ def test_ragged_tiles_give_the_same_result(torch):
     assert _rel_err(got, want).max() < 1e-5
 
 
-@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0), (32, 9.0, 12.0)])
+@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (72, 13.48, 25.0), (32, 9.0, 12.0), (64, 11.0, 25.0),
+                                      (48, 10.0, 20.0)])
 def test_kernel_variants_fp32(torch, n, a, ecut):
     """Every plane-pass variant (compact pair densities on / off, staged / register-resident /
-    paired register z pass, loop / atomic accumulation) gives the oracle's L. The 24^3 grid aliases
-    pair densities (pruning stays off there); 72^3 and 32^3 do not."""
+    paired register z pass, loop / atomic accumulation, staged / register-line xy passes with one or
+    two lanes per line) gives the
+    oracle's L. The 24^3 grid aliases pair densities (pruning stays off there); 72^3, 64^3, 48^3 and
+    32^3 do not (the register-line xy passes exist for 32, 48 and 64)."""
     wl = _workload(n, a, ecut, 6, 2, seed=15)
     want = O.system_from_workload(wl).apply(wl.X)
     for prune in (0, 1):
         for z in (0, 1, 2):
             for acc in (0, 1):
-                got = _run(torch, wl, T.PREC_FP32, tiling=dict(targets=3, sources=4, k1d_block=5, accumulate=acc,
-                                                              prune=prune, z_kernel=z))
-                assert _rel_err(got, want).max() < 1e-5, (prune, z, acc)
+                for xy in (0, 1, 2, 3):
+                    if xy != 0 and (prune == 0 or z == 0):
+                        continue  # full planes: the xy passes are the staged ones whatever xy_kernel says
+                    if xy in (2, 3) and acc == 0:
+                        continue  # the loop accumulation runs the staged inverse pass
+                    got = _run(torch, wl, T.PREC_FP32, tiling=dict(targets=3, sources=4, k1d_block=5,
+                                                                  accumulate=acc, prune=prune, z_kernel=z,
+                                                                  xy_kernel=xy))
+                    assert _rel_err(got, want).max() < 1e-5, (prune, z, acc, xy)
     got = _run(torch, wl, T.PREC_FP64, tiling=(3, 4, 5, 1, -1, 1, 0))
     assert _rel_err(got, want).max() < 1e-11
 
@@ -198,7 +207,8 @@ def test_tuning_fields_round_trip(torch):
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
                dict(z_kernel=2),
                dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
-               dict(k1d_cache=1), dict(k1d_cache=0), dict(exchange_grid=0), dict(exchange_grid=1)):
+               dict(k1d_cache=1), dict(k1d_cache=0), dict(exchange_grid=0), dict(exchange_grid=1),
+               dict(xy_kernel=0), dict(xy_kernel=2), dict(xy_kernel=3), dict(xy_kernel=1)):
         before = s.get_tuning()
         s.set_tuning(**kw)
         after = s.get_tuning()
@@ -211,6 +221,8 @@ def test_tuning_fields_round_trip(torch):
         s.set_tuning(k1d_cache=2)
     with pytest.raises(T.TddftError):
         s.set_tuning(exchange_grid=2)
+    with pytest.raises(T.TddftError):
+        s.set_tuning(xy_kernel=4)
     s.close()
 
 
