@@ -421,7 +421,10 @@ def run_native(args):
 
 def bench_uneven(torch, T, dev, stream, steps=2):
     """12 uneven systems (grids 48..96, 32..256 orbitals, 4..16 trial vectors, mixed
-    spin-conserving / spin-flip) in one CUDA-graph launch; applications/s over all systems."""
+    spin-conserving / spin-flip) in one CUDA-graph launch with one branch per system;
+    applications/s over all systems. Beside it the same systems applied one after the
+    other on one stream, and the sum of their times alone: the graph's time against
+    that sum shows how much the branches overlap (1.0 = none)."""
     from paper_2309_03513_b300 import synth
     systems, Xs = [], []
     total_nb = 0
@@ -448,10 +451,20 @@ def bench_uneven(torch, T, dev, stream, steps=2):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    alone = []
+    for s, X, o in zip(systems, Xs, outs):
+        s.apply(X, out=o, stream=stream)
+        e0.record(stream)
+        s.apply(X, out=o, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        alone.append(e0.elapsed_time(e1))
     for s in systems:
         s.close()
     return {"value": total_nb / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "trial_vectors": total_nb,
-            "steps": steps, "systems": 12, "note": "one CUDA-graph launch per step, one branch per system"}
+            "steps": steps, "systems": 12, "sum_of_systems_alone_ms": sum(alone),
+            "graph_over_sum_alone": ms / sum(alone), "systems_alone_ms": alone,
+            "note": "one CUDA-graph launch per step, one branch per system"}
 
 
 def bench_ace(torch, T, dev, stream, wl, X, LA, steps=3):
@@ -618,14 +631,19 @@ def bench_taucache(torch, T, dev, stream, wl, X, LA, steps=5):
 
 
 def bench_sf216(torch, T, dev, stream, steps=1):
-    """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path."""
+    """216-atom spin-flip cell (108^3, 433/431 orbitals, 16 trial vectors), FP32 path, pair
+    convolutions on the 96^3 exchange grid; one warm-up, then `steps` timed applications. Row
+    (b = 0, v = 0) is compared with the oracle's digest of that row in tests/golden (written by
+    tests/golden/make_sf216_row_digest.py from the oracle alone)."""
     from paper_2309_03513_b300 import synth
     n, a = 108, 20.2
     wl = synth.make_workload(n=n, a=a, ecut=25.0, npw=T.sphere_size(n, a, 25.0), nocc_src=433, nb=16, seed=0,
                              spin_flip=True, nocc_tgt=431)
     s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    n_exchange = s.query()["n_exchange"]
     X = torch.from_numpy(wl.X).to(dev, torch.complex64)
     LA = torch.empty_like(X)
+    s.apply(X, out=LA, stream=stream)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -634,9 +652,29 @@ def bench_sf216(torch, T, dev, stream, steps=1):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    out = {"value": 16 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": 1,
+           "exchange_grid": n_exchange, "pairs_per_step": 16 * 433 * 431 + 433 * 434 // 2}
+    # 48 B per point per pair convolution on the exchange grid (the HBM model of the pair stage)
+    model_s = out["pairs_per_step"] * n_exchange ** 3 * 48.0 / (measured_peaks()["hbm_gbs"] * 1e9)
+    out["model_48B_per_point_s"] = model_s
+    out["fraction_of_model_rate"] = model_s / (ms / 1e3)
+    gold = os.path.join(ROOT, "tests", "golden", "sf216_row_digest.json")
+    if os.path.exists(gold):
+        with open(gold) as fh:
+            g = json.load(fh)
+        b, v = g["row"]
+        row = LA[b, v].cpu().numpy().astype(np.complex128)
+        x = wl.X[b, v]
+        idx = np.array([t[0] for t in g["samples"]])
+        want = np.array([complex(t[1], t[2]) for t in g["samples"]])
+        out["errors_vs_oracle_row"] = {
+            "row": [b, v],
+            "sampled_coefficients_rel_err": float(np.linalg.norm(row[idx] - want) / np.linalg.norm(want)),
+            "norm_rel_err": float(abs(np.linalg.norm(row) - g["norm"]) / g["norm"]),
+            "omega_row_abs_err_Ha": float(abs(np.vdot(x, row).real - g["omega_row"])),
+        }
     s.close()
-    return {"value": 16 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": 0,
-            "pairs_per_step": 16 * 433 * 431 + 433 * 434 // 2}
+    return out
 
 
 def main():
@@ -650,7 +688,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--term-split", type=int, default=1, help="time each term alone (one step each)")
-    ap.add_argument("--extra", default="", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
+    ap.add_argument("--extra", default="sf216,uneven", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
                                              "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch), "
                                              "pairtrunc (K1d pair truncation, localised orbitals), "
                                              "taucache (K1d from stored tau of every pair)")

@@ -152,6 +152,137 @@ __global__ void __launch_bounds__(K1D_THREADS)
   }
 }
 
+// K1d from the tau of every unordered orbital pair at once (Eq. 6):
+//   out[b][v] += s * sum_v' a[b][v'] tau_vv',   tau_v'v = conj(tau_vv').
+// tau holds the pairs block pair after block pair (16 x 16 orbital blocks I <= J,
+// field vi * tj + vj of block pair (I, J) at K1dAll::off[I][J] fields; diagonal
+// blocks hold both orders). A CTA takes K1D_ALL_PTS points and every output row
+// (nocc <= 128): thread (row pair, point) holds rows v and v + 8 of one block and
+// keeps the sums of NB trial vectors for both in registers, so that each trial-vector
+// value read from shared memory serves two rows. The trial vectors of the CTA's
+// points are staged in shared memory once per group of NB. The off-diagonal block
+// pairs are visited in rounds of disjoint pairs (the round-robin pairing of the
+// blocks, K1dAll::pi/pj): in a round every block meets one partner, the tau tiles
+// of the round are staged in shared memory with coalesced loads, and the rows of
+// both blocks of a pair read them (the I rows as tau, the J rows conjugated and
+// transposed), so each tau value leaves global memory once. The diagonal blocks
+// are read straight from global memory.
+constexpr int K1D_ALL_THREADS = 512;
+constexpr int K1D_ALL_PTS = 8;
+constexpr int K1D_ALL_BLOCKS = 8;  // orbital blocks (nocc <= 128)
+constexpr int K1D_ALL_ROWS = 16 * K1D_ALL_BLOCKS;
+struct K1dAll {
+  long long off[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS];  // field offset of block pair (I <= J)
+  // per round and block: partner block (-1: none), slot of the pair in the round, 1 if the block is I
+  signed char partner[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS];
+  signed char slot[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS];
+  signed char first[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS];
+  signed char pi[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS / 2];  // (I, J) of slot k in round r, -1 unused
+  signed char pj[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS / 2];
+  int rounds, nblk;
+};
+
+// acc += a * t for the two rows of a thread
+template <typename T, int NB>
+__device__ __forceinline__ void k1d_all_mac(cplx<T> (&acc)[2][NB], const cplx<T>* av, cplx<T> t0, cplx<T> t1) {
+  constexpr int QS = K1D_ALL_ROWS * K1D_ALL_PTS;  // stride of one trial vector in the staged block
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const cplx<T> x = av[q * QS];
+    acc[0][q] = cadd(acc[0][q], cmul(x, t0));
+    acc[1][q] = cadd(acc[1][q], cmul(x, t1));
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
+    k_k1d_all(const cplx<T>* __restrict__ tau, K1dAll kt, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out,
+              int nocc, int nb, T s, long long n3) {
+  constexpr int PTS = K1D_ALL_PTS, TP = 17;  // TP: vi pitch of a staged tile
+  constexpr int QS = K1D_ALL_ROWS * PTS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* as = reinterpret_cast<cplx<T>*>(smem_raw);  // [NB][K1D_ALL_ROWS][PTS]
+  cplx<T>* ts = as + NB * QS;                            // [K1D_ALL_BLOCKS / 2][16][TP][PTS]
+  const int tid = threadIdx.x;
+  const int p = tid % PTS, rp = tid / PTS;  // rp: row pair 0..63
+  const int B = rp / 8, vb = rp % 8;        // rows 16 B + vb and 16 B + vb + 8
+  const int v0 = 16 * B + vb;
+  const long long r0 = (long long)blockIdx.x * PTS;
+  const int npts = (int)min((long long)PTS, n3 - r0);
+  auto bsize = [nocc](int blk) { return min(16, nocc - 16 * blk); };
+  const bool live = B < kt.nblk && p < npts;
+  for (int b0 = 0; b0 < nb; b0 += NB) {
+    const int nbc = min(NB, nb - b0);
+    __syncthreads();  // the previous group's reads of the staged values are done
+    for (int e = tid; e < NB * QS; e += K1D_ALL_THREADS) {
+      const int pp = e % PTS, rest = e / PTS, vv = rest % K1D_ALL_ROWS, bb = rest / K1D_ALL_ROWS;
+      as[e] = (bb < nbc && vv < nocc && pp < npts) ? a[((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp]
+                                                    : cplx<T>{T(0), T(0)};
+    }
+    cplx<T> acc[2][NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) acc[0][q] = acc[1][q] = {T(0), T(0)};
+    for (int r = 0; r < kt.rounds; ++r) {
+      __syncthreads();  // the previous round's tiles are read
+      for (int k = 0; k < K1D_ALL_BLOCKS / 2; ++k) {
+        const int I = kt.pi[r][k], J = kt.pj[r][k];
+        if (I < 0) continue;
+        const int ti = bsize(I), tj = bsize(J);
+        const cplx<T>* tb = tau + kt.off[I][J] * n3 + r0;
+        for (int e = tid; e < 256 * PTS; e += K1D_ALL_THREADS) {
+          const int pp = e % PTS, f = e / PTS, vi = f / 16, vj = f - 16 * vi;
+          ts[((k * 16 + vj) * TP + vi) * PTS + pp] =
+              (vi < ti && vj < tj && pp < npts) ? tb[(long long)(vi * tj + vj) * n3 + pp] : cplx<T>{T(0), T(0)};
+        }
+      }
+      __syncthreads();
+      const int partner = live ? kt.partner[r][B] : -1;
+      if (partner >= 0) {
+        const cplx<T>* tile = ts + kt.slot[r][B] * 16 * TP * PTS;
+        const cplx<T>* av = as + partner * 16 * PTS + p;
+        const int np = bsize(partner);
+        if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj)
+          for (int vj = 0; vj < np; ++vj) {
+            const cplx<T>* tv = tile + (vj * TP + vb) * PTS + p;
+            k1d_all_mac<T, NB>(acc, av + vj * PTS, tv[0], tv[8 * PTS]);
+          }
+        } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v))
+          for (int vi = 0; vi < np; ++vi) {
+            const cplx<T>* tv = tile + (vb * TP + vi) * PTS + p;
+            k1d_all_mac<T, NB>(acc, av + vi * PTS, cconj(tv[0]), cconj(tv[8 * TP * PTS]));
+          }
+        }
+      }
+    }
+    if (kt.rounds == 0) __syncthreads();  // the staged trial vectors are visible
+    if (live) {
+      // diagonal block, straight from global memory
+      const int tb_ = bsize(B);
+      const bool r1 = vb + 8 < tb_;
+      const cplx<T>* t0 = tau + (kt.off[B][B] + (long long)vb * tb_) * n3 + r0 + p;
+      const cplx<T>* t1 = t0 + (long long)8 * tb_ * n3;
+      const cplx<T>* av = as + B * 16 * PTS + p;
+      for (int vj = 0; vj < tb_; ++vj) {
+        const cplx<T> x0 = vb < tb_ ? t0[(long long)vj * n3] : cplx<T>{T(0), T(0)};
+        const cplx<T> x1 = r1 ? t1[(long long)vj * n3] : cplx<T>{T(0), T(0)};
+        k1d_all_mac<T, NB>(acc, av + vj * PTS, x0, x1);
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nbc) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int v = v0 + 8 * h;
+            if (v < nocc) {
+              cplx<T>* o = out + ((long long)(b0 + q) * nocc + v) * n3 + r0 + p;
+              *o = cadd(*o, cscale(acc[h][q], s));
+            }
+          }
+        }
+    }
+  }
+}
+
 // K1d contraction over a list of kept pairs (pair truncation, Sec. 3.2).
 // tau[slot] (slot < np) holds Conv_x[conj(phi_n) phi_m] of the batch's pairs.
 // Output rows: row i adds to orbital row_out[i], over its entries

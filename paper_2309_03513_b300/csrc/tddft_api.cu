@@ -302,7 +302,7 @@ struct tddft_system {
   long long n3 = 0;
   int nb_chunk = 0;
   int ibuf_fields = 0;
-  int tile_targets = 64, tile_sources = 8, k1d_block = 16;
+  int tile_targets = 128, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
   int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
   bool prune = true;     // pair convolutions keep only the columns a pair density can occupy (compact)
@@ -342,6 +342,12 @@ struct tddft_system {
   void* tau_cache = nullptr;
   size_t tau_cache_bytes = 0;
   bool k1d_cache_req = false;  // tuning.k1d_cache as set (the stored tau live where K1d runs)
+  // K1d of the recomputing path with the tau of every pair materialised in device scratch per
+  // application (tuning.k1d_all), allocated at the first K1d outside stream capture when it fits
+  bool k1d_all = false;
+  bool tau_all_tried = false;
+  void* tau_all = nullptr;
+  size_t tau_all_bytes = 0;
   // Exchange terms (D_EXX, K1d, K2d) on a smaller grid on which they are exact (tuning.exchange_grid):
   // an internal system on that grid and its plane-wave results [nb_max][nocc_src][npw]
   tddft_system* xsub = nullptr;
@@ -613,8 +619,9 @@ static tddft_status pair_accumulate(tddft_system* h, const cplx<T>* qb, const cp
   const ColumnList cl = pair_columns<T>(h);  // pair densities: compact intermediates when pruning
   int TT = std::max(1, std::min(h->tile_targets, pg.ntargets));
   int KS = std::max(1, std::min(h->tile_sources, pg.nsources));
-  while (TT * KS > h->ibuf_fields) {
-    if (KS > 1) KS = (KS + 1) / 2;
+  while (TT * KS > h->ibuf_fields) {  // shrink the targets to 32 first, then the sources
+    if (TT > 32) TT = (TT + 1) / 2;
+    else if (KS > 1) KS = (KS + 1) / 2;
     else TT = (TT + 1) / 2;
   }
   for (int t0 = 0; t0 < pg.ntargets; t0 += TT) {
@@ -665,12 +672,12 @@ static size_t tau_cache_fields(int nocc) {
 }
 
 template <typename T>
-static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
+static tddft_status build_tau_fields(tddft_system* h, void* dst, cudaStream_t st) {
   PlaneOps<T>& o = ops_of<T>(h);
   const cplx<T>* tw = (const cplx<T>*)h->b.tw;
   const cplx<T>* phi = (const cplx<T>*)h->b.phi_src_r;
   const int nocc = h->d.nocc_src;
-  cplx<T>* blk = (cplx<T>*)h->tau_cache;
+  cplx<T>* blk = (cplx<T>*)dst;
   for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {
     const int ti = std::min(K1D_CACHE_BLOCK, nocc - i0);
     for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) {
@@ -693,7 +700,85 @@ static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
       blk += (long long)ti * tj * h->n3;
     }
   }
-  return check_launch("tau cache build");
+  return check_launch("tau build");
+}
+
+template <typename T>
+static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
+  return build_tau_fields<T>(h, h->tau_cache, st);
+}
+
+// the round-robin schedule of the all-pairs K1d contraction (k_k1d_all) and the
+// field offsets of the block pairs in the tau layout of build_tau_fields
+static K1dAll k1d_all_table(int nocc) {
+  K1dAll t{};
+  const int nblk = (nocc + K1D_CACHE_BLOCK - 1) / K1D_CACHE_BLOCK;
+  t.nblk = nblk;
+  long long f = 0;
+  for (int i = 0; i < nblk; ++i)
+    for (int j = i; j < nblk; ++j) {
+      t.off[i][j] = f;
+      f += (long long)std::min(K1D_CACHE_BLOCK, nocc - i * K1D_CACHE_BLOCK) *
+           std::min(K1D_CACHE_BLOCK, nocc - j * K1D_CACHE_BLOCK);
+    }
+  const int M = nblk + (nblk & 1), m1 = M - 1;
+  t.rounds = nblk >= 2 ? m1 : 0;
+  for (int r = 0; r < K1D_ALL_BLOCKS; ++r)
+    for (int b = 0; b < K1D_ALL_BLOCKS; ++b) {
+      t.partner[r][b] = -1;
+      t.slot[r][b] = 0;
+      t.first[r][b] = 0;
+      if (b < K1D_ALL_BLOCKS / 2) t.pi[r][b] = t.pj[r][b] = -1;
+    }
+  for (int r = 0; r < t.rounds; ++r)
+    for (int k = 0; k < M / 2; ++k) {
+      int p = k == 0 ? M - 1 : (r + k) % m1, q = k == 0 ? r : (r - k + m1) % m1;
+      const int I = std::min(p, q), J = std::max(p, q);
+      if (J >= nblk) continue;
+      t.pi[r][k] = (signed char)I;
+      t.pj[r][k] = (signed char)J;
+      t.partner[r][I] = (signed char)J;
+      t.slot[r][I] = (signed char)k;
+      t.first[r][I] = 1;
+      t.partner[r][J] = (signed char)I;
+      t.slot[r][J] = (signed char)k;
+      t.first[r][J] = 0;
+    }
+  return t;
+}
+
+template <typename T, int NB>
+static constexpr size_t k1d_all_smem() {
+  return ((size_t)NB * K1D_ALL_ROWS * K1D_ALL_PTS + (size_t)(K1D_ALL_BLOCKS / 2) * 16 * 17 * K1D_ALL_PTS) *
+         sizeof(cplx<T>);
+}
+// trial vectors per pass of k_k1d_all: FP32 up to 8, FP64 up to 4 (shared memory)
+template <typename T>
+static constexpr int k1d_all_nb_max() { return sizeof(T) == 4 ? 8 : 4; }
+
+template <typename T>
+static tddft_status k1d_all_launch(tddft_system* h, const cplx<T>* tau, int nbc, cudaStream_t st) {
+  const int nocc = h->d.nocc_src;
+  const K1dAll kt = k1d_all_table(nocc);
+  const unsigned blocks = (unsigned)((h->n3 + K1D_ALL_PTS - 1) / K1D_ALL_PTS);
+  const T s = (T)(-h->d.alpha);
+  const cplx<T>* a = (const cplx<T>*)h->b.a_r;
+  cplx<T>* out = (cplx<T>*)h->b.out_r;
+  // the smallest group of trial vectors that covers nbc (one pass when nbc <= the maximum)
+  const int nbg = std::min(k1d_all_nb_max<T>(), nbc <= 1 ? 1 : nbc <= 2 ? 2 : nbc <= 4 ? 4 : 8);
+#define TDDFT_K1D_ALL(NBG)                                                                                 \
+  if constexpr (NBG <= k1d_all_nb_max<T>()) {                                                              \
+    constexpr size_t smem = k1d_all_smem<T, NBG>();                                                        \
+    CUDA_TRY(cudaFuncSetAttribute(k_k1d_all<T, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_k1d_all<T, NBG><<<blocks, K1D_ALL_THREADS, smem, st>>>(tau, kt, a, out, nocc, nbc, s, h->n3);        \
+    note_launch();                                                                                         \
+  }
+  if (nbg == 1) { TDDFT_K1D_ALL(1) }
+  else if (nbg == 2) { TDDFT_K1D_ALL(2) }
+  else if (nbg == 4) { TDDFT_K1D_ALL(4) }
+  else { TDDFT_K1D_ALL(8) }
+#undef TDDFT_K1D_ALL
+  return check_launch("k1d (all pairs)");
 }
 
 template <typename T>
@@ -722,6 +807,35 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
           pb.nrows, h->loc_ent, nocc, nbc, s, h->n3); note_launch(); }
     }
     return check_launch("k1d_term (pair list)");
+  }
+  const bool all_ok = h->k1d_all && !h->loc_on && nocc <= K1D_ALL_ROWS;
+  if (all_ok && h->k1d_cache && h->tau_cache) return k1d_all_launch<T>(h, (const cplx<T>*)h->tau_cache, nbc, st);
+  if (all_ok && !h->k1d_cache) {
+    if (!h->tau_all && !h->tau_all_tried) {
+      // scratch for the tau of every pair: allocated once, outside stream capture, when it
+      // takes at most a quarter of the free device memory
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+      if (cs == cudaStreamCaptureStatusNone) {
+        h->tau_all_tried = true;
+        const size_t bytes = tau_cache_fields(nocc) * (size_t)h->n3 * sizeof(cplx<T>);
+        size_t freeb = 0, totalb = 0;
+        CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+        if (bytes <= freeb / 4) {
+          if (cudaMalloc(&h->tau_all, bytes) == cudaSuccess) {
+            h->tau_all_bytes = bytes;
+            h->bytes += bytes;
+          } else {
+            cudaGetLastError();
+            h->tau_all = nullptr;
+          }
+        }
+      }
+    }
+    if (h->tau_all) {
+      STATUS_TRY(build_tau_fields<T>(h, h->tau_all, st));
+      return k1d_all_launch<T>(h, (const cplx<T>*)h->tau_all, nbc, st);
+    }
   }
   if (h->k1d_cache && h->tau_cache && !h->loc_on) {
     // stored tau: the contraction alone, block pair after block pair in the build order
@@ -1823,6 +1937,7 @@ tddft_status tddft_destroy(tddft_handle h) {
   if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocations) cudaFree(p);
   if (h->tau_cache) cudaFree(h->tau_cache);
+  if (h->tau_all) cudaFree(h->tau_all);
   if (h->xsub) tddft_destroy(h->xsub);
   delete h;
   return TDDFT_OK;
@@ -2015,6 +2130,18 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->ops32.kc.z = t->z_kernel;
     h->ops64.kc.z = t->z_kernel;
   }
+  if (t->k1d_all >= 0) {
+    if (t->k1d_all > 1) return fail(TDDFT_EINVAL, "k1d_all must be 0 or 1");
+    h->k1d_all = t->k1d_all == 1;
+    if (!h->k1d_all && h->tau_all) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      CUDA_TRY(cudaFree(h->tau_all));
+      h->bytes -= h->tau_all_bytes;
+      h->tau_all = nullptr;
+      h->tau_all_bytes = 0;
+    }
+    h->tau_all_tried = false;
+  }
   if (t->xy_kernel >= 0) {
     if (t->xy_kernel > 3) return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 3");
     h->xy_lines = t->xy_kernel;
@@ -2055,6 +2182,7 @@ tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
   t->k1d_cache = h->k1d_cache_req ? 1 : 0;
   t->exchange_grid = h->use_xsub ? 1 : 0;
   t->xy_kernel = h->xy_lines;
+  t->k1d_all = h->k1d_all ? 1 : 0;
   return TDDFT_OK;
 }
 

@@ -74,7 +74,7 @@ class Tuning(ctypes.Structure):
                 ("accumulate", ctypes.c_int), ("batch_fields", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prune", ctypes.c_int), ("z_kernel", ctypes.c_int), ("projector", ctypes.c_int),
                 ("k1d_sparse", ctypes.c_int), ("k1d_cache", ctypes.c_int), ("exchange_grid", ctypes.c_int),
-                ("xy_kernel", ctypes.c_int)]
+                ("xy_kernel", ctypes.c_int), ("k1d_all", ctypes.c_int)]
 
 
 class ZvectorOpts(ctypes.Structure):
@@ -288,10 +288,10 @@ class LiouvilleSystem:
 
     def set_tuning(self, targets: int = 0, sources: int = 0, k1d_block: int = 0, accumulate: int = -1,
                    graph: int = -1, prune: int = -1, z_kernel: int = -1, projector: int = -1, k1d_sparse: int = -1,
-                   k1d_cache: int = -1, exchange_grid: int = -1, xy_kernel: int = -1):
+                   k1d_cache: int = -1, exchange_grid: int = -1, xy_kernel: int = -1, k1d_all: int = -1):
         t = Tuning(int(targets), int(sources), int(k1d_block), int(accumulate), 0, int(graph), int(prune),
                    int(z_kernel), int(projector), int(k1d_sparse), int(k1d_cache), int(exchange_grid),
-                   int(xy_kernel))
+                   int(xy_kernel), int(k1d_all))
         _check(load().tddft_set_tuning(self._h, ctypes.byref(t)), "tddft_set_tuning")
 
     def query(self) -> dict:

@@ -186,6 +186,19 @@ def test_kernel_variants_fp32(torch, n, a, ecut):
     assert _rel_err(got, want).max() < 1e-11
 
 
+@pytest.mark.parametrize("nocc", [20, 40, 100])
+def test_k1d_all_pairs_and_blocks(torch, nocc):
+    """K1d (Eq. 6) with the tau of every pair contracted in one pass (tuning.k1d_all = 1; a ragged last
+    orbital block, and odd block counts, where one block sits out each round of the pairing) and by
+    16 x 16 blocks of pairs (k1d_all = 0), FP64 and FP32, against the oracle."""
+    wl = _workload(24, 10.0, 10.0, nocc, 2, seed=40 + nocc)
+    want = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
+    for prec in (T.PREC_FP64, T.PREC_FP32):
+        for k1d_all in (1, 0):
+            got = _run(torch, wl, prec, mask=T.TERM_K1D, tiling=dict(k1d_all=k1d_all))
+            assert _rel_err(got, want).max() < TOL[prec], (prec, k1d_all)
+
+
 def test_projector_tensor_cores_match_simt(torch):
     """The tcgen05 projector (3xTF32 products, FP32 accumulation) against the SIMT
     FP32 projector and the oracle, on a batch whose rows exceed one 128-row tile."""
@@ -208,7 +221,8 @@ def test_tuning_fields_round_trip(torch):
                dict(z_kernel=2),
                dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
                dict(k1d_cache=1), dict(k1d_cache=0), dict(exchange_grid=0), dict(exchange_grid=1),
-               dict(xy_kernel=0), dict(xy_kernel=2), dict(xy_kernel=3), dict(xy_kernel=1)):
+               dict(xy_kernel=0), dict(xy_kernel=2), dict(xy_kernel=3), dict(xy_kernel=1),
+               dict(k1d_all=0), dict(k1d_all=1)):
         before = s.get_tuning()
         s.set_tuning(**kw)
         after = s.get_tuning()
