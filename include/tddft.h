@@ -219,15 +219,16 @@ typedef struct tddft_tuning {
                        line in both passes; 2: two lanes per line in both; 3: forward pass
                        one thread per line, inverse pass two lanes per line; 0: the
                        shared-memory radix stages. -1 keeps the value */
-  int k1d_all;      /* K1d of the recomputing path (k1d_cache 0), handles with at most 128
-                       source orbitals: 1 the tau_vv' of every pair are convolved
-                       into a device scratch buffer (the layout and size of the stored tau,
-                       allocated at the first K1d outside stream capture when it takes at
-                       most a quarter of the free device memory) and contracted in one pass
-                       that reads each of them once; 0 (default, or when the scratch does not
-                       fit) by k1d_block x k1d_block blocks of pairs. The stored tau (k1d_cache 1)
-                       use the one-pass contraction whenever this is 1. 0 releases the
-                       scratch. -1 keeps the value */
+  int k1d_all;      /* K1d of the recomputing path (k1d_cache 0) for FP32 handles with at most
+                       128 source orbitals whose pair convolutions use compact intermediates
+                       and the register-line xy passes (n = 32, 48, 64 after the exchange
+                       grid): 1 (default) the tau_vv' of every pair are convolved into a
+                       point-tiled device scratch buffer (the size of the stored tau: 19.3 GB
+                       for 128 orbitals on 64^3; allocated at the first K1d outside stream
+                       capture when it takes at most a quarter of the free device memory)
+                       and contracted in one pass that reads each of them once; 0 (and
+                       wherever the above does not hold) by k1d_block x k1d_block blocks of
+                       pairs. 0 releases the scratch. -1 keeps the value */
 } tddft_tuning;
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t);
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t);

@@ -1,6 +1,8 @@
 // Pointwise and K1d-contraction kernels of the Liouville-operator path
 // (templated on the real type T). Field layout as in plane_kernels.cuh.
 #pragma once
+#include <cstdint>
+
 #include "plane_kernels.cuh"
 
 namespace tddft {
@@ -152,25 +154,31 @@ __global__ void __launch_bounds__(K1D_THREADS)
   }
 }
 
-// K1d from the tau of every unordered orbital pair at once (Eq. 6):
+// K1d from the tau of every unordered orbital pair at once (Eq. 6), FP32:
 //   out[b][v] += s * sum_v' a[b][v'] tau_vv',   tau_v'v = conj(tau_vv').
-// tau holds the pairs block pair after block pair (16 x 16 orbital blocks I <= J,
-// field vi * tj + vj of block pair (I, J) at K1dAll::off[I][J] fields; diagonal
-// blocks hold both orders). A CTA takes K1D_ALL_PTS points and every output row
-// (nocc <= 128): thread (row pair, point) holds rows v and v + 8 of one block and
-// keeps the sums of NB trial vectors for both in registers, so that each trial-vector
-// value read from shared memory serves two rows. The trial vectors of the CTA's
-// points are staged in shared memory once per group of NB. The off-diagonal block
-// pairs are visited in rounds of disjoint pairs (the round-robin pairing of the
-// blocks, K1dAll::pi/pj): in a round every block meets one partner, the tau tiles
-// of the round are staged in shared memory with coalesced loads, and the rows of
-// both blocks of a pair read them (the I rows as tau, the J rows conjugated and
-// transposed), so each tau value leaves global memory once. The diagonal blocks
-// are read straight from global memory.
+// tau is point-tiled (PairMap::tile_nf): for the POINT_TILE points of tile t, the values
+// of all nf pair fields follow each other, field f at (t * nf + f) * POINT_TILE. The
+// fields are ordered block pair after block pair (16 x 16 orbital blocks I <= J, field
+// vi * tj + vj of block pair (I, J) at K1dAll::off[I][J]; diagonal blocks hold both
+// orders), so the tau of one block pair at one tile is one contiguous run, which a
+// bulk copy (cp.async.bulk, completion on an mbarrier) brings into shared memory.
+// A CTA takes one tile and every output row (nocc <= 128): thread (row pair, point)
+// holds rows v and v + 8 of one block and keeps the sums of NB trial vectors for
+// both in registers, so that each trial-vector value read from shared memory serves
+// two rows. The trial vectors of the tile are staged once per group of NB. The
+// off-diagonal block pairs are visited in rounds of disjoint pairs (the round-robin
+// pairing of the blocks, K1dAll::pi/pj): in a round every block meets one partner and
+// the rows of both blocks read the round's tiles (the I rows as tau, the J rows
+// conjugated and transposed), so each tau value leaves global memory once. The copies
+// of round r + 1 are in flight while round r is computed (two buffers); the diagonal
+// blocks come last, into both buffers once the last round is done. Every wait on an mbarrier is bounded: on
+// timeout the CTA sets *err, waits (bounded) for the copies it issued and returns.
 constexpr int K1D_ALL_THREADS = 512;
-constexpr int K1D_ALL_PTS = 8;
+constexpr int K1D_ALL_PTS = POINT_TILE;
 constexpr int K1D_ALL_BLOCKS = 8;  // orbital blocks (nocc <= 128)
 constexpr int K1D_ALL_ROWS = 16 * K1D_ALL_BLOCKS;
+constexpr int K1D_ALL_SLOT = 256 * K1D_ALL_PTS;   // elements of one block-pair tile
+constexpr long long K1D_ALL_WAIT_LIMIT = 1LL << 22;
 struct K1dAll {
   long long off[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS];  // field offset of block pair (I <= J)
   // per round and block: partner block (-1: none), slot of the pair in the round, 1 if the block is I
@@ -180,6 +188,7 @@ struct K1dAll {
   signed char pi[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS / 2];  // (I, J) of slot k in round r, -1 unused
   signed char pj[K1D_ALL_BLOCKS][K1D_ALL_BLOCKS / 2];
   int rounds, nblk;
+  long long nf;  // fields per tile
 };
 
 // acc += a * t for the two rows of a thread
@@ -194,79 +203,155 @@ __device__ __forceinline__ void k1d_all_mac(cplx<T> (&acc)[2][NB], const cplx<T>
   }
 }
 
-template <typename T, int NB>
+__device__ __forceinline__ uint32_t k1d_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// bounded wait for phase `parity` of the mbarrier at bar; false on timeout
+__device__ __forceinline__ bool k1d_bar_wait(uint32_t bar, uint32_t parity) {
+  for (long long polls = 0; polls < K1D_ALL_WAIT_LIMIT; ++polls) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+// one bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared
+// memory, counted on the mbarrier at bar
+__device__ __forceinline__ void k1d_bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   k1d_smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+template <int NB>
 __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
-    k_k1d_all(const cplx<T>* __restrict__ tau, K1dAll kt, const cplx<T>* __restrict__ a, cplx<T>* __restrict__ out,
-              int nocc, int nb, T s, long long n3) {
-  constexpr int PTS = K1D_ALL_PTS, TP = 17;  // TP: vi pitch of a staged tile
+    k_k1d_all(const cplx<float>* __restrict__ tau, K1dAll kt, const cplx<float>* __restrict__ a,
+              cplx<float>* __restrict__ out, int nocc, int nb, float s, long long n3, int* __restrict__ err) {
+  using T = float;
+  constexpr int PTS = K1D_ALL_PTS;
   constexpr int QS = K1D_ALL_ROWS * PTS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* as = reinterpret_cast<cplx<T>*>(smem_raw);  // [NB][K1D_ALL_ROWS][PTS]
-  cplx<T>* ts = as + NB * QS;                            // [K1D_ALL_BLOCKS / 2][16][TP][PTS]
+  constexpr int NBUF = K1D_ALL_BLOCKS / 2 * K1D_ALL_SLOT;  // elements of one round buffer
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);  // two mbarriers
+  cplx<T>* as = reinterpret_cast<cplx<T>*>(smem_raw + 128);  // [NB][K1D_ALL_ROWS][PTS]
+  cplx<T>* ts = as + NB * QS;                                 // two round buffers, [slot][field][PTS]
   const int tid = threadIdx.x;
   const int p = tid % PTS, rp = tid / PTS;  // rp: row pair 0..63
   const int B = rp / 8, vb = rp % 8;        // rows 16 B + vb and 16 B + vb + 8
   const int v0 = 16 * B + vb;
-  const long long r0 = (long long)blockIdx.x * PTS;
-  const int npts = (int)min((long long)PTS, n3 - r0);
+  const long long tile = blockIdx.x, r0 = tile * PTS;
+  const cplx<T>* tt = tau + tile * kt.nf * PTS;  // this tile's fields
   auto bsize = [nocc](int blk) { return min(16, nocc - 16 * blk); };
-  const bool live = B < kt.nblk && p < npts;
-  for (int b0 = 0; b0 < nb; b0 += NB) {
+  const bool live = B < kt.nblk;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(k1d_smem_u32(bars)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(k1d_smem_u32(bars + 1)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // copies of stage g (round r of a group, or the diagonal blocks) go to buffer g & 1
+  uint32_t issued = 0, waited = 0;  // stages issued / completed
+  auto issue = [&](int r) {        // thread 0: round r's tiles, or the diagonal tiles for r < 0
+    cplx<T>* buf = ts + (issued & 1) * NBUF;
+    uint32_t bytes = 0;
+    const uint32_t bar = k1d_smem_u32(bars + (issued & 1));
+    if (r >= 0) {
+      for (int k = 0; k < K1D_ALL_BLOCKS / 2; ++k)
+        if (kt.pi[r][k] >= 0) bytes += (uint32_t)(bsize(kt.pi[r][k]) * bsize(kt.pj[r][k]) * PTS * sizeof(cplx<T>));
+    } else {
+      for (int blk = 0; blk < kt.nblk; ++blk) bytes += (uint32_t)(bsize(blk) * bsize(blk) * PTS * sizeof(cplx<T>));
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+    if (r >= 0) {
+      for (int k = 0; k < K1D_ALL_BLOCKS / 2; ++k) {
+        const int I = kt.pi[r][k], J = kt.pj[r][k];
+        if (I < 0) continue;
+        k1d_bulk_copy(buf + k * K1D_ALL_SLOT, tt + kt.off[I][J] * PTS,
+                      (uint32_t)(bsize(I) * bsize(J) * PTS * sizeof(cplx<T>)), bar);
+      }
+    } else {
+      for (int blk = 0; blk < kt.nblk; ++blk)  // diagonal block blk at slot blk of the two buffers
+        k1d_bulk_copy(ts + blk * K1D_ALL_SLOT, tt + kt.off[blk][blk] * PTS,
+                      (uint32_t)(bsize(blk) * bsize(blk) * PTS * sizeof(cplx<T>)), bar);
+    }
+  };
+  bool ok = true;
+  for (int b0 = 0; b0 < nb && ok; b0 += NB) {
     const int nbc = min(NB, nb - b0);
-    __syncthreads();  // the previous group's reads of the staged values are done
+    __syncthreads();  // the previous group's reads of the staged values and buffers are done
+    if (tid == 0) {
+      if (kt.rounds > 0) issue(0);
+      else issue(-1);
+      ++issued;
+    }
     for (int e = tid; e < NB * QS; e += K1D_ALL_THREADS) {
       const int pp = e % PTS, rest = e / PTS, vv = rest % K1D_ALL_ROWS, bb = rest / K1D_ALL_ROWS;
-      as[e] = (bb < nbc && vv < nocc && pp < npts) ? a[((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp]
-                                                    : cplx<T>{T(0), T(0)};
+      as[e] = (bb < nbc && vv < nocc) ? a[((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp] : cplx<T>{T(0), T(0)};
     }
     cplx<T> acc[2][NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) acc[0][q] = acc[1][q] = {T(0), T(0)};
-    for (int r = 0; r < kt.rounds; ++r) {
-      __syncthreads();  // the previous round's tiles are read
-      for (int k = 0; k < K1D_ALL_BLOCKS / 2; ++k) {
-        const int I = kt.pi[r][k], J = kt.pj[r][k];
-        if (I < 0) continue;
-        const int ti = bsize(I), tj = bsize(J);
-        const cplx<T>* tb = tau + kt.off[I][J] * n3 + r0;
-        for (int e = tid; e < 256 * PTS; e += K1D_ALL_THREADS) {
-          const int pp = e % PTS, f = e / PTS, vi = f / 16, vj = f - 16 * vi;
-          ts[((k * 16 + vj) * TP + vi) * PTS + pp] =
-              (vi < ti && vj < tj && pp < npts) ? tb[(long long)(vi * tj + vj) * n3 + pp] : cplx<T>{T(0), T(0)};
+    for (int r = 0; r <= kt.rounds && ok; ++r) {  // r == rounds: the diagonal blocks
+      __syncthreads();  // staged trial vectors visible; the buffer of stage `issued` is free
+      if (tid == 0) {
+        if (r + 1 < kt.rounds) {  // the next round's copies, in flight during this one
+          issue(r + 1);
+          ++issued;
+        } else if (r == kt.rounds && kt.rounds > 0) {  // the diagonal blocks fill both buffers: after the last round
+          issue(-1);
+          ++issued;
         }
       }
-      __syncthreads();
-      const int partner = live ? kt.partner[r][B] : -1;
-      if (partner >= 0) {
-        const cplx<T>* tile = ts + kt.slot[r][B] * 16 * TP * PTS;
-        const cplx<T>* av = as + partner * 16 * PTS + p;
-        const int np = bsize(partner);
-        if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj)
-          for (int vj = 0; vj < np; ++vj) {
-            const cplx<T>* tv = tile + (vj * TP + vb) * PTS + p;
-            k1d_all_mac<T, NB>(acc, av + vj * PTS, tv[0], tv[8 * PTS]);
+      const int stage_buf = waited & 1;
+      if (!k1d_bar_wait(k1d_smem_u32(bars + stage_buf), (waited >> 1) & 1)) ok = false;
+      ++waited;
+      if (__syncthreads_or(ok ? 0 : 1)) {
+        ok = false;
+        break;
+      }
+      const cplx<T>* buf = ts + stage_buf * NBUF;
+      if (r < kt.rounds) {
+        const int partner = live ? kt.partner[r][B] : -1;
+        if (partner >= 0) {
+          const cplx<T>* tile_s = buf + kt.slot[r][B] * K1D_ALL_SLOT;
+          const cplx<T>* av = as + partner * 16 * PTS + p;
+          const int np = bsize(partner), nself = bsize(B);
+          if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj), field vb * tj + vj
+            const bool r1 = vb + 8 < nself;
+            for (int vj = 0; vj < np; ++vj) {
+              const cplx<T> t0 = vb < nself ? tile_s[(vb * np + vj) * PTS + p] : cplx<T>{T(0), T(0)};
+              const cplx<T> t1 = r1 ? tile_s[((vb + 8) * np + vj) * PTS + p] : cplx<T>{T(0), T(0)};
+              k1d_all_mac<T, NB>(acc, av + vj * PTS, t0, t1);
+            }
+          } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v)), field vi * tj + vb
+            const bool r0ok = vb < nself, r1 = vb + 8 < nself;
+            for (int vi = 0; vi < np; ++vi) {
+              const cplx<T> t0 = r0ok ? cconj(tile_s[(vi * nself + vb) * PTS + p]) : cplx<T>{T(0), T(0)};
+              const cplx<T> t1 = r1 ? cconj(tile_s[(vi * nself + vb + 8) * PTS + p]) : cplx<T>{T(0), T(0)};
+              k1d_all_mac<T, NB>(acc, av + vi * PTS, t0, t1);
+            }
           }
-        } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v))
-          for (int vi = 0; vi < np; ++vi) {
-            const cplx<T>* tv = tile + (vb * TP + vi) * PTS + p;
-            k1d_all_mac<T, NB>(acc, av + vi * PTS, cconj(tv[0]), cconj(tv[8 * TP * PTS]));
-          }
+        }
+      } else if (live) {  // diagonal block B at slot B of the buffers (which follow each other)
+        const cplx<T>* tile_s = ts + B * K1D_ALL_SLOT;
+        const int tb = bsize(B);
+        const bool r0ok = vb < tb, r1 = vb + 8 < tb;
+        const cplx<T>* av = as + B * 16 * PTS + p;
+        for (int vj = 0; vj < tb; ++vj) {
+          const cplx<T> t0 = r0ok ? tile_s[(vb * tb + vj) * PTS + p] : cplx<T>{T(0), T(0)};
+          const cplx<T> t1 = r1 ? tile_s[((vb + 8) * tb + vj) * PTS + p] : cplx<T>{T(0), T(0)};
+          k1d_all_mac<T, NB>(acc, av + vj * PTS, t0, t1);
         }
       }
     }
-    if (kt.rounds == 0) __syncthreads();  // the staged trial vectors are visible
+    if (!ok) break;
     if (live) {
-      // diagonal block, straight from global memory
-      const int tb_ = bsize(B);
-      const bool r1 = vb + 8 < tb_;
-      const cplx<T>* t0 = tau + (kt.off[B][B] + (long long)vb * tb_) * n3 + r0 + p;
-      const cplx<T>* t1 = t0 + (long long)8 * tb_ * n3;
-      const cplx<T>* av = as + B * 16 * PTS + p;
-      for (int vj = 0; vj < tb_; ++vj) {
-        const cplx<T> x0 = vb < tb_ ? t0[(long long)vj * n3] : cplx<T>{T(0), T(0)};
-        const cplx<T> x1 = r1 ? t1[(long long)vj * n3] : cplx<T>{T(0), T(0)};
-        k1d_all_mac<T, NB>(acc, av + vj * PTS, x0, x1);
-      }
 #pragma unroll
       for (int q = 0; q < NB; ++q)
         if (q < nbc) {
@@ -280,6 +365,14 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
           }
         }
     }
+  }
+  if (!ok) {
+    // a wait ran out: report, and wait (bounded) for the copies this CTA still has in flight
+    if (tid == 0) {
+      atomicExch(err, 1);
+      for (; waited < issued; ++waited) k1d_bar_wait(k1d_smem_u32(bars + (waited & 1)), (waited >> 1) & 1);
+    }
+    __syncthreads();
   }
 }
 

@@ -20,7 +20,13 @@ struct PairMap {
   int o0, ot;
   // optional explicit (q, r) field indices per item for the forward pass (pair lists)
   const int2* list = nullptr;
+  // INV_WRITE of the register-line kernels: when > 0, the output is point-tiled: field f
+  // at point r goes to ((r / POINT_TILE) * tile_nf + f) * POINT_TILE + r % POINT_TILE
+  // (tile_nf fields in the buffer), so that the values of every field at POINT_TILE
+  // consecutive points are one contiguous run per tile
+  long long tile_nf = 0;
 };
+constexpr int POINT_TILE = 8;
 
 // A copy of p that the compiler cannot relate to p: walking it again for the stores of a
 // column keeps one address live instead of one per element (runtime column strides).

@@ -211,6 +211,12 @@ __global__ void __launch_bounds__(lines_threads<N, L>(), L == 1 ? 6 : 1)
     cplx<T>* O = ob + (long long)(pm.o0 + (long long)tt * pm.ot) * N3 + (long long)z * N2 + h * H * N + line;
 #pragma unroll
     for (int n = 0; n < H; ++n) atomic_cadd(O + n * N, cscale(cmul(P[n * N], v[n]), scale));
+  } else if (pm.tile_nf) {
+    const long long f = pm.o0 + (long long)item * pm.ot;
+    const long long r = (long long)z * N2 + h * H * N + line;  // point of n = 0; N is a multiple of POINT_TILE
+    cplx<T>* O = ob + ((r / POINT_TILE) * pm.tile_nf + f) * POINT_TILE + r % POINT_TILE;
+#pragma unroll
+    for (int n = 0; n < H; ++n) O[(long long)n * (N / POINT_TILE) * pm.tile_nf * POINT_TILE] = cscale(v[n], scale);
   } else {
     cplx<T>* O = ob + (long long)(pm.o0 + (long long)item * pm.ot) * N3 + (long long)z * N2 + h * H * N + line;
 #pragma unroll

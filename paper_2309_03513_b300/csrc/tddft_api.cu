@@ -344,7 +344,7 @@ struct tddft_system {
   bool k1d_cache_req = false;  // tuning.k1d_cache as set (the stored tau live where K1d runs)
   // K1d of the recomputing path with the tau of every pair materialised in device scratch per
   // application (tuning.k1d_all), allocated at the first K1d outside stream capture when it fits
-  bool k1d_all = false;
+  bool k1d_all = true;
   bool tau_all_tried = false;
   void* tau_all = nullptr;
   size_t tau_all_bytes = 0;
@@ -671,13 +671,22 @@ static size_t tau_cache_fields(int nocc) {
   return f;
 }
 
+// tau_vv' = Conv_x[conj(phi_v') phi_v] of every unordered 16 x 16 block pair of the source
+// orbitals (I <= J, block pair after block pair, field vi * tj + vj; diagonal blocks in both
+// orders) into dst. Plain layout: field after field. Point-tiled layout (tiled; only with the
+// register-line inverse pass of compact intermediates, see PairMap::tile_nf): the values of
+// all fields at POINT_TILE consecutive points follow each other.
 template <typename T>
-static tddft_status build_tau_fields(tddft_system* h, void* dst, cudaStream_t st) {
+static tddft_status build_tau_fields(tddft_system* h, void* dst, bool tiled, cudaStream_t st) {
   PlaneOps<T>& o = ops_of<T>(h);
   const cplx<T>* tw = (const cplx<T>*)h->b.tw;
   const cplx<T>* phi = (const cplx<T>*)h->b.phi_src_r;
   const int nocc = h->d.nocc_src;
   cplx<T>* blk = (cplx<T>*)dst;
+  const ColumnList cl = pair_columns<T>(h);
+  if (tiled && !(cl.cols && cl.cmapT)) return fail(TDDFT_EINVAL, "point-tiled tau need the register-line passes");
+  const long long nf = (long long)tau_cache_fields(nocc);
+  long long f0 = 0;
   for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {
     const int ti = std::min(K1D_CACHE_BLOCK, nocc - i0);
     for (int j0 = i0; j0 < nocc; j0 += K1D_CACHE_BLOCK) {
@@ -686,18 +695,25 @@ static tddft_status build_tau_fields(tddft_system* h, void* dst, cudaStream_t st
       // (through compact intermediates in the pair buffer when the grid allows them)
       PairMap pm{tj, j0, 1, 0, i0, 0, 1, 0, 0, 0, 0, 1};
       PairMap pw{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
-      const ColumnList cl = pair_columns<T>(h);
       if (cl.cols && ti * tj <= h->ibuf_fields) {
         cplx<T>* ib = (cplx<T>*)h->b.ibuf;
         o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, ib, tw, st, cl);
         o.z(Z_CONV, ib, ti * tj, pair_kernel<T>(h, (const T*)h->b.kx, cl), T(1), tw, st, cl);
-        o.xy_inv(INV_WRITE, ib, blk, nullptr, pw, ti * tj, T(1), tw, st, cl);
+        if (tiled) {
+          pw.o0 = (int)f0;
+          pw.tile_nf = nf;
+          o.xy_inv(INV_WRITE, ib, (cplx<T>*)dst, nullptr, pw, ti * tj, T(1), tw, st, cl);
+        } else {
+          o.xy_inv(INV_WRITE, ib, blk, nullptr, pw, ti * tj, T(1), tw, st, cl);
+        }
       } else {
+        if (tiled) return fail(TDDFT_EINVAL, "point-tiled tau need compact intermediates");
         o.xy_fwd(XY_PRODUCT, phi, phi, pm, ti * tj, blk, tw, st);
         o.z(Z_CONV, blk, ti * tj, (const T*)h->b.kx, T(1), tw, st);
         o.xy_inv(INV_WRITE, blk, blk, nullptr, pw, ti * tj, T(1), tw, st);
       }
       blk += (long long)ti * tj * h->n3;
+      f0 += (long long)ti * tj;
     }
   }
   return check_launch("tau build");
@@ -705,7 +721,7 @@ static tddft_status build_tau_fields(tddft_system* h, void* dst, cudaStream_t st
 
 template <typename T>
 static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
-  return build_tau_fields<T>(h, h->tau_cache, st);
+  return build_tau_fields<T>(h, h->tau_cache, false, st);
 }
 
 // the round-robin schedule of the all-pairs K1d contraction (k_k1d_all) and the
@@ -721,6 +737,7 @@ static K1dAll k1d_all_table(int nocc) {
       f += (long long)std::min(K1D_CACHE_BLOCK, nocc - i * K1D_CACHE_BLOCK) *
            std::min(K1D_CACHE_BLOCK, nocc - j * K1D_CACHE_BLOCK);
     }
+  t.nf = f;
   const int M = nblk + (nblk & 1), m1 = M - 1;
   t.rounds = nblk >= 2 ? m1 : 0;
   for (int r = 0; r < K1D_ALL_BLOCKS; ++r)
@@ -747,36 +764,33 @@ static K1dAll k1d_all_table(int nocc) {
   return t;
 }
 
-template <typename T, int NB>
+template <int NB>
 static constexpr size_t k1d_all_smem() {
-  return ((size_t)NB * K1D_ALL_ROWS * K1D_ALL_PTS + (size_t)(K1D_ALL_BLOCKS / 2) * 16 * 17 * K1D_ALL_PTS) *
-         sizeof(cplx<T>);
+  return 128 + ((size_t)NB * K1D_ALL_ROWS * K1D_ALL_PTS + (size_t)2 * (K1D_ALL_BLOCKS / 2) * K1D_ALL_SLOT) *
+                   sizeof(cplx<float>);
 }
-// trial vectors per pass of k_k1d_all: FP32 up to 8, FP64 up to 4 (shared memory)
-template <typename T>
-static constexpr int k1d_all_nb_max() { return sizeof(T) == 4 ? 8 : 4; }
 
-template <typename T>
-static tddft_status k1d_all_launch(tddft_system* h, const cplx<T>* tau, int nbc, cudaStream_t st) {
+// K1d from point-tiled tau of every pair (k_k1d_all), trial vectors in groups of up to 8
+static tddft_status k1d_all_launch(tddft_system* h, const cplx<float>* tau, int nbc, cudaStream_t st) {
   const int nocc = h->d.nocc_src;
   const K1dAll kt = k1d_all_table(nocc);
-  const unsigned blocks = (unsigned)((h->n3 + K1D_ALL_PTS - 1) / K1D_ALL_PTS);
-  const T s = (T)(-h->d.alpha);
-  const cplx<T>* a = (const cplx<T>*)h->b.a_r;
-  cplx<T>* out = (cplx<T>*)h->b.out_r;
-  // the smallest group of trial vectors that covers nbc (one pass when nbc <= the maximum)
-  const int nbg = std::min(k1d_all_nb_max<T>(), nbc <= 1 ? 1 : nbc <= 2 ? 2 : nbc <= 4 ? 4 : 8);
-#define TDDFT_K1D_ALL(NBG)                                                                                 \
-  if constexpr (NBG <= k1d_all_nb_max<T>()) {                                                              \
-    constexpr size_t smem = k1d_all_smem<T, NBG>();                                                        \
-    CUDA_TRY(cudaFuncSetAttribute(k_k1d_all<T, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k_k1d_all<T, NBG><<<blocks, K1D_ALL_THREADS, smem, st>>>(tau, kt, a, out, nocc, nbc, s, h->n3);        \
-    note_launch();                                                                                         \
+  const unsigned blocks = (unsigned)(h->n3 / K1D_ALL_PTS);
+  const float s = (float)(-h->d.alpha);
+  const cplx<float>* a = (const cplx<float>*)h->b.a_r;
+  cplx<float>* out = (cplx<float>*)h->b.out_r;
+  // the smallest group of trial vectors that covers nbc (one pass when nbc <= 8)
+  const int nbg = nbc <= 1 ? 1 : nbc <= 2 ? 2 : nbc <= 4 ? 4 : 8;
+#define TDDFT_K1D_ALL(NBG)                                                                                   \
+  {                                                                                                          \
+    constexpr size_t smem = k1d_all_smem<NBG>();                                                             \
+    CUDA_TRY(cudaFuncSetAttribute(k_k1d_all<NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));  \
+    k_k1d_all<NBG><<<blocks, K1D_ALL_THREADS, smem, st>>>(tau, kt, a, out, nocc, nbc, s, h->n3, h->b.dev_err); \
+    note_launch();                                                                                           \
   }
-  if (nbg == 1) { TDDFT_K1D_ALL(1) }
-  else if (nbg == 2) { TDDFT_K1D_ALL(2) }
-  else if (nbg == 4) { TDDFT_K1D_ALL(4) }
-  else { TDDFT_K1D_ALL(8) }
+  if (nbg == 1) TDDFT_K1D_ALL(1)
+  else if (nbg == 2) TDDFT_K1D_ALL(2)
+  else if (nbg == 4) TDDFT_K1D_ALL(4)
+  else TDDFT_K1D_ALL(8)
 #undef TDDFT_K1D_ALL
   return check_launch("k1d (all pairs)");
 }
@@ -808,9 +822,13 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
     }
     return check_launch("k1d_term (pair list)");
   }
-  const bool all_ok = h->k1d_all && !h->loc_on && nocc <= K1D_ALL_ROWS;
-  if (all_ok && h->k1d_cache && h->tau_cache) return k1d_all_launch<T>(h, (const cplx<T>*)h->tau_cache, nbc, st);
-  if (all_ok && !h->k1d_cache) {
+  // the tau of every pair at once: FP32, register-line passes of compact intermediates
+  // (point-tiled tau), at most 128 orbitals, recomputing path
+  const ColumnList acl = pair_columns<T>(h);
+  const bool all_ok = sizeof(T) == 4 && h->k1d_all && !h->loc_on && !h->k1d_cache && nocc <= K1D_ALL_ROWS &&
+                      acl.cols && acl.cmapT && K1D_CACHE_BLOCK * K1D_CACHE_BLOCK <= h->ibuf_fields &&
+                      h->n3 % K1D_ALL_PTS == 0;
+  if (all_ok) {
     if (!h->tau_all && !h->tau_all_tried) {
       // scratch for the tau of every pair: allocated once, outside stream capture, when it
       // takes at most a quarter of the free device memory
@@ -833,8 +851,8 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       }
     }
     if (h->tau_all) {
-      STATUS_TRY(build_tau_fields<T>(h, h->tau_all, st));
-      return k1d_all_launch<T>(h, (const cplx<T>*)h->tau_all, nbc, st);
+      STATUS_TRY(build_tau_fields<T>(h, h->tau_all, true, st));
+      if constexpr (sizeof(T) == 4) return k1d_all_launch(h, (const cplx<float>*)h->tau_all, nbc, st);
     }
   }
   if (h->k1d_cache && h->tau_cache && !h->loc_on) {

@@ -188,15 +188,18 @@ def test_kernel_variants_fp32(torch, n, a, ecut):
 
 @pytest.mark.parametrize("nocc", [20, 40, 100])
 def test_k1d_all_pairs_and_blocks(torch, nocc):
-    """K1d (Eq. 6) with the tau of every pair contracted in one pass (tuning.k1d_all = 1; a ragged last
-    orbital block, and odd block counts, where one block sits out each round of the pairing) and by
-    16 x 16 blocks of pairs (k1d_all = 0), FP64 and FP32, against the oracle."""
-    wl = _workload(24, 10.0, 10.0, nocc, 2, seed=40 + nocc)
-    want = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
-    for prec in (T.PREC_FP64, T.PREC_FP32):
-        for k1d_all in (1, 0):
-            got = _run(torch, wl, prec, mask=T.TERM_K1D, tiling=dict(k1d_all=k1d_all))
-            assert _rel_err(got, want).max() < TOL[prec], (prec, k1d_all)
+    """K1d (Eq. 6) with the tau of every pair contracted in one pass (tuning.k1d_all = 1: FP32, compact
+    intermediates on an alias-free grid, point-tiled tau; a ragged last orbital block, and odd block
+    counts, where one block sits out each round of the pairing) and by 16 x 16 blocks of pairs
+    (k1d_all = 0; also what k1d_all = 1 falls back to in FP64 and on the aliasing 24^3 grid), against
+    the oracle."""
+    for n, a, ecut in ((32, 9.0, 12.0), (24, 10.0, 10.0)):
+        wl = _workload(n, a, ecut, nocc, 3, seed=40 + nocc)
+        want = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
+        for prec in (T.PREC_FP32, T.PREC_FP64):
+            for k1d_all in (1, 0):
+                got = _run(torch, wl, prec, mask=T.TERM_K1D, tiling=dict(k1d_all=k1d_all))
+                assert _rel_err(got, want).max() < TOL[prec], (n, prec, k1d_all)
 
 
 def test_projector_tensor_cores_match_simt(torch):
