@@ -30,20 +30,24 @@ WORKLOAD = dict(n=72, a=13.48, ecut=25.0, nocc=128, nb=8, alpha=0.18, seed=0)
 WORKLOAD_NAME = ("diamond64: 64-atom diamond-like cubic cell a=13.48 bohr, 72^3 grid, Ecut 25 Ha "
                  "(14771 plane waves), Nocc 128, Nb 8 trial vectors, alpha 0.18, all occupied pairs")
 
-# DRAM traffic per launch of the dominant kernel class from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel
-# sources it was taken on and the grid of the pair convolutions; reported as null
-# when either differs.
+# DRAM traffic per launch of the plane-kernel classes from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the kernel sources
+# it was taken on and the grid of the pair convolutions; reported as null when either
+# differs. Captured launch: a 128 x 8 pair batch (1024 pair convolutions of 64^3) of the
+# exchange term inside D; its algorithmic bytes (the library profiler's model) beside it.
 NCU_TRAFFIC = {
-    # one 256-pair launch of each class on 72^3 (pair convolutions on the caller's grid)
-    "eaaf4f527de1/72": {"xy_fwd_pair_product": 538.4e6, "z_kernel_multiply": 792.8e6,
-                        "xy_inv_remultiply_accumulate": 661.7e6},
+    "3b1bbbb341a2/64": {
+        "launch": "128 x 8 pair batch of the exchange term inside D (1024 pair convolutions of 64^3)",
+        "xy_fwd_pair_product": {"dram": 1.816e9, "algorithmic": 5.807e9},
+        "z_kernel_multiply": {"dram": 2.970e9, "algorithmic": 3.024e9},
+        "xy_inv_remultiply_accumulate": {"dram": 2.115e9, "algorithmic": 4.196e9},
+    },
 }
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha1()
-    for f in ("fft.cuh", "plane_kernels.cuh", "plane_ops.cuh"):
+    for f in ("fft.cuh", "plane_kernels.cuh", "plane_lines.cuh", "plane_ops.cuh"):
         with open(os.path.join(ROOT, "paper_2309_03513_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -247,7 +251,7 @@ def run_native(args):
     sys_ = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
     npw = sys_.npw
     # pair convolutions on the smallest grid on which they are exact (the same operator as on n^3)
-    sys_.set_tuning(exchange_grid=args.exchange_grid, xy_kernel=args.xy_kernel)
+    sys_.set_tuning(exchange_grid=args.exchange_grid, xy_kernel=args.xy_kernel, k1d_all=args.k1d_all)
     n_exchange = sys_.query()["n_exchange"]
     X = torch.from_numpy(wl.X).to(dev, torch.complex64)
     LA = torch.empty_like(X)
@@ -369,7 +373,11 @@ def run_native(args):
     d = cls[dom]
     achieved = (d["bytes"] / d["launches"]) / (d["ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else None
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(f"{src_hash}/{n_exchange}", {}).get(dom)
+    cap = NCU_TRAFFIC.get(f"{src_hash}/{n_exchange}", {})
+    traffic = cap.get(dom, {}).get("dram")
+    traffic_launch = ({"launch": cap["launch"], "algorithmic_bytes": cap[dom]["algorithmic"],
+                       "dram_over_algorithmic": cap[dom]["dram"] / cap[dom]["algorithmic"]}
+                      if traffic is not None else None)
     shares = {k: round(v["ms"] / max(1e-9, sum(c["ms"] for c in cls.values())), 4) for k, v in cls.items()}
     cfg = bench_config(ws)
     cfg["npw"] = npw
@@ -378,11 +386,11 @@ def run_native(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": cfg,
-        "schedule": {"exchange_grid": n_exchange, "xy_kernel": args.xy_kernel,
+        "schedule": {"exchange_grid": n_exchange, "xy_kernel": args.xy_kernel, "k1d_all": args.k1d_all,
                      "step": "one tddft_apply_liouville on the whole batch"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
-                     "traffic": traffic, "peak_source": peaks["source"],
+                     "traffic": traffic, "traffic_launch": traffic_launch, "peak_source": peaks["source"],
                      "avg_launch_ms": d["ms"] / max(1, d["launches"]),
                      "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                      "class_time_share": shares, "kernel_sources": src_hash,
@@ -697,6 +705,8 @@ def main():
     ap.add_argument("--xy-kernel", type=int, default=1, choices=[0, 1, 2, 3],
                     help="register-line xy passes where they exist: 1 one thread per line (the default), 2 two "
                          "lanes per line, 3 forward one thread, inverse two lanes; 0: shared-memory radix stages")
+    ap.add_argument("--k1d-all", type=int, default=1, choices=[0, 1],
+                    help="1: K1d over the tau of every pair in one pass (the default); 0: by 16 x 16 blocks")
     ap.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                     help="trial vectors per batch (smaller cases for profiler captures; the bench line uses 8)")
     args = ap.parse_args()
