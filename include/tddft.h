@@ -85,8 +85,9 @@ typedef struct tddft_desc {
   int nb_max;         /* largest batch of trial vectors one call may pass */
 } tddft_desc;
 
-/* Host inputs of tddft_init_system, all FP64. The library copies them; the
- * caller may free them when the call returns. */
+/* Inputs of tddft_init_system, all FP64, each in host or device memory (the
+ * library copies them with cudaMemcpyDefault). The library keeps its own copies;
+ * the caller may free the inputs when the call returns. */
 typedef struct tddft_inputs {
   const double* phi_src; /* complex128 [nocc_src][npw], orthonormal */
   const double* phi_tgt; /* complex128 [nocc_tgt][npw], orthonormal; spin-flip only (NULL for SC) */
@@ -180,10 +181,15 @@ typedef struct tddft_tuning {
                        convolutions on two threads per column (at n = 96 only those; its
                        other z passes are the shared-memory ones). -1 keeps the value in
                        set_tuning */
-  int projector;    /* FP32 handles: 1 projector GEMMs on tcgen05 tensor cores with
+  int projector;    /* FP32 handles: projector (and ACE) GEMMs on tcgen05 tensor cores with
                        split-precision TF32 products (hi*hi + hi*lo + lo*hi, FP32
-                       accumulation in tensor memory); 0 SIMT FP32. FP64 handles
-                       always use SIMT FP64. -1 keeps the value in set_tuning */
+                       accumulation in tensor memory): 1 (default) the operands are first
+                       packed as TF32 high / low tiles in the layout of the MMA (a device
+                       buffer of at most 1 GiB, grown outside stream capture) and brought
+                       into shared memory by bulk copies in a three-stage pipeline; where
+                       the packed operands do not fit, as 2; 2 every CTA stages its
+                       operands through registers; 0 SIMT FP32. FP64 handles always use
+                       SIMT FP64. -1 keeps the value in set_tuning */
   int k1d_sparse;   /* K1d in the localised frame with truncated pairs
                        (tddft_set_localization): 1 only the kept pairs, from a pair
                        list; 0 blocks of k1d_block x k1d_block pairs, blocks without a

@@ -304,7 +304,10 @@ struct tddft_system {
   int ibuf_fields = 0;
   int tile_targets = 128, tile_sources = 8, k1d_block = 16;
   int accumulate = INV_ATOMIC;
-  int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32); 0: SIMT
+  int projector_tc = 1;  // FP32 projector GEMMs on tcgen05 tensor cores (3xTF32): 1 packed operands with
+                         // bulk copies where they fit, 2 operands staged through registers; 0: SIMT
+  uint32_t* tc_pack = nullptr;  // packed TF32 operands of the tensor-core GEMMs (k_umma_pack)
+  size_t tc_pack_words = 0;
   bool prune = true;     // pair convolutions keep only the columns a pair density can occupy (compact)
   int xy_lines = 1;      // compact xy passes on the register-line kernels where they exist (tuning.xy_kernel)
   // adaptively compressed exchange for the exchange term inside D (tddft_ace_build)
@@ -502,6 +505,43 @@ static tddft_status real_to_pw(tddft_system* h, const cplx<T>* src, int nf, cplx
 // one split of the whole K, 4e-6 with nine), so long K is always split.
 constexpr int TC_CHAIN_CHUNKS = 256;
 
+// Packed operands of the tensor-core GEMMs: words for mt + nt row blocks of kchunks K chunks
+// (high and low tiles), at most TC_PACK_MAX_WORDS; the buffer grows on demand outside stream
+// capture (otherwise, and beyond the limit, the GEMM stages its operands through registers).
+constexpr size_t TC_PACK_MAX_WORDS = (size_t)1 << 28;  // 1 GiB
+static size_t tc_pack_words(int mt, int nt, int kchunks) {
+  return (size_t)(mt + nt) * kchunks * 2 * UMMA_TILE_WORDS;
+}
+static bool tc_pack_ready(tddft_system* h, size_t words, cudaStream_t st) {
+  if (words > TC_PACK_MAX_WORDS) return false;
+  if (words <= h->tc_pack_words) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (h->tc_pack) {
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaFree(h->tc_pack) != cudaSuccess) {
+      cudaGetLastError();
+      h->tc_pack = nullptr;
+      h->bytes -= h->tc_pack_words * 4;
+      h->tc_pack_words = 0;
+      return false;
+    }
+    h->bytes -= h->tc_pack_words * 4;
+    h->tc_pack = nullptr;
+    h->tc_pack_words = 0;
+  }
+  if (cudaMalloc((void**)&h->tc_pack, words * 4) != cudaSuccess) {
+    cudaGetLastError();
+    h->tc_pack = nullptr;
+    return false;
+  }
+  h->tc_pack_words = words;
+  h->bytes += words * 4;
+  return true;
+}
+
 // overlap: C[u][r] = sum_g conj(P[u][g]) Y[r][g]   (C: [M][nrows], split-K partials in part)
 
 static tddft_status tc_overlap(tddft_system* h, const cplx<float>* P, int M, const cplx<float>* Y, int nrows,
@@ -520,7 +560,17 @@ static tddft_status tc_overlap(tddft_system* h, const cplx<float>* P, int M, con
   OvA la{P, M, K, Kp};
   OvB lb{Y, nrows, Rp, K, Kp};
   OvEp ep{part, M, nrows, Rp};
-  { k_umma_gemm<OvA, OvB, OvEp><<<dim3(nt, mt, splits), 128, UMMA_SMEM, st>>>(la, lb, ep, kchunks, per, h->b.dev_err); note_launch(); }
+  if (h->projector_tc == 1 && tc_pack_ready(h, tc_pack_words(mt, nt, kchunks), st)) {
+    uint32_t* pa = h->tc_pack;
+    uint32_t* pb = pa + (size_t)mt * kchunks * 2 * UMMA_TILE_WORDS;
+    { k_umma_pack<OvA><<<dim3(kchunks, mt), 256, 0, st>>>(la, kchunks, pa); note_launch(); }
+    { k_umma_pack<OvB><<<dim3(kchunks, nt), 256, 0, st>>>(lb, kchunks, pb); note_launch(); }
+    { k_umma_tiles<OvEp><<<dim3(nt, mt, splits), 128, UMMA_TILES_SMEM, st>>>(pa, pb, ep, kchunks, per, h->b.dev_err);
+      note_launch(); }
+  } else {
+    k_umma_gemm<OvA, OvB, OvEp><<<dim3(nt, mt, splits), 128, UMMA_SMEM, st>>>(la, lb, ep, kchunks, per, h->b.dev_err);
+    note_launch();
+  }
   { k_reduce_split<float><<<grid_for((long long)M * nrows, 256), 256, 0, st>>>(part, splits, (long long)M * nrows, C); note_launch(); }
   return check_launch("overlap (tensor cores)");
 }
@@ -535,8 +585,18 @@ static tddft_status tc_update(tddft_system* h, const cplx<float>* P, int M, cons
   UpB lb{P, M, Up, K, Gp};
   UpEp ep{Y, nrows, K, Gp, s};
   const int kc2 = 2 * Up / UMMA_KC;
-  { k_umma_gemm<UpA, UpB, UpEp><<<dim3(2 * Gp / UMMA_N, (nrows + UMMA_M - 1) / UMMA_M, 1), 128, UMMA_SMEM, st>>>(
-        la, lb, ep, kc2, kc2, h->b.dev_err); note_launch(); }
+  const int nt = 2 * Gp / UMMA_N, mt = (nrows + UMMA_M - 1) / UMMA_M;
+  if (h->projector_tc == 1 && tc_pack_ready(h, tc_pack_words(mt, nt, kc2), st)) {
+    uint32_t* pa = h->tc_pack;
+    uint32_t* pb = pa + (size_t)mt * kc2 * 2 * UMMA_TILE_WORDS;
+    { k_umma_pack<UpA><<<dim3(kc2, mt), 256, 0, st>>>(la, kc2, pa); note_launch(); }
+    { k_umma_pack<UpB><<<dim3(kc2, nt), 256, 0, st>>>(lb, kc2, pb); note_launch(); }
+    { k_umma_tiles<UpEp><<<dim3(nt, mt, 1), 128, UMMA_TILES_SMEM, st>>>(pa, pb, ep, kc2, kc2, h->b.dev_err);
+      note_launch(); }
+  } else {
+    k_umma_gemm<UpA, UpB, UpEp><<<dim3(nt, mt, 1), 128, UMMA_SMEM, st>>>(la, lb, ep, kc2, kc2, h->b.dev_err);
+    note_launch();
+  }
   return check_launch("update (tensor cores)");
 }
 
@@ -1063,6 +1123,8 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
                                 (int)(k1d_sparse_np_max<T>() * K1D_SPARSE_PTS * sizeof(cplx<T>))));
   CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<OvA, OvB, OvEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
   CUDA_TRY(cudaFuncSetAttribute(k_umma_gemm<UpA, UpB, UpEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM));
+  CUDA_TRY(cudaFuncSetAttribute(k_umma_tiles<OvEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_TILES_SMEM));
+  CUDA_TRY(cudaFuncSetAttribute(k_umma_tiles<UpEp>, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_TILES_SMEM));
   STATUS_TRY(dalloc(h, (void**)&h->b.dev_err, sizeof(int)));
   CUDA_TRY(cudaMemsetAsync(h->b.dev_err, 0, sizeof(int), st));
 
@@ -1097,7 +1159,10 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
     g2h[i] = (T)(0.5 * (tpiba2 * (double)sph[i].m2));
   }
   std::vector<T> eps(d.nocc_src);
-  for (int v = 0; v < d.nocc_src; ++v) eps[v] = (T)in->eps_src[v];
+  // the eigenvalues on the host (the input may be host or device memory)
+  std::vector<double> eps_in(d.nocc_src);
+  CUDA_TRY(cudaMemcpy(eps_in.data(), in->eps_src, d.nocc_src * sizeof(double), cudaMemcpyDefault));
+  for (int v = 0; v < d.nocc_src; ++v) eps[v] = (T)eps_in[v];
   // z-pass columns of pair densities: the product of two sphere functions has
   // |m| < 2 R_m (R_m = sqrt(2 ecut) / tpiba); without aliasing (2 max|m_i| <=
   // n/2 - 1) every (k_x, k_y) column with m_x^2 + m_y^2 > 4 R_m^2 is exactly
@@ -1204,7 +1269,7 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   CUDA_TRY(cudaMemcpyAsync(B.pos, pos.data(), npw * sizeof(int), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.g2h, g2h.data(), npw * rz, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B.eps, eps.data(), d.nocc_src * rz, cudaMemcpyHostToDevice, st));
-  h->eps64.assign(in->eps_src, in->eps_src + d.nocc_src);
+  h->eps64 = eps_in;
 
   // orbitals: FP64 upload, orthonormality check, cast to the working precision
   const int nsets = h->sf() ? 2 : 1;
@@ -1213,9 +1278,9 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   cplx<double>* phi_src64 = nullptr;
   STATUS_TRY(dalloc(h, (void**)&phi_src64, (size_t)d.nocc_src * npw * sizeof(cplx<double>)));
   B.phi_src_pw64 = phi_src64;
-  CUDA_TRY(cudaMemcpyAsync(phi_src64, in->phi_src, (size_t)d.nocc_src * npw * 16, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(phi_src64, in->phi_src, (size_t)d.nocc_src * npw * 16, cudaMemcpyDefault, st));
   if (h->sf())
-    CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, in->phi_tgt, (size_t)ntgt * npw * 16, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, in->phi_tgt, (size_t)ntgt * npw * 16, cudaMemcpyDefault, st));
   else
     CUDA_TRY(cudaMemcpyAsync(B.phi_tgt_pw64, phi_src64, (size_t)ntgt * npw * 16, cudaMemcpyDeviceToDevice, st));
 
@@ -1267,13 +1332,13 @@ static tddft_status init_impl(tddft_system* h, const tddft_inputs* in, cudaStrea
   if (in->vloc || in->fxc) STATUS_TRY(tmp.get((void**)&tmp64, n3 * sizeof(double)));
   if (in->vloc) {
     STATUS_TRY(dalloc(h, &B.vloc, n3 * rz));
-    CUDA_TRY(cudaMemcpyAsync(tmp64, in->vloc, n3 * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(tmp64, in->vloc, n3 * 8, cudaMemcpyDefault, st));
     { k_real_cast<T><<<grid_for(n3, 256), 256, 0, st>>>(tmp64, (T*)B.vloc, n3); note_launch(); }
     CUDA_TRY(cudaStreamSynchronize(st));
   }
   if (in->fxc) {
     STATUS_TRY(dalloc(h, &B.fxc, n3 * rz));
-    CUDA_TRY(cudaMemcpyAsync(tmp64, in->fxc, n3 * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(tmp64, in->fxc, n3 * 8, cudaMemcpyDefault, st));
     { k_real_cast<T><<<grid_for(n3, 256), 256, 0, st>>>(tmp64, (T*)B.fxc, n3); note_launch(); }
     CUDA_TRY(cudaStreamSynchronize(st));
   }
@@ -1956,6 +2021,7 @@ tddft_status tddft_destroy(tddft_handle h) {
   for (void* p : h->allocations) cudaFree(p);
   if (h->tau_cache) cudaFree(h->tau_cache);
   if (h->tau_all) cudaFree(h->tau_all);
+  if (h->tc_pack) cudaFree(h->tc_pack);
   if (h->xsub) tddft_destroy(h->xsub);
   delete h;
   return TDDFT_OK;
@@ -2131,7 +2197,7 @@ tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
     h->prune = t->prune == 1;
   }
   if (t->projector >= 0) {
-    if (t->projector > 1) return fail(TDDFT_EINVAL, "projector must be 0 or 1");
+    if (t->projector > 2) return fail(TDDFT_EINVAL, "projector must be 0, 1 or 2");
     h->projector_tc = t->projector;
   }
   if (t->k1d_sparse >= 0) {

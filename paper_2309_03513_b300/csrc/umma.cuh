@@ -233,6 +233,9 @@ struct OvEp {
     float* d = reinterpret_cast<float*>(part + ((long long)split * M + m) * R + r);
     d[im ? 1 : 0] = v;
   }
+  // two-phase form of the packed path's epilogue: load the value a store needs (none here), then store
+  __device__ __forceinline__ float load(int, int, int) const { return 0.f; }
+  __device__ __forceinline__ void store(int m, int n, float, float v, int split) const { (*this)(m, n, v, split); }
 };
 struct UpA {
   const cplx<float>* c;  // [U][R]
@@ -271,6 +274,208 @@ struct UpEp {
     float* d = reinterpret_cast<float*>(y + (long long)r * G + g);
     d[im ? 1 : 0] += s * v;
   }
+  __device__ __forceinline__ float* addr(int r, int n) const {
+    const bool im = n >= Gp;
+    const int g = im ? n - Gp : n;
+    if (r >= R || g >= G) return nullptr;
+    return reinterpret_cast<float*>(y + (long long)r * G + g) + (im ? 1 : 0);
+  }
+  __device__ __forceinline__ float load(int r, int n, int) const {
+    const float* d = addr(r, n);
+    return d ? *d : 0.f;
+  }
+  __device__ __forceinline__ void store(int r, int n, float old, float v, int) const {
+    float* d = addr(r, n);
+    if (d) *d = old + s * v;
+  }
 };
+
+// ---------------------------------------------------------------------------
+// Packed-operand path (used where the packed operands fit the handle's buffer).
+// k_umma_pack writes a real operand, given by one of the loaders above, as TF32
+// high and low tiles in the canonical layout of the MMA (the image that the
+// staging loop of k_umma_gemm builds in shared memory): tile (row block rb, K
+// chunk c) at ((rb * kchunks + c) * 2 + part) * UMMA_M * UMMA_KC words, part 0 =
+// high, 1 = low. Consecutive threads write consecutive words.
+// k_umma_tiles brings the tile pairs of a K chunk into shared memory with one bulk
+// copy per operand (cp.async.bulk, completion counted on an mbarrier), in a ring of
+// UMMA_STAGES stages; one thread waits for a stage's copies, issues its 12 MMAs,
+// commits them to the stage's second mbarrier and refills the stage once those
+// MMAs are done, so copies of later chunks overlap the MMAs of earlier ones and no
+// thread touches the operands in between. The accumulator tile goes through shared
+// memory to the epilogue, one row after the other across the CTA's threads
+// (consecutive threads take consecutive columns). Every wait is bounded: on a
+// timeout the CTA waits (bounded) for what it issued, sets *err, frees its tensor
+// memory and returns.
+// ---------------------------------------------------------------------------
+constexpr int UMMA_TILE_WORDS = UMMA_M * UMMA_KC;           // 4096
+constexpr int UMMA_PAIR_BYTES = 2 * UMMA_TILE_BYTES;        // high + low tile, 32 KB
+constexpr int UMMA_STAGES = 3;
+constexpr int UMMA_STAGE_BYTES = 2 * UMMA_PAIR_BYTES;       // A pair + B pair
+constexpr int UMMA_DPITCH = UMMA_N + 1;                     // epilogue staging row pitch (words)
+constexpr int UMMA_TILES_SMEM = UMMA_STAGES * UMMA_STAGE_BYTES + 128;
+
+template <class LD>
+__global__ void __launch_bounds__(256) k_umma_pack(LD ld, int kchunks, uint32_t* __restrict__ out) {
+  const int c = blockIdx.x, rb = blockIdx.y;
+  uint32_t* hi = out + (size_t)(rb * kchunks + c) * 2 * UMMA_TILE_WORDS;
+  uint32_t* lo = hi + UMMA_TILE_WORDS;
+  for (int o = threadIdx.x; o < UMMA_TILE_WORDS; o += 256) {
+    // word o = ((row / 8) * 8 + k / 4) * 32 + (row % 8) * 4 + k % 4 (see umma_offset)
+    const int row = (o >> 8) * 8 + ((o >> 2) & 7), k = ((o >> 5) & 7) * 4 + (o & 3);
+    const float v = ld(rb * UMMA_M + row, c * UMMA_KC + k);
+    const uint32_t h = to_tf32(v);
+    hi[o] = h;
+    lo[o] = to_tf32(v - __uint_as_float(h));
+  }
+}
+
+__device__ __forceinline__ bool umma_bar_wait(uint32_t bar, uint32_t parity) {
+  for (long long polls = 0; polls < UMMA_WAIT_LIMIT; ++polls) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+// pa: packed A [mtiles][kchunks][2][4096]; pb: packed B [ntiles][kchunks][2][4096]
+template <class EP>
+__global__ void __launch_bounds__(128)
+    k_umma_tiles(const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb, EP ep, int kchunks,
+                 int chunks_per_split, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char umma_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(umma_smem + UMMA_STAGES * UMMA_STAGE_BYTES);
+  uint64_t* empty = full + UMMA_STAGES;
+  uint64_t* done = empty + UMMA_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.y * UMMA_M, n0 = blockIdx.x * UMMA_N, split = blockIdx.z;
+  const int c0 = split * chunks_per_split, c1 = min(kchunks, c0 + chunks_per_split), nch = max(0, c1 - c0);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(UMMA_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < 2 * UMMA_STAGES + 1; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + s)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = *tmem_slot;
+
+  int bad = 0;
+  if (tid == 0 && nch > 0) {
+    const uint32_t* abase = pa + (size_t)blockIdx.y * kchunks * 2 * UMMA_TILE_WORDS;
+    const uint32_t* bbase = pb + (size_t)blockIdx.x * kchunks * 2 * UMMA_TILE_WORDS;
+    int loaded = 0, consumed = 0;
+    auto load = [&](int i) {  // chunk c0 + i into stage i % UMMA_STAGES
+      unsigned char* st = umma_smem + (i % UMMA_STAGES) * UMMA_STAGE_BYTES;
+      const uint32_t bar = smem_u32(full + i % UMMA_STAGES);
+      const size_t off = (size_t)(c0 + i) * 2 * UMMA_TILE_WORDS;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(2 * UMMA_PAIR_BYTES)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                       smem_u32(st)),
+                   "l"(abase + off), "r"(UMMA_PAIR_BYTES), "r"(bar)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                       smem_u32(st + UMMA_PAIR_BYTES)),
+                   "l"(bbase + off), "r"(UMMA_PAIR_BYTES), "r"(bar)
+                   : "memory");
+      ++loaded;
+    };
+    for (int i = 0; i < min(UMMA_STAGES, nch); ++i) load(i);
+    constexpr uint32_t idesc = umma_idesc_tf32();
+    for (int i = 0; i < nch && !bad; ++i) {
+      const int s = i % UMMA_STAGES;
+      const uint32_t ph = (uint32_t)(i / UMMA_STAGES) & 1u;
+      if (!umma_bar_wait(smem_u32(full + s), ph)) {
+        bad = 1;
+        break;
+      }
+      ++consumed;
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const uint32_t sa = smem_u32(umma_smem + s * UMMA_STAGE_BYTES), sb = sa + UMMA_PAIR_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < UMMA_KC / 8; ++kk) {
+        const uint32_t koff = kk * 256;  // 8 tf32 = 2 core matrices along K
+        const uint64_t ah = umma_desc(sa + koff), al = umma_desc(sa + UMMA_TILE_BYTES + koff);
+        const uint64_t bh = umma_desc(sb + koff), bl = umma_desc(sb + UMMA_TILE_BYTES + koff);
+        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+        umma_tf32(tmem, ah, bh, idesc, acc0);
+        umma_tf32(tmem, ah, bl, idesc, 1u);
+        umma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(empty + s)));
+      // refill the previous chunk's stage once its MMAs have read it (this chunk's MMAs queue behind them)
+      const int ip = i - 1;
+      if (ip >= 0 && ip + UMMA_STAGES < nch) {
+        if (!umma_bar_wait(smem_u32(empty + ip % UMMA_STAGES), (uint32_t)(ip / UMMA_STAGES) & 1u)) {
+          bad = 1;
+          break;
+        }
+        load(ip + UMMA_STAGES);
+      }
+    }
+    // all MMAs issued so far complete before the accumulator is read (or the CTA leaves)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        smem_u32(done)));
+    if (!umma_bar_wait(smem_u32(done), 0u)) bad = 1;
+    // copies still in flight (after a timeout) land before the shared memory is reused
+    for (; consumed < loaded; ++consumed)
+      umma_bar_wait(smem_u32(full + consumed % UMMA_STAGES), (uint32_t)(consumed / UMMA_STAGES) & 1u);
+    if (bad) atomicExch(err, 1);
+  }
+  const int failed = __syncthreads_or(bad);
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if (!failed) {
+    float* dst = reinterpret_cast<float*>(umma_smem);  // [UMMA_M][UMMA_DPITCH], over the stage buffers
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int cb = 0; cb < UMMA_N; cb += 16) {
+      uint32_t r[16];
+      if (nch > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + lane_base + (uint32_t)cb));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dst[tid * UMMA_DPITCH + cb + j] = __uint_as_float(r[j]);
+    }
+    __syncthreads();
+    // rows in groups of 16: the group's loads (for read-modify-write epilogues) are in flight together
+#pragma unroll 1
+    for (int mg = 0; mg < UMMA_M; mg += 16) {
+      float old[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) old[j] = ep.load(m0 + mg + j, n0 + tid, split);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ep.store(m0 + mg + j, n0 + tid, old[j], dst[(mg + j) * UMMA_DPITCH + tid], split);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(UMMA_N));
+  }
+}
 
 }  // namespace tddft

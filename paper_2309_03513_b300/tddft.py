@@ -150,8 +150,27 @@ def _check(status: int, where: str):
         raise TddftError(status, where, detail)
 
 
-def _ptr(a: np.ndarray | None):
-    return None if a is None else a.ctypes.data
+def _ptr(a):
+    """Address of a host array (numpy) or a device array (a tensor with data_ptr)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _input_array(x, dtype):
+    """A contiguous FP64 / complex128 input: a CUDA tensor stays on the device, anything else
+    becomes a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        want = torch.complex128 if dtype == np.complex128 else torch.float64
+        if x.dtype != want:
+            raise TypeError(f"device input must be {want}")
+        return x.contiguous()
+    return np.ascontiguousarray(np.asarray(x), dtype=dtype)
 
 
 def exchange_grid(n: int, a: float, ecut: float, precision: int = PREC_FP32) -> int:
@@ -246,13 +265,14 @@ class LiouvilleSystem:
         self.n, self.a, self.ecut = int(n), float(a), float(ecut)
         self.precision = int(precision)
         self.spin_flip = bool(spin_flip)
-        phi_src = np.ascontiguousarray(phi_src, dtype=np.complex128)
+        # inputs: numpy arrays (host) or CUDA tensors (device); the library copies either
+        phi_src = _input_array(phi_src, np.complex128)
         self.nocc_src, self.npw = phi_src.shape
-        phi_tgt_c = None if phi_tgt is None else np.ascontiguousarray(phi_tgt, dtype=np.complex128)
+        phi_tgt_c = _input_array(phi_tgt, np.complex128)
         self.nocc_tgt = phi_tgt_c.shape[0] if (spin_flip and phi_tgt_c is not None) else self.nocc_src
-        eps = np.ascontiguousarray(eps_src, dtype=np.float64)
-        vl = None if vloc is None else np.ascontiguousarray(vloc, dtype=np.float64)
-        fx = None if fxc is None else np.ascontiguousarray(fxc, dtype=np.float64)
+        eps = _input_array(eps_src, np.float64)
+        vl = _input_array(vloc, np.float64)
+        fx = _input_array(fxc, np.float64)
         self.nb_max = int(nb_max)
         d = Desc(self.n, self.a, self.ecut, SPIN_FLIP if spin_flip else SPIN_CONSERVING, self.nocc_src,
                  self.nocc_tgt, float(alpha), float(kx_g0), self.precision, int(term_mask), self.nb_max)

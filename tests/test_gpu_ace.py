@@ -71,7 +71,7 @@ def test_ace_operator_matches_oracle(torch, prec, n_extra):
     assert _rel_err(got, want).max() < TOL[prec]
 
 
-@pytest.mark.parametrize("projector", [0, 1])
+@pytest.mark.parametrize("projector", [0, 1, 2])
 def test_ace_fp32_simt_and_tensor_core_gemms(torch, projector):
     """n_ace = 8 + 136 = 144 spans two 128-row tensor-core tiles; 72^3 grid plan, ragged sphere."""
     wl = _workload(36, 10.0, 18.0, 8, 3, seed=42)

@@ -202,15 +202,38 @@ def test_k1d_all_pairs_and_blocks(torch, nocc):
                 assert _rel_err(got, want).max() < TOL[prec], (n, prec, k1d_all)
 
 
+@pytest.mark.parametrize("sf", [False, True])
+def test_init_from_device_inputs(torch, sf):
+    """tddft_init_system with every input in device memory (CUDA tensors: orbitals of both spins,
+    eigenvalues, V_loc, f_xc) builds the same operator as with host arrays, bit for bit."""
+    wl = _workload(24, 10.0, 10.0, 6, 2, seed=50, sf=sf, nocc_tgt=4 if sf else None)
+    X = torch.from_numpy(wl.X).cuda()
+    outs = []
+    for dev in (False, True):
+        put = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()) if dev else (lambda a: a)
+        s = T.LiouvilleSystem(n=wl.n, a=wl.a, ecut=wl.ecut, phi_src=put(wl.phi_src), eps_src=put(wl.eps_src),
+                              alpha=wl.alpha, kx_g0=wl.kx_g0, precision=T.PREC_FP64, nb_max=wl.nb,
+                              spin_flip=wl.spin_flip, phi_tgt=put(wl.phi_tgt) if sf else None,
+                              vloc=put(wl.vloc), fxc=put(wl.fxc))
+        outs.append(s.apply(X).cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    want = O.system_from_workload(wl).apply(wl.X)
+    assert _rel_err(outs[1], want).max() < TOL[T.PREC_FP64]
+
+
 def test_projector_tensor_cores_match_simt(torch):
     """The tcgen05 projector (3xTF32 products, FP32 accumulation) against the SIMT
     FP32 projector and the oracle, on a batch whose rows exceed one 128-row tile."""
     wl = _workload(24, 10.0, 10.0, 40, 5, seed=16)
     want = O.system_from_workload(wl).apply(wl.X)
     tc = _run(torch, wl, T.PREC_FP32, tiling=(0, 0, 0, -1, -1, -1, -1, 1))
+    staged = _run(torch, wl, T.PREC_FP32, tiling=(0, 0, 0, -1, -1, -1, -1, 2))
     simt = _run(torch, wl, T.PREC_FP32, tiling=(0, 0, 0, -1, -1, -1, -1, 0))
     assert _rel_err(tc, want).max() < 1e-5
+    assert _rel_err(staged, want).max() < 1e-5
     assert _rel_err(tc, simt).max() < 2e-6
+    assert _rel_err(tc, staged).max() < 1e-6  # the same products, packed or staged
     only_proj = _run(torch, wl, T.PREC_FP32, mask=T.TERM_D_KIN | T.TERM_PROJ, tiling=(0, 0, 0, -1, -1, -1, -1, 1))
     assert _rel_err(only_proj, O.system_from_workload(wl).apply(wl.X, T.TERM_D_KIN | T.TERM_PROJ)).max() < 1e-5
 
@@ -222,7 +245,7 @@ def test_tuning_fields_round_trip(torch):
     for kw in (dict(targets=4), dict(sources=2), dict(k1d_block=8), dict(accumulate=0), dict(accumulate=1),
                dict(graph=1), dict(graph=0), dict(prune=1), dict(prune=0), dict(z_kernel=0), dict(z_kernel=1),
                dict(z_kernel=2),
-               dict(projector=0), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
+               dict(projector=0), dict(projector=2), dict(projector=1), dict(k1d_sparse=0), dict(k1d_sparse=1), dict(k1d_sparse=2),
                dict(k1d_cache=1), dict(k1d_cache=0), dict(exchange_grid=0), dict(exchange_grid=1),
                dict(xy_kernel=0), dict(xy_kernel=2), dict(xy_kernel=3), dict(xy_kernel=1),
                dict(k1d_all=0), dict(k1d_all=1)):
@@ -233,7 +256,7 @@ def test_tuning_fields_round_trip(torch):
         assert after[k] == v, (kw, after)
         assert {x: after[x] for x in after if x != k} == {x: before[x] for x in before if x != k}, (kw, before, after)
     with pytest.raises(T.TddftError):
-        s.set_tuning(projector=2)
+        s.set_tuning(projector=3)
     with pytest.raises(T.TddftError):
         s.set_tuning(k1d_cache=2)
     with pytest.raises(T.TddftError):
