@@ -311,7 +311,7 @@ def run_native(args):
     io_bytes = nb * nocc * npw * 8
 
     # per-term split (one step each, same batch): K1d-only apps/s etc.
-    term_ms = {}
+    term_ms, term_marginal_ms = {}, {}
     if args.term_split:
         for name, mask in (("D_exchange", T.TERM_D_EXX), ("K1d", T.TERM_K1D), ("K1e", T.TERM_K1E_H | T.TERM_K1E_XC),
                            ("diagonal_and_projector", T.TERM_D_KIN | T.TERM_D_VLOC | T.TERM_PROJ),
@@ -326,6 +326,22 @@ def run_native(args):
             t1e.record(stream)
             torch.cuda.synchronize(dev)
             term_ms[name] = t0e.elapsed_time(t1e)
+        # marginal cost in the full operator: L minus L without the term (shared field transforms
+        # of the trial vectors and results are not charged to a term)
+        def one_step(mask):
+            sys_.set_terms(mask)
+            sys_.apply(X, out=LA, stream=stream)
+            t0e = torch.cuda.Event(enable_timing=True)
+            t1e = torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            sys_.apply(X, out=LA, stream=stream)
+            t1e.record(stream)
+            torch.cuda.synchronize(dev)
+            return t0e.elapsed_time(t1e)
+        full_ms = one_step(T.TERMS_ALL)
+        for name, mask in (("D_exchange", T.TERM_D_EXX), ("K1d", T.TERM_K1D), ("K1e", T.TERM_K1E_H | T.TERM_K1E_XC),
+                           ("diagonal_and_projector", T.TERM_D_KIN | T.TERM_D_VLOC | T.TERM_PROJ)):
+            term_marginal_ms[name] = full_ms - one_step(T.TERMS_ALL & ~mask)
         sys_.set_terms(T.TERMS_ALL)
 
     extras = {}
@@ -400,6 +416,7 @@ def run_native(args):
         "measured_alu_peaks": alu_peaks,
         "clocks": clocks,
         "terms_ms_per_step": term_ms or None,
+        "terms_marginal_ms_per_step": term_marginal_ms or None,
         "k1d_only_apps_per_s": (nb / (term_ms["K1d"] / 1e3)) if term_ms else None,
         "extras": extras or None,
         "fp64_path": fp64,

@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(K1D_THREADS)
 // vi * tj + vj of block pair (I, J) at K1dAll::off[I][J]; diagonal blocks hold both
 // orders), so the tau of one block pair at one tile is one contiguous run, which a
 // bulk copy (cp.async.bulk, completion on an mbarrier) brings into shared memory.
-// A CTA takes one tile and every output row (nocc <= 128): thread (row pair, point)
-// holds rows v and v + 8 of one block and keeps the sums of NB trial vectors for
-// both in registers, so that each trial-vector value read from shared memory serves
-// two rows. The trial vectors of the tile are staged once per group of NB. The
+// A CTA takes one tile and every output row (nocc <= 128): thread (row pair, point pair)
+// holds rows v and v + 8 of one block at two neighbouring points and keeps the sums of
+// NB trial vectors for the four in registers; every shared-memory read is 16 bytes (two
+// points), each trial-vector value serves two rows and each tau value NB vectors. The trial vectors of the tile are staged once per group of NB. The
 // off-diagonal block pairs are visited in rounds of disjoint pairs (the round-robin
 // pairing of the blocks, K1dAll::pi/pj): in a round every block meets one partner and
 // the rows of both blocks read the round's tiles (the I rows as tau, the J rows
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(K1D_THREADS)
 // of round r + 1 are in flight while round r is computed (two buffers); the diagonal
 // blocks come last, into both buffers once the last round is done. Every wait on an mbarrier is bounded: on
 // timeout the CTA sets *err, waits (bounded) for the copies it issued and returns.
-constexpr int K1D_ALL_THREADS = 512;
+constexpr int K1D_ALL_THREADS = 256;
 constexpr int K1D_ALL_PTS = POINT_TILE;
 constexpr int K1D_ALL_BLOCKS = 8;  // orbital blocks (nocc <= 128)
 constexpr int K1D_ALL_ROWS = 16 * K1D_ALL_BLOCKS;
@@ -191,17 +191,33 @@ struct K1dAll {
   long long nf;  // fields per tile
 };
 
-// acc += a * t for the two rows of a thread
-template <typename T, int NB>
-__device__ __forceinline__ void k1d_all_mac(cplx<T> (&acc)[2][NB], const cplx<T>* av, cplx<T> t0, cplx<T> t1) {
+// acc[row][point][q] += a_q * t for the two rows and two points of a thread; t0 / t1 hold the
+// tau of the two rows at the two points (x, y: first point; z, w: second), av the first
+// point's value of trial vector 0
+// acc += x * t as four fused multiply-adds (the product is not rounded before the sum)
+__device__ __forceinline__ void k1d_cmac(cplx<float>& acc, float xr, float xi, float tr, float ti) {
+  acc.x = fmaf(xr, tr, acc.x);
+  acc.x = fmaf(-xi, ti, acc.x);
+  acc.y = fmaf(xr, ti, acc.y);
+  acc.y = fmaf(xi, tr, acc.y);
+}
+template <int NB>
+__device__ __forceinline__ void k1d_all_mac(cplx<float> (&acc)[2][2][NB], const cplx<float>* av, float4 t0,
+                                            float4 t1) {
   constexpr int QS = K1D_ALL_ROWS * K1D_ALL_PTS;  // stride of one trial vector in the staged block
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
-    const cplx<T> x = av[q * QS];
-    acc[0][q] = cadd(acc[0][q], cmul(x, t0));
-    acc[1][q] = cadd(acc[1][q], cmul(x, t1));
+    const float4 x = *reinterpret_cast<const float4*>(av + q * QS);
+    k1d_cmac(acc[0][0][q], x.x, x.y, t0.x, t0.y);
+    k1d_cmac(acc[0][1][q], x.z, x.w, t0.z, t0.w);
+    k1d_cmac(acc[1][0][q], x.x, x.y, t1.x, t1.y);
+    k1d_cmac(acc[1][1][q], x.z, x.w, t1.z, t1.w);
   }
 }
+__device__ __forceinline__ float4 k1d_ld2(const cplx<float>* p, bool ok) {
+  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float4 k1d_conj2(float4 t) { return make_float4(t.x, -t.y, t.z, -t.w); }
 
 __device__ __forceinline__ uint32_t k1d_smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
   cplx<T>* as = reinterpret_cast<cplx<T>*>(smem_raw + 128);  // [NB][K1D_ALL_ROWS][PTS]
   cplx<T>* ts = as + NB * QS;                                 // two round buffers, [slot][field][PTS]
   const int tid = threadIdx.x;
-  const int p = tid % PTS, rp = tid / PTS;  // rp: row pair 0..63
-  const int B = rp / 8, vb = rp % 8;        // rows 16 B + vb and 16 B + vb + 8
+  const int p = 2 * (tid % (PTS / 2)), rp = tid / (PTS / 2);  // points p, p + 1; rp: row pair 0..63
+  const int B = rp / 8, vb = rp % 8;                          // rows 16 B + vb and 16 B + vb + 8
   const int v0 = 16 * B + vb;
   const long long tile = blockIdx.x, r0 = tile * PTS;
   const cplx<T>* tt = tau + tile * kt.nf * PTS;  // this tile's fields
@@ -290,13 +306,15 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
       else issue(-1);
       ++issued;
     }
-    for (int e = tid; e < NB * QS; e += K1D_ALL_THREADS) {
+    for (int e = 2 * tid; e < NB * QS; e += 2 * K1D_ALL_THREADS) {  // two points per 16-byte copy
       const int pp = e % PTS, rest = e / PTS, vv = rest % K1D_ALL_ROWS, bb = rest / K1D_ALL_ROWS;
-      as[e] = (bb < nbc && vv < nocc) ? a[((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp] : cplx<T>{T(0), T(0)};
+      *reinterpret_cast<float4*>(as + e) =
+          (bb < nbc && vv < nocc) ? *reinterpret_cast<const float4*>(a + ((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    cplx<T> acc[2][NB];
+    cplx<T> acc[2][2][NB];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) acc[0][q] = acc[1][q] = {T(0), T(0)};
+    for (int q = 0; q < NB; ++q) acc[0][0][q] = acc[0][1][q] = acc[1][0][q] = acc[1][1][q] = {T(0), T(0)};
     for (int r = 0; r <= kt.rounds && ok; ++r) {  // r == rounds: the diagonal blocks
       __syncthreads();  // staged trial vectors visible; the buffer of stage `issued` is free
       if (tid == 0) {
@@ -323,18 +341,20 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
           const cplx<T>* av = as + partner * 16 * PTS + p;
           const int np = bsize(partner), nself = bsize(B);
           if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj), field vb * tj + vj
-            const bool r1 = vb + 8 < nself;
+            const bool r0ok = vb < nself, r1 = vb + 8 < nself;
+#pragma unroll 4
             for (int vj = 0; vj < np; ++vj) {
-              const cplx<T> t0 = vb < nself ? tile_s[(vb * np + vj) * PTS + p] : cplx<T>{T(0), T(0)};
-              const cplx<T> t1 = r1 ? tile_s[((vb + 8) * np + vj) * PTS + p] : cplx<T>{T(0), T(0)};
-              k1d_all_mac<T, NB>(acc, av + vj * PTS, t0, t1);
+              const float4 t0 = k1d_ld2(tile_s + (vb * np + vj) * PTS + p, r0ok);
+              const float4 t1 = k1d_ld2(tile_s + ((vb + 8) * np + vj) * PTS + p, r1);
+              k1d_all_mac<NB>(acc, av + vj * PTS, t0, t1);
             }
           } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v)), field vi * tj + vb
             const bool r0ok = vb < nself, r1 = vb + 8 < nself;
+#pragma unroll 4
             for (int vi = 0; vi < np; ++vi) {
-              const cplx<T> t0 = r0ok ? cconj(tile_s[(vi * nself + vb) * PTS + p]) : cplx<T>{T(0), T(0)};
-              const cplx<T> t1 = r1 ? cconj(tile_s[(vi * nself + vb + 8) * PTS + p]) : cplx<T>{T(0), T(0)};
-              k1d_all_mac<T, NB>(acc, av + vi * PTS, t0, t1);
+              const float4 t0 = k1d_conj2(k1d_ld2(tile_s + (vi * nself + vb) * PTS + p, r0ok));
+              const float4 t1 = k1d_conj2(k1d_ld2(tile_s + (vi * nself + vb + 8) * PTS + p, r1));
+              k1d_all_mac<NB>(acc, av + vi * PTS, t0, t1);
             }
           }
         }
@@ -343,10 +363,11 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
         const int tb = bsize(B);
         const bool r0ok = vb < tb, r1 = vb + 8 < tb;
         const cplx<T>* av = as + B * 16 * PTS + p;
+#pragma unroll 4
         for (int vj = 0; vj < tb; ++vj) {
-          const cplx<T> t0 = r0ok ? tile_s[(vb * tb + vj) * PTS + p] : cplx<T>{T(0), T(0)};
-          const cplx<T> t1 = r1 ? tile_s[((vb + 8) * tb + vj) * PTS + p] : cplx<T>{T(0), T(0)};
-          k1d_all_mac<T, NB>(acc, av + vj * PTS, t0, t1);
+          const float4 t0 = k1d_ld2(tile_s + (vb * tb + vj) * PTS + p, r0ok);
+          const float4 t1 = k1d_ld2(tile_s + ((vb + 8) * tb + vj) * PTS + p, r1);
+          k1d_all_mac<NB>(acc, av + vj * PTS, t0, t1);
         }
       }
     }
@@ -358,10 +379,9 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int v = v0 + 8 * h;
-            if (v < nocc) {
-              cplx<T>* o = out + ((long long)(b0 + q) * nocc + v) * n3 + r0 + p;
-              *o = cadd(*o, cscale(acc[h][q], s));
-            }
+            if (v < nocc)  // the only contribution to these points in this launch: one rounding, as a plain add
+              atomicAdd(reinterpret_cast<float4*>(out + ((long long)(b0 + q) * nocc + v) * n3 + r0 + p),
+                        make_float4(s * acc[h][0][q].x, s * acc[h][0][q].y, s * acc[h][1][q].x, s * acc[h][1][q].y));
           }
         }
     }
