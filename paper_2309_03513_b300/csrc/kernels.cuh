@@ -162,10 +162,12 @@ __global__ void __launch_bounds__(K1D_THREADS)
 // vi * tj + vj of block pair (I, J) at K1dAll::off[I][J]; diagonal blocks hold both
 // orders), so the tau of one block pair at one tile is one contiguous run, which a
 // bulk copy (cp.async.bulk, completion on an mbarrier) brings into shared memory.
-// A CTA takes one tile and every output row (nocc <= 128): thread (row pair, point pair)
-// holds rows v and v + 8 of one block at two neighbouring points and keeps the sums of
-// NB trial vectors for the four in registers; every shared-memory read is 16 bytes (two
-// points), each trial-vector value serves two rows and each tau value NB vectors. The trial vectors of the tile are staged once per group of NB. The
+// A CTA takes one tile and every output row (nocc <= 128): thread (row quad, point) holds
+// rows v, v + 4, v + 8, v + 12 of one block at one point and keeps the sums of NB trial
+// vectors for the four in registers, so that each trial-vector value read from shared
+// memory serves four rows and each tau value NB vectors; the four row quads of a block and
+// the eight points of the tile make one warp (one block per warp). The trial vectors of the
+// tile are staged once per group of NB. The
 // off-diagonal block pairs are visited in rounds of disjoint pairs (the round-robin
 // pairing of the blocks, K1dAll::pi/pj): in a round every block meets one partner and
 // the rows of both blocks read the round's tiles (the I rows as tau, the J rows
@@ -191,9 +193,6 @@ struct K1dAll {
   long long nf;  // fields per tile
 };
 
-// acc[row][point][q] += a_q * t for the two rows and two points of a thread; t0 / t1 hold the
-// tau of the two rows at the two points (x, y: first point; z, w: second), av the first
-// point's value of trial vector 0
 // acc += x * t as four fused multiply-adds (the product is not rounded before the sum)
 __device__ __forceinline__ void k1d_cmac(cplx<float>& acc, float xr, float xi, float tr, float ti) {
   acc.x = fmaf(xr, tr, acc.x);
@@ -201,23 +200,20 @@ __device__ __forceinline__ void k1d_cmac(cplx<float>& acc, float xr, float xi, f
   acc.y = fmaf(xr, ti, acc.y);
   acc.y = fmaf(xi, tr, acc.y);
 }
+// acc[h][q] += a_q * t[h] for the four rows of a thread; av: trial vector 0 of the partner row
 template <int NB>
-__device__ __forceinline__ void k1d_all_mac(cplx<float> (&acc)[2][2][NB], const cplx<float>* av, float4 t0,
-                                            float4 t1) {
+__device__ __forceinline__ void k1d_all_mac(cplx<float> (&acc)[4][NB], const cplx<float>* av, const cplx<float> (&t)[4]) {
   constexpr int QS = K1D_ALL_ROWS * K1D_ALL_PTS;  // stride of one trial vector in the staged block
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
-    const float4 x = *reinterpret_cast<const float4*>(av + q * QS);
-    k1d_cmac(acc[0][0][q], x.x, x.y, t0.x, t0.y);
-    k1d_cmac(acc[0][1][q], x.z, x.w, t0.z, t0.w);
-    k1d_cmac(acc[1][0][q], x.x, x.y, t1.x, t1.y);
-    k1d_cmac(acc[1][1][q], x.z, x.w, t1.z, t1.w);
+    const cplx<float> x = av[q * QS];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) k1d_cmac(acc[h][q], x.x, x.y, t[h].x, t[h].y);
   }
 }
-__device__ __forceinline__ float4 k1d_ld2(const cplx<float>* p, bool ok) {
-  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ cplx<float> k1d_ld(const cplx<float>* p, bool ok) {
+  return ok ? *p : cplx<float>{0.f, 0.f};
 }
-__device__ __forceinline__ float4 k1d_conj2(float4 t) { return make_float4(t.x, -t.y, t.z, -t.w); }
 
 __device__ __forceinline__ uint32_t k1d_smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -258,8 +254,8 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
   cplx<T>* as = reinterpret_cast<cplx<T>*>(smem_raw + 128);  // [NB][K1D_ALL_ROWS][PTS]
   cplx<T>* ts = as + NB * QS;                                 // two round buffers, [slot][field][PTS]
   const int tid = threadIdx.x;
-  const int p = 2 * (tid % (PTS / 2)), rp = tid / (PTS / 2);  // points p, p + 1; rp: row pair 0..63
-  const int B = rp / 8, vb = rp % 8;                          // rows 16 B + vb and 16 B + vb + 8
+  const int p = tid % PTS, rq = tid / PTS;  // point p; rq: row quad 0..31
+  const int B = rq / 4, vb = rq % 4;        // rows 16 B + vb + 4 h, h < 4
   const int v0 = 16 * B + vb;
   const long long tile = blockIdx.x, r0 = tile * PTS;
   const cplx<T>* tt = tau + tile * kt.nf * PTS;  // this tile's fields
@@ -312,9 +308,9 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
           (bb < nbc && vv < nocc) ? *reinterpret_cast<const float4*>(a + ((long long)(b0 + bb) * nocc + vv) * n3 + r0 + pp)
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    cplx<T> acc[2][2][NB];
+    cplx<T> acc[4][NB];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) acc[0][0][q] = acc[0][1][q] = acc[1][0][q] = acc[1][1][q] = {T(0), T(0)};
+    for (int q = 0; q < NB; ++q) acc[0][q] = acc[1][q] = acc[2][q] = acc[3][q] = {T(0), T(0)};
     for (int r = 0; r <= kt.rounds && ok; ++r) {  // r == rounds: the diagonal blocks
       __syncthreads();  // staged trial vectors visible; the buffer of stage `issued` is free
       if (tid == 0) {
@@ -340,34 +336,35 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
           const cplx<T>* tile_s = buf + kt.slot[r][B] * K1D_ALL_SLOT;
           const cplx<T>* av = as + partner * 16 * PTS + p;
           const int np = bsize(partner), nself = bsize(B);
-          if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj), field vb * tj + vj
-            const bool r0ok = vb < nself, r1 = vb + 8 < nself;
+          if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj), field vi * tj + vj
 #pragma unroll 4
             for (int vj = 0; vj < np; ++vj) {
-              const float4 t0 = k1d_ld2(tile_s + (vb * np + vj) * PTS + p, r0ok);
-              const float4 t1 = k1d_ld2(tile_s + ((vb + 8) * np + vj) * PTS + p, r1);
-              k1d_all_mac<NB>(acc, av + vj * PTS, t0, t1);
+              cplx<T> t[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) t[h] = k1d_ld(tile_s + ((vb + 4 * h) * np + vj) * PTS + p, vb + 4 * h < nself);
+              k1d_all_mac<NB>(acc, av + vj * PTS, t);
             }
-          } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v)), field vi * tj + vb
-            const bool r0ok = vb < nself, r1 = vb + 8 < nself;
+          } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v)), field vi * tj + vj
 #pragma unroll 4
             for (int vi = 0; vi < np; ++vi) {
-              const float4 t0 = k1d_conj2(k1d_ld2(tile_s + (vi * nself + vb) * PTS + p, r0ok));
-              const float4 t1 = k1d_conj2(k1d_ld2(tile_s + (vi * nself + vb + 8) * PTS + p, r1));
-              k1d_all_mac<NB>(acc, av + vi * PTS, t0, t1);
+              cplx<T> t[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h)
+                t[h] = cconj(k1d_ld(tile_s + (vi * nself + vb + 4 * h) * PTS + p, vb + 4 * h < nself));
+              k1d_all_mac<NB>(acc, av + vi * PTS, t);
             }
           }
         }
       } else if (live) {  // diagonal block B at slot B of the buffers (which follow each other)
         const cplx<T>* tile_s = ts + B * K1D_ALL_SLOT;
         const int tb = bsize(B);
-        const bool r0ok = vb < tb, r1 = vb + 8 < tb;
         const cplx<T>* av = as + B * 16 * PTS + p;
 #pragma unroll 4
         for (int vj = 0; vj < tb; ++vj) {
-          const float4 t0 = k1d_ld2(tile_s + (vb * tb + vj) * PTS + p, r0ok);
-          const float4 t1 = k1d_ld2(tile_s + ((vb + 8) * tb + vj) * PTS + p, r1);
-          k1d_all_mac<NB>(acc, av + vj * PTS, t0, t1);
+          cplx<T> t[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) t[h] = k1d_ld(tile_s + ((vb + 4 * h) * tb + vj) * PTS + p, vb + 4 * h < tb);
+          k1d_all_mac<NB>(acc, av + vj * PTS, t);
         }
       }
     }
@@ -377,11 +374,11 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
       for (int q = 0; q < NB; ++q)
         if (q < nbc) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int v = v0 + 8 * h;
-            if (v < nocc)  // the only contribution to these points in this launch: one rounding, as a plain add
-              atomicAdd(reinterpret_cast<float4*>(out + ((long long)(b0 + q) * nocc + v) * n3 + r0 + p),
-                        make_float4(s * acc[h][0][q].x, s * acc[h][0][q].y, s * acc[h][1][q].x, s * acc[h][1][q].y));
+          for (int h = 0; h < 4; ++h) {
+            const int v = v0 + 4 * h;
+            if (v < nocc)  // the only contribution to this value in this launch: one rounding, as a plain add
+              atomicAdd(reinterpret_cast<float2*>(out + ((long long)(b0 + q) * nocc + v) * n3 + r0 + p),
+                        make_float2(s * acc[h][q].x, s * acc[h][q].y));
           }
         }
     }

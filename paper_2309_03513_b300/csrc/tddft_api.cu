@@ -1005,7 +1005,7 @@ static tddft_status apply_core(tddft_system* h, int nb, const cplx<T>* A, cplx<T
   const bool vloc = (mask & TDDFT_TERM_D_VLOC) && h->b.vloc;
   // the pair-convolution terms on the exchange grid: same plane-wave result, fewer points
   unsigned xmask = 0;
-  if (h->xsub && h->use_xsub && !h->loc_on && h->d.alpha != 0.0) {
+  if (h->xsub && h->use_xsub && h->xsub->loc_on == h->loc_on && h->d.alpha != 0.0) {
     xmask = mask & (TDDFT_TERM_K1D | TDDFT_TERM_K2D | (h->ace_on ? 0u : TDDFT_TERM_D_EXX));
     if (xmask) STATUS_TRY(apply_core<T>(h->xsub, nb, A, (cplx<T>*)h->x_pw, xmask, st));
     mask &= ~xmask;
@@ -1632,6 +1632,11 @@ static tddft_status localization_impl(tddft_system* h, const double* Uh, double 
   if (!U) {  // back to the given orbitals
     h->loc_on = false;
     STATUS_TRY(load_source_orbitals<T>(h, h->b.phi_src_pw64, st));
+    if (h->xsub) {
+      drop_graphs(h->xsub);
+      h->xsub->loc_on = false;
+      STATUS_TRY(load_source_orbitals<T>(h->xsub, h->xsub->b.phi_src_pw64, st));
+    }
     CUDA_TRY(cudaStreamSynchronize(st));
     if (kept) *kept = nocc * nocc;
     return TDDFT_OK;
@@ -1714,6 +1719,20 @@ static tddft_status localization_impl(tddft_system* h, const double* Uh, double 
     }
   CUDA_TRY(cudaMemcpyAsync(h->loc_keep, h->loc_keep_host.data(), h->loc_keep_host.size(), cudaMemcpyHostToDevice, st));
   STATUS_TRY(build_pair_batches<T>(h, st));
+  if (h->xsub) {
+    // the exchange-grid system (D_EXX, K1d, K2d) works in the same frame with the same kept
+    // pairs (the overlap function of the caller's grid decides them)
+    tddft_system* x = h->xsub;
+    drop_graphs(x);
+    x->loc_on = false;
+    STATUS_TRY(load_source_orbitals<T>(x, phil, st));
+    if (!x->loc_keep) STATUS_TRY(dalloc(x, (void**)&x->loc_keep, (size_t)nocc * nocc));
+    x->loc_keep_host = h->loc_keep_host;
+    CUDA_TRY(cudaMemcpyAsync(x->loc_keep, x->loc_keep_host.data(), x->loc_keep_host.size(), cudaMemcpyHostToDevice, st));
+    STATUS_TRY(build_pair_batches<T>(x, st));
+    x->loc_kept = cnt;
+    x->loc_on = true;
+  }
   CUDA_TRY(cudaStreamSynchronize(st));
   h->loc_kept = cnt;
   if (kept) *kept = cnt;

@@ -155,6 +155,36 @@ def test_truncation_mid_size_fp32(torch):
         assert _rel(got, want).max() < TOL[T.PREC_FP32], tun
 
 
+@pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
+def test_truncation_on_the_exchange_grid(torch, prec):
+    """36^3 at 12 Ha (max |m_i| = 7): the pair-convolution terms run on the 32^3 exchange grid, in the
+    localised frame with the kept pairs decided on the 36^3 grid; against the oracle's truncated
+    operator and against the same handle with every term on 36^3; the frame switches back."""
+    wl = _loc_wl(n=36, a=10.0, ecut=12.0, nocc=16, nb=2, seed=10, sigma=1.0)
+    Ssys = O.system_from_workload(wl)
+    S_o = Ssys.set_localization(wl.loc_U, 0.0)
+    thr = _gap_thresholds(S_o, 1)[0]
+    Ssys.set_localization(wl.loc_U, thr)
+    want = Ssys.apply(wl.X)
+    canon = O.system_from_workload(wl).apply(wl.X)
+    s = T.system_from_workload(wl, precision=prec)
+    assert s.query()["n_exchange"] == 32
+    X = torch.from_numpy(wl.X).to("cuda", s.complex_dtype)
+    for sparse in (0, 1):
+        s.set_tuning(k1d_sparse=sparse, exchange_grid=1)
+        _, kept = s.set_localization(wl.loc_U, thr)
+        assert kept == int(Ssys.loc_keep.sum()) < 256
+        got = s.apply(X).cpu().numpy().astype(np.complex128)
+        assert _rel(got, want).max() < TOL[prec], sparse
+        s.set_tuning(exchange_grid=0)
+        on_n = s.apply(X).cpu().numpy().astype(np.complex128)
+        assert _rel(got, on_n).max() < (1e-12 if prec == T.PREC_FP64 else 2e-6), sparse
+    s.set_tuning(exchange_grid=1)
+    s.set_localization(None)
+    assert _rel(s.apply(X).cpu().numpy().astype(np.complex128), canon).max() < TOL[prec]
+    s.close()
+
+
 def test_pair_list_batches_and_everything_truncated(torch):
     """A pair list longer than one batch (FP64: 192 slots; 24 localised orbitals at
     S_thr = 0 give 300 unique pairs), and a threshold above every S_mn (no K1d at all)."""
