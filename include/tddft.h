@@ -204,7 +204,10 @@ typedef struct tddft_tuning {
                        orbitals on 72^3 in FP32) and fails with TDDFT_ENOMEM when they
                        do not fit, or with TDDFT_ENOTSUP while the localised frame is on
                        (the truncated K1d of that frame recomputes its pairs; the stored
-                       tau serve again once it is switched off). The result equals that
+                       tau serve again once it is switched off). Where the one-pass contraction
+                       of k1d_all applies (FP32, at most 128 orbitals, compact intermediates with
+                       the register-line passes) the tau are stored point-tiled and contracted by
+                       it, whatever k1d_all says. The result equals that
                        of the recomputing path up to rounding. 0 (default): recompute;
                        releases the stored tau. -1 keeps the value in set_tuning */
   int exchange_grid; /* 1 (default): the pair-convolution terms (D_EXX, K1d, K2d) run on the

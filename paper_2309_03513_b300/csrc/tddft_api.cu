@@ -345,6 +345,7 @@ struct tddft_system {
   void* tau_cache = nullptr;
   size_t tau_cache_bytes = 0;
   bool k1d_cache_req = false;  // tuning.k1d_cache as set (the stored tau live where K1d runs)
+  bool tau_cache_tiled = false;  // the stored tau are point-tiled (k_k1d_all reads them)
   // K1d of the recomputing path with the tau of every pair materialised in device scratch per
   // application (tuning.k1d_all), allocated at the first K1d outside stream capture when it fits
   bool k1d_all = true;
@@ -779,9 +780,21 @@ static tddft_status build_tau_fields(tddft_system* h, void* dst, bool tiled, cud
   return check_launch("tau build");
 }
 
+// the point-tiled tau of every pair and their one-pass contraction (k_k1d_all) apply: FP32, at
+// most 128 source orbitals, the register-line passes of compact intermediates, whole point tiles
+template <typename T>
+static bool k1d_all_layout_ok(tddft_system* h) {
+  const ColumnList cl = pair_columns<T>(h);
+  return sizeof(T) == 4 && h->d.nocc_src <= K1D_ALL_ROWS && cl.cols && cl.cmapT &&
+         K1D_CACHE_BLOCK * K1D_CACHE_BLOCK <= h->ibuf_fields && h->n3 % K1D_ALL_PTS == 0;
+}
+
+// stored tau: point-tiled (contracted by k_k1d_all) where that layout applies, else block pair
+// after block pair (contracted by k_k1d_contract)
 template <typename T>
 static tddft_status build_tau_cache(tddft_system* h, cudaStream_t st) {
-  return build_tau_fields<T>(h, h->tau_cache, false, st);
+  h->tau_cache_tiled = k1d_all_layout_ok<T>(h);
+  return build_tau_fields<T>(h, h->tau_cache, h->tau_cache_tiled, st);
 }
 
 // the round-robin schedule of the all-pairs K1d contraction (k_k1d_all) and the
@@ -884,10 +897,7 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
   }
   // the tau of every pair at once: FP32, register-line passes of compact intermediates
   // (point-tiled tau), at most 128 orbitals, recomputing path
-  const ColumnList acl = pair_columns<T>(h);
-  const bool all_ok = sizeof(T) == 4 && h->k1d_all && !h->loc_on && !h->k1d_cache && nocc <= K1D_ALL_ROWS &&
-                      acl.cols && acl.cmapT && K1D_CACHE_BLOCK * K1D_CACHE_BLOCK <= h->ibuf_fields &&
-                      h->n3 % K1D_ALL_PTS == 0;
+  const bool all_ok = h->k1d_all && !h->loc_on && !h->k1d_cache && k1d_all_layout_ok<T>(h);
   if (all_ok) {
     if (!h->tau_all && !h->tau_all_tried) {
       // scratch for the tau of every pair: allocated once, outside stream capture, when it
@@ -915,7 +925,11 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
       if constexpr (sizeof(T) == 4) return k1d_all_launch(h, (const cplx<float>*)h->tau_all, nbc, st);
     }
   }
-  if (h->k1d_cache && h->tau_cache && !h->loc_on) {
+  if (h->k1d_cache && h->tau_cache && !h->loc_on && h->tau_cache_tiled) {
+    // stored point-tiled tau: the one-pass contraction alone
+    if constexpr (sizeof(T) == 4) return k1d_all_launch(h, (const cplx<float>*)h->tau_cache, nbc, st);
+  }
+  if (h->k1d_cache && h->tau_cache && !h->loc_on && !h->tau_cache_tiled) {
     // stored tau: the contraction alone, block pair after block pair in the build order
     const cplx<T>* blk = (const cplx<T>*)h->tau_cache;
     for (int i0 = 0; i0 < nocc; i0 += K1D_CACHE_BLOCK) {

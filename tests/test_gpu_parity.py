@@ -269,11 +269,14 @@ def test_tuning_fields_round_trip(torch):
 
 
 @pytest.mark.parametrize("prec", [T.PREC_FP64, T.PREC_FP32])
-def test_stored_tau_give_the_recomputed_k1d(torch, prec):
+@pytest.mark.parametrize("n,a,ecut", [(24, 10.0, 10.0), (32, 9.0, 12.0)])
+def test_stored_tau_give_the_recomputed_k1d(torch, prec, n, a, ecut):
     """K1d from the stored tau_vv' (tuning.k1d_cache) against the oracle and against the recomputing
     path, on 20 orbitals (a full 16-orbital block and a ragged 4-orbital one), with plain launches and
-    under graph replay; the stored tau take the expected device memory and are released again."""
-    wl = _workload(24, 10.0, 10.0, 20, 3, seed=18)
+    under graph replay; the stored tau take the expected device memory and are released again. On
+    24^3 (pair densities alias) they are stored block pair after block pair; on 32^3 in FP32 they are
+    point-tiled and contracted in one pass."""
+    wl = _workload(n, a, ecut, 20, 3, seed=18)
     want = O.system_from_workload(wl).apply(wl.X)
     want_k1d = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
     s = T.system_from_workload(wl, precision=prec)
@@ -282,7 +285,7 @@ def test_stored_tau_give_the_recomputed_k1d(torch, prec):
     before = s.query()["device_bytes"]
     s.set_tuning(k1d_cache=1)
     fields = 16 * 16 + 16 * 4 + 4 * 4  # block pairs (0,0), (0,16), (16,16)
-    assert s.query()["device_bytes"] - before == fields * 24 ** 3 * (16 if prec == T.PREC_FP64 else 8)
+    assert s.query()["device_bytes"] - before == fields * n ** 3 * (16 if prec == T.PREC_FP64 else 8)
     got = s.apply(Xd).cpu().numpy().astype(np.complex128)
     assert _rel_err(got, want).max() < TOL[prec]
     assert _rel_err(got, plain).max() < (1e-13 if prec == T.PREC_FP64 else 1e-6)
