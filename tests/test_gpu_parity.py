@@ -202,6 +202,21 @@ def test_k1d_all_pairs_and_blocks(torch, nocc):
                 assert _rel_err(got, want).max() < TOL[prec], (n, prec, k1d_all)
 
 
+def test_k1d_all_pairs_is_reproducible(torch):
+    """The K1d term through the one-pass contraction sums in a fixed order (tau written once per
+    point, one atomic add per output value and launch): two applications agree bit for bit, on a
+    batch larger than one group of eight trial vectors."""
+    wl = _workload(32, 9.0, 12.0, 40, 11, seed=44)
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, term_mask=T.TERM_K1D)
+    X = torch.from_numpy(wl.X).to("cuda", torch.complex64)
+    first = s.apply(X).cpu().numpy()
+    second = s.apply(X).cpu().numpy()
+    s.close()
+    assert np.array_equal(first, second)
+    want = O.system_from_workload(wl).apply(wl.X, T.TERM_K1D)
+    assert _rel_err(first.astype(np.complex128), want).max() < 1e-5
+
+
 @pytest.mark.parametrize("sf", [False, True])
 def test_init_from_device_inputs(torch, sf):
     """tddft_init_system with every input in device memory (CUDA tensors: orbitals of both spins,
