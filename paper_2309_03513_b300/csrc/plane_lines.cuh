@@ -156,15 +156,22 @@ __global__ void __launch_bounds__(lines_threads<N, L>())
       for (int n = 0; n < H; ++n) v[n] = R[n * N];
     }
   }
-  line_fwd_any<T, N, L>(v, h);  // column `line` along y
-  static_for<0, H>([&](auto jc) {
-    constexpr int j = decltype(jc)::value;
-    s[line_pos<N, L, j>(h) * PITCH + line] = v[j];
-  });
-  __syncthreads();
+  // pass 0: column `line` along y, then the transpose; pass 1: the row at y position `line`
+  // along x. One copy of the line-transform code serves both (a smaller instruction footprint:
+  // the warps of an SM are at different points of the kernel)
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    line_fwd_any<T, N, L>(v, h);
+    if (pass == 0) {
+      static_for<0, H>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        s[line_pos<N, L, j>(h) * PITCH + line] = v[j];
+      });
+      __syncthreads();
 #pragma unroll
-  for (int n = 0; n < H; ++n) v[n] = s[line * PITCH + n + h * H];
-  line_fwd_any<T, N, L>(v, h);  // row at y position `line` along x
+      for (int n = 0; n < H; ++n) v[n] = s[line * PITCH + n + h * H];
+    }
+  }
   cplx<T>* O = ibuf + (long long)item * N3 + (long long)z * nact;
   static_for<0, H>([&](auto jc) {
     constexpr int j = decltype(jc)::value;
@@ -196,15 +203,21 @@ __global__ void __launch_bounds__(lines_threads<N, L>(), L == 1 ? 6 : 1)
       v[j] = c >= 0 ? I[c] : cplx<T>{T(0), T(0)};
     });
   }
-  line_inv_any<T, N, L>(v, h);  // row at y position `line` along x
+  // pass 0: the row at y position `line` along x, then the transpose; pass 1: column `line`
+  // along y (points y = n + h H). One copy of the line-transform code serves both
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    line_inv_any<T, N, L>(v, h);
+    if (pass == 0) {
 #pragma unroll
-  for (int n = 0; n < H; ++n) s[line * PITCH + n + h * H] = v[n];
-  __syncthreads();
-  static_for<0, H>([&](auto jc) {
-    constexpr int j = decltype(jc)::value;
-    v[j] = s[line_pos<N, L, j>(h) * PITCH + line];
-  });
-  line_inv_any<T, N, L>(v, h);  // column `line` along y: points y = n + h H
+      for (int n = 0; n < H; ++n) s[line * PITCH + n + h * H] = v[n];
+      __syncthreads();
+      static_for<0, H>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        v[j] = s[line_pos<N, L, j>(h) * PITCH + line];
+      });
+    }
+  }
   if constexpr (MODE == INV_ATOMIC) {
     const int tt = item / pm.kdim, k = item - tt * pm.kdim;
     const cplx<T>* P = plane_ptr(pb, pm.p0 + (long long)k * pm.pk + (long long)tt * pm.pt, z, N3, N2) + h * H * N + line;
