@@ -330,45 +330,42 @@ __global__ void __launch_bounds__(K1D_ALL_THREADS, 1)
         break;
       }
       const cplx<T>* buf = ts + stage_buf * NBUF;
-      // this stage's tau tile, partner rows and strides: tau of (row vl, partner index j) at
-      // tile_s[(vl * sr + j * sj) * PTS + p], conjugated (sg = -1) for the rows of J; one loop
-      // serves the rows of I, of J and the diagonal blocks (one copy of the code for all warps)
-      const cplx<T>* tile_s = nullptr;
-      const cplx<T>* av = nullptr;
-      int np = 0, sr = 0, sj = 0;
-      T sg = T(1);
-      const int nself = bsize(B);
       if (r < kt.rounds) {
         const int partner = live ? kt.partner[r][B] : -1;
         if (partner >= 0) {
-          tile_s = buf + kt.slot[r][B] * K1D_ALL_SLOT;
-          av = as + partner * 16 * PTS + p;
-          np = bsize(partner);
+          const cplx<T>* tile_s = buf + kt.slot[r][B] * K1D_ALL_SLOT;
+          const cplx<T>* av = as + partner * 16 * PTS + p;
+          const int np = bsize(partner), nself = bsize(B);
           if (kt.first[r][B]) {  // rows of I: tau_(v, J*16 + vj), field vi * tj + vj
-            sr = np;
-            sj = 1;
+#pragma unroll 4
+            for (int vj = 0; vj < np; ++vj) {
+              cplx<T> t[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) t[h] = k1d_ld(tile_s + ((vb + 4 * h) * np + vj) * PTS + p, vb + 4 * h < nself);
+              k1d_all_mac<NB>(acc, av + vj * PTS, t);
+            }
           } else {  // rows of J: tau_(v, I*16 + vi) = conj(tau_(I*16 + vi, v)), field vi * tj + vj
-            sr = 1;
-            sj = nself;
-            sg = T(-1);
+#pragma unroll 4
+            for (int vi = 0; vi < np; ++vi) {
+              cplx<T> t[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h)
+                t[h] = cconj(k1d_ld(tile_s + (vi * nself + vb + 4 * h) * PTS + p, vb + 4 * h < nself));
+              k1d_all_mac<NB>(acc, av + vi * PTS, t);
+            }
           }
         }
       } else if (live) {  // diagonal block B at slot B of the buffers (which follow each other)
-        tile_s = ts + B * K1D_ALL_SLOT;
-        av = as + B * 16 * PTS + p;
-        np = nself;
-        sr = nself;
-        sj = 1;
-      }
+        const cplx<T>* tile_s = ts + B * K1D_ALL_SLOT;
+        const int tb = bsize(B);
+        const cplx<T>* av = as + B * 16 * PTS + p;
 #pragma unroll 4
-      for (int j = 0; j < np; ++j) {
-        cplx<T> t[4];
+        for (int vj = 0; vj < tb; ++vj) {
+          cplx<T> t[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          t[h] = k1d_ld(tile_s + ((vb + 4 * h) * sr + j * sj) * PTS + p, vb + 4 * h < nself);
-          t[h].y *= sg;
+          for (int h = 0; h < 4; ++h) t[h] = k1d_ld(tile_s + ((vb + 4 * h) * tb + vj) * PTS + p, vb + 4 * h < tb);
+          k1d_all_mac<NB>(acc, av + vj * PTS, t);
         }
-        k1d_all_mac<NB>(acc, av + j * PTS, t);
       }
     }
     if (!ok) break;
