@@ -38,6 +38,45 @@ __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
 }
 template <typename T>
 __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
+
+// Sums and differences of two plain complex values (neither one a rotated view such as
+// mul_di(a), whose swapped halves would first have to be moved into place). In FP32 the
+// two halves go through one packed instruction (add/sub.rn.f32x2, sm_100 and later):
+// the same two IEEE round-to-nearest operations, half the instructions to issue.
+__device__ __forceinline__ unsigned long long pack2(cplx<float> a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ cplx<float> unpack2(unsigned long long r) {
+  cplx<float> a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+// PK = false keeps both halves as separate scalar instructions (for kernels whose register
+// budget does not allow the aligned register pairs that packed operands need)
+template <bool PK = true, typename T>
+__device__ __forceinline__ cplx<T> padd(cplx<T> a, cplx<T> b) {
+  if constexpr (PK && sizeof(T) == 4) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(d);
+  } else {
+    return cadd(a, b);
+  }
+}
+template <bool PK = true, typename T>
+__device__ __forceinline__ cplx<T> psub(cplx<T> a, cplx<T> b) {
+  if constexpr (PK && sizeof(T) == 4) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(d);
+  } else {
+    return csub(a, b);
+  }
+}
+
+
 template <typename T>
 __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.x, -a.y}; }
 // multiply by +i / -i
@@ -76,46 +115,46 @@ struct TwPtr {
 // Radix codelets: v[k] <- sum_n v[n] exp(DIR 2 pi i n k / R), natural order.
 // Mathematical constants: sqrt(3)/2, cos/sin(2 pi/5), cos/sin(4 pi/5), 1/sqrt(2).
 // ---------------------------------------------------------------------------
-template <int DIR, typename T>
+template <int DIR, bool PK = true, typename T>
 __device__ __forceinline__ void dft2(cplx<T>* v) {
   cplx<T> a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
+  v[0] = padd<PK>(a, b);
+  v[1] = psub<PK>(a, b);
 }
 
-template <int DIR, typename T>
+template <int DIR, bool PK = true, typename T>
 __device__ __forceinline__ void dft3(cplx<T>* v) {
   const T c = T(-0.5);
   const T s = T(0.86602540378443864676372317075293618);
-  cplx<T> t1 = cadd(v[1], v[2]);
+  cplx<T> t1 = padd<PK>(v[1], v[2]);
   cplx<T> t2 = cadd(v[0], cscale(t1, c));
-  cplx<T> t3 = cscale(csub(v[1], v[2]), s);
-  v[0] = cadd(v[0], t1);
+  cplx<T> t3 = cscale(psub<PK>(v[1], v[2]), s);
+  v[0] = padd<PK>(v[0], t1);
   cplx<T> it3 = mul_di<DIR>(t3);
   v[1] = cadd(t2, it3);
   v[2] = csub(t2, it3);
 }
 
-template <int DIR, typename T>
+template <int DIR, bool PK = true, typename T>
 __device__ __forceinline__ void dft4(cplx<T>* v) {
-  cplx<T> t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  cplx<T> t2 = cadd(v[1], v[3]), t3 = mul_di<DIR>(csub(v[1], v[3]));
-  v[0] = cadd(t0, t2);
-  v[2] = csub(t0, t2);
+  cplx<T> t0 = padd<PK>(v[0], v[2]), t1 = psub<PK>(v[0], v[2]);
+  cplx<T> t2 = padd<PK>(v[1], v[3]), t3 = mul_di<DIR>(psub<PK>(v[1], v[3]));
+  v[0] = padd<PK>(t0, t2);
+  v[2] = psub<PK>(t0, t2);
   v[1] = cadd(t1, t3);
   v[3] = csub(t1, t3);
 }
 
-template <int DIR, typename T>
+template <int DIR, bool PK = true, typename T>
 __device__ __forceinline__ void dft5(cplx<T>* v) {
   const T c1 = T(0.30901699437494742410229341718281906);
   const T c2 = T(-0.80901699437494742410229341718281906);
   const T s1 = T(0.95105651629515357211643933337938214);
   const T s2 = T(0.58778525229247312916870595463907277);
-  cplx<T> a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
-  cplx<T> a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+  cplx<T> a1 = padd<PK>(v[1], v[4]), b1 = psub<PK>(v[1], v[4]);
+  cplx<T> a2 = padd<PK>(v[2], v[3]), b2 = psub<PK>(v[2], v[3]);
   cplx<T> x0 = v[0];
-  v[0] = cadd(x0, cadd(a1, a2));
+  v[0] = padd<PK>(x0, padd<PK>(a1, a2));
   cplx<T> r1 = cadd(x0, cadd(cscale(a1, c1), cscale(a2, c2)));
   cplx<T> r2 = cadd(x0, cadd(cscale(a1, c2), cscale(a2, c1)));
   cplx<T> i1 = mul_di<DIR>(cadd(cscale(b1, s1), cscale(b2, s2)));
@@ -141,18 +180,21 @@ __device__ __forceinline__ cplx<T> rot(cplx<T> a, const TW& tw, int twstride) {
   } else if constexpr ((8 * e) % R == 0) {
     constexpr int o = (8 * e) / R;  // odd number of eighth turns: 1, 3, 5, 7
     const T h = T(0.70710678118654752440084436210484904);
-    // exp(DIR i pi/4) = h (1 + DIR i)
-    cplx<T> w1 = cscale(cadd(a, mul_di<DIR>(a)), h);
-    if constexpr (o == 1) return w1;
-    else if constexpr (o == 3) return mul_di<DIR>(w1);
-    else if constexpr (o == 5) return {-w1.x, -w1.y};
-    else return mul_di<-DIR>(w1);
+    // exp(DIR i pi o/4) a from s = a.x + a.y and d = a.x - a.y, each half written in its
+    // final place and sign (no swapped view left for a packed consumer to move into place);
+    // the inverse turn by o eighths is the forward turn by 8 - o
+    constexpr int of = (DIR == FWD) ? o : 8 - o;
+    const T sh = (a.x + a.y) * h, dh = (a.x - a.y) * h;
+    if constexpr (of == 1) return {sh, -dh};
+    else if constexpr (of == 3) return {-dh, -sh};
+    else if constexpr (of == 5) return {-sh, dh};
+    else return {dh, sh};
   } else {
     return twmul<DIR>(a, tw(e * twstride));
   }
 }
 
-template <int R, int DIR, typename T, typename TW>
+template <int R, int DIR, bool PK = true, typename T, typename TW>
 __device__ __forceinline__ void dft(cplx<T>* v, const TW& tw, int twstride);
 
 template <int P, int Q, int DIR, typename T, int Q0, int K1, typename TW>
@@ -164,55 +206,55 @@ __device__ __forceinline__ void comp_rot(cplx<T>* t, cplx<T>* u, const TW& tw, i
 }
 
 // Composite codelet R = P * Q: input index n = q + Q p, output k = k1 + P k2.
-template <int P, int Q, int DIR, typename T, int Q0 = 0, typename TW>
+template <int P, int Q, int DIR, bool PK, typename T, int Q0 = 0, typename TW>
 __device__ __forceinline__ void comp_first(cplx<T>* v, cplx<T>* u, const TW& tw, int twstride) {
   if constexpr (Q0 < Q) {
     cplx<T> t[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) t[p] = v[Q0 + Q * p];
-    dft<P, DIR>(t, tw, twstride * Q);
+    dft<P, DIR, PK>(t, tw, twstride * Q);
     comp_rot<P, Q, DIR, T, Q0, 0>(t, u, tw, twstride);
-    comp_first<P, Q, DIR, T, Q0 + 1>(v, u, tw, twstride);
+    comp_first<P, Q, DIR, PK, T, Q0 + 1>(v, u, tw, twstride);
   }
 }
 
-template <int P, int Q, int DIR, typename T, typename TW>
+template <int P, int Q, int DIR, bool PK, typename T, typename TW>
 __device__ __forceinline__ void dft_comp(cplx<T>* v, const TW& tw, int twstride) {
   cplx<T> u[P * Q];
-  comp_first<P, Q, DIR, T, 0>(v, u, tw, twstride);
+  comp_first<P, Q, DIR, PK, T, 0>(v, u, tw, twstride);
 #pragma unroll
   for (int k1 = 0; k1 < P; ++k1) {
     cplx<T> t[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) t[q] = u[q * P + k1];
-    dft<Q, DIR>(t, tw, twstride * P);
+    dft<Q, DIR, PK>(t, tw, twstride * P);
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = t[k2];
   }
 }
 
 // twstride: index step in the length-N table for W_R (N / R).
-template <int R, int DIR, typename T, typename TW>
+template <int R, int DIR, bool PK, typename T, typename TW>
 __device__ __forceinline__ void dft(cplx<T>* v, const TW& tw, int twstride) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
-    dft2<DIR>(v);
+    dft2<DIR, PK>(v);
   } else if constexpr (R == 3) {
-    dft3<DIR>(v);
+    dft3<DIR, PK>(v);
   } else if constexpr (R == 4) {
-    dft4<DIR>(v);
+    dft4<DIR, PK>(v);
   } else if constexpr (R == 5) {
-    dft5<DIR>(v);
+    dft5<DIR, PK>(v);
   } else if constexpr (R == 6) {
-    dft_comp<2, 3, DIR>(v, tw, twstride);
+    dft_comp<2, 3, DIR, PK>(v, tw, twstride);
   } else if constexpr (R == 8) {
-    dft_comp<2, 4, DIR>(v, tw, twstride);
+    dft_comp<2, 4, DIR, PK>(v, tw, twstride);
   } else if constexpr (R == 9) {
-    dft_comp<3, 3, DIR>(v, tw, twstride);
+    dft_comp<3, 3, DIR, PK>(v, tw, twstride);
   } else if constexpr (R == 12) {
-    dft_comp<4, 3, DIR>(v, tw, twstride);
+    dft_comp<4, 3, DIR, PK>(v, tw, twstride);
   } else if constexpr (R == 16) {
-    dft_comp<4, 4, DIR>(v, tw, twstride);
+    dft_comp<4, 4, DIR, PK>(v, tw, twstride);
   } else {
     static_assert(R == 2, "unsupported radix");
   }
@@ -420,7 +462,7 @@ struct TwConst {
 
 // Whole length-N transform of v[0..N) held in registers: forward = DIF
 // (natural in, digit-reversed out), inverse = DIT (digit-reversed in, natural out).
-template <typename T, int N, int DIR, typename TW, int S = 0>
+template <typename T, int N, int DIR, typename TW, int S = 0, bool PK = true>
 __device__ __forceinline__ void fft_reg(cplx<T>* v, const TW& tw) {
   constexpr int NS = Plan<N>::S;
   if constexpr (S < NS) {
@@ -438,7 +480,7 @@ __device__ __forceinline__ void fft_reg(cplx<T>* v, const TW& tw) {
         if constexpr (DIR == FWD) {
 #pragma unroll
           for (int n2 = 0; n2 < R; ++n2) x[n2] = v[base + M * n2];
-          dft<R, FWD>(x, tw, N / R);
+          dft<R, FWD, PK>(x, tw, N / R);
 #pragma unroll
           for (int k2 = 1; k2 < R; ++k2)
             if (n1) x[k2] = twmul<FWD>(x[k2], tw(n1 * k2 * TWS));
@@ -450,13 +492,13 @@ __device__ __forceinline__ void fft_reg(cplx<T>* v, const TW& tw) {
             x[k2] = v[base + M * k2];
             if (k2 && n1) x[k2] = twmul<INV>(x[k2], tw(n1 * k2 * TWS));
           }
-          dft<R, INV>(x, tw, N / R);
+          dft<R, INV, PK>(x, tw, N / R);
 #pragma unroll
           for (int n2 = 0; n2 < R; ++n2) v[base + M * n2] = x[n2];
         }
       }
     }
-    fft_reg<T, N, DIR, TW, S + 1>(v, tw);
+    fft_reg<T, N, DIR, TW, S + 1, PK>(v, tw);
   }
 }
 

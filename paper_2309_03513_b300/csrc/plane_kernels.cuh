@@ -256,12 +256,14 @@ __global__ void __launch_bounds__(ZREG_THREADS)
     const cplx<T> p = shfl_xor_c(v[n], 1);
     v[n] = h ? cmul(csub(p, v[n]), twn(n)) : cadd(v[n], p);
   }
+  // scalar halves (no packed pairs): packed operands need aligned register pairs, which
+  // would cost this memory-bound kernel a third of its resident warps
   TwConst<T, H> twh;
-  fft_reg<T, H, FWD>(v, twh);
+  fft_reg<T, H, FWD, TwConst<T, H>, 0, false>(v, twh);
   const T* K = opaque_ptr(kern2 + c + (long long)h * H * nact);
 #pragma unroll
   for (int j = 0; j < H; ++j, K += nact) v[j] = cscale(v[j], *K * kscale);
-  fft_reg<T, H, INV>(v, twh);
+  fft_reg<T, H, INV, TwConst<T, H>, 0, false>(v, twh);
 #pragma unroll
   for (int n = 0; n < H; ++n) {  // lane 0: A_n + conj(W_N^n) B_n; lane 1: A_n - conj(W_N^n) B_n
     const cplx<T> p = shfl_xor_c(v[n], 1);
