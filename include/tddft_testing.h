@@ -2,7 +2,8 @@
  * Test entry points to the library's small dense FP64 routines. They are the routines that
  * the Davidson step uses for its Rayleigh-Ritz problem (Hermitian eigenproblem, solved on
  * the device) and that the ACE build uses for -M = L L^dagger and L^{-1} (Sec. 3.1); they
- * are not part of the operator's interface.
+ * are not part of the operator's interface. Also the measured arithmetic peaks and the
+ * host-side fault injector.
  *
  * Matrices are row-major n x n arrays of interleaved complex128 (2n^2 doubles), owned by
  * the caller, in host memory. Only tddft_testing_herm_eig_device touches the GPU.
@@ -43,6 +44,30 @@ tddft_status tddft_testing_cholesky(int n, double* A);
 
 /* X = L^{-1} for a lower-triangular L with non-zero diagonal. */
 tddft_status tddft_testing_lower_inverse(int n, const double* L, double* X);
+
+/* Host-side fault injection, for testing how callers handle the library's failure statuses
+ * (failure detection; the paper has no counterpart). Nothing fails on
+ * the GPU: the library reports an allocation or a bounded device wait as failed.
+ *   TDDFT_FAULT_NONE: disarm every fault.
+ *   TDDFT_FAULT_ALLOC: the library's device allocation number `after` from now (0 = the next one;
+ *     every cudaMalloc the library makes counts) fails as cudaMalloc does when memory runs out.
+ *     The entry point that made it returns TDDFT_ENOMEM after releasing what it had allocated
+ *     ("(injected fault)" in tddft_last_error), or, where the allocation is optional (the
+ *     all-pairs K1d scratch, the packed projector operands), takes its fallback path.
+ *   TDDFT_FAULT_DEVICE_WAIT: the next check of a handle's device-wait flag (tddft_query,
+ *     tddft_apply_liouville_host, the Davidson step, the Z-vector solve) reports that a bounded
+ *     device wait ran out: TDDFT_ETIMEOUT ("results of the call are invalid"); `after` is not used.
+ * Each armed fault fires once. The environment variable TDDFT_FAULT ("alloc", "alloc:N" or
+ * "wait"), read when the library is loaded, arms the same faults. Process-wide and thread-safe;
+ * host only. EINVAL for an unknown kind or after < 0. */
+#define TDDFT_FAULT_NONE 0
+#define TDDFT_FAULT_ALLOC 1
+#define TDDFT_FAULT_DEVICE_WAIT 2
+tddft_status tddft_testing_inject_fault(int kind, int after);
+
+/* The armed faults: *alloc_after = allocations still let through before the injected failure
+ * (-1: none armed), *wait = 1 while a device-wait fault is armed. Host only. */
+tddft_status tddft_testing_fault_state(int* alloc_after, int* wait);
 
 #ifdef __cplusplus
 }

@@ -4,10 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -28,6 +32,77 @@ static thread_local std::string g_last_error;
 static tddft_status fail(tddft_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// host-side fault injection (tddft_testing_inject_fault; TDDFT_FAULT when the library is
+// loaded): the library reports an allocation or a device wait as failed without any
+// failure on the GPU, so callers' error handling can be tested
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_fault_mu;
+std::atomic<bool> g_fault_armed{false};
+int g_fault_alloc = -1;     // allocations to let through before the injected failure; -1: none
+bool g_fault_wait = false;  // the next check of a device-wait flag reports a wait that ran out
+thread_local bool t_alloc_injected = false;
+
+void fault_rearm_locked() { g_fault_armed.store(g_fault_alloc >= 0 || g_fault_wait, std::memory_order_release); }
+
+// TDDFT_FAULT = "alloc" (the first allocation), "alloc:N" (allocation N, counted from 0) or
+// "wait"; anything else is ignored
+struct FaultFromEnvironment {
+  FaultFromEnvironment() {
+    const char* v = std::getenv("TDDFT_FAULT");
+    if (!v) return;
+    const std::string e(v);
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (e == "wait") {
+      g_fault_wait = true;
+    } else if (e == "alloc") {
+      g_fault_alloc = 0;
+    } else if (e.rfind("alloc:", 0) == 0 && e.size() > 6) {
+      char* end = nullptr;
+      const long n = std::strtol(e.c_str() + 6, &end, 10);
+      if (end && *end == 0 && n >= 0 && n < INT_MAX) g_fault_alloc = (int)n;
+    }
+    fault_rearm_locked();
+  }
+} g_fault_from_environment;
+
+bool fault_take_alloc() {
+  if (!g_fault_armed.load(std::memory_order_acquire)) return false;
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  if (g_fault_alloc < 0) return false;
+  const bool now = g_fault_alloc == 0;
+  --g_fault_alloc;  // -1 once it has fired
+  fault_rearm_locked();
+  return now;
+}
+
+bool fault_take_wait() {
+  if (!g_fault_armed.load(std::memory_order_acquire)) return false;
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  const bool now = g_fault_wait;
+  g_fault_wait = false;
+  fault_rearm_locked();
+  return now;
+}
+}  // namespace
+
+// cudaMalloc of the library's device memory, through the fault injector
+static cudaError_t lib_malloc(void** p, size_t bytes) {
+  t_alloc_injected = false;
+  if (fault_take_alloc()) {
+    *p = nullptr;
+    t_alloc_injected = true;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+static std::string alloc_error(size_t bytes, cudaError_t e) {
+  return "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e) +
+         (t_alloc_injected ? " (injected fault)" : "");
 }
 
 #define CUDA_TRY(expr)                                                                                 \
@@ -418,10 +493,11 @@ static const T* pair_kernel(tddft_system* h, const T* kern, const ColumnList& cl
 static tddft_status dalloc(tddft_system* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return TDDFT_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = lib_malloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    *p = nullptr;
+    return fail(TDDFT_ENOMEM, alloc_error(bytes, e));
   }
   h->allocations.push_back(*p);
   h->bytes += bytes;
@@ -433,10 +509,11 @@ namespace {
 struct TempAllocs {
   std::vector<void*> p;
   tddft_status get(void** out, size_t bytes) {
-    cudaError_t e = cudaMalloc(out, bytes);
+    cudaError_t e = lib_malloc(out, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+      *out = nullptr;
+      return fail(TDDFT_ENOMEM, alloc_error(bytes, e));
     }
     p.push_back(*out);
     return TDDFT_OK;
@@ -533,7 +610,7 @@ static bool tc_pack_ready(tddft_system* h, size_t words, cudaStream_t st) {
     h->tc_pack = nullptr;
     h->tc_pack_words = 0;
   }
-  if (cudaMalloc((void**)&h->tc_pack, words * 4) != cudaSuccess) {
+  if (lib_malloc((void**)&h->tc_pack, words * 4) != cudaSuccess) {
     cudaGetLastError();
     h->tc_pack = nullptr;
     return false;
@@ -910,7 +987,7 @@ static tddft_status k1d_term(tddft_system* h, int nbc, cudaStream_t st) {
         size_t freeb = 0, totalb = 0;
         CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
         if (bytes <= freeb / 4) {
-          if (cudaMalloc(&h->tau_all, bytes) == cudaSuccess) {
+          if (lib_malloc(&h->tau_all, bytes) == cudaSuccess) {
             h->tau_all_bytes = bytes;
             h->bytes += bytes;
           } else {
@@ -1955,6 +2032,10 @@ static tddft_status build_multi_graph(int nsys, const tddft_handle* hs, const in
 // Reads (and clears) the device error flag; synchronises the stream.
 static tddft_status check_device_flag(tddft_system* h, cudaStream_t st) {
   if (!h->b.dev_err) return TDDFT_OK;
+  if (fault_take_wait()) {
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return fail(TDDFT_ETIMEOUT, "a bounded device wait ran out (injected fault); results of the call are invalid");
+  }
   int flag = 0;
   CUDA_TRY(cudaMemcpyAsync(&flag, h->b.dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -2166,12 +2247,11 @@ static tddft_status set_tau_cache(tddft_system* h, bool on) {
   // the source orbitals must be the given ones (the localised frame replaces them while it is on)
   if (h->loc_on) return fail(TDDFT_ENOTSUP, "stored tau are built in the given frame: switch localisation off first");
   const size_t bytes = tau_cache_fields(h->d.nocc_src) * (size_t)h->n3 * h->esz();
-  cudaError_t e = cudaMalloc(&h->tau_cache, bytes);
+  cudaError_t e = lib_malloc(&h->tau_cache, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     h->tau_cache = nullptr;
-    return fail(TDDFT_ENOMEM, "stored tau need " + std::to_string(bytes) + " bytes of device memory: " +
-                                  cudaGetErrorString(e));
+    return fail(TDDFT_ENOMEM, "stored tau: " + alloc_error(bytes, e));
   }
   h->tau_cache_bytes = bytes;
   h->bytes += bytes;
@@ -3022,11 +3102,11 @@ struct tddft_davidson {
 };
 
 static tddft_status dav_alloc(tddft_davidson* d, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = lib_malloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(TDDFT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return fail(TDDFT_ENOMEM, alloc_error(bytes, e));
   }
   d->allocs.push_back(*p);
   return TDDFT_OK;
@@ -3184,6 +3264,8 @@ tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converge
   std::vector<double> info(2 * nr + 2);
   CUDA_TRY(cudaMemcpyAsync(info.data(), d->info, info.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (fault_take_wait())
+    return fail(TDDFT_ETIMEOUT, "a bounded device wait ran out (injected fault); results of the call are invalid");
   if (info[2 * nr + 1] != 0.0) {
     CUDA_TRY(cudaMemsetAsync(d->h->b.dev_err, 0, sizeof(int), st));
     return fail(TDDFT_ETIMEOUT, "a bounded device wait (tensor-core projector) ran out; results of the call are invalid");
@@ -3421,6 +3503,35 @@ tddft_status tddft_testing_lower_inverse(int n, const double* L, double* X) {
     if (l[(size_t)i * n + i] == 0.0) return fail(TDDFT_EINVAL, "zero on the diagonal");
   const std::vector<std::complex<double>> inv = lower_inverse(n, std::vector<std::complex<double>>(l, l + (size_t)n * n));
   std::copy(inv.begin(), inv.end(), reinterpret_cast<std::complex<double>*>(X));
+  return TDDFT_OK;
+}
+
+tddft_status tddft_testing_inject_fault(int kind, int after) {
+  if (after < 0) return fail(TDDFT_EINVAL, "after must be >= 0");
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  switch (kind) {
+    case TDDFT_FAULT_NONE:
+      g_fault_alloc = -1;
+      g_fault_wait = false;
+      break;
+    case TDDFT_FAULT_ALLOC:
+      g_fault_alloc = after;
+      break;
+    case TDDFT_FAULT_DEVICE_WAIT:
+      g_fault_wait = true;
+      break;
+    default:
+      return fail(TDDFT_EINVAL, "unknown fault kind " + std::to_string(kind));
+  }
+  fault_rearm_locked();
+  return TDDFT_OK;
+}
+
+tddft_status tddft_testing_fault_state(int* alloc_after, int* wait) {
+  if (!alloc_after || !wait) return fail(TDDFT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  *alloc_after = g_fault_alloc;
+  *wait = g_fault_wait ? 1 : 0;
   return TDDFT_OK;
 }
 

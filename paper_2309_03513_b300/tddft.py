@@ -46,8 +46,11 @@ EXPORTS = [
     "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
     # include/tddft_testing.h
     "tddft_testing_herm_eig", "tddft_testing_cholesky", "tddft_testing_lower_inverse",
-    "tddft_testing_herm_eig_device", "tddft_testing_peak",
+    "tddft_testing_herm_eig_device", "tddft_testing_peak", "tddft_testing_inject_fault", "tddft_testing_fault_state",
 ]
+FAULT_NONE = 0
+FAULT_ALLOC = 1
+FAULT_DEVICE_WAIT = 2
 PROFILE_CLASSES = ("xy_fwd_pair_product", "z_kernel_multiply", "xy_inv_remultiply_accumulate")
 
 
@@ -135,6 +138,8 @@ def load() -> ctypes.CDLL:
         "tddft_testing_lower_inverse": ([ci, vp, vp], st),
         "tddft_testing_herm_eig_device": ([ci, ci, vp, vp, vp], st),
         "tddft_testing_peak": ([ci, vp, vp], st),
+        "tddft_testing_inject_fault": ([ci, ci], st),
+        "tddft_testing_fault_state": ([ctypes.POINTER(ci), ctypes.POINTER(ci)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +206,21 @@ def measure_peak(which: int) -> dict:
     ms = ctypes.c_double()
     _check(load().tddft_testing_peak(int(which), ctypes.byref(tf), ctypes.byref(ms)), "tddft_testing_peak")
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def inject_fault(kind: int, after: int = 0):
+    """Arm a host-side fault (tddft_testing_inject_fault): FAULT_ALLOC makes the library's
+    device allocation number `after` from now fail (ENOMEM), FAULT_DEVICE_WAIT makes the next
+    device-wait check report a wait that ran out (ETIMEOUT), FAULT_NONE disarms."""
+    _check(load().tddft_testing_inject_fault(int(kind), int(after)), "tddft_testing_inject_fault")
+
+
+def fault_state() -> dict:
+    """The armed faults: {"alloc_after": allocations let through before the failure (-1: none),
+    "wait": True while a device-wait fault is armed}."""
+    n, w = ctypes.c_int(), ctypes.c_int()
+    _check(load().tddft_testing_fault_state(ctypes.byref(n), ctypes.byref(w)), "tddft_testing_fault_state")
+    return {"alloc_after": n.value, "wait": bool(w.value)}
 
 
 def profile_enable(on: bool = True):
