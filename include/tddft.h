@@ -340,6 +340,25 @@ tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, v
 tddft_status tddft_set_localization(tddft_handle h, const double* U, double s_thr, double* S, int* kept_pairs,
                                     void* stream);
 
+/* Maximally localised orbitals at the Gamma point: the unitary U of the localised frame
+ * that tddft_set_localization takes (Sec. 3.2: the pair truncation of Eq. 31 works on
+ * maximally localised Wannier functions). Host only, FP64; no handle and no GPU needed.
+ * phi_pw: HOST complex128 [nocc][npw], the orbitals on the sphere of (n, a, ecut) in the
+ * library's order (tddft_sphere_miller), orthonormal. Minimises the spread of a cubic cell
+ * Omega = (a/2pi)^2 sum_alpha sum_n (1 - |Z^alpha_nn|^2), Z^alpha_mn = <phi~_m| exp(i 2 pi r_alpha/a)
+ * |phi~_n> (evaluated exactly on the plane-wave basis), over unitary rotations: complex
+ * Jacobi sweeps over all pairs (m, n), each rotation the closed-form optimum of the joint
+ * diagonalisation of the six Hermitian parts of Z^x, Z^y, Z^z (Cardoso and Souloumiac 1996;
+ * used for Wannier functions by Gygi, Fattebert and Schwegler 2003), until the largest
+ * rotation of a sweep is below tol or max_sweeps sweeps have run.
+ * U: HOST complex128 [nocc][nocc] output with phi_v = sum_n U_vn phi~_n (the convention of
+ * tddft_set_localization). spread: optional HOST [2], Omega before and after (bohr^2);
+ * sweeps: optional HOST count of sweeps run. EINVAL for bad arguments; ENOTCONV when
+ * max_sweeps ran out first (U then holds the last iterate, still unitary). The result is a
+ * local maximum of sum |Z_nn|^2 reached from the given orbitals. */
+tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps, double tol,
+                            double* U, double* spread, int* sweeps);
+
 /* Adaptively compressed exchange (ACE, Sec. 3.1, Eqs. 29-30) for the exchange
  * term inside D: V_X^ACE = -sum_k |xi_k><xi_k| with xi = W L^{-dagger},
  * W = V_X Psi (exact pair convolutions), -Psi^dagger W = L L^dagger (FP64

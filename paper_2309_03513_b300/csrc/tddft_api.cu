@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -2085,6 +2086,181 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller) {
     miller[3 * i + 2] = s[i].z;
   }
   return TDDFT_OK;
+}
+
+// Maximally localised orbitals at the Gamma point (host, FP64): the localised frame of the pair
+// truncation of Sec. 3.2 (Eq. 31). Spread functional of a cubic cell (Resta; Silvestrelli):
+// Omega = (a/2pi)^2 sum_alpha sum_n (1 - |Z^alpha_nn|^2), Z^alpha_mn = <phi_m| exp(i 2 pi r_alpha / a) |phi_n>,
+// minimised over unitary rotations by maximising sum_alpha sum_n |Z^alpha_nn|^2, i.e. by the joint
+// approximate diagonalisation of the six Hermitian matrices (Z + Z^H)/2, (Z - Z^H)/2i with complex
+// Jacobi rotations in closed form (Cardoso and Souloumiac, SIAM J. Matrix Anal. Appl. 17, 161 (1996);
+// for Wannier functions: Gygi, Fattebert and Schwegler, Comput. Phys. Commun. 155, 1 (2003)).
+namespace {
+using cd = std::complex<double>;
+
+// eigenvector of the largest eigenvalue of a real symmetric 3 x 3 matrix (cyclic Jacobi)
+void top_eigvec3(double A[3][3], double v[3]) {
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double th = 0.5 * std::atan2(2.0 * A[p][q], A[q][q] - A[p][p]);
+        const double c = std::cos(th), s = std::sin(th);
+        for (int k = 0; k < 3; ++k) {  // A <- J^T A J, J the rotation in the (p, q) plane
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  int best = 0;
+  for (int k = 1; k < 3; ++k)
+    if (A[k][k] > A[best][best]) best = k;
+  for (int k = 0; k < 3; ++k) v[k] = V[k][best];
+}
+
+// Z^alpha (alpha = x, y, z) of nocc plane-wave rows c [nocc][npw] on the sphere sph:
+// Z_mn = sum_G conj(c_m(G)) c_n(G - b_alpha), the coefficients of exp(i b_alpha . r) phi_n being
+// c_n(G - b_alpha); exact on the basis (both G and G - b_alpha on the sphere)
+void position_matrices(int n, const std::vector<Miller>& sph, int nocc, const cd* c, std::vector<cd> Z[3]) {
+  const int npw = (int)sph.size(), h = n / 2;
+  std::vector<int> cube((size_t)n * n * n, -1);
+  auto at = [n, h](int x, int y, int z) { return ((size_t)(z + h) * n + (y + h)) * n + (x + h); };
+  for (int g = 0; g < npw; ++g) cube[at(sph[g].x, sph[g].y, sph[g].z)] = g;
+  const int nthr = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  for (int al = 0; al < 3; ++al) {
+    std::vector<int> sh(npw);
+    for (int g = 0; g < npw; ++g) {
+      int x = sph[g].x - (al == 0), y = sph[g].y - (al == 1), z = sph[g].z - (al == 2);
+      sh[g] = (x < -h || y < -h || z < -h) ? -1 : cube[at(x, y, z)];
+    }
+    std::vector<cd> cs((size_t)nocc * npw);  // shifted rows
+    for (int v = 0; v < nocc; ++v)
+      for (int g = 0; g < npw; ++g) cs[(size_t)v * npw + g] = sh[g] >= 0 ? c[(size_t)v * npw + sh[g]] : cd(0.0, 0.0);
+    Z[al].assign((size_t)nocc * nocc, cd(0.0, 0.0));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthr; ++t)
+      pool.emplace_back([&, t] {
+        for (int m = t; m < nocc; m += nthr)
+          for (int k = 0; k < nocc; ++k) {
+            double re = 0.0, im = 0.0;
+            const cd* a = c + (size_t)m * npw;
+            const cd* b = cs.data() + (size_t)k * npw;
+            for (int g = 0; g < npw; ++g) {  // conj(a) b
+              re += a[g].real() * b[g].real() + a[g].imag() * b[g].imag();
+              im += a[g].real() * b[g].imag() - a[g].imag() * b[g].real();
+            }
+            Z[al][(size_t)m * nocc + k] = cd(re, im);
+          }
+      });
+    for (auto& th : pool) th.join();
+  }
+}
+
+double spread_of(const std::vector<cd> M[6], int nocc, double a) {
+  double s = 0.0;
+  for (int al = 0; al < 3; ++al)
+    for (int v = 0; v < nocc; ++v) {
+      const double x = M[2 * al][(size_t)v * nocc + v].real(), y = M[2 * al + 1][(size_t)v * nocc + v].real();
+      s += 1.0 - (x * x + y * y);
+    }
+  return s * (a / (2.0 * M_PI)) * (a / (2.0 * M_PI));
+}
+}  // namespace
+
+tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps, double tol,
+                            double* U, double* spread, int* sweeps) {
+  if (!phi_pw || !U) return fail(TDDFT_EINVAL, "null argument");
+  if (nocc < 1 || max_sweeps < 0 || !(tol > 0.0)) return fail(TDDFT_EINVAL, "need nocc >= 1, max_sweeps >= 0, tol > 0");
+  std::vector<Miller> sph;
+  STATUS_TRY(build_sphere(n, a, ecut, sph));
+  if ((int)sph.size() < nocc) return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
+  std::vector<cd> Z[3];
+  position_matrices(n, sph, nocc, reinterpret_cast<const cd*>(phi_pw), Z);
+  // the six Hermitian matrices: Z = A + i B with A = (Z + Z^H)/2, B = (Z - Z^H)/2i
+  std::vector<cd> M[6];
+  for (int al = 0; al < 3; ++al) {
+    M[2 * al].resize((size_t)nocc * nocc);
+    M[2 * al + 1].resize((size_t)nocc * nocc);
+    for (int i = 0; i < nocc; ++i)
+      for (int j = 0; j < nocc; ++j) {
+        const cd zij = Z[al][(size_t)i * nocc + j], zji = std::conj(Z[al][(size_t)j * nocc + i]);
+        M[2 * al][(size_t)i * nocc + j] = 0.5 * (zij + zji);
+        M[2 * al + 1][(size_t)i * nocc + j] = (zij - zji) / cd(0.0, 2.0);
+      }
+  }
+  const double before = spread_of(M, nocc, a);
+  std::vector<cd> R((size_t)nocc * nocc, cd(0.0, 0.0));  // accumulated rotation: w_n = sum_v R_vn phi_v
+  for (int i = 0; i < nocc; ++i) R[(size_t)i * nocc + i] = 1.0;
+  int done = 0;
+  bool converged = max_sweeps == 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double maxrot = 0.0;
+    for (int i = 0; i < nocc; ++i)
+      for (int j = i + 1; j < nocc; ++j) {
+        // diagonal difference of every matrix after the rotation = h_k . v for a unit v; the best
+        // v is the top eigenvector of G = sum_k h_k h_k^T, h_k = (M_ii - M_jj, 2 Re M_ij, 2 Im M_ij)
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < 6; ++k) {
+          const std::vector<cd>& Mk = M[k];
+          const double hk[3] = {Mk[(size_t)i * nocc + i].real() - Mk[(size_t)j * nocc + j].real(),
+                                2.0 * Mk[(size_t)i * nocc + j].real(), 2.0 * Mk[(size_t)i * nocc + j].imag()};
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) G[p][q] += hk[p] * hk[q];
+        }
+        double v[3];
+        top_eigvec3(G, v);
+        if (v[0] < 0.0) v[0] = -v[0], v[1] = -v[1], v[2] = -v[2];
+        const double c = std::sqrt(0.5 * (1.0 + std::min(1.0, v[0])));
+        const cd s = cd(v[1], -v[2]) / (2.0 * c);
+        const double as = std::abs(s);
+        if (!(as > 1e-15)) continue;
+        maxrot = std::max(maxrot, as);
+        // R = identity but R_ii = c, R_ji = s, R_ij = -conj(s), R_jj = c; M <- R^H M R, R_total <- R_total R
+        for (int k = 0; k < 7; ++k) {
+          std::vector<cd>& X = k < 6 ? M[k] : R;
+          for (int p = 0; p < nocc; ++p) {
+            const cd xi = X[(size_t)p * nocc + i], xj = X[(size_t)p * nocc + j];
+            X[(size_t)p * nocc + i] = xi * c + xj * s;
+            X[(size_t)p * nocc + j] = -xi * std::conj(s) + xj * c;
+          }
+          if (k == 6) break;
+          for (int q = 0; q < nocc; ++q) {
+            const cd xi = X[(size_t)i * nocc + q], xj = X[(size_t)j * nocc + q];
+            X[(size_t)i * nocc + q] = c * xi + std::conj(s) * xj;
+            X[(size_t)j * nocc + q] = -s * xi + c * xj;
+          }
+        }
+      }
+    done = sweep + 1;
+    if (maxrot < tol) {
+      converged = true;
+      break;
+    }
+  }
+  // the library's convention for the localised frame: phi_v = sum_n U_vn phi~_n, so U = conj(R)
+  cd* u = reinterpret_cast<cd*>(U);
+  for (size_t e = 0; e < R.size(); ++e) u[e] = std::conj(R[e]);
+  if (spread) {
+    spread[0] = before;
+    spread[1] = spread_of(M, nocc, a);
+  }
+  if (sweeps) *sweeps = done;
+  return converged ? TDDFT_OK : fail(TDDFT_ENOTCONV, "localisation sweeps did not converge (U is the last iterate)");
 }
 
 tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange) {

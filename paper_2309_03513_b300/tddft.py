@@ -40,7 +40,7 @@ EXPORTS = [
     "tddft_sphere_size", "tddft_sphere_miller", "tddft_init_system", "tddft_query", "tddft_set_terms",
     "tddft_set_tuning", "tddft_get_tuning", "tddft_autotune", "tddft_apply_liouville_multi",
     "tddft_ace_build", "tddft_ace_enable", "tddft_zvector_solve", "tddft_zvector_rhs",
-    "tddft_set_localization", "tddft_relaxed_density", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
+    "tddft_set_localization", "tddft_localize", "tddft_relaxed_density", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
     "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
@@ -118,6 +118,7 @@ def load() -> ctypes.CDLL:
         "tddft_zvector_solve": ([vp, ci, vp, vp, vp, vp, vp, vp, vp], st),
         "tddft_zvector_rhs": ([vp, ci, vp, vp, vp], st),
         "tddft_set_localization": ([vp, vp, ctypes.c_double, vp, vp, vp], st),
+        "tddft_localize": ([ci, cd, cd, ci, vp, ci, cd, vp, vp, vp], st),
         "tddft_relaxed_density": ([vp, ci, vp, vp, vp, vp, vp], st),
         "tddft_apply_liouville": ([vp, ci, vp, vp, vp], st),
         "tddft_apply_liouville_host": ([vp, ci, vp, vp, vp], st),
@@ -206,6 +207,23 @@ def measure_peak(which: int) -> dict:
     ms = ctypes.c_double()
     _check(load().tddft_testing_peak(int(which), ctypes.byref(tf), ctypes.byref(ms)), "tddft_testing_peak")
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def localize(n: int, a: float, ecut: float, phi_pw, max_sweeps: int = 200, tol: float = 1e-10,
+             require_convergence: bool = True) -> tuple:
+    """Unitary U [nocc, nocc] of the maximally localised frame of the orbitals phi_pw [nocc, npw]
+    (host complex128, the library's sphere order): phi_v = sum_n U_vn phi~_n (tddft_localize).
+    Returns (U, (spread before, spread after) in bohr^2, sweeps)."""
+    c = np.ascontiguousarray(np.asarray(phi_pw), dtype=np.complex128)
+    nocc = c.shape[0]
+    U = np.zeros((nocc, nocc), dtype=np.complex128)
+    sp = np.zeros(2)
+    sw = ctypes.c_int()
+    st = load().tddft_localize(int(n), float(a), float(ecut), nocc, c.ctypes.data, int(max_sweeps), float(tol),
+                               U.ctypes.data, sp.ctypes.data, ctypes.byref(sw))
+    if st != 6 or require_convergence:
+        _check(st, "tddft_localize")
+    return U, (float(sp[0]), float(sp[1])), sw.value
 
 
 def inject_fault(kind: int, after: int = 0):
