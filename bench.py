@@ -344,7 +344,11 @@ def run_native(args):
             term_marginal_ms[name] = full_ms - one_step(T.TERMS_ALL & ~mask)
         sys_.set_terms(T.TERMS_ALL)
 
+    # the extras describe other workloads beside the metric: one GPU only (under torchrun every
+    # rank would build them, holding all GPUs for minutes of host-side input generation)
     extras = {}
+    if ws > 1:
+        args.extra = ""
     if "uneven" in args.extra:
         extras["uneven12"] = bench_uneven(torch, T, dev, stream)
     if "sf216" in args.extra:
