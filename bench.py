@@ -361,6 +361,8 @@ def run_native(args):
         extras["pairtrunc"] = bench_pairtrunc(torch, T, dev, stream)
     if "taucache" in args.extra:
         extras["taucache"] = bench_taucache(torch, T, dev, stream, wl, X, LA)
+    if "combined" in args.extra:
+        extras["combined"] = bench_combined(torch, T, dev, stream)
 
     # plain FP64 GPU path on the same batch
     fp64 = None
@@ -627,6 +629,71 @@ def bench_pairtrunc(torch, T, dev, stream, s_thr=1e-3):
     return out
 
 
+def bench_combined(torch, T, dev, stream, s_thr=1e-3, lambda_thr=1e-4, tol=1e-6, max_iter=40):
+    """The approximations of Sec. 3 together, as the paper combines them: the compressed
+    exchange inside D (N_ACE = 4 N_occ: the occupied orbitals plus 3 N_occ random orthonormal
+    rows orthogonal to them), K1d truncated at S_thr = 1e-3 in the frame tddft_localize finds,
+    and the inexact-Krylov switch at lambda_thr = 1e-4 in the Z-vector CG; against the exact
+    operator and an exact-operator CG on the same batch (the pair-truncation workload: 128
+    localised orbitals mixed by a random unitary, 8 trial vectors), FP32. Reports one operator
+    application and one Z-vector solve each way, and the deviations of the approximate L X and
+    Z from the exact ones."""
+    from paper_2309_03513_b300 import synth
+    w = WORKLOAD
+    n, a, ecut = w["n"], w["a"], w["ecut"]
+    wl = synth.make_workload(n=n, a=a, ecut=ecut, npw=T.sphere_size(n, a, ecut), nocc_src=w["nocc"], nb=w["nb"],
+                             seed=11, localized_sigma=1.0, miller=T.sphere_miller(n, a, ecut))
+    s = T.system_from_workload(wl, precision=T.PREC_FP32, stream=stream)
+    X = torch.from_numpy(wl.X).to(dev, torch.complex64)
+    LA = torch.empty_like(X)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed_apply():
+        s.apply(X, out=LA, stream=stream)
+        e0.record(stream)
+        s.apply(X, out=LA, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    def solve(lam):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Z, it, ex, res = s.zvector_solve(U, lambda_thr=lam, tol=tol, max_iter=max_iter, precondition=True,
+                                         stream=stream, require_convergence=False)
+        torch.cuda.synchronize(dev)
+        return Z, time.perf_counter() - t0, it, ex, res
+
+    out = {"s_thr": s_thr, "lambda_thr": lambda_thr, "n_ace": 4 * w["nocc"], "tol": tol, "max_iter": max_iter}
+    out["L_ms_exact"] = timed_apply()
+    L_exact = LA.clone()
+    U = s.zvector_rhs(X, stream=stream)  # right-hand sides from the exact operator's adjoint
+    Z_exact, t_exact, it_e, _, res_e = solve(0.0)
+    out["zvector_exact"] = {"solve_s": t_exact, "iterations": it_e.tolist(), "residual": res_e.tolist()}
+    # the approximations on
+    extra = synth.complement_rows(np.random.default_rng(1234), wl.phi_tgt, 3 * w["nocc"])
+    t0 = time.perf_counter()
+    s.ace_build(extra, stream=stream)
+    Uloc, spreads, _ = T.localize(n, a, ecut, wl.phi_src)
+    _, kept = s.set_localization(Uloc, s_thr, stream=stream)
+    s.set_tuning(k1d_sparse=1)
+    torch.cuda.synchronize(dev)
+    out["setup_s"] = time.perf_counter() - t0
+    out["kept_fraction"] = kept / float(w["nocc"] ** 2)
+    out["L_ms_approx"] = timed_apply()
+    out["L_rel_deviation"] = float(torch.linalg.vector_norm(LA - L_exact) / torch.linalg.vector_norm(L_exact))
+    Z_apx, t_apx, it_a, ex_a, res_a = solve(lambda_thr)
+    out["zvector_approx"] = {"solve_s": t_apx, "iterations": it_a.tolist(), "exact_iterations": ex_a.tolist(),
+                             "residual": res_a.tolist()}
+    out["Z_rel_deviation"] = float(torch.linalg.vector_norm(Z_apx - Z_exact) / torch.linalg.vector_norm(Z_exact))
+    out["speedup_L"] = out["L_ms_exact"] / out["L_ms_approx"]
+    out["speedup_zvector_solve"] = t_exact / t_apx
+    out["note"] = "approximate operator (Sec. 3 combined); not the bench metric"
+    s.close()
+    return out
+
+
 def bench_taucache(torch, T, dev, stream, wl, X, LA, steps=5):
     """The bench batch with K1d read from the stored tau_vv' of every occupied pair
     (tuning.k1d_cache: built once from the occupied orbitals, then only the
@@ -727,7 +794,8 @@ def main():
     ap.add_argument("--extra", default="sf216,uneven", help="comma list: uneven (12-system graph), sf216 (216-atom spin-flip), "
                                              "ace (compressed exchange on the bench batch), zvector (Z-vector CG on the bench batch), "
                                              "pairtrunc (K1d pair truncation, localised orbitals), "
-                                             "taucache (K1d from stored tau of every pair)")
+                                             "taucache (K1d from stored tau of every pair), "
+                                             "combined (the approximations of Sec. 3 together against the exact operator)")
     ap.add_argument("--exchange-grid", type=int, default=1, choices=[0, 1],
                     help="1: pair convolutions on the smallest exact grid (64^3 here; the default); 0: on the 72^3 grid")
     ap.add_argument("--xy-kernel", type=int, default=1, choices=[0, 1, 2, 3],
