@@ -122,6 +122,23 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller);
  * unsupported (n, precision) or when S does not fit the grid. */
 tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange);
 
+/* Local exchange-correlation kernels of the operator from a ground-state spin density, in the
+ * local density approximation (the paper's LDA: Slater exchange and the Perdew-Zunger 1981
+ * correlation with its spin interpolation). Host only, FP64, point by point.
+ * rho_up, rho_dn: HOST [npts] spin densities (bohr^-3, finite and >= 0, else EINVAL).
+ * Optional HOST [npts] outputs (NULL skips one):
+ *   vxc_up, vxc_dn: the potentials V_xc,sigma = d(rho eps_xc)/d rho_sigma (Ha);
+ *   fxc: the adiabatic local kernel of the spin-up channel, d V_xc,up / d rho_up (Ha bohr^3),
+ *     in closed form: the f_xc array of a spin-conserving handle (Eq. 4 with one spin channel);
+ *   fxc_sf: the spin-flip kernel (V_xc,up - V_xc,dn) / (rho_up - rho_dn) of Sec. 2.3, set to 0
+ *     where |rho_up - rho_dn| < sf_cutoff (the paper uses 1e-3, Supporting Information Sec. S2)
+ *     or where the two densities are equal: the f_xc array of a spin-flip handle.
+ * Points where the density vanishes get zero potentials and kernels, and fxc is 0 where rho_up
+ * vanishes (it diverges like rho_up^(-2/3) there). Near rs = 1 the two branches of the
+ * correlation fit meet with a small mismatch of value and slope, as published. */
+tddft_status tddft_lda_kernels(long long npts, const double* rho_up, const double* rho_dn, double sf_cutoff,
+                               double* vxc_up, double* vxc_dn, double* fxc, double* fxc_sf);
+
 /* Build a system: the inputs of the operator of Eq. 9 (spin-flip: Eq. 21) --
  * the occupied orbitals phi_v and eigenvalues eps_v of Eq. 3 (both spins for
  * spin-flip, Sec. 2.3), the local part of H^KS (Eq. 3), the local kernel f_xc of

@@ -30,6 +30,10 @@ What it computes (Jin, Yu, Govoni, Xu, Galli, arXiv:2309.03513):
   equation (Eq. 19) and its conjugate-gradient solution with the inexact
   Krylov switch of Sec. 3.3 (exact operator while the residual norm is at
   least lambda_thr, then the operator without K2d);
+* the local xc kernels of Eq. 4 (f_xc) and Sec. 2.3 (f_xc^SF, with the
+  spin-density cutoff of the Supporting Information) from a spin density in
+  the local density approximation (Slater exchange, Perdew-Zunger 1981
+  correlation), by numerical differentiation of the energy density;
 
 Discretisation (the paper works in plane waves at the Gamma point, Sec. 2):
 cubic cell of side a, Omega = a^3, grid N^3 (N_r points), r_j = a j / N,
@@ -729,3 +733,90 @@ def zvector_cg(sys: System, U: np.ndarray, lam_thr: float, tol: float, max_iter:
             conv[b] = np.sqrt(ip(r, r)) < tol
         res[b] = np.sqrt(ip(r, r))
     return Z, iters, n_exact, res, conv
+
+
+# --------------------------------------------------------------------------
+# Local xc kernels from a spin density (the f_xc of Eq. 4 and the f_xc^SF of Sec. 2.3) in the
+# local density approximation the paper uses for some of its checks (Perdew and Zunger 1981)
+# --------------------------------------------------------------------------
+
+# eps_c(rs) of the two spin limits: gamma / (1 + beta1 sqrt(rs) + beta2 rs) for rs >= 1,
+# A ln rs + B + C rs ln rs + D rs for rs < 1 (Ha)
+PZ81 = {"U": (-0.1423, 1.0529, 0.3334, 0.0311, -0.048, 0.0020, -0.0116),
+        "P": (-0.0843, 1.3981, 0.2611, 0.01555, -0.0269, 0.0007, -0.0048)}
+
+
+def pz81_eps(rs, limit: str):
+    """Correlation energy per electron of the unpolarised ("U") or fully polarised ("P") gas."""
+    g, b1, b2, A, B, C, D = PZ81[limit]
+    rs = np.asarray(rs, dtype=np.float64)
+    hi = g / (1.0 + b1 * np.sqrt(rs) + b2 * rs)
+    lo = A * np.log(rs) + B + C * rs * np.log(rs) + D * rs
+    return np.where(rs >= 1.0, hi, lo)
+
+
+def spin_interpolation(zeta):
+    """f(zeta) = ((1+zeta)^(4/3) + (1-zeta)^(4/3) - 2) / (2^(4/3) - 2)."""
+    zeta = np.asarray(zeta, dtype=np.float64)
+    return ((1 + zeta) ** (4 / 3) + (1 - zeta) ** (4 / 3) - 2) / (2 ** (4 / 3) - 2)
+
+
+def lda_exchange_energy_density(rs_):
+    """Slater exchange of one spin channel, -(3/4)(6/pi)^(1/3) rho_sigma^(4/3) (Ha bohr^-3)."""
+    return -0.75 * (6 / np.pi) ** (1 / 3) * np.asarray(rs_, dtype=np.float64) ** (4 / 3)
+
+
+def lda_correlation_energy_density(ru, rd):
+    """rho (eps_U + f(zeta) (eps_P - eps_U)) with rs = (3 / (4 pi rho))^(1/3) (Ha bohr^-3)."""
+    ru = np.asarray(ru, dtype=np.float64)
+    rd = np.asarray(rd, dtype=np.float64)
+    rho = ru + rd
+    safe = np.where(rho > 0, rho, 1.0)
+    rs = (3 / (4 * np.pi * safe)) ** (1 / 3)
+    zeta = (ru - rd) / safe
+    ec = pz81_eps(rs, "U") + spin_interpolation(zeta) * (pz81_eps(rs, "P") - pz81_eps(rs, "U"))
+    return np.where(rho > 0, rho * ec, 0.0)
+
+
+def lda_energy_density(ru, rd):
+    """rho eps_xc (Ha bohr^-3): Slater exchange of both spins plus the correlation."""
+    return lda_exchange_energy_density(ru) + lda_exchange_energy_density(rd) + lda_correlation_energy_density(ru, rd)
+
+
+def lda_potentials(ru, rd, rel_step: float = 1e-4):
+    """(V_xc,up, V_xc,dn) = d(rho eps_xc)/d rho_sigma, by the fourth-order central difference of
+    lda_energy_density with a step of rel_step * rho_sigma."""
+    ru = np.asarray(ru, dtype=np.float64)
+    rd = np.asarray(rd, dtype=np.float64)
+
+    def d1(f, x, h):
+        return (f(x - 2 * h) - 8 * f(x - h) + 8 * f(x + h) - f(x + 2 * h)) / (12 * h)
+
+    hu = rel_step * ru
+    hd = rel_step * rd
+    vu = np.where(ru > 0, d1(lambda x: lda_energy_density(x, rd), ru, np.where(hu > 0, hu, 1.0)), 0.0)
+    vd = np.where(rd > 0, d1(lambda x: lda_energy_density(ru, x), rd, np.where(hd > 0, hd, 1.0)), 0.0)
+    return vu, vd
+
+
+def lda_fxc_same_spin(ru, rd, rel_step: float = 1e-3):
+    """d^2 (rho eps_xc) / d rho_up^2 by the five-point stencil (-1, 16, -30, 16, -1) / (12 h^2),
+    the stencil the Supporting Information uses for the g_xc term."""
+    ru = np.asarray(ru, dtype=np.float64)
+    rd = np.asarray(rd, dtype=np.float64)
+    h = np.where(ru > 0, rel_step * ru, 1.0)
+
+    def d2(f):  # only the parts that depend on rho_up (the spin-down exchange drops out exactly)
+        e = [f(ru + k * h) for k in (-2, -1, 0, 1, 2)]
+        return (-e[0] + 16 * e[1] - 30 * e[2] + 16 * e[3] - e[4]) / (12 * h * h)
+
+    f = d2(lda_exchange_energy_density) + d2(lambda x: lda_correlation_energy_density(x, rd))
+    return np.where(ru > 0, f, 0.0)
+
+
+def spin_flip_kernel(vu, vd, ru, rd, cutoff: float = 1e-3):
+    """f_xc^SF = (V_xc,up - V_xc,dn) / (rho_up - rho_dn) (Sec. 2.3), zero where
+    |rho_up - rho_dn| < cutoff (the Supporting Information's 1e-3) or where the densities are equal."""
+    sd = np.asarray(ru, dtype=np.float64) - np.asarray(rd, dtype=np.float64)
+    keep = (np.abs(sd) >= cutoff) & (sd != 0)
+    return np.where(keep, (np.asarray(vu) - np.asarray(vd)) / np.where(keep, sd, 1.0), 0.0)

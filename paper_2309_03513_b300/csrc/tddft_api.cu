@@ -2088,6 +2088,105 @@ tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller) {
   return TDDFT_OK;
 }
 
+// Local exchange-correlation kernels from a ground-state spin density (host, FP64), for the local
+// density approximation: Slater exchange, E_x = -(3/4)(6/pi)^(1/3) sum_sigma int rho_sigma^(4/3), and
+// the Perdew-Zunger (1981) parametrisation of the correlation energy per electron with its
+// spin interpolation eps_c = eps_U + f(zeta) (eps_P - eps_U).
+namespace {
+struct PzBranch {  // one of the two spin limits (U: unpolarised, P: fully polarised)
+  double gamma, beta1, beta2, A, B, C, D;
+};
+constexpr PzBranch kPzU{-0.1423, 1.0529, 0.3334, 0.0311, -0.048, 0.0020, -0.0116};
+constexpr PzBranch kPzP{-0.0843, 1.3981, 0.2611, 0.01555, -0.0269, 0.0007, -0.0048};
+
+// eps(rs) and its first two derivatives of one branch
+void pz_eps(const PzBranch& q, double rs, double* e, double* de, double* dde) {
+  if (rs >= 1.0) {
+    const double sr = std::sqrt(rs), den = 1.0 + q.beta1 * sr + q.beta2 * rs;
+    const double g = 0.5 * q.beta1 / sr + q.beta2, dg = -0.25 * q.beta1 / (rs * sr);  // d den / d rs and its derivative
+    *e = q.gamma / den;
+    *de = -q.gamma * g / (den * den);
+    *dde = -q.gamma * (dg / (den * den) - 2.0 * g * g / (den * den * den));
+  } else {
+    const double l = std::log(rs);
+    *e = q.A * l + q.B + q.C * rs * l + q.D * rs;
+    *de = q.A / rs + q.C * (l + 1.0) + q.D;
+    *dde = -q.A / (rs * rs) + q.C / rs;
+  }
+}
+
+// V_xc of both spins (Ha) and d V_xc,up / d rho_up (Ha bohr^3) at one point, in closed form;
+// zero where the density vanishes
+void lda_point(double ru, double rd, double* vu, double* vd, double* fuu) {
+  ru = std::max(ru, 0.0);
+  rd = std::max(rd, 0.0);
+  const double rho = ru + rd;
+  if (!(rho > 1e-14)) {
+    *vu = *vd = *fuu = 0.0;
+    return;
+  }
+  const double cx = std::cbrt(6.0 / M_PI);
+  const double vxu = -cx * std::cbrt(ru), vxd = -cx * std::cbrt(rd);
+  const double rs = std::cbrt(3.0 / (4.0 * M_PI * rho));
+  const double zeta = std::min(1.0, std::max(-1.0, (ru - rd) / rho));
+  const double den = 2.0 * std::cbrt(2.0) - 2.0;  // 2^(4/3) - 2
+  const double zp = std::cbrt(1.0 + zeta), zm = std::cbrt(1.0 - zeta);
+  const double f = ((1.0 + zeta) * zp + (1.0 - zeta) * zm - 2.0) / den;
+  const double df = (4.0 / 3.0) * (zp - zm) / den;
+  double eu, deu, ddeu, ep, dep, ddep;
+  pz_eps(kPzU, rs, &eu, &deu, &ddeu);
+  pz_eps(kPzP, rs, &ep, &dep, &ddep);
+  // E(rs, zeta) = eps_U + f(zeta) (eps_P - eps_U) and its partial derivatives
+  const double E = eu + f * (ep - eu), Er = deu + f * (dep - deu), Ez = df * (ep - eu);
+  const double Err = ddeu + f * (ddep - ddeu), Erz = df * (dep - deu);
+  // V_c,sigma = E - (rs/3) E_r + (s_sigma - zeta) E_z, s_up = +1, s_dn = -1
+  const double base = E - rs / 3.0 * Er;
+  *vu = vxu + base + (1.0 - zeta) * Ez;
+  *vd = vxd + base - (1.0 + zeta) * Ez;
+  // d V_c,up / d rho_up with d rs / d rho_up = -rs / (3 rho), d zeta / d rho_up = (1 - zeta) / rho:
+  // dV/drs = (2/3) E_r - (rs/3) E_rr + (1 - zeta) E_rz, dV/dzeta = -(rs/3) E_rz + (1 - zeta) E_zz.
+  // (1 - zeta)^2 E_zz stays finite as zeta -> 1; as zeta -> -1 (rho_up -> 0) it grows like the
+  // exchange term, rho_up^(-2/3)
+  double fx = 0.0, term_zz = 0.0;
+  if (ru > 0.0) {
+    fx = -(1.0 / 3.0) * cx * std::cbrt(ru) / ru;
+    const double opz = 1.0 + zeta, omz = 1.0 - zeta;  // d^2 f / d zeta^2 = (4/9)((1+z)^(-2/3) + (1-z)^(-2/3)) / den
+    const double a = opz > 0.0 ? 1.0 / (std::cbrt(opz) * std::cbrt(opz)) : 0.0;
+    const double b = omz > 0.0 ? omz * omz / (std::cbrt(omz) * std::cbrt(omz)) : 0.0;  // (1-z)^(4/3)
+    // (1 - zeta)^2 E_zz = (1 - zeta)^2 f''(zeta) (eps_P - eps_U)
+    term_zz = (4.0 / 9.0) * (omz * omz * a + b) / den * (ep - eu);
+  }
+  const double dVdrs = (2.0 / 3.0) * Er - rs / 3.0 * Err + (1.0 - zeta) * Erz;
+  const double dVdz_times_omz = -(rs / 3.0) * Erz * (1.0 - zeta) + term_zz;
+  *fuu = ru > 0.0 ? fx + (dVdrs * (-rs / 3.0) + dVdz_times_omz) / rho : 0.0;  // diverges as rho_up -> 0
+}
+}  // namespace
+
+tddft_status tddft_lda_kernels(long long npts, const double* rho_up, const double* rho_dn, double sf_cutoff,
+                               double* vxc_up, double* vxc_dn, double* fxc, double* fxc_sf) {
+  if (npts < 0 || !rho_up || !rho_dn) return fail(TDDFT_EINVAL, "need npts >= 0 and both densities");
+  if (!(sf_cutoff >= 0.0)) return fail(TDDFT_EINVAL, "sf_cutoff must be >= 0");
+  for (long long i = 0; i < npts; ++i) {
+    if (!(rho_up[i] >= 0.0) || !(rho_dn[i] >= 0.0))
+      return fail(TDDFT_EINVAL, "densities must be finite and non-negative (point " + std::to_string(i) + ")");
+  }
+  for (long long i = 0; i < npts; ++i) {
+    const double ru = rho_up[i], rd = rho_dn[i];
+    double vu, vd, fuu;
+    lda_point(ru, rd, &vu, &vd, &fuu);
+    if (vxc_up) vxc_up[i] = vu;
+    if (vxc_dn) vxc_dn[i] = vd;
+    if (fxc) fxc[i] = fuu;
+    if (fxc_sf) {
+      // spin-flip kernel (V_xc,up - V_xc,dn) / (rho_up - rho_dn), zero where the spin density is
+      // below the cutoff (Sec. 2.3; the cutoff of the Supporting Information is 1e-3)
+      const double sd = ru - rd;
+      fxc_sf[i] = std::abs(sd) < sf_cutoff || sd == 0.0 ? 0.0 : (vu - vd) / sd;
+    }
+  }
+  return TDDFT_OK;
+}
+
 // Maximally localised orbitals at the Gamma point (host, FP64): the localised frame of the pair
 // truncation of Sec. 3.2 (Eq. 31). Spread functional of a cubic cell (Resta; Silvestrelli):
 // Omega = (a/2pi)^2 sum_alpha sum_n (1 - |Z^alpha_nn|^2), Z^alpha_mn = <phi_m| exp(i 2 pi r_alpha / a) |phi_n>,

@@ -43,7 +43,7 @@ EXPORTS = [
     "tddft_set_localization", "tddft_localize", "tddft_relaxed_density", "tddft_apply_liouville", "tddft_apply_liouville_host", "tddft_apply_liouville_adjoint",
     "tddft_davidson_create", "tddft_davidson_step", "tddft_davidson_vectors", "tddft_davidson_destroy",
     "tddft_destroy", "tddft_status_string", "tddft_last_error", "tddft_profile_enable", "tddft_profile_read",
-    "tddft_exchange_pair_noalloc", "tddft_exchange_grid",
+    "tddft_exchange_pair_noalloc", "tddft_exchange_grid", "tddft_lda_kernels",
     # include/tddft_testing.h
     "tddft_testing_herm_eig", "tddft_testing_cholesky", "tddft_testing_lower_inverse",
     "tddft_testing_herm_eig_device", "tddft_testing_peak", "tddft_testing_inject_fault", "tddft_testing_fault_state",
@@ -134,6 +134,7 @@ def load() -> ctypes.CDLL:
         "tddft_profile_read": ([vp, vp, vp, vp], st),
         "tddft_exchange_pair_noalloc": ([ci, cd, cd, cd, cd, vp, vp, vp, vp], st),
         "tddft_exchange_grid": ([ci, cd, cd, ci, vp], st),
+        "tddft_lda_kernels": ([ctypes.c_longlong, vp, vp, cd, vp, vp, vp, vp], st),
         "tddft_testing_herm_eig": ([ci, vp, vp, vp], st),
         "tddft_testing_cholesky": ([ci, vp], st),
         "tddft_testing_lower_inverse": ([ci, vp, vp], st),
@@ -207,6 +208,21 @@ def measure_peak(which: int) -> dict:
     ms = ctypes.c_double()
     _check(load().tddft_testing_peak(int(which), ctypes.byref(tf), ctypes.byref(ms)), "tddft_testing_peak")
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def lda_kernels(rho_up, rho_dn, sf_cutoff: float = 1e-3) -> dict:
+    """LDA potentials and the local kernels of the operator from a spin density (host arrays of
+    any shape; tddft_lda_kernels): {"vxc_up", "vxc_dn", "fxc" (spin-conserving f_xc),
+    "fxc_sf" (spin-flip kernel, zero where |rho_up - rho_dn| < sf_cutoff)}."""
+    ru = np.ascontiguousarray(rho_up, dtype=np.float64)
+    rd = np.ascontiguousarray(rho_dn, dtype=np.float64)
+    if ru.shape != rd.shape:
+        raise ValueError("the two spin densities must have the same shape")
+    out = {k: np.empty_like(ru) for k in ("vxc_up", "vxc_dn", "fxc", "fxc_sf")}
+    _check(load().tddft_lda_kernels(ru.size, ru.ctypes.data, rd.ctypes.data, float(sf_cutoff),
+                                    out["vxc_up"].ctypes.data, out["vxc_dn"].ctypes.data, out["fxc"].ctypes.data,
+                                    out["fxc_sf"].ctypes.data), "tddft_lda_kernels")
+    return out
 
 
 def localize(n: int, a: float, ecut: float, phi_pw, max_sweeps: int = 200, tol: float = 1e-10,
