@@ -2303,8 +2303,10 @@ tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double
       }
   }
   const double before = spread_of(M, nocc, a);
-  std::vector<cd> R((size_t)nocc * nocc, cd(0.0, 0.0));  // accumulated rotation: w_n = sum_v R_vn phi_v
-  for (int i = 0; i < nocc; ++i) R[(size_t)i * nocc + i] = 1.0;
+  // accumulated rotation, stored transposed (RT[n][v] = R_vn, w_n = sum_v R_vn phi_v) so that the
+  // column updates of R run over contiguous memory
+  std::vector<cd> RT((size_t)nocc * nocc, cd(0.0, 0.0));
+  for (int i = 0; i < nocc; ++i) RT[(size_t)i * nocc + i] = 1.0;
   int done = 0;
   bool converged = max_sweeps == 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -2325,24 +2327,47 @@ tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double
         top_eigvec3(G, v);
         if (v[0] < 0.0) v[0] = -v[0], v[1] = -v[1], v[2] = -v[2];
         const double c = std::sqrt(0.5 * (1.0 + std::min(1.0, v[0])));
-        const cd s = cd(v[1], -v[2]) / (2.0 * c);
-        const double as = std::abs(s);
+        const double sr = v[1] / (2.0 * c), si = -v[2] / (2.0 * c);  // s = sr + i si
+        const double as = std::hypot(sr, si);
         if (!(as > 1e-15)) continue;
         maxrot = std::max(maxrot, as);
-        // R = identity but R_ii = c, R_ji = s, R_ij = -conj(s), R_jj = c; M <- R^H M R, R_total <- R_total R
-        for (int k = 0; k < 7; ++k) {
-          std::vector<cd>& X = k < 6 ? M[k] : R;
-          for (int p = 0; p < nocc; ++p) {
-            const cd xi = X[(size_t)p * nocc + i], xj = X[(size_t)p * nocc + j];
-            X[(size_t)p * nocc + i] = xi * c + xj * s;
-            X[(size_t)p * nocc + j] = -xi * std::conj(s) + xj * c;
-          }
-          if (k == 6) break;
+        // R = identity but R_ii = c, R_ji = s, R_ij = -conj(s), R_jj = c. Each M is Hermitian, so
+        // M <- R^H M R is its rows i, j updated (row i <- c row i + conj(s) row j, row j <- -s row i
+        // + c row j) off the 2 x 2 block, the columns i, j their conjugates, and the block itself
+        for (int k = 0; k < 6; ++k) {
+          cd* X = M[k].data();
+          cd* Xi = X + (size_t)i * nocc;
+          cd* Xj = X + (size_t)j * nocc;
+          const cd a = Xi[i], b = Xi[j], d = Xj[j];
           for (int q = 0; q < nocc; ++q) {
-            const cd xi = X[(size_t)i * nocc + q], xj = X[(size_t)j * nocc + q];
-            X[(size_t)i * nocc + q] = c * xi + std::conj(s) * xj;
-            X[(size_t)j * nocc + q] = -s * xi + c * xj;
+            const double air = Xi[q].real(), aii = Xi[q].imag(), bjr = Xj[q].real(), bji = Xj[q].imag();
+            const double nir = c * air + sr * bjr + si * bji, nii = c * aii + sr * bji - si * bjr;
+            const double njr = -sr * air + si * aii + c * bjr, nji = -sr * aii - si * air + c * bji;
+            Xi[q] = cd(nir, nii);
+            Xj[q] = cd(njr, nji);
+            X[(size_t)q * nocc + i] = cd(nir, -nii);
+            X[(size_t)q * nocc + j] = cd(njr, -nji);
           }
+          // the 2 x 2 block: M'_ii = c^2 a + |s|^2 d + 2c Re(s b), M'_jj = |s|^2 a + c^2 d - 2c Re(s b),
+          // M'_ij = c^2 b - conj(s)^2 conj(b) + c conj(s) (d - a)
+          const cd sc(sr, -si);  // conj(s)
+          const double resb = sr * b.real() - si * b.imag();
+          const double s2 = sr * sr + si * si;
+          const double mii = c * c * a.real() + s2 * d.real() + 2.0 * c * resb;
+          const double mjj = s2 * a.real() + c * c * d.real() - 2.0 * c * resb;
+          const cd mij = c * c * b - sc * sc * std::conj(b) + c * sc * (d - a);
+          Xi[i] = mii;
+          Xj[j] = mjj;
+          Xi[j] = mij;
+          Xj[i] = std::conj(mij);
+        }
+        // R_total <- R_total R: columns i, j of R = rows i, j of RT
+        cd* Ri = RT.data() + (size_t)i * nocc;
+        cd* Rj = RT.data() + (size_t)j * nocc;
+        for (int p = 0; p < nocc; ++p) {
+          const double xr = Ri[p].real(), xi_ = Ri[p].imag(), yr = Rj[p].real(), yi = Rj[p].imag();
+          Ri[p] = cd(c * xr + sr * yr - si * yi, c * xi_ + sr * yi + si * yr);   // c x + s y
+          Rj[p] = cd(-sr * xr - si * xi_ + c * yr, -sr * xi_ + si * xr + c * yi);  // -conj(s) x + c y
         }
       }
     done = sweep + 1;
@@ -2351,6 +2376,9 @@ tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double
       break;
     }
   }
+  std::vector<cd> R((size_t)nocc * nocc);
+  for (int n = 0; n < nocc; ++n)
+    for (int v = 0; v < nocc; ++v) R[(size_t)v * nocc + n] = RT[(size_t)n * nocc + v];
   // the library's convention for the localised frame: phi_v = sum_n U_vn phi~_n, so U = conj(R)
   cd* u = reinterpret_cast<cd*>(U);
   for (size_t e = 0; e < R.size(); ++e) u[e] = std::conj(R[e]);
