@@ -12,6 +12,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -2281,8 +2283,23 @@ double spread_of(const std::vector<cd> M[6], int nocc, double a) {
 }
 }  // namespace
 
+static tddft_status localize_impl(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps,
+                                  double tol, double* U, double* spread, int* sweeps);
+
 tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps, double tol,
                             double* U, double* spread, int* sweeps) {
+  // host memory and worker threads: their exceptions stay on this side of the C ABI
+  try {
+    return localize_impl(n, a, ecut, nocc, phi_pw, max_sweeps, tol, U, spread, sweeps);
+  } catch (const std::bad_alloc&) {
+    return fail(TDDFT_ENOMEM, "tddft_localize: host memory exhausted");
+  } catch (const std::exception& e) {
+    return fail(TDDFT_ENOMEM, std::string("tddft_localize: ") + e.what());
+  }
+}
+
+static tddft_status localize_impl(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps,
+                                  double tol, double* U, double* spread, int* sweeps) {
   if (!phi_pw || !U) return fail(TDDFT_EINVAL, "null argument");
   if (nocc < 1 || max_sweeps < 0 || !(tol > 0.0)) return fail(TDDFT_EINVAL, "need nocc >= 1, max_sweeps >= 0, tol > 0");
   std::vector<Miller> sph;
