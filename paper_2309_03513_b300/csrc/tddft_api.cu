@@ -108,6 +108,30 @@ static std::string alloc_error(size_t bytes, cudaError_t e) {
          (t_alloc_injected ? " (injected fault)" : "");
 }
 
+// Every entry point runs its body through abi_guard: a C++ exception (host memory exhausted, a
+// worker thread that cannot start) becomes a status and a last-error message, never crossing
+// the C ABI.
+template <typename F>
+static tddft_status abi_guard(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    try {
+      return fail(TDDFT_ENOMEM, "host memory exhausted");
+    } catch (...) {
+      return TDDFT_ENOMEM;
+    }
+  } catch (const std::exception& e) {
+    try {
+      return fail(TDDFT_ENOMEM, std::string("host exception: ") + e.what());
+    } catch (...) {
+      return TDDFT_ENOMEM;
+    }
+  } catch (...) {
+    return TDDFT_ENOMEM;
+  }
+}
+
 #define CUDA_TRY(expr)                                                                                 \
   do {                                                                                                 \
     cudaError_t _e = (expr);                                                                           \
@@ -2071,23 +2095,27 @@ const char* tddft_status_string(tddft_status s) {
 const char* tddft_last_error(void) { return g_last_error.c_str(); }
 
 tddft_status tddft_sphere_size(int n, double a, double ecut, int* npw) {
-  if (!npw) return fail(TDDFT_EINVAL, "null output");
-  std::vector<Miller> s;
-  STATUS_TRY(build_sphere(n, a, ecut, s));
-  *npw = (int)s.size();
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!npw) return fail(TDDFT_EINVAL, "null output");
+    std::vector<Miller> s;
+    STATUS_TRY(build_sphere(n, a, ecut, s));
+    *npw = (int)s.size();
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_sphere_miller(int n, double a, double ecut, int* miller) {
-  if (!miller) return fail(TDDFT_EINVAL, "null output");
-  std::vector<Miller> s;
-  STATUS_TRY(build_sphere(n, a, ecut, s));
-  for (size_t i = 0; i < s.size(); ++i) {
-    miller[3 * i] = s[i].x;
-    miller[3 * i + 1] = s[i].y;
-    miller[3 * i + 2] = s[i].z;
-  }
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!miller) return fail(TDDFT_EINVAL, "null output");
+    std::vector<Miller> s;
+    STATUS_TRY(build_sphere(n, a, ecut, s));
+    for (size_t i = 0; i < s.size(); ++i) {
+      miller[3 * i] = s[i].x;
+      miller[3 * i + 1] = s[i].y;
+      miller[3 * i + 2] = s[i].z;
+    }
+    return TDDFT_OK;
+  });
 }
 
 // Local exchange-correlation kernels from a ground-state spin density (host, FP64), for the local
@@ -2166,27 +2194,29 @@ void lda_point(double ru, double rd, double* vu, double* vd, double* fuu) {
 
 tddft_status tddft_lda_kernels(long long npts, const double* rho_up, const double* rho_dn, double sf_cutoff,
                                double* vxc_up, double* vxc_dn, double* fxc, double* fxc_sf) {
-  if (npts < 0 || !rho_up || !rho_dn) return fail(TDDFT_EINVAL, "need npts >= 0 and both densities");
-  if (!(sf_cutoff >= 0.0)) return fail(TDDFT_EINVAL, "sf_cutoff must be >= 0");
-  for (long long i = 0; i < npts; ++i) {
-    if (!(rho_up[i] >= 0.0) || !(rho_dn[i] >= 0.0))
-      return fail(TDDFT_EINVAL, "densities must be finite and non-negative (point " + std::to_string(i) + ")");
-  }
-  for (long long i = 0; i < npts; ++i) {
-    const double ru = rho_up[i], rd = rho_dn[i];
-    double vu, vd, fuu;
-    lda_point(ru, rd, &vu, &vd, &fuu);
-    if (vxc_up) vxc_up[i] = vu;
-    if (vxc_dn) vxc_dn[i] = vd;
-    if (fxc) fxc[i] = fuu;
-    if (fxc_sf) {
-      // spin-flip kernel (V_xc,up - V_xc,dn) / (rho_up - rho_dn), zero where the spin density is
-      // below the cutoff (Sec. 2.3; the cutoff of the Supporting Information is 1e-3)
-      const double sd = ru - rd;
-      fxc_sf[i] = std::abs(sd) < sf_cutoff || sd == 0.0 ? 0.0 : (vu - vd) / sd;
+  return abi_guard([&]() -> tddft_status {
+    if (npts < 0 || !rho_up || !rho_dn) return fail(TDDFT_EINVAL, "need npts >= 0 and both densities");
+    if (!(sf_cutoff >= 0.0)) return fail(TDDFT_EINVAL, "sf_cutoff must be >= 0");
+    for (long long i = 0; i < npts; ++i) {
+      if (!(rho_up[i] >= 0.0) || !(rho_dn[i] >= 0.0))
+        return fail(TDDFT_EINVAL, "densities must be finite and non-negative (point " + std::to_string(i) + ")");
     }
-  }
-  return TDDFT_OK;
+    for (long long i = 0; i < npts; ++i) {
+      const double ru = rho_up[i], rd = rho_dn[i];
+      double vu, vd, fuu;
+      lda_point(ru, rd, &vu, &vd, &fuu);
+      if (vxc_up) vxc_up[i] = vu;
+      if (vxc_dn) vxc_dn[i] = vd;
+      if (fxc) fxc[i] = fuu;
+      if (fxc_sf) {
+        // spin-flip kernel (V_xc,up - V_xc,dn) / (rho_up - rho_dn), zero where the spin density is
+        // below the cutoff (Sec. 2.3; the cutoff of the Supporting Information is 1e-3)
+        const double sd = ru - rd;
+        fxc_sf[i] = std::abs(sd) < sf_cutoff || sd == 0.0 ? 0.0 : (vu - vd) / sd;
+      }
+    }
+    return TDDFT_OK;
+  });
 }
 
 // Maximally localised orbitals at the Gamma point (host, FP64): the localised frame of the pair
@@ -2283,269 +2313,270 @@ double spread_of(const std::vector<cd> M[6], int nocc, double a) {
 }
 }  // namespace
 
-static tddft_status localize_impl(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps,
-                                  double tol, double* U, double* spread, int* sweeps);
-
 tddft_status tddft_localize(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps, double tol,
                             double* U, double* spread, int* sweeps) {
-  // host memory and worker threads: their exceptions stay on this side of the C ABI
-  try {
-    return localize_impl(n, a, ecut, nocc, phi_pw, max_sweeps, tol, U, spread, sweeps);
-  } catch (const std::bad_alloc&) {
-    return fail(TDDFT_ENOMEM, "tddft_localize: host memory exhausted");
-  } catch (const std::exception& e) {
-    return fail(TDDFT_ENOMEM, std::string("tddft_localize: ") + e.what());
-  }
-}
-
-static tddft_status localize_impl(int n, double a, double ecut, int nocc, const double* phi_pw, int max_sweeps,
-                                  double tol, double* U, double* spread, int* sweeps) {
-  if (!phi_pw || !U) return fail(TDDFT_EINVAL, "null argument");
-  if (nocc < 1 || max_sweeps < 0 || !(tol > 0.0)) return fail(TDDFT_EINVAL, "need nocc >= 1, max_sweeps >= 0, tol > 0");
-  std::vector<Miller> sph;
-  STATUS_TRY(build_sphere(n, a, ecut, sph));
-  if ((int)sph.size() < nocc) return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
-  std::vector<cd> Z[3];
-  position_matrices(n, sph, nocc, reinterpret_cast<const cd*>(phi_pw), Z);
-  // the six Hermitian matrices: Z = A + i B with A = (Z + Z^H)/2, B = (Z - Z^H)/2i
-  std::vector<cd> M[6];
-  for (int al = 0; al < 3; ++al) {
-    M[2 * al].resize((size_t)nocc * nocc);
-    M[2 * al + 1].resize((size_t)nocc * nocc);
-    for (int i = 0; i < nocc; ++i)
-      for (int j = 0; j < nocc; ++j) {
-        const cd zij = Z[al][(size_t)i * nocc + j], zji = std::conj(Z[al][(size_t)j * nocc + i]);
-        M[2 * al][(size_t)i * nocc + j] = 0.5 * (zij + zji);
-        M[2 * al + 1][(size_t)i * nocc + j] = (zij - zji) / cd(0.0, 2.0);
-      }
-  }
-  const double before = spread_of(M, nocc, a);
-  // accumulated rotation, stored transposed (RT[n][v] = R_vn, w_n = sum_v R_vn phi_v) so that the
-  // column updates of R run over contiguous memory
-  std::vector<cd> RT((size_t)nocc * nocc, cd(0.0, 0.0));
-  for (int i = 0; i < nocc; ++i) RT[(size_t)i * nocc + i] = 1.0;
-  int done = 0;
-  bool converged = max_sweeps == 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double maxrot = 0.0;
-    for (int i = 0; i < nocc; ++i)
-      for (int j = i + 1; j < nocc; ++j) {
-        // diagonal difference of every matrix after the rotation = h_k . v for a unit v; the best
-        // v is the top eigenvector of G = sum_k h_k h_k^T, h_k = (M_ii - M_jj, 2 Re M_ij, 2 Im M_ij)
-        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int k = 0; k < 6; ++k) {
-          const std::vector<cd>& Mk = M[k];
-          const double hk[3] = {Mk[(size_t)i * nocc + i].real() - Mk[(size_t)j * nocc + j].real(),
-                                2.0 * Mk[(size_t)i * nocc + j].real(), 2.0 * Mk[(size_t)i * nocc + j].imag()};
-          for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) G[p][q] += hk[p] * hk[q];
+  return abi_guard([&]() -> tddft_status {
+    if (!phi_pw || !U) return fail(TDDFT_EINVAL, "null argument");
+    if (nocc < 1 || max_sweeps < 0 || !(tol > 0.0)) return fail(TDDFT_EINVAL, "need nocc >= 1, max_sweeps >= 0, tol > 0");
+    std::vector<Miller> sph;
+    STATUS_TRY(build_sphere(n, a, ecut, sph));
+    if ((int)sph.size() < nocc) return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
+    std::vector<cd> Z[3];
+    position_matrices(n, sph, nocc, reinterpret_cast<const cd*>(phi_pw), Z);
+    // the six Hermitian matrices: Z = A + i B with A = (Z + Z^H)/2, B = (Z - Z^H)/2i
+    std::vector<cd> M[6];
+    for (int al = 0; al < 3; ++al) {
+      M[2 * al].resize((size_t)nocc * nocc);
+      M[2 * al + 1].resize((size_t)nocc * nocc);
+      for (int i = 0; i < nocc; ++i)
+        for (int j = 0; j < nocc; ++j) {
+          const cd zij = Z[al][(size_t)i * nocc + j], zji = std::conj(Z[al][(size_t)j * nocc + i]);
+          M[2 * al][(size_t)i * nocc + j] = 0.5 * (zij + zji);
+          M[2 * al + 1][(size_t)i * nocc + j] = (zij - zji) / cd(0.0, 2.0);
         }
-        double v[3];
-        top_eigvec3(G, v);
-        if (v[0] < 0.0) v[0] = -v[0], v[1] = -v[1], v[2] = -v[2];
-        const double c = std::sqrt(0.5 * (1.0 + std::min(1.0, v[0])));
-        const double sr = v[1] / (2.0 * c), si = -v[2] / (2.0 * c);  // s = sr + i si
-        const double as = std::hypot(sr, si);
-        if (!(as > 1e-15)) continue;
-        maxrot = std::max(maxrot, as);
-        // R = identity but R_ii = c, R_ji = s, R_ij = -conj(s), R_jj = c. Each M is Hermitian, so
-        // M <- R^H M R is its rows i, j updated (row i <- c row i + conj(s) row j, row j <- -s row i
-        // + c row j) off the 2 x 2 block, the columns i, j their conjugates, and the block itself
-        for (int k = 0; k < 6; ++k) {
-          cd* X = M[k].data();
-          cd* Xi = X + (size_t)i * nocc;
-          cd* Xj = X + (size_t)j * nocc;
-          const cd a = Xi[i], b = Xi[j], d = Xj[j];
-          for (int q = 0; q < nocc; ++q) {
-            const double air = Xi[q].real(), aii = Xi[q].imag(), bjr = Xj[q].real(), bji = Xj[q].imag();
-            const double nir = c * air + sr * bjr + si * bji, nii = c * aii + sr * bji - si * bjr;
-            const double njr = -sr * air + si * aii + c * bjr, nji = -sr * aii - si * air + c * bji;
-            Xi[q] = cd(nir, nii);
-            Xj[q] = cd(njr, nji);
-            X[(size_t)q * nocc + i] = cd(nir, -nii);
-            X[(size_t)q * nocc + j] = cd(njr, -nji);
-          }
-          // the 2 x 2 block: M'_ii = c^2 a + |s|^2 d + 2c Re(s b), M'_jj = |s|^2 a + c^2 d - 2c Re(s b),
-          // M'_ij = c^2 b - conj(s)^2 conj(b) + c conj(s) (d - a)
-          const cd sc(sr, -si);  // conj(s)
-          const double resb = sr * b.real() - si * b.imag();
-          const double s2 = sr * sr + si * si;
-          const double mii = c * c * a.real() + s2 * d.real() + 2.0 * c * resb;
-          const double mjj = s2 * a.real() + c * c * d.real() - 2.0 * c * resb;
-          const cd mij = c * c * b - sc * sc * std::conj(b) + c * sc * (d - a);
-          Xi[i] = mii;
-          Xj[j] = mjj;
-          Xi[j] = mij;
-          Xj[i] = std::conj(mij);
-        }
-        // R_total <- R_total R: columns i, j of R = rows i, j of RT
-        cd* Ri = RT.data() + (size_t)i * nocc;
-        cd* Rj = RT.data() + (size_t)j * nocc;
-        for (int p = 0; p < nocc; ++p) {
-          const double xr = Ri[p].real(), xi_ = Ri[p].imag(), yr = Rj[p].real(), yi = Rj[p].imag();
-          Ri[p] = cd(c * xr + sr * yr - si * yi, c * xi_ + sr * yi + si * yr);   // c x + s y
-          Rj[p] = cd(-sr * xr - si * xi_ + c * yr, -sr * xi_ + si * xr + c * yi);  // -conj(s) x + c y
-        }
-      }
-    done = sweep + 1;
-    if (maxrot < tol) {
-      converged = true;
-      break;
     }
-  }
-  std::vector<cd> R((size_t)nocc * nocc);
-  for (int n = 0; n < nocc; ++n)
-    for (int v = 0; v < nocc; ++v) R[(size_t)v * nocc + n] = RT[(size_t)n * nocc + v];
-  // the library's convention for the localised frame: phi_v = sum_n U_vn phi~_n, so U = conj(R)
-  cd* u = reinterpret_cast<cd*>(U);
-  for (size_t e = 0; e < R.size(); ++e) u[e] = std::conj(R[e]);
-  if (spread) {
-    spread[0] = before;
-    spread[1] = spread_of(M, nocc, a);
-  }
-  if (sweeps) *sweeps = done;
-  return converged ? TDDFT_OK : fail(TDDFT_ENOTCONV, "localisation sweeps did not converge (U is the last iterate)");
+    const double before = spread_of(M, nocc, a);
+    // accumulated rotation, stored transposed (RT[n][v] = R_vn, w_n = sum_v R_vn phi_v) so that the
+    // column updates of R run over contiguous memory
+    std::vector<cd> RT((size_t)nocc * nocc, cd(0.0, 0.0));
+    for (int i = 0; i < nocc; ++i) RT[(size_t)i * nocc + i] = 1.0;
+    int done = 0;
+    bool converged = max_sweeps == 0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      double maxrot = 0.0;
+      for (int i = 0; i < nocc; ++i)
+        for (int j = i + 1; j < nocc; ++j) {
+          // diagonal difference of every matrix after the rotation = h_k . v for a unit v; the best
+          // v is the top eigenvector of G = sum_k h_k h_k^T, h_k = (M_ii - M_jj, 2 Re M_ij, 2 Im M_ij)
+          double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+          for (int k = 0; k < 6; ++k) {
+            const std::vector<cd>& Mk = M[k];
+            const double hk[3] = {Mk[(size_t)i * nocc + i].real() - Mk[(size_t)j * nocc + j].real(),
+                                  2.0 * Mk[(size_t)i * nocc + j].real(), 2.0 * Mk[(size_t)i * nocc + j].imag()};
+            for (int p = 0; p < 3; ++p)
+              for (int q = 0; q < 3; ++q) G[p][q] += hk[p] * hk[q];
+          }
+          double v[3];
+          top_eigvec3(G, v);
+          if (v[0] < 0.0) v[0] = -v[0], v[1] = -v[1], v[2] = -v[2];
+          const double c = std::sqrt(0.5 * (1.0 + std::min(1.0, v[0])));
+          const double sr = v[1] / (2.0 * c), si = -v[2] / (2.0 * c);  // s = sr + i si
+          const double as = std::hypot(sr, si);
+          if (!(as > 1e-15)) continue;
+          maxrot = std::max(maxrot, as);
+          // R = identity but R_ii = c, R_ji = s, R_ij = -conj(s), R_jj = c. Each M is Hermitian, so
+          // M <- R^H M R is its rows i, j updated (row i <- c row i + conj(s) row j, row j <- -s row i
+          // + c row j) off the 2 x 2 block, the columns i, j their conjugates, and the block itself
+          for (int k = 0; k < 6; ++k) {
+            cd* X = M[k].data();
+            cd* Xi = X + (size_t)i * nocc;
+            cd* Xj = X + (size_t)j * nocc;
+            const cd a = Xi[i], b = Xi[j], d = Xj[j];
+            for (int q = 0; q < nocc; ++q) {
+              const double air = Xi[q].real(), aii = Xi[q].imag(), bjr = Xj[q].real(), bji = Xj[q].imag();
+              const double nir = c * air + sr * bjr + si * bji, nii = c * aii + sr * bji - si * bjr;
+              const double njr = -sr * air + si * aii + c * bjr, nji = -sr * aii - si * air + c * bji;
+              Xi[q] = cd(nir, nii);
+              Xj[q] = cd(njr, nji);
+              X[(size_t)q * nocc + i] = cd(nir, -nii);
+              X[(size_t)q * nocc + j] = cd(njr, -nji);
+            }
+            // the 2 x 2 block: M'_ii = c^2 a + |s|^2 d + 2c Re(s b), M'_jj = |s|^2 a + c^2 d - 2c Re(s b),
+            // M'_ij = c^2 b - conj(s)^2 conj(b) + c conj(s) (d - a)
+            const cd sc(sr, -si);  // conj(s)
+            const double resb = sr * b.real() - si * b.imag();
+            const double s2 = sr * sr + si * si;
+            const double mii = c * c * a.real() + s2 * d.real() + 2.0 * c * resb;
+            const double mjj = s2 * a.real() + c * c * d.real() - 2.0 * c * resb;
+            const cd mij = c * c * b - sc * sc * std::conj(b) + c * sc * (d - a);
+            Xi[i] = mii;
+            Xj[j] = mjj;
+            Xi[j] = mij;
+            Xj[i] = std::conj(mij);
+          }
+          // R_total <- R_total R: columns i, j of R = rows i, j of RT
+          cd* Ri = RT.data() + (size_t)i * nocc;
+          cd* Rj = RT.data() + (size_t)j * nocc;
+          for (int p = 0; p < nocc; ++p) {
+            const double xr = Ri[p].real(), xi_ = Ri[p].imag(), yr = Rj[p].real(), yi = Rj[p].imag();
+            Ri[p] = cd(c * xr + sr * yr - si * yi, c * xi_ + sr * yi + si * yr);   // c x + s y
+            Rj[p] = cd(-sr * xr - si * xi_ + c * yr, -sr * xi_ + si * xr + c * yi);  // -conj(s) x + c y
+          }
+        }
+      done = sweep + 1;
+      if (maxrot < tol) {
+        converged = true;
+        break;
+      }
+    }
+    std::vector<cd> R((size_t)nocc * nocc);
+    for (int n = 0; n < nocc; ++n)
+      for (int v = 0; v < nocc; ++v) R[(size_t)v * nocc + n] = RT[(size_t)n * nocc + v];
+    // the library's convention for the localised frame: phi_v = sum_n U_vn phi~_n, so U = conj(R)
+    cd* u = reinterpret_cast<cd*>(U);
+    for (size_t e = 0; e < R.size(); ++e) u[e] = std::conj(R[e]);
+    if (spread) {
+      spread[0] = before;
+      spread[1] = spread_of(M, nocc, a);
+    }
+    if (sweeps) *sweeps = done;
+    return converged ? TDDFT_OK : fail(TDDFT_ENOTCONV, "localisation sweeps did not converge (U is the last iterate)");
+  });
 }
 
 tddft_status tddft_exchange_grid(int n, double a, double ecut, int precision, int* n_exchange) {
-  if (!n_exchange) return fail(TDDFT_EINVAL, "null output");
-  if (precision != TDDFT_PREC_FP64 && precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
-  if (!supported_n(n, precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
-  std::vector<Miller> s;
-  STATUS_TRY(build_sphere(n, a, ecut, s));
-  *n_exchange = exchange_grid_for(n, precision, s);
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!n_exchange) return fail(TDDFT_EINVAL, "null output");
+    if (precision != TDDFT_PREC_FP64 && precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
+    if (!supported_n(n, precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
+    std::vector<Miller> s;
+    STATUS_TRY(build_sphere(n, a, ecut, s));
+    *n_exchange = exchange_grid_for(n, precision, s);
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_profile_enable(int enable) {
-  g_prof.on = enable != 0;
-  g_prof.used = 0;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    g_prof.on = enable != 0;
+    g_prof.used = 0;
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_profile_read(double* ms, long long* launches, double* bytes, long long* total_launches) {
-  if (total_launches) *total_launches = g_prof.launches;
-  for (int c = 0; c < TDDFT_PROFILE_CLASSES; ++c) {
-    if (ms) ms[c] = 0.0;
-    if (launches) launches[c] = 0;
-    if (bytes) bytes[c] = 0.0;
-  }
-  for (size_t i = 0; i < g_prof.used; ++i) {
-    CUDA_TRY(cudaEventSynchronize(g_prof.pool[2 * i + 1]));
-    float t = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&t, g_prof.pool[2 * i], g_prof.pool[2 * i + 1]));
-    const int c = g_prof.cls[i];
-    if (ms) ms[c] += t;
-    if (launches) launches[c] += 1;
-    if (bytes) bytes[c] += g_prof.bytes[i];
-  }
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (total_launches) *total_launches = g_prof.launches;
+    for (int c = 0; c < TDDFT_PROFILE_CLASSES; ++c) {
+      if (ms) ms[c] = 0.0;
+      if (launches) launches[c] = 0;
+      if (bytes) bytes[c] = 0.0;
+    }
+    for (size_t i = 0; i < g_prof.used; ++i) {
+      CUDA_TRY(cudaEventSynchronize(g_prof.pool[2 * i + 1]));
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, g_prof.pool[2 * i], g_prof.pool[2 * i + 1]));
+      const int c = g_prof.cls[i];
+      if (ms) ms[c] += t;
+      if (launches) launches[c] += 1;
+      if (bytes) bytes[c] += g_prof.bytes[i];
+    }
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_destroy(tddft_handle h) {
-  if (!h) return TDDFT_OK;
-  // a cached multi-system graph that refers to this handle is dropped
-  if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
-    cudaGraphExecDestroy(g_multi.exec);
-    g_multi.exec = nullptr;
-    g_multi.key.k.clear();
-  }
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->cap) cudaStreamDestroy(h->cap);
-  for (void* p : h->allocations) cudaFree(p);
-  if (h->tau_cache) cudaFree(h->tau_cache);
-  if (h->tau_all) cudaFree(h->tau_all);
-  if (h->tc_pack) cudaFree(h->tc_pack);
-  if (h->xsub) tddft_destroy(h->xsub);
-  delete h;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return TDDFT_OK;
+    // a cached multi-system graph that refers to this handle is dropped
+    if (g_multi.exec && std::find(g_multi.key.k.begin(), g_multi.key.k.end(), (const void*)h) != g_multi.key.k.end()) {
+      cudaGraphExecDestroy(g_multi.exec);
+      g_multi.exec = nullptr;
+      g_multi.key.k.clear();
+    }
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (void* p : h->allocations) cudaFree(p);
+    if (h->tau_cache) cudaFree(h->tau_cache);
+    if (h->tau_all) cudaFree(h->tau_all);
+    if (h->tc_pack) cudaFree(h->tc_pack);
+    if (h->xsub) tddft_destroy(h->xsub);
+    delete h;
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_init_system(const tddft_desc* desc, const tddft_inputs* in, void* stream, tddft_handle* out) {
-  if (!desc || !in || !out) return fail(TDDFT_EINVAL, "null argument");
-  *out = nullptr;
-  const tddft_desc& d = *desc;
-  if (d.spin_mode != TDDFT_SPIN_CONSERVING && d.spin_mode != TDDFT_SPIN_FLIP)
-    return fail(TDDFT_EINVAL, "unknown spin mode");
-  if (d.precision != TDDFT_PREC_FP64 && d.precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
-  if (!supported_n(d.n, d.precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(d.n));
-  if (d.nocc_src < 1 || d.nb_max < 1) return fail(TDDFT_EINVAL, "nocc_src and nb_max must be >= 1");
-  if (d.spin_mode == TDDFT_SPIN_CONSERVING && d.nocc_tgt != d.nocc_src)
-    return fail(TDDFT_EINVAL, "spin-conserving systems need nocc_tgt == nocc_src");
-  if (d.nocc_tgt < 1) return fail(TDDFT_EINVAL, "nocc_tgt must be >= 1");
-  if (d.term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
-  if (d.spin_mode == TDDFT_SPIN_FLIP && (d.term_mask & ~TDDFT_TERMS_ALL))
-    return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
-  if (!in->phi_src || !in->eps_src) return fail(TDDFT_EINVAL, "orbitals and eigenvalues are required");
-  if (d.spin_mode == TDDFT_SPIN_FLIP && !in->phi_tgt) return fail(TDDFT_EINVAL, "spin-flip needs phi_tgt");
-  std::vector<Miller> sph;
-  STATUS_TRY(build_sphere(d.n, d.a, d.ecut, sph));
-  if ((int)sph.size() < std::max(d.nocc_src, d.nocc_tgt))
-    return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
-  tddft_system* h = new tddft_system();
-  h->d = d;
-  h->n = d.n;
-  h->n3 = (long long)d.n * d.n * d.n;
-  h->npw = (int)sph.size();
-  cudaStream_t st = (cudaStream_t)stream;
-  tddft_status s = d.precision == TDDFT_PREC_FP64 ? init_impl<double>(h, in, st) : init_impl<float>(h, in, st);
-  if (s != TDDFT_OK) {
-    std::string msg = g_last_error;
-    tddft_destroy(h);
-    g_last_error = msg;
-    return s;
-  }
-  const int nx = exchange_grid_for(d.n, d.precision, sph);
-  if (nx < d.n) {
-    // the exchange terms on the nx grid: an internal system with the same orbitals and no
-    // local fields; without room for it the n grid serves (same result, more points)
-    tddft_desc dx = d;
-    dx.n = nx;
-    tddft_inputs ix = *in;
-    ix.vloc = nullptr;
-    ix.fxc = nullptr;
-    const std::string saved = g_last_error;
-    tddft_handle hx = nullptr;
-    if (tddft_init_system(&dx, &ix, stream, &hx) == TDDFT_OK) {
-      void* xpw = nullptr;
-      // the same sphere in the same order (it fits: N_x > 4M), so plane-wave rows are shared
-      if (hx->npw == h->npw && dalloc(h, &xpw, (size_t)d.nb_max * d.nocc_src * h->npw * h->esz()) == TDDFT_OK) {
-        h->xsub = hx;
-        h->x_pw = xpw;
-      } else {
-        tddft_destroy(hx);
-      }
+  return abi_guard([&]() -> tddft_status {
+    if (!desc || !in || !out) return fail(TDDFT_EINVAL, "null argument");
+    *out = nullptr;
+    const tddft_desc& d = *desc;
+    if (d.spin_mode != TDDFT_SPIN_CONSERVING && d.spin_mode != TDDFT_SPIN_FLIP)
+      return fail(TDDFT_EINVAL, "unknown spin mode");
+    if (d.precision != TDDFT_PREC_FP64 && d.precision != TDDFT_PREC_FP32) return fail(TDDFT_EINVAL, "unknown precision");
+    if (!supported_n(d.n, d.precision)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(d.n));
+    if (d.nocc_src < 1 || d.nb_max < 1) return fail(TDDFT_EINVAL, "nocc_src and nb_max must be >= 1");
+    if (d.spin_mode == TDDFT_SPIN_CONSERVING && d.nocc_tgt != d.nocc_src)
+      return fail(TDDFT_EINVAL, "spin-conserving systems need nocc_tgt == nocc_src");
+    if (d.nocc_tgt < 1) return fail(TDDFT_EINVAL, "nocc_tgt must be >= 1");
+    if (d.term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
+    if (d.spin_mode == TDDFT_SPIN_FLIP && (d.term_mask & ~TDDFT_TERMS_ALL))
+      return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
+    if (!in->phi_src || !in->eps_src) return fail(TDDFT_EINVAL, "orbitals and eigenvalues are required");
+    if (d.spin_mode == TDDFT_SPIN_FLIP && !in->phi_tgt) return fail(TDDFT_EINVAL, "spin-flip needs phi_tgt");
+    std::vector<Miller> sph;
+    STATUS_TRY(build_sphere(d.n, d.a, d.ecut, sph));
+    if ((int)sph.size() < std::max(d.nocc_src, d.nocc_tgt))
+      return fail(TDDFT_EINVAL, "sphere smaller than the number of orbitals");
+    tddft_system* h = new tddft_system();
+    h->d = d;
+    h->n = d.n;
+    h->n3 = (long long)d.n * d.n * d.n;
+    h->npw = (int)sph.size();
+    cudaStream_t st = (cudaStream_t)stream;
+    tddft_status s = d.precision == TDDFT_PREC_FP64 ? init_impl<double>(h, in, st) : init_impl<float>(h, in, st);
+    if (s != TDDFT_OK) {
+      std::string msg = g_last_error;
+      tddft_destroy(h);
+      g_last_error = msg;
+      return s;
     }
-    g_last_error = saved;
-  }
-  *out = h;
-  return TDDFT_OK;
+    const int nx = exchange_grid_for(d.n, d.precision, sph);
+    if (nx < d.n) {
+      // the exchange terms on the nx grid: an internal system with the same orbitals and no
+      // local fields; without room for it the n grid serves (same result, more points)
+      tddft_desc dx = d;
+      dx.n = nx;
+      tddft_inputs ix = *in;
+      ix.vloc = nullptr;
+      ix.fxc = nullptr;
+      const std::string saved = g_last_error;
+      tddft_handle hx = nullptr;
+      if (tddft_init_system(&dx, &ix, stream, &hx) == TDDFT_OK) {
+        void* xpw = nullptr;
+        // the same sphere in the same order (it fits: N_x > 4M), so plane-wave rows are shared
+        if (hx->npw == h->npw && dalloc(h, &xpw, (size_t)d.nb_max * d.nocc_src * h->npw * h->esz()) == TDDFT_OK) {
+          h->xsub = hx;
+          h->x_pw = xpw;
+        } else {
+          tddft_destroy(hx);
+        }
+      }
+      g_last_error = saved;
+    }
+    *out = h;
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_query(tddft_handle h, tddft_info* info) {
-  if (!h || !info) return fail(TDDFT_EINVAL, "null argument");
-  STATUS_TRY(check_device_flag(h, nullptr));
-  info->npw = h->npw;
-  info->n = h->n;
-  info->nb_chunk = h->nb_chunk;
-  info->precision = h->d.precision;
-  info->device_bytes = h->bytes;
-  info->n_exchange = h->n;
-  if (h->xsub) {
-    STATUS_TRY(check_device_flag(h->xsub, nullptr));
-    info->device_bytes += h->xsub->bytes;
-    if (h->use_xsub) info->n_exchange = h->xsub->n;
-  }
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !info) return fail(TDDFT_EINVAL, "null argument");
+    STATUS_TRY(check_device_flag(h, nullptr));
+    info->npw = h->npw;
+    info->n = h->n;
+    info->nb_chunk = h->nb_chunk;
+    info->precision = h->d.precision;
+    info->device_bytes = h->bytes;
+    info->n_exchange = h->n;
+    if (h->xsub) {
+      STATUS_TRY(check_device_flag(h->xsub, nullptr));
+      info->device_bytes += h->xsub->bytes;
+      if (h->use_xsub) info->n_exchange = h->xsub->n;
+    }
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_set_terms(tddft_handle h, unsigned term_mask) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
-  if (h->sf() && (term_mask & ~TDDFT_TERMS_ALL))
-    return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
-  h->d.term_mask = term_mask;  // a cached graph is re-captured when the mask differs
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (term_mask & ~TDDFT_TERMS_ZVEC) return fail(TDDFT_EINVAL, "unknown term bits");
+    if (h->sf() && (term_mask & ~TDDFT_TERMS_ALL))
+      return fail(TDDFT_ENOTSUP, "K2 terms are implemented for spin-conserving systems");
+    h->d.term_mask = term_mask;  // a cached graph is re-captured when the mask differs
+    return TDDFT_OK;
+  });
 }
 
 // tuning.k1d_cache: build the stored tau (synchronises) or release them
@@ -2615,245 +2646,265 @@ static bool z_kernel_ok(const tddft_system* h, int z) {
 }
 
 tddft_status tddft_set_tuning(tddft_handle h, const tddft_tuning* t) {
-  if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
-  if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 16)
-    return fail(TDDFT_EINVAL, "tile sizes must be >= 0 and k1d_block <= 16");
-  if (t->accumulate < -1 || t->accumulate > 1) return fail(TDDFT_EINVAL, "accumulate must be -1, 0 or 1");
-  if (t->graph < -1 || t->graph > 1) return fail(TDDFT_EINVAL, "graph must be -1, 0 or 1");
-  if (t->targets) h->tile_targets = t->targets;
-  if (t->sources) h->tile_sources = t->sources;
-  if (t->k1d_block) h->k1d_block = t->k1d_block;
-  if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
-  if (t->graph >= 0) h->use_graph = t->graph == 1;
-  if (t->prune >= 0) {
-    if (t->prune > 1) return fail(TDDFT_EINVAL, "prune must be 0 or 1");
-    h->prune = t->prune == 1;
-  }
-  if (t->projector >= 0) {
-    if (t->projector > 2) return fail(TDDFT_EINVAL, "projector must be 0, 1 or 2");
-    h->projector_tc = t->projector;
-  }
-  if (t->k1d_sparse >= 0) {
-    if (t->k1d_sparse > 2) return fail(TDDFT_EINVAL, "k1d_sparse must be 0, 1 or 2");
-    h->k1d_sparse = t->k1d_sparse;
-  }
-  if (t->z_kernel >= 0) {
-    if (t->z_kernel > 2) return fail(TDDFT_EINVAL, "z_kernel must be 0, 1 or 2");
-    const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
-    const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
-    if (t->z_kernel == 1 && !reg) return fail(TDDFT_EINVAL, "the register-resident z pass needs FP32 and n <= 80");
-    if (t->z_kernel == 2 && !pair)
-      return fail(TDDFT_EINVAL, "the paired z pass needs FP32, n <= 80 or n = 96, and a supported n / 2");
-    h->ops32.kc.z = t->z_kernel;
-    h->ops64.kc.z = t->z_kernel;
-  }
-  if (t->k1d_all >= 0) {
-    if (t->k1d_all > 1) return fail(TDDFT_EINVAL, "k1d_all must be 0 or 1");
-    h->k1d_all = t->k1d_all == 1;
-    if (!h->k1d_all && h->tau_all) {
-      CUDA_TRY(cudaDeviceSynchronize());
-      CUDA_TRY(cudaFree(h->tau_all));
-      h->bytes -= h->tau_all_bytes;
-      h->tau_all = nullptr;
-      h->tau_all_bytes = 0;
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
+    if (t->targets < 0 || t->sources < 0 || t->k1d_block < 0 || t->k1d_block > 16)
+      return fail(TDDFT_EINVAL, "tile sizes must be >= 0 and k1d_block <= 16");
+    if (t->accumulate < -1 || t->accumulate > 1) return fail(TDDFT_EINVAL, "accumulate must be -1, 0 or 1");
+    if (t->graph < -1 || t->graph > 1) return fail(TDDFT_EINVAL, "graph must be -1, 0 or 1");
+    if (t->targets) h->tile_targets = t->targets;
+    if (t->sources) h->tile_sources = t->sources;
+    if (t->k1d_block) h->k1d_block = t->k1d_block;
+    if (t->accumulate >= 0) h->accumulate = t->accumulate == 1 ? INV_ATOMIC : INV_ACCUM;
+    if (t->graph >= 0) h->use_graph = t->graph == 1;
+    if (t->prune >= 0) {
+      if (t->prune > 1) return fail(TDDFT_EINVAL, "prune must be 0 or 1");
+      h->prune = t->prune == 1;
     }
-    h->tau_all_tried = false;
-  }
-  if (t->xy_kernel >= 0) {
-    if (t->xy_kernel > 3) return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 3");
-    h->xy_lines = t->xy_kernel;
-  }
-  tddft_status cs = TDDFT_OK;
-  if (t->exchange_grid > 1) cs = fail(TDDFT_EINVAL, "exchange_grid must be 0 or 1");
-  if (t->k1d_cache > 1) cs = fail(TDDFT_EINVAL, "k1d_cache must be 0 or 1");
-  if (cs == TDDFT_OK && h->xsub) {
-    // the same schedule for the exchange-grid system (its z pass where that grid has it)
-    tddft_tuning tx = *t;
-    tx.k1d_cache = -1;
-    tx.exchange_grid = -1;
-    if (tx.z_kernel >= 0 && !z_kernel_ok(h->xsub, tx.z_kernel)) tx.z_kernel = -1;
-    cs = tddft_set_tuning(h->xsub, &tx);
-  }
-  if (cs == TDDFT_OK && (t->exchange_grid >= 0 || t->k1d_cache >= 0)) {
-    if (t->exchange_grid >= 0) h->use_xsub = t->exchange_grid == 1;
-    if (t->k1d_cache >= 0) h->k1d_cache_req = t->k1d_cache == 1;
-    cs = sync_tau_cache(h);
-  }
-  drop_graphs(h);  // the schedule changed: the next graph call captures again
-  return cs;
+    if (t->projector >= 0) {
+      if (t->projector > 2) return fail(TDDFT_EINVAL, "projector must be 0, 1 or 2");
+      h->projector_tc = t->projector;
+    }
+    if (t->k1d_sparse >= 0) {
+      if (t->k1d_sparse > 2) return fail(TDDFT_EINVAL, "k1d_sparse must be 0, 1 or 2");
+      h->k1d_sparse = t->k1d_sparse;
+    }
+    if (t->z_kernel >= 0) {
+      if (t->z_kernel > 2) return fail(TDDFT_EINVAL, "z_kernel must be 0, 1 or 2");
+      const bool reg = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.reg_ok : h->ops64.reg_ok;
+      const bool pair = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.pair_ok : h->ops64.pair_ok;
+      if (t->z_kernel == 1 && !reg) return fail(TDDFT_EINVAL, "the register-resident z pass needs FP32 and n <= 80");
+      if (t->z_kernel == 2 && !pair)
+        return fail(TDDFT_EINVAL, "the paired z pass needs FP32, n <= 80 or n = 96, and a supported n / 2");
+      h->ops32.kc.z = t->z_kernel;
+      h->ops64.kc.z = t->z_kernel;
+    }
+    if (t->k1d_all >= 0) {
+      if (t->k1d_all > 1) return fail(TDDFT_EINVAL, "k1d_all must be 0 or 1");
+      h->k1d_all = t->k1d_all == 1;
+      if (!h->k1d_all && h->tau_all) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaFree(h->tau_all));
+        h->bytes -= h->tau_all_bytes;
+        h->tau_all = nullptr;
+        h->tau_all_bytes = 0;
+      }
+      h->tau_all_tried = false;
+    }
+    if (t->xy_kernel >= 0) {
+      if (t->xy_kernel > 3) return fail(TDDFT_EINVAL, "xy_kernel must be 0, 1, 2 or 3");
+      h->xy_lines = t->xy_kernel;
+    }
+    tddft_status cs = TDDFT_OK;
+    if (t->exchange_grid > 1) cs = fail(TDDFT_EINVAL, "exchange_grid must be 0 or 1");
+    if (t->k1d_cache > 1) cs = fail(TDDFT_EINVAL, "k1d_cache must be 0 or 1");
+    if (cs == TDDFT_OK && h->xsub) {
+      // the same schedule for the exchange-grid system (its z pass where that grid has it)
+      tddft_tuning tx = *t;
+      tx.k1d_cache = -1;
+      tx.exchange_grid = -1;
+      if (tx.z_kernel >= 0 && !z_kernel_ok(h->xsub, tx.z_kernel)) tx.z_kernel = -1;
+      cs = tddft_set_tuning(h->xsub, &tx);
+    }
+    if (cs == TDDFT_OK && (t->exchange_grid >= 0 || t->k1d_cache >= 0)) {
+      if (t->exchange_grid >= 0) h->use_xsub = t->exchange_grid == 1;
+      if (t->k1d_cache >= 0) h->k1d_cache_req = t->k1d_cache == 1;
+      cs = sync_tau_cache(h);
+    }
+    drop_graphs(h);  // the schedule changed: the next graph call captures again
+    return cs;
+  });
 }
 
 tddft_status tddft_get_tuning(tddft_handle h, tddft_tuning* t) {
-  if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
-  t->targets = h->tile_targets;
-  t->sources = h->tile_sources;
-  t->k1d_block = h->k1d_block;
-  t->accumulate = h->accumulate == INV_ATOMIC ? 1 : 0;
-  t->batch_fields = h->ibuf_fields;
-  t->graph = h->use_graph ? 1 : 0;
-  const KernelChoice kc = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.kc : h->ops64.kc;
-  t->prune = h->prune ? 1 : 0;
-  t->z_kernel = kc.z;
-  t->projector = h->projector_tc;
-  t->k1d_sparse = h->k1d_sparse;
-  t->k1d_cache = h->k1d_cache_req ? 1 : 0;
-  t->exchange_grid = h->use_xsub ? 1 : 0;
-  t->xy_kernel = h->xy_lines;
-  t->k1d_all = h->k1d_all ? 1 : 0;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !t) return fail(TDDFT_EINVAL, "null argument");
+    t->targets = h->tile_targets;
+    t->sources = h->tile_sources;
+    t->k1d_block = h->k1d_block;
+    t->accumulate = h->accumulate == INV_ATOMIC ? 1 : 0;
+    t->batch_fields = h->ibuf_fields;
+    t->graph = h->use_graph ? 1 : 0;
+    const KernelChoice kc = h->d.precision == TDDFT_PREC_FP32 ? h->ops32.kc : h->ops64.kc;
+    t->prune = h->prune ? 1 : 0;
+    t->z_kernel = kc.z;
+    t->projector = h->projector_tc;
+    t->k1d_sparse = h->k1d_sparse;
+    t->k1d_cache = h->k1d_cache_req ? 1 : 0;
+    t->exchange_grid = h->use_xsub ? 1 : 0;
+    t->xy_kernel = h->xy_lines;
+    t->k1d_all = h->k1d_all ? 1 : 0;
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_apply_liouville(tddft_handle h, int nb, const void* A, void* LA, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
-  if (nb == 0) return TDDFT_OK;
-  if (!A || !LA) return fail(TDDFT_EINVAL, "null buffer");
-  if (A == LA) return fail(TDDFT_EINVAL, "A and LA must not alias");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->use_graph) return apply_graph(h, nb, A, LA, st);
-  return apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
+    if (nb == 0) return TDDFT_OK;
+    if (!A || !LA) return fail(TDDFT_EINVAL, "null buffer");
+    if (A == LA) return fail(TDDFT_EINVAL, "A and LA must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->use_graph) return apply_graph(h, nb, A, LA, st);
+    return apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
+  });
 }
 
 tddft_status tddft_apply_liouville_host(tddft_handle h, int nb, const void* A_host, void* LA_host, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
-  if (nb == 0) return TDDFT_OK;
-  if (!A_host || !LA_host) return fail(TDDFT_EINVAL, "null buffer");
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t bytes = (size_t)nb * h->d.nocc_src * h->npw * h->esz();
-  CUDA_TRY(cudaMemcpyAsync(h->b.io_a, A_host, bytes, cudaMemcpyHostToDevice, st));
-  STATUS_TRY(tddft_apply_liouville(h, nb, h->b.io_a, h->b.io_b, stream));
-  CUDA_TRY(cudaMemcpyAsync(LA_host, h->b.io_b, bytes, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  return check_device_flag(h, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (nb < 0 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max]");
+    if (nb == 0) return TDDFT_OK;
+    if (!A_host || !LA_host) return fail(TDDFT_EINVAL, "null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)nb * h->d.nocc_src * h->npw * h->esz();
+    CUDA_TRY(cudaMemcpyAsync(h->b.io_a, A_host, bytes, cudaMemcpyHostToDevice, st));
+    STATUS_TRY(tddft_apply_liouville(h, nb, h->b.io_a, h->b.io_b, stream));
+    CUDA_TRY(cudaMemcpyAsync(LA_host, h->b.io_b, bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return check_device_flag(h, st);
+  });
 }
 
 tddft_status tddft_apply_liouville_multi(int nsys, const tddft_handle* hs, const int* nb, const void* const* A,
                                          void* const* LA, void* stream) {
-  if (nsys < 1 || !hs || !nb || !A || !LA) return fail(TDDFT_EINVAL, "null or empty argument");
-  for (int i = 0; i < nsys; ++i) {
-    if (!hs[i]) return fail(TDDFT_EINVAL, "null handle in the list");
-    if (nb[i] < 0 || nb[i] > hs[i]->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max] for system " + std::to_string(i));
-    if (nb[i] > 0 && (!A[i] || !LA[i] || A[i] == LA[i])) return fail(TDDFT_EINVAL, "bad buffers for system " + std::to_string(i));
-    for (int j = 0; j < i; ++j)
-      if (hs[j] == hs[i]) return fail(TDDFT_EINVAL, "a handle appears twice (one workspace per handle)");
-  }
-  MultiKey key;
-  for (int i = 0; i < nsys; ++i) {
-    key.k.push_back(hs[i]);
-    key.k.push_back((const void*)(size_t)nb[i]);
-    key.k.push_back(A[i]);
-    key.k.push_back(LA[i]);
-    key.k.push_back((const void*)(size_t)hs[i]->d.term_mask);
-  }
-  if (!(g_multi.exec && g_multi.key == key)) {
-    if (g_multi.exec) {
-      cudaGraphExecDestroy(g_multi.exec);
-      g_multi.exec = nullptr;
+  return abi_guard([&]() -> tddft_status {
+    if (nsys < 1 || !hs || !nb || !A || !LA) return fail(TDDFT_EINVAL, "null or empty argument");
+    for (int i = 0; i < nsys; ++i) {
+      if (!hs[i]) return fail(TDDFT_EINVAL, "null handle in the list");
+      if (nb[i] < 0 || nb[i] > hs[i]->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [0, nb_max] for system " + std::to_string(i));
+      if (nb[i] > 0 && (!A[i] || !LA[i] || A[i] == LA[i])) return fail(TDDFT_EINVAL, "bad buffers for system " + std::to_string(i));
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) return fail(TDDFT_EINVAL, "a handle appears twice (one workspace per handle)");
     }
-    STATUS_TRY(build_multi_graph(nsys, hs, nb, A, LA, &g_multi.exec, g_multi.events));
-    g_multi.key = key;
-  }
-  CUDA_TRY(cudaGraphLaunch(g_multi.exec, (cudaStream_t)stream));
-  return TDDFT_OK;
+    MultiKey key;
+    for (int i = 0; i < nsys; ++i) {
+      key.k.push_back(hs[i]);
+      key.k.push_back((const void*)(size_t)nb[i]);
+      key.k.push_back(A[i]);
+      key.k.push_back(LA[i]);
+      key.k.push_back((const void*)(size_t)hs[i]->d.term_mask);
+    }
+    if (!(g_multi.exec && g_multi.key == key)) {
+      if (g_multi.exec) {
+        cudaGraphExecDestroy(g_multi.exec);
+        g_multi.exec = nullptr;
+      }
+      STATUS_TRY(build_multi_graph(nsys, hs, nb, A, LA, &g_multi.exec, g_multi.events));
+      g_multi.key = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(g_multi.exec, (cudaStream_t)stream));
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_ace_build(tddft_handle h, int n_extra, const double* extra, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (n_extra < 0 || (n_extra > 0 && !extra)) return fail(TDDFT_EINVAL, "bad extra rows");
-  if (h->d.nocc_tgt + n_extra > h->npw) return fail(TDDFT_EINVAL, "more ACE vectors than plane waves");
-  cudaStream_t st = (cudaStream_t)stream;
-  drop_graphs(h);  // a captured graph would keep the old exchange path
-  if (h->d.precision == TDDFT_PREC_FP64) return ace_build_impl<double>(h, n_extra, extra, st);
-  return ace_build_impl<float>(h, n_extra, extra, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (n_extra < 0 || (n_extra > 0 && !extra)) return fail(TDDFT_EINVAL, "bad extra rows");
+    if (h->d.nocc_tgt + n_extra > h->npw) return fail(TDDFT_EINVAL, "more ACE vectors than plane waves");
+    cudaStream_t st = (cudaStream_t)stream;
+    drop_graphs(h);  // a captured graph would keep the old exchange path
+    if (h->d.precision == TDDFT_PREC_FP64) return ace_build_impl<double>(h, n_extra, extra, st);
+    return ace_build_impl<float>(h, n_extra, extra, st);
+  });
 }
 
 tddft_status tddft_set_localization(tddft_handle h, const double* U, double s_thr, double* S, int* kept_pairs,
                                     void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (U && !(s_thr >= 0.0)) return fail(TDDFT_EINVAL, "s_thr must be >= 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64) return localization_impl<double>(h, U, s_thr, S, kept_pairs, st);
-  return localization_impl<float>(h, U, s_thr, S, kept_pairs, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (U && !(s_thr >= 0.0)) return fail(TDDFT_EINVAL, "s_thr must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->d.precision == TDDFT_PREC_FP64) return localization_impl<double>(h, U, s_thr, S, kept_pairs, st);
+    return localization_impl<float>(h, U, s_thr, S, kept_pairs, st);
+  });
 }
 
 tddft_status tddft_ace_enable(tddft_handle h, int enable) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (enable && !h->ace_xi) return fail(TDDFT_EINVAL, "ACE has not been built");
-  h->ace_on = enable != 0;
-  drop_graphs(h);
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (enable && !h->ace_xi) return fail(TDDFT_EINVAL, "ACE has not been built");
+    h->ace_on = enable != 0;
+    drop_graphs(h);
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_autotune(tddft_handle h, int nb, const void* A, void* LA, void* stream, tddft_tuning* best) {
-  if (!h || !A || !LA) return fail(TDDFT_EINVAL, "null argument");
-  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
-  cudaStream_t st = (cudaStream_t)stream;
-  struct Cand {
-    int tt, ks, acc, kb;
-  };
-  const Cand cands[] = {{64, 8, 1, 16}, {128, 8, 1, 16}, {32, 8, 1, 16}, {64, 16, 1, 16}, {16, 8, 1, 16},
-                        {32, 4, 1, 16}, {32, 8, 0, 16}, {8, 8, 1, 8}};
-  cudaEvent_t e0, e1;
-  CUDA_TRY(cudaEventCreate(&e0));
-  CUDA_TRY(cudaEventCreate(&e1));
-  const bool graph = h->use_graph;
-  h->use_graph = false;
-  float best_ms = 1e30f;
-  Cand bc = cands[0];
-  tddft_status s = TDDFT_OK;
-  auto set_tiles = [h](const Cand& c) {
-    for (tddft_system* x : {h, h->xsub}) {
-      if (!x) continue;
-      x->tile_targets = c.tt;
-      x->tile_sources = c.ks;
-      x->accumulate = c.acc ? INV_ATOMIC : INV_ACCUM;
-      x->k1d_block = c.kb;
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !A || !LA) return fail(TDDFT_EINVAL, "null argument");
+    if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Cand {
+      int tt, ks, acc, kb;
+    };
+    const Cand cands[] = {{64, 8, 1, 16}, {128, 8, 1, 16}, {32, 8, 1, 16}, {64, 16, 1, 16}, {16, 8, 1, 16},
+                          {32, 4, 1, 16}, {32, 8, 0, 16}, {8, 8, 1, 8}};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const bool graph = h->use_graph;
+    h->use_graph = false;
+    float best_ms = 1e30f;
+    Cand bc = cands[0];
+    tddft_status s = TDDFT_OK;
+    auto set_tiles = [h](const Cand& c) {
+      for (tddft_system* x : {h, h->xsub}) {
+        if (!x) continue;
+        x->tile_targets = c.tt;
+        x->tile_sources = c.ks;
+        x->accumulate = c.acc ? INV_ATOMIC : INV_ACCUM;
+        x->k1d_block = c.kb;
+      }
+    };
+    for (const Cand& c : cands) {
+      set_tiles(c);
+      s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);  // warm
+      if (s != TDDFT_OK) break;
+      cudaEventRecord(e0, st);
+      s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
+      if (s != TDDFT_OK) break;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        s = fail(TDDFT_ECUDA, "autotune timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        bc = c;
+      }
     }
-  };
-  for (const Cand& c : cands) {
-    set_tiles(c);
-    s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);  // warm
-    if (s != TDDFT_OK) break;
-    cudaEventRecord(e0, st);
-    s = apply_dispatch(h, nb, A, LA, h->d.term_mask, st);
-    if (s != TDDFT_OK) break;
-    cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      s = fail(TDDFT_ECUDA, "autotune timing failed");
-      break;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->use_graph = graph;
+    set_tiles(bc);
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      bc = c;
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  h->use_graph = graph;
-  set_tiles(bc);
-  if (h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  if (s != TDDFT_OK) return s;
-  if (best) STATUS_TRY(tddft_get_tuning(h, best));
-  return TDDFT_OK;
+    if (s != TDDFT_OK) return s;
+    if (best) STATUS_TRY(tddft_get_tuning(h, best));
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_apply_liouville_adjoint(tddft_handle h, int nb, const void* X, const double* w, double* omega,
                                            void* grad_phi, double* grad_vloc, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (h->ace_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact exchange; disable ACE first");
-  if (h->loc_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact K1d; disable the localised frame first");
-  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
-  if (!X || !w || !omega || !grad_phi) return fail(TDDFT_EINVAL, "null buffer");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64)
-    return adjoint_impl<double>(h, nb, (const cplx<double>*)X, w, omega, (cplx<double>*)grad_phi, grad_vloc, st);
-  return adjoint_impl<float>(h, nb, (const cplx<float>*)X, w, omega, (cplx<float>*)grad_phi, grad_vloc, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (h->ace_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact exchange; disable ACE first");
+    if (h->loc_on) return fail(TDDFT_ENOTSUP, "the adjoint differentiates the exact K1d; disable the localised frame first");
+    if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+    if (!X || !w || !omega || !grad_phi) return fail(TDDFT_EINVAL, "null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->d.precision == TDDFT_PREC_FP64)
+      return adjoint_impl<double>(h, nb, (const cplx<double>*)X, w, omega, (cplx<double>*)grad_phi, grad_vloc, st);
+    return adjoint_impl<float>(h, nb, (const cplx<float>*)X, w, omega, (cplx<float>*)grad_phi, grad_vloc, st);
+  });
 }
 
 }  // extern "C"
@@ -2918,15 +2969,17 @@ static tddft_status relaxed_density_impl(tddft_system* h, int nb, const cplx<T>*
 
 extern "C" tddft_status tddft_relaxed_density(tddft_handle h, int nb, const void* X, const void* Z, const double* w,
                                               double* drho, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
-  if (!X || !w || !drho) return fail(TDDFT_EINVAL, "null buffer");
-  if (Z && h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector part is implemented for spin-conserving systems");
-  if (h->loc_on) return fail(TDDFT_ENOTSUP, "disable the localised frame first (the density uses the given orbitals)");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64)
-    return relaxed_density_impl<double>(h, nb, (const cplx<double>*)X, (const cplx<double>*)Z, w, drho, st);
-  return relaxed_density_impl<float>(h, nb, (const cplx<float>*)X, (const cplx<float>*)Z, w, drho, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+    if (!X || !w || !drho) return fail(TDDFT_EINVAL, "null buffer");
+    if (Z && h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector part is implemented for spin-conserving systems");
+    if (h->loc_on) return fail(TDDFT_ENOTSUP, "disable the localised frame first (the density uses the given orbitals)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->d.precision == TDDFT_PREC_FP64)
+      return relaxed_density_impl<double>(h, nb, (const cplx<double>*)X, (const cplx<double>*)Z, w, drho, st);
+    return relaxed_density_impl<float>(h, nb, (const cplx<float>*)X, (const cplx<float>*)Z, w, drho, st);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -3107,36 +3160,40 @@ static tddft_status zvector_impl(tddft_system* h, int nb, const cplx<T>* U, cplx
 extern "C" {
 
 tddft_status tddft_zvector_rhs(tddft_handle h, int nb, const void* X, void* U, void* stream) {
-  if (!h) return fail(TDDFT_EINVAL, "null handle");
-  if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
-  if (h->ace_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact exchange; disable ACE first");
-  if (h->loc_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact K1d; disable the localised frame first");
-  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
-  if (!X || !U) return fail(TDDFT_EINVAL, "null buffer");
-  if (X == U) return fail(TDDFT_EINVAL, "X and U must not alias");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64)
-    return zvector_rhs_impl<double>(h, nb, (const cplx<double>*)X, (cplx<double>*)U, st);
-  return zvector_rhs_impl<float>(h, nb, (const cplx<float>*)X, (cplx<float>*)U, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h) return fail(TDDFT_EINVAL, "null handle");
+    if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
+    if (h->ace_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact exchange; disable ACE first");
+    if (h->loc_on) return fail(TDDFT_ENOTSUP, "the right-hand side differentiates the exact K1d; disable the localised frame first");
+    if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+    if (!X || !U) return fail(TDDFT_EINVAL, "null buffer");
+    if (X == U) return fail(TDDFT_EINVAL, "X and U must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->d.precision == TDDFT_PREC_FP64)
+      return zvector_rhs_impl<double>(h, nb, (const cplx<double>*)X, (cplx<double>*)U, st);
+    return zvector_rhs_impl<float>(h, nb, (const cplx<float>*)X, (cplx<float>*)U, st);
+  });
 }
 
 tddft_status tddft_zvector_solve(tddft_handle h, int nb, const void* U, void* Z, const tddft_zvector_opts* opts,
                                  int* iterations, int* exact_iterations, double* residual, void* stream) {
-  if (!h || !opts) return fail(TDDFT_EINVAL, "null argument");
-  if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
-  if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
-  if (!U || !Z) return fail(TDDFT_EINVAL, "null buffer");
-  if (U == Z) return fail(TDDFT_EINVAL, "U and Z must not alias");
-  if (!(opts->tol > 0.0) || !(opts->lambda_thr >= 0.0) || opts->max_iter < 0 || opts->precondition < 0 ||
-      opts->precondition > 1)
-    return fail(TDDFT_EINVAL, "need tol > 0, lambda_thr >= 0, max_iter >= 0, precondition 0 or 1");
-  if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "the Z-vector solve needs the projector term");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->d.precision == TDDFT_PREC_FP64)
-    return zvector_impl<double>(h, nb, (const cplx<double>*)U, (cplx<double>*)Z, *opts, iterations, exact_iterations,
-                                residual, st);
-  return zvector_impl<float>(h, nb, (const cplx<float>*)U, (cplx<float>*)Z, *opts, iterations, exact_iterations,
-                             residual, st);
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !opts) return fail(TDDFT_EINVAL, "null argument");
+    if (h->sf()) return fail(TDDFT_ENOTSUP, "the Z-vector equation is implemented for spin-conserving systems");
+    if (nb < 1 || nb > h->d.nb_max) return fail(TDDFT_EINVAL, "nb outside [1, nb_max]");
+    if (!U || !Z) return fail(TDDFT_EINVAL, "null buffer");
+    if (U == Z) return fail(TDDFT_EINVAL, "U and Z must not alias");
+    if (!(opts->tol > 0.0) || !(opts->lambda_thr >= 0.0) || opts->max_iter < 0 || opts->precondition < 0 ||
+        opts->precondition > 1)
+      return fail(TDDFT_EINVAL, "need tol > 0, lambda_thr >= 0, max_iter >= 0, precondition 0 or 1");
+    if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "the Z-vector solve needs the projector term");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->d.precision == TDDFT_PREC_FP64)
+      return zvector_impl<double>(h, nb, (const cplx<double>*)U, (cplx<double>*)Z, *opts, iterations, exact_iterations,
+                                  residual, st);
+    return zvector_impl<float>(h, nb, (const cplx<float>*)U, (cplx<float>*)Z, *opts, iterations, exact_iterations,
+                               residual, st);
+  });
 }
 
 }  // extern "C"
@@ -3490,147 +3547,155 @@ extern "C" {
 
 tddft_status tddft_davidson_create(tddft_handle h, int nroots, int nguess, const double* X0, int max_basis,
                                    void* stream, tddft_dav_handle* out) {
-  if (!h || !X0 || !out) return fail(TDDFT_EINVAL, "null argument");
-  *out = nullptr;
-  if (nroots < 1 || nguess < nroots) return fail(TDDFT_EINVAL, "need 1 <= nroots <= nguess");
-  if (max_basis < 2 * nroots || max_basis < nguess) return fail(TDDFT_EINVAL, "max_basis must be >= 2*nroots and >= nguess");
-  if (max_basis > JACOBI_MAX_N)
-    return fail(TDDFT_EINVAL, "max_basis above the Rayleigh-Ritz solver's limit of " + std::to_string(JACOBI_MAX_N));
-  if (h->d.nb_max < nroots) return fail(TDDFT_EINVAL, "the handle's nb_max must be >= nroots");
-  if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "Davidson needs the projector term");
-  if (h->d.term_mask & ~TDDFT_TERMS_ALL)
-    return fail(TDDFT_EINVAL, "Davidson diagonalises the Tamm-Dancoff operator: no K2 terms");
-  cudaStream_t st = (cudaStream_t)stream;
-  tddft_davidson* d = new tddft_davidson();
-  d->h = h;
-  d->nroots = nroots;
-  d->max_basis = max_basis;
-  d->len = (long long)h->d.nocc_src * h->npw;
-  d->nsplit = (int)std::max<long long>(1, std::min<long long>(64, d->len / 4096));
-  const size_t vb = (size_t)d->len * sizeof(cplx<double>);
-  tddft_status s = TDDFT_OK;
-  auto A = [&](void** p, size_t b) {
-    if (s == TDDFT_OK) s = dav_alloc(d, p, b);
-  };
-  A((void**)&d->V, vb * max_basis);
-  A((void**)&d->LV, vb * max_basis);
-  A((void**)&d->X, vb * nroots);
-  A((void**)&d->W, vb * nroots);
-  A((void**)&d->R, vb * std::max(nroots, nguess));
-  A(&d->tin, (size_t)d->len * h->esz() * h->d.nb_max);
-  A(&d->tout, (size_t)d->len * h->esz() * h->d.nb_max);
-  A((void**)&d->part, sizeof(cplx<double>) * d->nsplit * max_basis * max_basis);
-  A((void**)&d->small, sizeof(cplx<double>) * max_basis * max_basis);
-  A((void**)&d->g2h, sizeof(double) * h->npw);
-  A((void**)&d->eps, sizeof(double) * h->d.nocc_src);
-  A((void**)&d->nrm, sizeof(double) * max_basis);
-  A((void**)&d->evec, sizeof(cplx<double>) * max_basis * max_basis);
-  A((void**)&d->ritz, sizeof(cplx<double>) * max_basis * nroots);
-  A((void**)&d->info, sizeof(double) * (2 * nroots + 2));
-  if (s != TDDFT_OK) {
-    delete d;
-    return s;
-  }
-  // FP64 preconditioner tables
-  std::vector<Miller> sph;
-  tddft_status sb = build_sphere(h->n, h->d.a, h->d.ecut, sph);
-  if (sb != TDDFT_OK) {
-    delete d;
-    return sb;
-  }
-  const double tpiba = 2.0 * M_PI / h->d.a, tpiba2 = tpiba * tpiba;
-  std::vector<double> g2h(h->npw);
-  for (int i = 0; i < h->npw; ++i) g2h[i] = 0.5 * (tpiba2 * (double)sph[i].m2);
-  // the preconditioner's eigenvalues in FP64: the values given at set-up (the handle's
-  // device copy is in the working precision)
-  const std::vector<double>& eps = h->eps64;
-  cudaMemcpyAsync(d->g2h, g2h.data(), g2h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d->eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d->R, X0, vb * nguess, cudaMemcpyHostToDevice, st);
-  for (int i = 0; i < nguess && s == TDDFT_OK; ++i) s = dav_append(d, d->R + (long long)i * d->len, st);
-  if (s == TDDFT_OK) s = dav_apply(d, 0, st);
-  if (s == TDDFT_OK) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) s = fail(TDDFT_ECUDA, std::string("davidson create: ") + cudaGetErrorString(e));
-  }
-  if (s != TDDFT_OK) {
-    delete d;
-    return s;
-  }
-  *out = d;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!h || !X0 || !out) return fail(TDDFT_EINVAL, "null argument");
+    *out = nullptr;
+    if (nroots < 1 || nguess < nroots) return fail(TDDFT_EINVAL, "need 1 <= nroots <= nguess");
+    if (max_basis < 2 * nroots || max_basis < nguess) return fail(TDDFT_EINVAL, "max_basis must be >= 2*nroots and >= nguess");
+    if (max_basis > JACOBI_MAX_N)
+      return fail(TDDFT_EINVAL, "max_basis above the Rayleigh-Ritz solver's limit of " + std::to_string(JACOBI_MAX_N));
+    if (h->d.nb_max < nroots) return fail(TDDFT_EINVAL, "the handle's nb_max must be >= nroots");
+    if ((h->d.term_mask & TDDFT_TERM_PROJ) == 0) return fail(TDDFT_EINVAL, "Davidson needs the projector term");
+    if (h->d.term_mask & ~TDDFT_TERMS_ALL)
+      return fail(TDDFT_EINVAL, "Davidson diagonalises the Tamm-Dancoff operator: no K2 terms");
+    cudaStream_t st = (cudaStream_t)stream;
+    tddft_davidson* d = new tddft_davidson();
+    d->h = h;
+    d->nroots = nroots;
+    d->max_basis = max_basis;
+    d->len = (long long)h->d.nocc_src * h->npw;
+    d->nsplit = (int)std::max<long long>(1, std::min<long long>(64, d->len / 4096));
+    const size_t vb = (size_t)d->len * sizeof(cplx<double>);
+    tddft_status s = TDDFT_OK;
+    auto A = [&](void** p, size_t b) {
+      if (s == TDDFT_OK) s = dav_alloc(d, p, b);
+    };
+    A((void**)&d->V, vb * max_basis);
+    A((void**)&d->LV, vb * max_basis);
+    A((void**)&d->X, vb * nroots);
+    A((void**)&d->W, vb * nroots);
+    A((void**)&d->R, vb * std::max(nroots, nguess));
+    A(&d->tin, (size_t)d->len * h->esz() * h->d.nb_max);
+    A(&d->tout, (size_t)d->len * h->esz() * h->d.nb_max);
+    A((void**)&d->part, sizeof(cplx<double>) * d->nsplit * max_basis * max_basis);
+    A((void**)&d->small, sizeof(cplx<double>) * max_basis * max_basis);
+    A((void**)&d->g2h, sizeof(double) * h->npw);
+    A((void**)&d->eps, sizeof(double) * h->d.nocc_src);
+    A((void**)&d->nrm, sizeof(double) * max_basis);
+    A((void**)&d->evec, sizeof(cplx<double>) * max_basis * max_basis);
+    A((void**)&d->ritz, sizeof(cplx<double>) * max_basis * nroots);
+    A((void**)&d->info, sizeof(double) * (2 * nroots + 2));
+    if (s != TDDFT_OK) {
+      delete d;
+      return s;
+    }
+    // FP64 preconditioner tables
+    std::vector<Miller> sph;
+    tddft_status sb = build_sphere(h->n, h->d.a, h->d.ecut, sph);
+    if (sb != TDDFT_OK) {
+      delete d;
+      return sb;
+    }
+    const double tpiba = 2.0 * M_PI / h->d.a, tpiba2 = tpiba * tpiba;
+    std::vector<double> g2h(h->npw);
+    for (int i = 0; i < h->npw; ++i) g2h[i] = 0.5 * (tpiba2 * (double)sph[i].m2);
+    // the preconditioner's eigenvalues in FP64: the values given at set-up (the handle's
+    // device copy is in the working precision)
+    const std::vector<double>& eps = h->eps64;
+    cudaMemcpyAsync(d->g2h, g2h.data(), g2h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d->eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d->R, X0, vb * nguess, cudaMemcpyHostToDevice, st);
+    for (int i = 0; i < nguess && s == TDDFT_OK; ++i) s = dav_append(d, d->R + (long long)i * d->len, st);
+    if (s == TDDFT_OK) s = dav_apply(d, 0, st);
+    if (s == TDDFT_OK) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) s = fail(TDDFT_ECUDA, std::string("davidson create: ") + cudaGetErrorString(e));
+    }
+    if (s != TDDFT_OK) {
+      delete d;
+      return s;
+    }
+    *out = d;
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_davidson_step(tddft_dav_handle d, double tol, int* n_converged, double* ritz_values,
                                  double* residual_norms, void* stream) {
-  if (!d || !n_converged || !ritz_values) return fail(TDDFT_EINVAL, "null argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  const int m = d->m, nr = d->nroots;
-  // Rayleigh-Ritz on the device: H = V^H L V (FP64), its lowest nr eigenpairs by Jacobi rotations
-  dav_overlap(d, d->V, m, d->LV, m, st);
-  { k_herm_jacobi<<<1, JACOBI_THREADS, 0, st>>>(d->small, d->evec, m, nr, d->info, d->ritz, d->info + 2 * nr);
-    note_launch(); }
-  // Ritz vectors X = V S, W = L V S, residuals R = W - theta X and their norms
-  const size_t vb = (size_t)d->len * sizeof(cplx<double>);
-  CUDA_TRY(cudaMemsetAsync(d->X, 0, vb * nr, st));
-  CUDA_TRY(cudaMemsetAsync(d->W, 0, vb * nr, st));
-  dav_combine(d, d->V, m, d->ritz, nr, 1.0, d->X, st);
-  dav_combine(d, d->LV, m, d->ritz, nr, 1.0, d->W, st);
-  { k_residuals<<<grid_for(d->len * nr, 256), 256, 0, st>>>(d->W, d->X, d->info, d->R, d->len, nr); note_launch(); }
-  { k_row_norms<<<nr, 256, 0, st>>>(d->R, d->len, d->info + nr); note_launch(); }
-  { k_copy_flag<<<1, 1, 0, st>>>(d->h->b.dev_err, d->info + 2 * nr + 1); note_launch(); }
-  STATUS_TRY(check_launch("davidson step"));
-  // the one host synchronisation: Ritz values, residual norms and both flags in one copy
-  std::vector<double> info(2 * nr + 2);
-  CUDA_TRY(cudaMemcpyAsync(info.data(), d->info, info.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  if (fault_take_wait())
-    return fail(TDDFT_ETIMEOUT, "a bounded device wait ran out (injected fault); results of the call are invalid");
-  if (info[2 * nr + 1] != 0.0) {
-    CUDA_TRY(cudaMemsetAsync(d->h->b.dev_err, 0, sizeof(int), st));
-    return fail(TDDFT_ETIMEOUT, "a bounded device wait (tensor-core projector) ran out; results of the call are invalid");
-  }
-  if (info[2 * nr] != 1.0) return fail(TDDFT_ENUMERIC, "subspace eigensolver did not converge");
-  d->theta.assign(info.begin(), info.begin() + nr);
-  int nconv = 0;
-  for (int i = 0; i < nr; ++i) {
-    const double rn = info[nr + i];
-    nconv += rn < tol;
-    ritz_values[i] = d->theta[i];
-    if (residual_norms) residual_norms[i] = rn;
-  }
-  *n_converged = nconv;
-  if (nconv == nr) return TDDFT_OK;
-  // corrections for the unconverged roots
-  std::vector<int> todo;
-  for (int i = 0; i < nr; ++i)
-    if (!(info[nr + i] < tol)) todo.push_back(i);
-  for (int i : todo)
-    { k_precondition<<<grid_for(d->len, 256), 256, 0, st>>>(d->R + (long long)i * d->len, d->g2h, d->eps, d->theta[i],
-                                                           d->h->npw, d->len, d->R + (long long)i * d->len); note_launch(); }
-  // restart on the Ritz vectors when the basis would overflow
-  if (d->m + (int)todo.size() > d->max_basis) {
-    CUDA_TRY(cudaMemcpyAsync(d->V, d->X, vb * nr, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(d->LV, d->W, vb * nr, cudaMemcpyDeviceToDevice, st));
-    d->m = nr;
-  }
-  const int m0 = d->m;
-  for (int i : todo) STATUS_TRY(dav_append(d, d->R + (long long)i * d->len, st));
-  STATUS_TRY(dav_apply(d, m0, st));
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!d || !n_converged || !ritz_values) return fail(TDDFT_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = d->m, nr = d->nroots;
+    // Rayleigh-Ritz on the device: H = V^H L V (FP64), its lowest nr eigenpairs by Jacobi rotations
+    dav_overlap(d, d->V, m, d->LV, m, st);
+    { k_herm_jacobi<<<1, JACOBI_THREADS, 0, st>>>(d->small, d->evec, m, nr, d->info, d->ritz, d->info + 2 * nr);
+      note_launch(); }
+    // Ritz vectors X = V S, W = L V S, residuals R = W - theta X and their norms
+    const size_t vb = (size_t)d->len * sizeof(cplx<double>);
+    CUDA_TRY(cudaMemsetAsync(d->X, 0, vb * nr, st));
+    CUDA_TRY(cudaMemsetAsync(d->W, 0, vb * nr, st));
+    dav_combine(d, d->V, m, d->ritz, nr, 1.0, d->X, st);
+    dav_combine(d, d->LV, m, d->ritz, nr, 1.0, d->W, st);
+    { k_residuals<<<grid_for(d->len * nr, 256), 256, 0, st>>>(d->W, d->X, d->info, d->R, d->len, nr); note_launch(); }
+    { k_row_norms<<<nr, 256, 0, st>>>(d->R, d->len, d->info + nr); note_launch(); }
+    { k_copy_flag<<<1, 1, 0, st>>>(d->h->b.dev_err, d->info + 2 * nr + 1); note_launch(); }
+    STATUS_TRY(check_launch("davidson step"));
+    // the one host synchronisation: Ritz values, residual norms and both flags in one copy
+    std::vector<double> info(2 * nr + 2);
+    CUDA_TRY(cudaMemcpyAsync(info.data(), d->info, info.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (fault_take_wait())
+      return fail(TDDFT_ETIMEOUT, "a bounded device wait ran out (injected fault); results of the call are invalid");
+    if (info[2 * nr + 1] != 0.0) {
+      CUDA_TRY(cudaMemsetAsync(d->h->b.dev_err, 0, sizeof(int), st));
+      return fail(TDDFT_ETIMEOUT, "a bounded device wait (tensor-core projector) ran out; results of the call are invalid");
+    }
+    if (info[2 * nr] != 1.0) return fail(TDDFT_ENUMERIC, "subspace eigensolver did not converge");
+    d->theta.assign(info.begin(), info.begin() + nr);
+    int nconv = 0;
+    for (int i = 0; i < nr; ++i) {
+      const double rn = info[nr + i];
+      nconv += rn < tol;
+      ritz_values[i] = d->theta[i];
+      if (residual_norms) residual_norms[i] = rn;
+    }
+    *n_converged = nconv;
+    if (nconv == nr) return TDDFT_OK;
+    // corrections for the unconverged roots
+    std::vector<int> todo;
+    for (int i = 0; i < nr; ++i)
+      if (!(info[nr + i] < tol)) todo.push_back(i);
+    for (int i : todo)
+      { k_precondition<<<grid_for(d->len, 256), 256, 0, st>>>(d->R + (long long)i * d->len, d->g2h, d->eps, d->theta[i],
+                                                             d->h->npw, d->len, d->R + (long long)i * d->len); note_launch(); }
+    // restart on the Ritz vectors when the basis would overflow
+    if (d->m + (int)todo.size() > d->max_basis) {
+      CUDA_TRY(cudaMemcpyAsync(d->V, d->X, vb * nr, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(d->LV, d->W, vb * nr, cudaMemcpyDeviceToDevice, st));
+      d->m = nr;
+    }
+    const int m0 = d->m;
+    for (int i : todo) STATUS_TRY(dav_append(d, d->R + (long long)i * d->len, st));
+    STATUS_TRY(dav_apply(d, m0, st));
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_davidson_vectors(tddft_dav_handle d, double* X_host, void* stream) {
-  if (!d || !X_host) return fail(TDDFT_EINVAL, "null argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  CUDA_TRY(cudaMemcpyAsync(X_host, d->X, (size_t)d->nroots * d->len * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!d || !X_host) return fail(TDDFT_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(X_host, d->X, (size_t)d->nroots * d->len * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_davidson_destroy(tddft_dav_handle d) {
-  delete d;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    delete d;
+    return TDDFT_OK;
+  });
 }
 }
 
@@ -3672,101 +3737,103 @@ NoallocDevice g_noalloc_dev[NOALLOC_MAX_DEVICES];
 extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut, double alpha, double kx_g0,
                                                      const void* phi_pw, const void* a_pw, void* out_pw,
                                                      void* stream) {
-  if (!phi_pw || !a_pw || !out_pw) return fail(TDDFT_EINVAL, "null buffer");
-  if (n > NOALLOC_MAX_N)
-    return fail(TDDFT_EINVAL, "grid size " + std::to_string(n) + " exceeds the allocation-free limit of " +
-                                  std::to_string(NOALLOC_MAX_N));
-  if (!supported_n(n, TDDFT_PREC_FP32)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(TDDFT_EINVAL, "device index out of range");
-  NoallocDevice& D = g_noalloc_dev[dev];
-  if (!D.ptr) {
-    // set-up, once per device: the device address of the scratch array
-    void* p = nullptr;
-    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    D.ptr = (unsigned char*)p;
-  }
-  unsigned char* base = D.ptr;
-  PlaneOps<float> o = plane_ops_for<float>(n);
-  if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
-  if (std::find(D.prepared.begin(), D.prepared.end(), n) == D.prepared.end()) {
-    // set-up, once per device and grid size: launch attributes and constant twiddles
-    CUDA_TRY(o.prepare());
-    D.prepared.push_back(n);
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  const long long n3 = (long long)n * n * n;
-  cplx<float>* tw = (cplx<float>*)(base + NA_TW);
-  float* kern = (float*)(base + NA_KERN);
-  int* pos = (int*)(base + NA_POS);
-  cplx<float>* phi_r = (cplx<float>*)(base + NA_PHI);
-  cplx<float>* a_r = (cplx<float>*)(base + NA_A);
-  cplx<float>* gbuf = (cplx<float>*)(base + NA_G);
+  return abi_guard([&]() -> tddft_status {
+    if (!phi_pw || !a_pw || !out_pw) return fail(TDDFT_EINVAL, "null buffer");
+    if (n > NOALLOC_MAX_N)
+      return fail(TDDFT_EINVAL, "grid size " + std::to_string(n) + " exceeds the allocation-free limit of " +
+                                    std::to_string(NOALLOC_MAX_N));
+    if (!supported_n(n, TDDFT_PREC_FP32)) return fail(TDDFT_EINVAL, "unsupported grid size " + std::to_string(n));
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(TDDFT_EINVAL, "device index out of range");
+    NoallocDevice& D = g_noalloc_dev[dev];
+    if (!D.ptr) {
+      // set-up, once per device: the device address of the scratch array
+      void* p = nullptr;
+      CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      D.ptr = (unsigned char*)p;
+    }
+    unsigned char* base = D.ptr;
+    PlaneOps<float> o = plane_ops_for<float>(n);
+    if (o.n != n) return fail(TDDFT_EINVAL, "unsupported grid size");
+    if (std::find(D.prepared.begin(), D.prepared.end(), n) == D.prepared.end()) {
+      // set-up, once per device and grid size: launch attributes and constant twiddles
+      CUDA_TRY(o.prepare());
+      D.prepared.push_back(n);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n3 = (long long)n * n * n;
+    cplx<float>* tw = (cplx<float>*)(base + NA_TW);
+    float* kern = (float*)(base + NA_KERN);
+    int* pos = (int*)(base + NA_POS);
+    cplx<float>* phi_r = (cplx<float>*)(base + NA_PHI);
+    cplx<float>* a_r = (cplx<float>*)(base + NA_A);
+    cplx<float>* gbuf = (cplx<float>*)(base + NA_G);
 
-  if (!(D.tables && D.n == n && D.a == a && D.ecut == ecut && D.kx_g0 == kx_g0)) {
-    // tables of this geometry (the same host arithmetic as a handle's set-up), uploaded
-    // only when the geometry differs from the one the array holds
-    std::vector<Miller> sph;
-    STATUS_TRY(build_sphere(n, a, ecut, sph));
-    const int npw_new = (int)sph.size();
-    std::vector<int> radices = plan_radices(n), rev(n);
-    for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
-    std::vector<cplx<float>> twh = host_twiddles<float>(n, radices);
-    if (twh.size() * sizeof(cplx<float>) > NA_KERN - NA_TW)
-      return fail(TDDFT_EINVAL, "twiddle table of grid " + std::to_string(n) + " exceeds its scratch region");
-    const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
-    auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
-    std::vector<float> kh(n3);
-    for (int kz = 0; kz < n; ++kz)
-      for (int ky = 0; ky < n; ++ky)
-        for (int kxx = 0; kxx < n; ++kxx) {
-          const long long m2 =
-              (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
-          const double vx = m2 == 0 ? kx_g0 : 4.0 * M_PI / (tpiba2 * (double)m2);
-          kh[((long long)rev[kz] * n + rev[ky]) * n + rev[kxx]] = (float)(vx / (double)n3);
-        }
-    std::vector<int> posh(npw_new);
-    for (int i = 0; i < npw_new; ++i)
-      posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
-    D.tables = false;
-    CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw_new * sizeof(int), cudaMemcpyHostToDevice, st));
-    D.tables = true;
-    D.n = n;
-    D.a = a;
-    D.ecut = ecut;
-    D.kx_g0 = kx_g0;
-    D.npw = npw_new;
-  }
-  const int npw = D.npw;
+    if (!(D.tables && D.n == n && D.a == a && D.ecut == ecut && D.kx_g0 == kx_g0)) {
+      // tables of this geometry (the same host arithmetic as a handle's set-up), uploaded
+      // only when the geometry differs from the one the array holds
+      std::vector<Miller> sph;
+      STATUS_TRY(build_sphere(n, a, ecut, sph));
+      const int npw_new = (int)sph.size();
+      std::vector<int> radices = plan_radices(n), rev(n);
+      for (int k = 0; k < n; ++k) rev[k] = dif_position(k, radices, n);
+      std::vector<cplx<float>> twh = host_twiddles<float>(n, radices);
+      if (twh.size() * sizeof(cplx<float>) > NA_KERN - NA_TW)
+        return fail(TDDFT_EINVAL, "twiddle table of grid " + std::to_string(n) + " exceeds its scratch region");
+      const double tpiba = 2.0 * M_PI / a, tpiba2 = tpiba * tpiba;
+      auto mof = [n](int k) { return k < n - n / 2 ? k : k - n; };
+      std::vector<float> kh(n3);
+      for (int kz = 0; kz < n; ++kz)
+        for (int ky = 0; ky < n; ++ky)
+          for (int kxx = 0; kxx < n; ++kxx) {
+            const long long m2 =
+                (long long)mof(kz) * mof(kz) + (long long)mof(ky) * mof(ky) + (long long)mof(kxx) * mof(kxx);
+            const double vx = m2 == 0 ? kx_g0 : 4.0 * M_PI / (tpiba2 * (double)m2);
+            kh[((long long)rev[kz] * n + rev[ky]) * n + rev[kxx]] = (float)(vx / (double)n3);
+          }
+      std::vector<int> posh(npw_new);
+      for (int i = 0; i < npw_new; ++i)
+        posh[i] = (rev[(sph[i].z % n + n) % n] * n + rev[(sph[i].y % n + n) % n]) * n + rev[(sph[i].x % n + n) % n];
+      D.tables = false;
+      CUDA_TRY(cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(kern, kh.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(pos, posh.data(), npw_new * sizeof(int), cudaMemcpyHostToDevice, st));
+      D.tables = true;
+      D.n = n;
+      D.a = a;
+      D.ecut = ecut;
+      D.kx_g0 = kx_g0;
+      D.npw = npw_new;
+    }
+    const int npw = D.npw;
 
-  // both orbitals to real space (cube cleared first: it keeps the previous call's contents)
-  const float s_in = (float)(1.0 / std::sqrt(a * a * a));
-  const cplx<float>* srcs[2] = {(const cplx<float>*)phi_pw, (const cplx<float>*)a_pw};
-  cplx<float>* dsts[2] = {phi_r, a_r};
-  for (int i = 0; i < 2; ++i) {
-    CUDA_TRY(cudaMemsetAsync(gbuf, 0, n3 * sizeof(cplx<float>), st));
-    { k_scatter<float><<<grid_for(npw, 256), 256, 0, st>>>(srcs[i], gbuf, pos, npw, 1, s_in, n3); note_launch(); }
-    o.z(Z_INV, gbuf, 1, nullptr, 1.f, tw, st);
-    PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
-    o.xy_inv(INV_WRITE, gbuf, dsts[i], nullptr, pm, 1, 1.f, tw, st);
-  }
-  // -alpha phi Conv_x[conj(phi) a], accumulated into the cleared trial field
-  PairMap pp{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
-  o.xy_fwd(XY_PRODUCT, phi_r, a_r, pp, 1, gbuf, tw, st);
-  o.z(Z_CONV, gbuf, 1, kern, 1.f, tw, st);
-  CUDA_TRY(cudaMemsetAsync(a_r, 0, n3 * sizeof(cplx<float>), st));
-  o.xy_inv(INV_ACCUM, gbuf, a_r, phi_r, pp, 1, (float)(-alpha), tw, st);
-  // back to plane waves on the sphere
-  PairMap pl{1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0};
-  o.xy_fwd(XY_LOAD, nullptr, a_r, pl, 1, gbuf, tw, st);
-  o.z(Z_FWD, gbuf, 1, nullptr, 1.f, tw, st);
-  const float s_out = (float)(std::sqrt(a * a * a) / (double)n3);
-  { k_gather<float><<<grid_for(npw, 256), 256, 0, st>>>(gbuf, pos, npw, 1, s_out, nullptr, nullptr, nullptr, 1, 0,
-                                                         (cplx<float>*)out_pw, n3); note_launch(); }
-  return check_launch("tddft_exchange_pair_noalloc");
+    // both orbitals to real space (cube cleared first: it keeps the previous call's contents)
+    const float s_in = (float)(1.0 / std::sqrt(a * a * a));
+    const cplx<float>* srcs[2] = {(const cplx<float>*)phi_pw, (const cplx<float>*)a_pw};
+    cplx<float>* dsts[2] = {phi_r, a_r};
+    for (int i = 0; i < 2; ++i) {
+      CUDA_TRY(cudaMemsetAsync(gbuf, 0, n3 * sizeof(cplx<float>), st));
+      { k_scatter<float><<<grid_for(npw, 256), 256, 0, st>>>(srcs[i], gbuf, pos, npw, 1, s_in, n3); note_launch(); }
+      o.z(Z_INV, gbuf, 1, nullptr, 1.f, tw, st);
+      PairMap pm{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+      o.xy_inv(INV_WRITE, gbuf, dsts[i], nullptr, pm, 1, 1.f, tw, st);
+    }
+    // -alpha phi Conv_x[conj(phi) a], accumulated into the cleared trial field
+    PairMap pp{1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+    o.xy_fwd(XY_PRODUCT, phi_r, a_r, pp, 1, gbuf, tw, st);
+    o.z(Z_CONV, gbuf, 1, kern, 1.f, tw, st);
+    CUDA_TRY(cudaMemsetAsync(a_r, 0, n3 * sizeof(cplx<float>), st));
+    o.xy_inv(INV_ACCUM, gbuf, a_r, phi_r, pp, 1, (float)(-alpha), tw, st);
+    // back to plane waves on the sphere
+    PairMap pl{1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0};
+    o.xy_fwd(XY_LOAD, nullptr, a_r, pl, 1, gbuf, tw, st);
+    o.z(Z_FWD, gbuf, 1, nullptr, 1.f, tw, st);
+    const float s_out = (float)(std::sqrt(a * a * a) / (double)n3);
+    { k_gather<float><<<grid_for(npw, 256), 256, 0, st>>>(gbuf, pos, npw, 1, s_out, nullptr, nullptr, nullptr, 1, 0,
+                                                           (cplx<float>*)out_pw, n3); note_launch(); }
+    return check_launch("tddft_exchange_pair_noalloc");
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -3775,84 +3842,96 @@ extern "C" tddft_status tddft_exchange_pair_noalloc(int n, double a, double ecut
 extern "C" {
 
 tddft_status tddft_testing_herm_eig(int n, const double* A, double* w, double* V) {
-  if (n < 1 || !A || !w || !V) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
-  const std::complex<double>* a = reinterpret_cast<const std::complex<double>*>(A);
-  std::vector<std::complex<double>> M(a, a + (size_t)n * n), vecs;
-  std::vector<double> vals;
-  const bool ok = herm_eig(n, M, vals, vecs);
-  std::copy(vals.begin(), vals.end(), w);
-  std::copy(vecs.begin(), vecs.end(), reinterpret_cast<std::complex<double>*>(V));
-  return ok ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+  return abi_guard([&]() -> tddft_status {
+    if (n < 1 || !A || !w || !V) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
+    const std::complex<double>* a = reinterpret_cast<const std::complex<double>*>(A);
+    std::vector<std::complex<double>> M(a, a + (size_t)n * n), vecs;
+    std::vector<double> vals;
+    const bool ok = herm_eig(n, M, vals, vecs);
+    std::copy(vals.begin(), vals.end(), w);
+    std::copy(vecs.begin(), vecs.end(), reinterpret_cast<std::complex<double>*>(V));
+    return ok ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+  });
 }
 
 tddft_status tddft_testing_herm_eig_device(int n, int nr, const double* A, double* w, double* V) {
-  if (n < 1 || nr < 1 || nr > n || !A || !w || !V) return fail(TDDFT_EINVAL, "1 <= nr <= n and non-null arrays required");
-  if (n > JACOBI_MAX_N) return fail(TDDFT_EINVAL, "n above the device solver's limit of " + std::to_string(JACOBI_MAX_N));
-  TempAllocs tmp;
-  void *dA = nullptr, *dV = nullptr, *dS = nullptr, *dw = nullptr;
-  const size_t nn = (size_t)n * n * sizeof(cplx<double>);
-  STATUS_TRY(tmp.get(&dA, nn));
-  STATUS_TRY(tmp.get(&dV, nn));
-  STATUS_TRY(tmp.get(&dS, (size_t)n * nr * sizeof(cplx<double>)));
-  STATUS_TRY(tmp.get(&dw, (size_t)(nr + 1) * sizeof(double)));
-  CUDA_TRY(cudaMemcpy(dA, A, nn, cudaMemcpyHostToDevice));
-  k_herm_jacobi<<<1, JACOBI_THREADS>>>((cplx<double>*)dA, (cplx<double>*)dV, n, nr, (double*)dw, (cplx<double>*)dS,
-                                       (double*)dw + nr);
-  note_launch();
-  STATUS_TRY(check_launch("device Jacobi"));
-  std::vector<double> wf(nr + 1);
-  CUDA_TRY(cudaMemcpy(wf.data(), dw, wf.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(V, dS, (size_t)n * nr * sizeof(cplx<double>), cudaMemcpyDeviceToHost));
-  std::copy(wf.begin(), wf.begin() + nr, w);
-  return wf[nr] == 1.0 ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+  return abi_guard([&]() -> tddft_status {
+    if (n < 1 || nr < 1 || nr > n || !A || !w || !V) return fail(TDDFT_EINVAL, "1 <= nr <= n and non-null arrays required");
+    if (n > JACOBI_MAX_N) return fail(TDDFT_EINVAL, "n above the device solver's limit of " + std::to_string(JACOBI_MAX_N));
+    TempAllocs tmp;
+    void *dA = nullptr, *dV = nullptr, *dS = nullptr, *dw = nullptr;
+    const size_t nn = (size_t)n * n * sizeof(cplx<double>);
+    STATUS_TRY(tmp.get(&dA, nn));
+    STATUS_TRY(tmp.get(&dV, nn));
+    STATUS_TRY(tmp.get(&dS, (size_t)n * nr * sizeof(cplx<double>)));
+    STATUS_TRY(tmp.get(&dw, (size_t)(nr + 1) * sizeof(double)));
+    CUDA_TRY(cudaMemcpy(dA, A, nn, cudaMemcpyHostToDevice));
+    k_herm_jacobi<<<1, JACOBI_THREADS>>>((cplx<double>*)dA, (cplx<double>*)dV, n, nr, (double*)dw, (cplx<double>*)dS,
+                                         (double*)dw + nr);
+    note_launch();
+    STATUS_TRY(check_launch("device Jacobi"));
+    std::vector<double> wf(nr + 1);
+    CUDA_TRY(cudaMemcpy(wf.data(), dw, wf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(V, dS, (size_t)n * nr * sizeof(cplx<double>), cudaMemcpyDeviceToHost));
+    std::copy(wf.begin(), wf.begin() + nr, w);
+    return wf[nr] == 1.0 ? TDDFT_OK : fail(TDDFT_ENUMERIC, "Jacobi sweeps did not converge");
+  });
 }
 
 tddft_status tddft_testing_cholesky(int n, double* A) {
-  if (n < 1 || !A) return fail(TDDFT_EINVAL, "n >= 1 and a non-null array required");
-  std::complex<double>* a = reinterpret_cast<std::complex<double>*>(A);
-  std::vector<std::complex<double>> M(a, a + (size_t)n * n);
-  if (!cholesky_lower(n, M)) return fail(TDDFT_ENUMERIC, "matrix is not positive definite");
-  std::copy(M.begin(), M.end(), a);
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (n < 1 || !A) return fail(TDDFT_EINVAL, "n >= 1 and a non-null array required");
+    std::complex<double>* a = reinterpret_cast<std::complex<double>*>(A);
+    std::vector<std::complex<double>> M(a, a + (size_t)n * n);
+    if (!cholesky_lower(n, M)) return fail(TDDFT_ENUMERIC, "matrix is not positive definite");
+    std::copy(M.begin(), M.end(), a);
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_testing_lower_inverse(int n, const double* L, double* X) {
-  if (n < 1 || !L || !X) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
-  const std::complex<double>* l = reinterpret_cast<const std::complex<double>*>(L);
-  for (int i = 0; i < n; ++i)
-    if (l[(size_t)i * n + i] == 0.0) return fail(TDDFT_EINVAL, "zero on the diagonal");
-  const std::vector<std::complex<double>> inv = lower_inverse(n, std::vector<std::complex<double>>(l, l + (size_t)n * n));
-  std::copy(inv.begin(), inv.end(), reinterpret_cast<std::complex<double>*>(X));
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (n < 1 || !L || !X) return fail(TDDFT_EINVAL, "n >= 1 and non-null arrays required");
+    const std::complex<double>* l = reinterpret_cast<const std::complex<double>*>(L);
+    for (int i = 0; i < n; ++i)
+      if (l[(size_t)i * n + i] == 0.0) return fail(TDDFT_EINVAL, "zero on the diagonal");
+    const std::vector<std::complex<double>> inv = lower_inverse(n, std::vector<std::complex<double>>(l, l + (size_t)n * n));
+    std::copy(inv.begin(), inv.end(), reinterpret_cast<std::complex<double>*>(X));
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_testing_inject_fault(int kind, int after) {
-  if (after < 0) return fail(TDDFT_EINVAL, "after must be >= 0");
-  std::lock_guard<std::mutex> lk(g_fault_mu);
-  switch (kind) {
-    case TDDFT_FAULT_NONE:
-      g_fault_alloc = -1;
-      g_fault_wait = false;
-      break;
-    case TDDFT_FAULT_ALLOC:
-      g_fault_alloc = after;
-      break;
-    case TDDFT_FAULT_DEVICE_WAIT:
-      g_fault_wait = true;
-      break;
-    default:
-      return fail(TDDFT_EINVAL, "unknown fault kind " + std::to_string(kind));
-  }
-  fault_rearm_locked();
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (after < 0) return fail(TDDFT_EINVAL, "after must be >= 0");
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    switch (kind) {
+      case TDDFT_FAULT_NONE:
+        g_fault_alloc = -1;
+        g_fault_wait = false;
+        break;
+      case TDDFT_FAULT_ALLOC:
+        g_fault_alloc = after;
+        break;
+      case TDDFT_FAULT_DEVICE_WAIT:
+        g_fault_wait = true;
+        break;
+      default:
+        return fail(TDDFT_EINVAL, "unknown fault kind " + std::to_string(kind));
+    }
+    fault_rearm_locked();
+    return TDDFT_OK;
+  });
 }
 
 tddft_status tddft_testing_fault_state(int* alloc_after, int* wait) {
-  if (!alloc_after || !wait) return fail(TDDFT_EINVAL, "null argument");
-  std::lock_guard<std::mutex> lk(g_fault_mu);
-  *alloc_after = g_fault_alloc;
-  *wait = g_fault_wait ? 1 : 0;
-  return TDDFT_OK;
+  return abi_guard([&]() -> tddft_status {
+    if (!alloc_after || !wait) return fail(TDDFT_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    *alloc_after = g_fault_alloc;
+    *wait = g_fault_wait ? 1 : 0;
+    return TDDFT_OK;
+  });
 }
 
 }  // extern "C"
