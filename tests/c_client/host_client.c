@@ -1,6 +1,6 @@
 /* A plain C99 client of the library's C ABI (include/tddft.h, include/tddft_testing.h), for the
  * entry points that need no GPU: sphere size, exchange grid, status strings and the last error,
- * the maximally localised frame, the fault injector and a dense FP64 routine. Built and run by
+ * the maximally localised frame, the LDA kernels, the fault injector and a dense FP64 routine. Built and run by
  * tests/test_c_client_cpu.py.
  *
  *   host_client ORBITALS U_OUT
@@ -64,6 +64,12 @@ int main(int argc, char** argv) {
   if (check(tddft_testing_fault_state(&after, &wait), "fault_state")) return 1;
   printf("fault %d %d\n", after, wait);
   if (check(tddft_testing_inject_fault(TDDFT_FAULT_NONE, 0), "inject")) return 1;
+
+  /* LDA kernels of two spin densities */
+  const double ru[3] = {0.1, 0.3, 0.02}, rd[3] = {0.1, 0.05, 0.02 + 5e-4};
+  double vu[3], vd[3], fx[3], fsf[3];
+  if (check(tddft_lda_kernels(3, ru, rd, 1e-3, vu, vd, fx, fsf), "lda")) return 1;
+  printf("lda %.17g %.17g %.17g %.17g %.17g %.17g\n", vu[1], vd[1], fx[1], fsf[1], fsf[0], fsf[2]);
 
   /* Cholesky of [[4, 2+i], [2-i, 3]] (row-major interleaved complex128) */
   double A[8] = {4.0, 0.0, 2.0, 1.0, 2.0, -1.0, 3.0, 0.0};

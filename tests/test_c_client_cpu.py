@@ -56,6 +56,9 @@ def test_c_client_matches_the_binding(client, tmp_path):
     assert (float(sb), float(sa), int(sw)) == (before, after, sweeps)
     assert lines["fault"] == "3 1"
     assert T.fault_state() == {"alloc_after": -1, "wait": False}  # another process: untouched here
+    lda = [float(x) for x in lines["lda"].split()]
+    ref = T.lda_kernels(np.array([0.1, 0.3, 0.02]), np.array([0.1, 0.05, 0.02 + 5e-4]), sf_cutoff=1e-3)
+    assert lda == [ref["vxc_up"][1], ref["vxc_dn"][1], ref["fxc"][1], ref["fxc_sf"][1], 0.0, 0.0]
     l00, l10r, l10i, l11 = (float(x) for x in lines["cholesky"].split())
     L = np.linalg.cholesky(np.array([[4, 2 + 1j], [2 - 1j, 3]]))
     assert np.allclose([l00, l10r, l10i, l11], [L[0, 0].real, L[1, 0].real, L[1, 0].imag, L[1, 1].real],
